@@ -1,0 +1,121 @@
+"""Pins of the oracle's discrete solution and GMRES (CPU only)."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import assemble, fd, gmres, kron, loads, matrices
+
+rng = np.random.default_rng(7)
+
+
+@pytest.mark.parametrize("d,p,p_t,n_el,T,gamma,nu", [
+    (1, 2, 1, 4, 1.0, 1.0, 1.0),
+    (2, 2, 1, 3, 1.5, 2.0, 0.5),
+    (2, 3, 2, 3, 1.0, 1.0, 1.0),
+    (3, 2, 2, 2, 0.7, 1.0, 1.3),
+])
+def test_manufactured_polynomial_is_exact(d, p, p_t, n_el, T, gamma, nu):
+    """u = t * prod_l x_l (1 - x_l) lies in the spline space for p_s >= 2,
+    p_t >= 1, vanishes on the spatial boundary and at t = 0, so the Galerkin
+    solution of Sec. 3.2 equals u. f = gamma u_t - nu Lap u (eq. problem).
+    This pins the basis, the matrices and their index order, the assembly,
+    the load vector and the boundary reduction together."""
+    def bubble(xs):
+        out = 1.0
+        for x in xs:
+            out = out * x * (1.0 - x)
+        return out
+
+    def f(*args):
+        xs, t = args[:-1], args[-1]
+        val = gamma * bubble(xs)
+        for l in range(d):
+            others = bubble([xs[k] for k in range(d) if k != l])
+            val = val + nu * t * 2.0 * others
+        return val + 0.0 * t
+
+    A = assemble.assemble_space_time(d, p, n_el, p_t, n_el, gamma, nu, T=T)
+    F = loads.load_quadrature(d, p, n_el, p_t, n_el, f, T=T)
+    c = spla.spsolve(A.tocsc(), F)
+    pts = rng.random((25, d + 1))
+    pts[:, d] *= T
+    uh = loads.evaluate(c, d, p, n_el, p_t, n_el, pts, T=T)
+    u = pts[:, d] * bubble([pts[:, l] for l in range(d)])
+    assert np.max(np.abs(uh - u)) <= 1e-10 * np.max(np.abs(u))
+
+
+def test_l2_convergence_rate():
+    """Sec. 5.1: optimal L2 order O(h^{p+1}) (here d = 1, p = 2, u = sin(pi x) sin t)."""
+    p = 2
+    errs = []
+    for n_el in [4, 8, 16]:
+        K, M = matrices.space_matrices(p, n_el)
+        Wt, Mt = matrices.time_matrices(p, n_el)
+        A = kron.st_matrix_kron([K], [M], Wt, Mt)
+        Fx = loads.load_1d(p, n_el, 1.0, lambda x: np.sin(np.pi * x), 10)
+        Ft = loads.load_1d(p, n_el, 1.0, lambda t: np.cos(t) + np.pi ** 2 * np.sin(t), 10, True, False)
+        c = spla.spsolve(A.tocsc(), loads.load_separable([Fx], Ft))
+        # L2 error by a tensor Gauss rule on every space-time element
+        g, w = np.polynomial.legendre.leggauss(p + 3)
+        pts, wts = [], []
+        for ex in range(n_el):
+            for et in range(n_el):
+                xs = (ex + 0.5 * (g + 1)) / n_el
+                ts = (et + 0.5 * (g + 1)) / n_el
+                X, Tt = np.meshgrid(xs, ts, indexing="ij")
+                pts.append(np.stack([X.ravel(), Tt.ravel()], axis=1))
+                wts.append(np.outer(w, w).ravel() / (4 * n_el * n_el))
+        pts = np.concatenate(pts)
+        wts = np.concatenate(wts)
+        uh = loads.evaluate(c, 1, p, n_el, p, n_el, pts)
+        u = np.sin(np.pi * pts[:, 0]) * np.sin(pts[:, 1])
+        errs.append(np.sqrt(np.sum(wts * (uh - u) ** 2)))
+    rate = np.log2(errs[-2] / errs[-1])
+    assert 2.6 < rate < 3.6, errs
+
+
+def test_separable_load_equals_quadrature_load():
+    """For separable f the Kronecker product of 1D loads equals the direct
+    (d+1)-D quadrature load (both oracle routes, different code)."""
+    d, p, n_el = 2, 2, 3
+    fx = lambda x: np.sin(np.pi * x)
+    ft = lambda t: np.cos(t) + 3 * np.sin(t)
+    F1 = loads.load_separable([loads.load_1d(p, n_el, 1.0, fx, 8)] * d,
+                              loads.load_1d(p, n_el, 1.0, ft, 8, True, False))
+    F2 = loads.load_quadrature(d, p, n_el, p, n_el, lambda x, y, t: fx(x) * fx(y) * ft(t), nq=8)
+    np.testing.assert_allclose(F1, F2, rtol=1e-13, atol=1e-16)
+
+
+def _problem(d, p, n_el, gamma=1.0, nu=1.0):
+    K, M = zip(*[matrices.space_matrices(p, n_el)] * d)
+    Wt, Mt = matrices.time_matrices(p, n_el)
+    return list(K), list(M), Wt, Mt
+
+
+def test_gmres_unit_cube_one_iteration():
+    """Unit cube, T = 1, constant coefficients: P = A (Sec. 4 with F = id), so
+    FD-preconditioned GMRES converges in one iteration."""
+    K, M, Wt, Mt = _problem(2, 2, 6)
+    fac = fd.setup(K, M, Wt, Mt)
+    f = rng.standard_normal(K[0].shape[0] ** 2 * Wt.shape[0])
+    x, info = gmres.gmres(lambda v: kron.st_matvec(v, K, M, Wt, Mt),
+                          lambda v: fd.apply(fac, v)[0], f)
+    assert info["converged"] and info["iters"] == 1
+    res = np.linalg.norm(f - kron.st_matvec(x, K, M, Wt, Mt)) / np.linalg.norm(f)
+    assert res < 1e-12
+
+
+def test_gmres_mismatched_preconditioner():
+    """nu_A = 2 vs nu_P = 1: several iterations, monotone residual history,
+    true residual <= 1e-8 and agreement with a direct solve."""
+    K, M, Wt, Mt = _problem(2, 3, 5)
+    fac = fd.setup(K, M, Wt, Mt)
+    A = kron.st_matrix_kron(K, M, Wt, Mt, 1.0, 2.0)
+    f = rng.standard_normal(A.shape[0])
+    x, info = gmres.gmres(lambda v: A @ v, lambda v: fd.apply(fac, v, 1.0, 1.0)[0], f, restart=10)
+    h = np.array(info["history"])
+    assert info["converged"] and info["iters"] > 2
+    assert np.all(np.diff(h) <= 1e-15)
+    assert np.linalg.norm(f - A @ x) / np.linalg.norm(f) <= 1e-8
+    xd = spla.spsolve(A.tocsc(), f)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-6
