@@ -1,0 +1,334 @@
+"""Benchmark: FD-preconditioned FGMRES solve of the space-time heat equation.
+
+Workload (the paper's method at scale, synthetic): unit cube x (0, 1), d = 3,
+p = 3, 64 elements per direction (n_s = 65, n_t = 66, N = 18,125,250 dofs),
+gamma = nu = 1, right-hand side = load of f = u_t - Lap u for the manufactured
+solution u = sin(pi x) sin(pi y) sin(pi z) sin(t). One step = one full solve to
+a relative residual of 1e-8 from f resident in HBM: every fd_apply (Algorithm
+1), st_matvec (eq. syst_mat), Gram-Schmidt and the true-residual check.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the method's unit of work is one independent solve, so N GPUs run N
+replicas (no data-path collective; "scaling": "weak"). `--impl reference`
+times the CPU FP64 oracle (the only reference this paper has) on the host.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1909_07309_gb300 import inputs  # noqa: E402
+
+METRIC = "fd_apply dofs/s and GMRES time-to-1e-8 residual, FP64 vs TF32/BF16-precond"
+UNIT = "dofs/s"
+L2_BYTES = 129 * 2 ** 20
+
+# DRAM bytes per launch of the dominant kernel from one ncu capture
+# (profiles/fd_mode_fp64_unit_cube_p3_nel64.txt); None until captured for the current kernel.
+NCU_TRAFFIC = {"kernel": "fd_mode_fp64", "bytes_per_launch": None}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, flag in zip(names, parts[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload(cfg):
+    """Univariate factors from the library's own spline assembly and the RHS load."""
+    from paper_1909_07309_gb300 import stfd
+    d, p, n_el, T = cfg["d"], cfg["p"], cfg["n_el"], cfg["T"]
+    gamma, nu = cfg["gamma"], cfg["nu"]
+    K, M, Wt, Mt = stfd.heat_problem(d, p, n_el, T=T)
+    Fx = stfd.stfd_spline_load_trig(p, n_el, 1.0, stfd.STFD_BC_DIRICHLET, np.pi, 1.0, 0.0)
+    Ft = stfd.stfd_spline_load_trig(p, n_el, T, stfd.STFD_BC_INITIAL, 1.0, d * np.pi ** 2 * nu, gamma)
+    f = np.ones(1)
+    for F in [Fx] * d + [Ft]:                 # vec order: direction 1 fastest, time slowest
+        f = np.outer(F, f).ravel()
+    return K, M, Wt, Mt, f
+
+
+def run_oracle_solve(cfg):
+    """One FD-preconditioned GMRES solve by the CPU oracle; returns (seconds, iters, N)."""
+    from oracle import fd as ofd, gmres as ogmres, kron as okron, loads as oloads, matrices as omat
+    d, p, n_el, T = cfg["d"], cfg["p"], cfg["n_el"], cfg["T"]
+    gamma, nu = cfg["gamma"], cfg["nu"]
+    t0 = time.perf_counter()
+    K, M = omat.space_matrices(p, n_el)
+    Wt, Mt = omat.time_matrices(p, n_el, T)
+    Fx = oloads.load_1d(p, n_el, 1.0, lambda x: np.sin(np.pi * x), 12)
+    Ft = oloads.load_1d(p, n_el, T, lambda t: d * np.pi ** 2 * nu * np.sin(t) + gamma * np.cos(t), 12, True, False)
+    f = oloads.load_separable([Fx] * d, Ft)
+    fac = ofd.setup([K] * d, [M] * d, Wt, Mt)
+    t1 = time.perf_counter()
+    x, info = ogmres.gmres(lambda v: okron.st_matvec(v, [K] * d, [M] * d, Wt, Mt, gamma, nu),
+                           lambda v: ofd.apply(fac, v, gamma, nu)[0], f, tol=1e-8, restart=100)
+    res = np.linalg.norm(f - okron.st_matvec(x, [K] * d, [M] * d, Wt, Mt, gamma, nu)) / np.linalg.norm(f)
+    t2 = time.perf_counter()
+    return t2 - t1, t1 - t0, info["iters"], f.size, res
+
+
+def blas_threads():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count() or 1
+
+
+def reference_main(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg = inputs.SCALE
+    for _ in range(args.warmup):
+        run_oracle_solve(cfg)
+    times = []
+    iters = N = 0
+    res = None
+    for _ in range(args.steps):
+        t, _, iters, N, res = run_oracle_solve(cfg)
+        times.append(t)
+    total = sum(times)
+    value = N * len(times) / total
+    cores = blas_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["name"], "N": N, "solve": "FD-preconditioned GMRES to 1e-8, x0 = 0",
+                   "gmres_iters": iters, "rel_res_true": res},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "one full oracle solve per step (numpy FP64, complex Algorithm 1, "
+                                   "mode-product matvec, MGS GMRES); setup excluded as in the GPU arm"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--restart", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_main(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    from paper_1909_07309_gb300 import stfd
+    stfd.load(build_if_missing=False)
+
+    cfg = inputs.SCALE
+    K, M, Wt, Mt, f_np = build_workload(cfg)
+    A = stfd.KronOp(K, M, Wt, Mt, cfg["gamma"], cfg["nu"])
+    P = stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"])
+    N = P.N
+    f = torch.from_numpy(f_np).cuda()
+    u = torch.empty_like(f)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def solve():
+        return A.gmres(P, f, u, tol=1e-8, restart=args.restart)
+
+    for _ in range(args.warmup):
+        _, info = solve()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K full solves, inputs resident in HBM (working set > L2)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = stfd.stfd_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        _, info = solve()
+        infos.append(info)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = stfd.stfd_launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t.item())
+    value = N * args.steps * world / (ms * 1e-3)
+
+    # ---- end to end through the public API: pinned host f -> solve -> host u
+    f_host = torch.from_numpy(f_np).pin_memory()
+    u_host = torch.empty_like(f_host).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f_dev = f_host.to("cuda", non_blocking=True)
+        u_dev = torch.empty_like(f_dev)
+        A.gmres(P, f_dev, u_dev, tol=1e-8, restart=args.restart)
+        u_host.copy_(u_dev, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": N * args.steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(f_np.nbytes), "d2h_bytes_per_step": int(f_np.nbytes)}
+
+    # ---- fd_apply and st_matvec alone (CUDA events on the launching stream)
+    r = torch.from_numpy(inputs.standard_normal(N, cfg["rhs_seed"])).cuda()
+    s = torch.empty_like(r)
+    y = torch.empty_like(r)
+    for _ in range(3):
+        P.apply(r, s)
+        A.matvec(s, y)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        P.apply(r, s)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fd_ms = e0.elapsed_time(e1) / args.steps
+    e0.record(stream)
+    for _ in range(args.steps):
+        A.matvec(s, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mv_ms = e0.elapsed_time(e1) / args.steps
+    resid = float(torch.linalg.norm(y - r) / torch.linalg.norm(r))
+
+    # ---- roofline of the dominant kernel: per-launch CUDA events inside the library
+    stfd.stfd_profile_reset()
+    stfd.stfd_profile_enable(True)
+    for _ in range(args.steps):
+        solve()
+    torch.cuda.synchronize()
+    stfd.stfd_profile_enable(False)
+    recs = stfd.stfd_profile_records()
+    stfd.stfd_profile_reset()
+    total_ms = sum(rc["ms"] for rc in recs) or 1.0
+    top = max(recs, key=lambda rc: rc["ms"])
+    fp64_peak = stfd.stfd_probe_fp64_peak()
+    per_launch_s = top["ms"] * 1e-3 / top["launches"]
+    achieved = top["flops"] / top["launches"] / per_launch_s
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["kernel"] == top["name"] else None
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": traffic, "kernel": top["name"],
+                "peak_source": "FP64 DFMA throughput measured in this run (stfd_probe_fp64_peak)",
+                "achieved_gbs": top["bytes"] / top["launches"] / per_launch_s / 1e9,
+                "share_of_step": top["ms"] / total_ms}
+    kernels = {rc["name"]: {"launches": rc["launches"], "ms": round(rc["ms"], 3),
+                            "share": round(rc["ms"] / total_ms, 4)} for rc in recs}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["name"], "N": N, "solve": "FD-preconditioned flexible GMRES to 1e-8, x0 = 0",
+                   "restart": args.restart, "gmres_iters": infos[-1]["iters"],
+                   "rel_res_true": infos[-1]["rel_res_true"], "precond": "FP64",
+                   "l2": "inputs larger than L2 (working set %.2f GB > 129 MB)" % (10 * N * 8 / 1e9),
+                   "parallelism": "replicas x%d" % world},
+        "fd_apply": {"ms": fd_ms, "dofs_per_s": N / (fd_ms * 1e-3)},
+        "st_matvec": {"ms": mv_ms, "dofs_per_s": N / (mv_ms * 1e-3), "residual_A_Pinv_r": resid},
+        "gmres_time_to_1e-8_ms": ms / args.steps,
+        "roofline": roofline, "kernels": kernels, "gpu_launches": launches,
+        "clocks": clocks, "e2e": e2e,
+    }
+    peaks, src = measured_peaks()
+    line["hbm_peak_gbs"] = {"value": peaks.get("hbm_gbs"), "source": src}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs, _, iters, Nc, res = run_oracle_solve(cfg)
+        line["cpu_baseline"] = {"value": Nc / secs, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                                "sample": "one full oracle solve of the same workload (setup excluded), "
+                                          "%d GMRES iteration(s), %.1f s" % (iters, secs)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * stfd.h -- C ABI of the GB300 space-time Fast Diagonalization library.
+ *
+ * Problem (Loli, Montardini, Sangalli, Tani, "An efficient solver for
+ * space-time isogeometric Galerkin methods for parabolic problems"):
+ * the Galerkin discretisation of  gamma d_t u - nu Lap u = f  with
+ * maximal-smoothness B-splines in space and time gives (Sec. 3.3, eq. syst_mat)
+ *
+ *     A = gamma W_t (x) M_s + nu M_t (x) K_s,
+ *
+ * M_s = M_d (x) .. (x) M_1 and K_s = sum_l M_d (x) .. K_l .. (x) M_1 on the
+ * parametric box (Sec. 4, eqs. prec_definition and space_univ_par_mat). The
+ * preconditioner P has the same form; it is applied exactly by the extended
+ * Fast Diagonalization of Algorithm 1 (Sec. 4.3).
+ *
+ * Conventions common to every entry point
+ *  - Vectors of length N = n_1 * ... * n_d * n_t are stored in the paper's
+ *    vec order (Sec. 2.3, eq. kron_vec_multi): i_1 fastest, time slowest.
+ *    Several right-hand sides are stored one after another (nrhs * N).
+ *  - Pointers named "dev" are CUDA device pointers owned by the caller; all
+ *    others are host pointers owned by the caller. The library never frees
+ *    caller memory and copies what it keeps.
+ *  - Dense matrices on the host are column-major n x n.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Device work is stream-ordered and asynchronous unless stated.
+ *  - Every int-returning call returns STFD_OK (0) or a negative STFD_ERR_*
+ *    code (STFD_NOT_CONVERGED = 1 is a warning); nothing is thrown across
+ *    the ABI. stfd_strerror() names a code.
+ *  - Handles are immutable after creation, except the Krylov workspace that
+ *    stfd_gmres_solve caches inside an stfd_op (one solve per op at a time).
+ */
+#ifndef STFD_H
+#define STFD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  STFD_OK = 0,
+  STFD_ERR_ARG = -1,        /* bad size, NULL pointer, unsupported option */
+  STFD_ERR_NOT_SPD = -2,    /* Cholesky of a mass matrix failed */
+  STFD_ERR_EIG = -3,        /* eigen-solver did not converge or structure check failed */
+  STFD_ERR_CUDA = -4,       /* a CUDA runtime call or kernel launch failed */
+  STFD_ERR_NAN = -5,        /* non-finite value met (e.g. in the right-hand side) */
+  STFD_ERR_BREAKDOWN = -6,  /* Krylov breakdown other than a lucky one */
+  STFD_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up */
+  STFD_ERR_ALLOC = -8,      /* device or host allocation failed */
+  STFD_NOT_CONVERGED = 1    /* solver stopped at max_it above the tolerance */
+};
+
+/* Arithmetic of the preconditioner's mode products. */
+enum { STFD_FP64 = 0 };
+
+/* Boundary treatment of a univariate basis (Sec. 2.2). */
+enum {
+  STFD_BC_NONE = 0,         /* all m = n_el + p B-splines */
+  STFD_BC_INITIAL = 1,      /* drop b_1: time direction, zero initial condition (n = m - 1) */
+  STFD_BC_DIRICHLET = 2     /* drop b_1 and b_m: space direction, Dirichlet (n = m - 2) */
+};
+
+const char* stfd_strerror(int code);
+int stfd_version(void);
+
+/* ------------------------------------------------------------------------
+ * Univariate spline matrices (host, CPU only).
+ * Sec. 2.1 (open uniform knot vector on [0, length], Cox-de Boor B-splines of
+ * degree p, n_el elements), eq. time_mat and the univariate factors of eq.
+ * space_univ_par_mat:
+ *     M[i,j] = int b_i b_j,   K[i,j] = int b'_i b'_j,   W[i,j] = int b'_j b_i,
+ * with the basis reduced by `bc`. Output: dense column-major n x n where
+ * n = n_el + p - {0,1,2} by bc. *n_out receives n. Any of M, K, W may be NULL
+ * (skipped); call with all three NULL to query n. Requires p >= 1, n_el >= 1,
+ * length > 0, and n >= 1 after the reduction.
+ * ------------------------------------------------------------------------ */
+int stfd_spline_matrices(int p, int n_el, double length, int bc,
+                         double* M, double* K, double* W, int* n_out);
+
+/* Load vector of a trigonometric source (host): out[i] = int_0^length
+ * (c_sin sin(freq x) + c_cos cos(freq x)) b_i(x) dx over the reduced basis,
+ * i.e. one factor of the linear form F of Sec. 3.1 for a separable f.
+ * `out` has n entries (as returned by stfd_spline_matrices). */
+int stfd_spline_load_trig(int p, int n_el, double length, int bc,
+                          double freq, double c_sin, double c_cos, double* out);
+
+/* ------------------------------------------------------------------------
+ * Fast Diagonalization factors (host, CPU only) -- Step 1 of Algorithm 1.
+ * Spatial pencils (eq. space_eig): K_l U_l = M_l U_l Lambda_l, U_l^T M_l U_l = I.
+ * Time pencil (Sec. 4.2.2, eqs. arrow..time_eig_2, real form of the Remark in
+ * Sec. 4.5): W_t U_t = M_t U_t Delta_t, U_t^T M_t U_t = I, with
+ *     Delta_t = [ blockdiag(B_1..B_q, [0]) | g ; -g^T | sigma ],
+ * B_j = [[0, lam_j], [-lam_j, 0]] for the q pairs of purely imaginary
+ * eigenvalues +-i lam_j of the skew leading block, then one 1 x 1 zero block
+ * when n_t - 1 is odd, then the last (arrow) index.
+ * Inputs: n[0..d-1] spatial sizes (K[l], M[l] are n[l] x n[l]), n[d] = n_t
+ * (Wt, Mt are n_t x n_t). Outputs (caller-allocated host arrays):
+ *     U[l]  n[l] x n[l] column-major,  lam[l]  n[l],
+ *     Ut    n_t x n_t column-major,    lamt  q entries,  g  n_t - 1,
+ *     sigma 1 value, *n_pairs = q, *has_zero = 1 if the zero block exists.
+ * Any output pointer may be NULL. Returns STFD_ERR_NOT_SPD if a mass matrix
+ * is not SPD and STFD_ERR_EIG if an eigen-solver fails its checks.
+ * ------------------------------------------------------------------------ */
+int stfd_fd_factors(int d, const int* n, const double* const* K, const double* const* M,
+                    const double* Wt, const double* Mt,
+                    double* const* U, double* const* lam, double* Ut, double* lamt,
+                    double* g, double* sigma, int* n_pairs, int* has_zero);
+
+/* ------------------------------------------------------------------------
+ * Preconditioner handle (Algorithm 1). d in {1, 2, 3}, 1 <= n[l] <= 256,
+ * 2 <= n_t <= 256, gamma > 0, nu > 0. The factorisation runs on the host;
+ * factors are uploaded on `stream` and the call synchronises that stream
+ * before returning. Device memory held: the factors, one N-vector of
+ * scratch and N_s Schur-complement reciprocals.
+ * ------------------------------------------------------------------------ */
+typedef struct stfd_fd stfd_fd;
+
+int stfd_fd_setup(stfd_fd** out, int d, const int* n,
+                  const double* const* K, const double* const* M,
+                  const double* Wt, const double* Mt,
+                  double gamma, double nu, int precision, void* stream);
+
+/* s_dev = P^{-1} r_dev for nrhs right-hand sides (Algorithm 1, Steps 2-4):
+ * s~ = (U_t^T (x) U_s^T) r, q~ = (gamma Delta_t (x) I + nu I (x) Lambda_s)^{-1} s~
+ * by the block LU of eq. block_LU, s = (U_t (x) U_s) q~. r_dev and s_dev may
+ * not overlap. Calls on one handle must not overlap in time (shared scratch). */
+int stfd_fd_apply(const stfd_fd* h, const double* r_dev, double* s_dev, int nrhs, void* stream);
+
+/* Problem sizes of a handle: n[0..d] (array of d+1 ints) and *N_out. */
+int stfd_fd_shape(const stfd_fd* h, int* d_out, int* n, long long* N_out);
+
+void stfd_fd_destroy(stfd_fd* h);
+
+/* ------------------------------------------------------------------------
+ * System operator A = gamma W_t (x) M_s + nu M_t (x) K_s (eq. syst_mat) with
+ * banded univariate factors (bandwidth 2p+1 is detected from the entries;
+ * any dense factor works, only slower). Same size limits as stfd_fd_setup.
+ * The factors are uploaded on `stream`, which is synchronised.
+ * ------------------------------------------------------------------------ */
+typedef struct stfd_op stfd_op;
+
+int stfd_op_create_kron(stfd_op** out, int d, const int* n,
+                        const double* const* K, const double* const* M,
+                        const double* Wt, const double* Mt,
+                        double gamma, double nu, void* stream);
+
+/* y_dev = A x_dev for nrhs vectors (matrix-free, sum-factorised through eq.
+ * kron_vec_multi: 3d+1 banded mode products). x_dev and y_dev may not
+ * overlap. Calls on one op must not overlap in time (shared scratch). */
+int stfd_st_matvec(const stfd_op* A, const double* x_dev, double* y_dev, int nrhs, void* stream);
+
+void stfd_op_destroy(stfd_op* A);
+
+/* ------------------------------------------------------------------------
+ * Right-preconditioned flexible GMRES(restart) for A u = f with x0 = 0
+ * (Sec. 4.5, Sec. 5: tolerance 1e-8, zero initial guess, Krylov dimension
+ * 100). Classical Gram-Schmidt with one re-orthogonalisation, Givens
+ * rotations on the host. Stops when the residual estimate
+ * |g_{j+1}| <= tol ||f||, then computes the true residual ||f - A u|| / ||f||.
+ * f_dev, u_dev: device N-vectors (one right-hand side). The call blocks the
+ * host (one small device-to-host read per iteration) and returns when u_dev
+ * is final. Krylov vectors (2 * restart + 1 N-vectors) are allocated on the
+ * first call and cached in the op. `history` (optional, host, hist_cap
+ * entries) receives the relative residual estimate per iteration.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  double tol;        /* relative residual target, default 1e-8 */
+  int restart;       /* Krylov dimension per cycle, default 100 */
+  int max_it;        /* total iterations, default 1000 */
+} stfd_gmres_opts;
+
+typedef struct {
+  int iters;              /* iterations done (preconditioner applications) */
+  int converged;          /* 1 if the estimate reached tol */
+  double rel_res_est;     /* |g_{j+1}| / ||f|| at exit */
+  double rel_res_true;    /* ||f - A u|| / ||f|| at exit */
+  double* history;        /* optional host array */
+  int hist_cap;           /* its capacity */
+  int hist_len;           /* entries written */
+} stfd_gmres_info;
+
+void stfd_gmres_default_opts(stfd_gmres_opts* opts);
+
+int stfd_gmres_solve(const stfd_op* A, const stfd_fd* P, const double* f_dev, double* u_dev,
+                     const stfd_gmres_opts* opts, stfd_gmres_info* info, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STFD_H */

@@ -1,0 +1,46 @@
+/*
+ * stfd_profile.h -- diagnostics of libstfd: per-kernel timing with CUDA
+ * events, a launch counter, and a DFMA throughput probe. The paper reports
+ * wall-clock only (Sec. 5, Tables 4-6 and Fig. 3); these calls exist so that
+ * a caller can attribute the time of a solve to the kernels of Algorithm 1,
+ * the system matvec and GMRES, and compare it with the FP64 peak of the GPU
+ * it runs on. Nothing here changes results.
+ */
+#ifndef STFD_PROFILE_H
+#define STFD_PROFILE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Turn per-launch event timing on (1) or off (0). While on, every kernel
+ * launch of the library is bracketed by two cudaEvents recorded on the
+ * stream it is launched on. Off by default. Returns STFD_OK. */
+int stfd_profile_enable(int on);
+
+/* Drop all timing records (synchronises on their events first). */
+int stfd_profile_reset(void);
+
+/* Number of distinct kernels with records; synchronises on pending events. */
+int stfd_profile_count(void);
+
+/* Record `idx` (0 <= idx < count): kernel name (NUL-terminated, truncated to
+ * name_cap), launches, total device milliseconds, and the algorithmic FLOPs
+ * and bytes (minimum HBM traffic: each input read once, each output written
+ * once) summed over its launches. Any output pointer may be NULL. Returns
+ * STFD_ERR_ARG for a bad index. */
+int stfd_profile_get(int idx, char* name, int name_cap, long long* launches, double* ms,
+                     double* flops, double* bytes);
+
+/* Kernel launches issued by the library since it was loaded (always counted). */
+long long stfd_launch_count(void);
+
+/* FP64 FMA throughput of the current device in FLOP/s, measured with
+ * independent DFMA chains on every SM (about 20 ms of device time). The
+ * result is the denominator of an FP64-ALU roofline. Synchronous. */
+int stfd_probe_fp64_peak(double* flops_per_s, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STFD_PROFILE_H */

@@ -1,0 +1,637 @@
+// C ABI: handles, Algorithm 1 (fd_apply), the Kronecker system matvec and the
+// flexible GMRES driver. Every step of the numerical path runs in the device
+// kernels of kernels.cu; the host only factorises once (fd_setup.cpp), drives
+// the launches and does the (restart+1) x restart Hessenberg/Givens work.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.h"
+#include "stfd.h"
+#include "stfd_internal.h"
+
+using namespace stfd;
+
+namespace {
+
+#define STFD_CU(x)                                   \
+  do {                                               \
+    if ((x) != cudaSuccess) return STFD_ERR_CUDA;    \
+  } while (0)
+
+template <class T>
+int dev_upload(T** dst, const T* src, size_t count, cudaStream_t st) {
+  *dst = nullptr;
+  if (count == 0) return STFD_OK;
+  if (cudaMalloc((void**)dst, count * sizeof(T)) != cudaSuccess) {
+    *dst = nullptr;
+    return STFD_ERR_ALLOC;
+  }
+  if (src && cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return STFD_ERR_CUDA;
+  return STFD_OK;
+}
+
+void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+// Row-major J[i*n + a] = A[i, a] from a column-major host matrix A.
+std::vector<double> row_major(int n, const double* A) {
+  std::vector<double> J((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < n; ++a) J[(size_t)i * n + a] = A[i + (size_t)n * a];
+  return J;
+}
+
+int bandwidth(int n, const double* A) {
+  int bw = 0;
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i)
+      if (A[i + (size_t)n * j] != 0.0) bw = std::max(bw, std::abs(i - j));
+  return bw;
+}
+
+bool sizes_ok(int d, const int* n) {
+  if (d < 1 || d > kMaxDim || !n) return false;
+  for (int l = 0; l < d; ++l)
+    if (n[l] < 1 || n[l] > kMaxN) return false;
+  return n[d] >= 2 && n[d] <= kMaxN;
+}
+
+}  // namespace
+
+struct stfd_fd {
+  int d = 0;
+  int n[kMaxDim + 1] = {0, 0, 0, 0};
+  long long Ns = 0, N = 0;
+  double gamma = 1.0, nu = 1.0;
+  int precision = STFD_FP64;
+  double* Jf[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};  // U_l^T, U_t^T (row-major J)
+  double* Jb[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};  // U_l,   U_t
+  double* lam[kMaxDim] = {nullptr, nullptr, nullptr};
+  double* lamt = nullptr;
+  double* g = nullptr;
+  double* Sinv = nullptr;
+  double* work = nullptr;
+  int n_pairs = 0, has_zero = 0;
+  double sigma = 0.0;
+};
+
+struct GmresWork {
+  std::vector<double*> V, Z;     // device N-vectors
+  double** dV = nullptr;         // device copy of the V pointers (capacity cap_v)
+  double** dZ = nullptr;
+  int cap_v = 0, cap_z = 0;
+  double* partial = nullptr;     // dot_blocks() * (restart + 1)
+  int partial_cap = 0;
+  double* h = nullptr;           // 2 restart + 6: h, h2, ||w||^2
+  double* hostbuf = nullptr;     // pinned mirror of h
+  int hcap = 0;
+};
+
+struct stfd_op {
+  int d = 0;
+  int n[kMaxDim + 1] = {0, 0, 0, 0};
+  long long N = 0;
+  double gamma = 1.0, nu = 1.0;
+  double* JM[kMaxDim] = {nullptr, nullptr, nullptr};
+  double* JK[kMaxDim] = {nullptr, nullptr, nullptr};
+  int bwM[kMaxDim] = {0, 0, 0}, bwK[kMaxDim] = {0, 0, 0};
+  double* JW = nullptr;
+  double* JMt = nullptr;
+  int bwW = 0, bwMt = 0;
+  double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
+  GmresWork* gw = nullptr;
+};
+
+extern "C" const char* stfd_strerror(int code) {
+  switch (code) {
+    case STFD_OK: return "ok";
+    case STFD_ERR_ARG: return "invalid argument";
+    case STFD_ERR_NOT_SPD: return "mass matrix is not symmetric positive definite";
+    case STFD_ERR_EIG: return "eigen-solver failed or factor structure check failed";
+    case STFD_ERR_CUDA: return "CUDA runtime error";
+    case STFD_ERR_NAN: return "non-finite value";
+    case STFD_ERR_BREAKDOWN: return "Krylov breakdown";
+    case STFD_ERR_TIMEOUT: return "bounded device wait timed out";
+    case STFD_ERR_ALLOC: return "allocation failed";
+    case STFD_NOT_CONVERGED: return "not converged";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int stfd_version(void) { return 1; }
+
+// ---------------------------------------------------------------------------
+// Preconditioner
+// ---------------------------------------------------------------------------
+
+extern "C" void stfd_fd_destroy(stfd_fd* h) {
+  if (!h) return;
+  for (int l = 0; l <= kMaxDim; ++l) {
+    dev_free(h->Jf[l]);
+    dev_free(h->Jb[l]);
+  }
+  for (int l = 0; l < kMaxDim; ++l) dev_free(h->lam[l]);
+  dev_free(h->lamt);
+  dev_free(h->g);
+  dev_free(h->Sinv);
+  dev_free(h->work);
+  delete h;
+}
+
+extern "C" int stfd_fd_setup(stfd_fd** out, int d, const int* n, const double* const* K,
+                             const double* const* M, const double* Wt, const double* Mt,
+                             double gamma, double nu, int precision, void* stream) {
+  if (!out) return STFD_ERR_ARG;
+  *out = nullptr;
+  if (!sizes_ok(d, n) || !K || !M || !Wt || !Mt) return STFD_ERR_ARG;
+  if (!(gamma > 0.0) || !(nu > 0.0) || !std::isfinite(gamma) || !std::isfinite(nu)) return STFD_ERR_ARG;
+  if (precision != STFD_FP64) return STFD_ERR_ARG;
+  HostFactors f;
+  int rc = factorize_host(d, n, K, M, Wt, Mt, f);
+  if (rc != STFD_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  stfd_fd* h = new (std::nothrow) stfd_fd;
+  if (!h) return STFD_ERR_ALLOC;
+  h->d = d;
+  h->Ns = 1;
+  for (int l = 0; l <= d; ++l) h->n[l] = n[l];
+  for (int l = 0; l < d; ++l) h->Ns *= n[l];
+  h->N = h->Ns * n[d];
+  h->gamma = gamma;
+  h->nu = nu;
+  h->precision = precision;
+  h->n_pairs = f.n_pairs;
+  h->has_zero = f.has_zero;
+  h->sigma = f.sigma;
+  // Step 2 uses J = U^T (row-major J[i][a] = U[a][i] = column-major U as is),
+  // Step 4 uses J = U.
+  std::vector<std::vector<double>> keep;
+  for (int l = 0; l <= d; ++l) {
+    const int nl = n[l];
+    const std::vector<double>& U = (l < d) ? f.U[l] : f.Ut;
+    keep.push_back(U);
+    keep.push_back(row_major(nl, U.data()));
+    if ((rc = dev_upload(&h->Jf[l], keep[keep.size() - 2].data(), (size_t)nl * nl, st)) != STFD_OK) break;
+    if ((rc = dev_upload(&h->Jb[l], keep.back().data(), (size_t)nl * nl, st)) != STFD_OK) break;
+    if (l < d && (rc = dev_upload(&h->lam[l], f.lam[l].data(), (size_t)nl, st)) != STFD_OK) break;
+  }
+  // Schur complement of the arrowhead per spatial index (eq. block_LU):
+  // S_k = gamma sigma + a + sum_j gamma^2 a |g_j|^2 / (a^2 + gamma^2 lam_j^2) [+ gamma^2 g_z^2 / a]
+  std::vector<double> Sinv;
+  if (rc == STFD_OK) {
+    Sinv.resize((size_t)h->Ns);
+    for (long long k = 0; k < h->Ns; ++k) {
+      long long rest = k;
+      double mu = 0.0;
+      for (int l = 0; l < d; ++l) {
+        mu += f.lam[l][rest % n[l]];
+        rest /= n[l];
+      }
+      const double a = nu * mu;
+      double S = gamma * f.sigma + a;
+      for (int j = 0; j < f.n_pairs; ++j) {
+        const double b = gamma * f.lamt[j];
+        const double g2 = f.g[2 * j] * f.g[2 * j] + f.g[2 * j + 1] * f.g[2 * j + 1];
+        S += gamma * gamma * a * g2 / (a * a + b * b);
+      }
+      if (f.has_zero) S += gamma * gamma * f.g[2 * f.n_pairs] * f.g[2 * f.n_pairs] / a;
+      Sinv[k] = 1.0 / S;
+    }
+    rc = dev_upload(&h->Sinv, Sinv.data(), Sinv.size(), st);
+  }
+  if (rc == STFD_OK && f.n_pairs > 0) rc = dev_upload(&h->lamt, f.lamt.data(), f.lamt.size(), st);
+  if (rc == STFD_OK) rc = dev_upload(&h->g, f.g.data(), f.g.size(), st);
+  if (rc == STFD_OK) rc = dev_upload<double>(&h->work, nullptr, (size_t)h->N, st);
+  if (rc == STFD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = STFD_ERR_CUDA;
+  if (rc != STFD_OK) {
+    stfd_fd_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return STFD_OK;
+}
+
+extern "C" int stfd_fd_shape(const stfd_fd* h, int* d_out, int* n, long long* N_out) {
+  if (!h) return STFD_ERR_ARG;
+  if (d_out) *d_out = h->d;
+  if (n)
+    for (int l = 0; l <= h->d; ++l) n[l] = h->n[l];
+  if (N_out) *N_out = h->N;
+  return STFD_OK;
+}
+
+namespace {
+
+// One right-hand side: s = P^{-1} r through 2(d+1) mode products and Step 3.
+int fd_apply_one(const stfd_fd* h, const double* r, double* s, double* work, cudaStream_t st) {
+  const int d = h->d;
+  const int P = 2 * (d + 1);
+  auto buf = [&](int k) { return ((P - k) % 2 == 0) ? s : work; };   // pass k writes buf(k), buf(P) = s
+  const double* src = r;
+  int pass = 0;
+  // Step 2: X x_1 U_1^T ... x_d U_d^T x_{d+1} U_t^T
+  long long inner = 1;
+  for (int l = 0; l <= d; ++l) {
+    const long long outer = h->N / (inner * h->n[l]);
+    double* dst = buf(++pass);
+    STFD_CU(launch_fd_mode_fp64(src, h->Jf[l], dst, h->n[l], inner, outer, st));
+    src = dst;
+    inner *= h->n[l];
+  }
+  // Step 3 in place
+  ArrowParams ap;
+  ap.d = d;
+  ap.n1 = h->n[0];
+  ap.n2 = d >= 2 ? h->n[1] : 1;
+  ap.nt = h->n[d];
+  ap.n_pairs = h->n_pairs;
+  ap.has_zero = h->has_zero;
+  ap.Ns = h->Ns;
+  for (int l = 0; l < 3; ++l) ap.lam[l] = l < d ? h->lam[l] : nullptr;
+  ap.lamt = h->lamt;
+  ap.g = h->g;
+  ap.Sinv = h->Sinv;
+  ap.gamma = h->gamma;
+  ap.nu = h->nu;
+  STFD_CU(launch_arrowhead_fp64(const_cast<double*>(src), ap, st));
+  // Step 4: x_{d+1} U_t, then x_d U_d ... x_1 U_1
+  for (int l = d; l >= 0; --l) {
+    inner /= h->n[l];
+    const long long outer = h->N / (inner * h->n[l]);
+    double* dst = buf(++pass);
+    STFD_CU(launch_fd_mode_fp64(src, h->Jb[l], dst, h->n[l], inner, outer, st));
+    src = dst;
+  }
+  return STFD_OK;
+}
+
+}  // namespace
+
+extern "C" int stfd_fd_apply(const stfd_fd* h, const double* r, double* s, int nrhs, void* stream) {
+  if (!h || nrhs < 0 || (nrhs > 0 && (!r || !s))) return STFD_ERR_ARG;
+  if (r == s) return STFD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int k = 0; k < nrhs; ++k) {
+    const int rc = fd_apply_one(h, r + (size_t)k * h->N, s + (size_t)k * h->N, h->work, st);
+    if (rc != STFD_OK) return rc;
+  }
+  return STFD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// System operator
+// ---------------------------------------------------------------------------
+
+static void gmres_free(GmresWork* w) {
+  if (!w) return;
+  for (double* p : w->V) dev_free(p);
+  for (double* p : w->Z) dev_free(p);
+  dev_free(w->dV);
+  dev_free(w->dZ);
+  dev_free(w->partial);
+  dev_free(w->h);
+  if (w->hostbuf) cudaFreeHost(w->hostbuf);
+  delete w;
+}
+
+extern "C" void stfd_op_destroy(stfd_op* A) {
+  if (!A) return;
+  for (int l = 0; l < kMaxDim; ++l) {
+    dev_free(A->JM[l]);
+    dev_free(A->JK[l]);
+  }
+  dev_free(A->JW);
+  dev_free(A->JMt);
+  for (int k = 0; k < 4; ++k) dev_free(A->tmp[k]);
+  gmres_free(A->gw);
+  delete A;
+}
+
+extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const double* const* K,
+                                   const double* const* M, const double* Wt, const double* Mt,
+                                   double gamma, double nu, void* stream) {
+  if (!out) return STFD_ERR_ARG;
+  *out = nullptr;
+  if (!sizes_ok(d, n) || !K || !M || !Wt || !Mt) return STFD_ERR_ARG;
+  for (int l = 0; l < d; ++l)
+    if (!K[l] || !M[l]) return STFD_ERR_ARG;
+  if (!std::isfinite(gamma) || !std::isfinite(nu)) return STFD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  stfd_op* A = new (std::nothrow) stfd_op;
+  if (!A) return STFD_ERR_ALLOC;
+  A->d = d;
+  A->N = 1;
+  for (int l = 0; l <= d; ++l) {
+    A->n[l] = n[l];
+    A->N *= n[l];
+  }
+  A->gamma = gamma;
+  A->nu = nu;
+  int rc = STFD_OK;
+  std::vector<std::vector<double>> keep;
+  for (int l = 0; l < d && rc == STFD_OK; ++l) {
+    keep.push_back(row_major(n[l], M[l]));
+    rc = dev_upload(&A->JM[l], keep.back().data(), keep.back().size(), st);
+    A->bwM[l] = bandwidth(n[l], M[l]);
+    if (rc != STFD_OK) break;
+    keep.push_back(row_major(n[l], K[l]));
+    rc = dev_upload(&A->JK[l], keep.back().data(), keep.back().size(), st);
+    A->bwK[l] = bandwidth(n[l], K[l]);
+  }
+  if (rc == STFD_OK) {
+    keep.push_back(row_major(n[d], Wt));
+    rc = dev_upload(&A->JW, keep.back().data(), keep.back().size(), st);
+    A->bwW = bandwidth(n[d], Wt);
+  }
+  if (rc == STFD_OK) {
+    keep.push_back(row_major(n[d], Mt));
+    rc = dev_upload(&A->JMt, keep.back().data(), keep.back().size(), st);
+    A->bwMt = bandwidth(n[d], Mt);
+  }
+  for (int k = 0; k < 4 && rc == STFD_OK; ++k) rc = dev_upload<double>(&A->tmp[k], nullptr, (size_t)A->N, st);
+  if (rc == STFD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = STFD_ERR_CUDA;
+  if (rc != STFD_OK) {
+    stfd_op_destroy(A);
+    return rc;
+  }
+  *out = A;
+  return STFD_OK;
+}
+
+namespace {
+
+// y = gamma (W_t x M_d x..x M_1) x + nu (M_t x sum_l M_d..K_l..M_1) x, sum-factorised:
+// direction 1: (u, v) = (x x_1 M_1, x x_1 K_1); direction l > 1:
+// (u, v) <- (u x_l M_l, u x_l K_l + v x_l M_l); time: y = gamma u x W_t + nu v x M_t.
+int matvec_one(const stfd_op* A, const double* x, double* y, cudaStream_t st) {
+  const int d = A->d;
+  double* const* T = A->tmp;
+  long long inner = 1;
+  const double* u = x;
+  const double* v = nullptr;
+  for (int l = 0; l < d; ++l) {
+    const int nl = A->n[l];
+    const long long outer = A->N / (inner * nl);
+    double* uo = (l % 2 == 0) ? T[0] : T[2];
+    double* vo = (l % 2 == 0) ? T[1] : T[3];
+    const int bwM = A->bwM[l], bwK = A->bwK[l];
+    STFD_CU(launch_band_mode_fp64(u, A->JM[l], 1.0, nullptr, nullptr, 0.0, uo, nl, inner, outer, bwM, st));
+    if (l == 0) {
+      STFD_CU(launch_band_mode_fp64(u, A->JK[l], 1.0, nullptr, nullptr, 0.0, vo, nl, inner, outer, bwK, st));
+    } else {
+      STFD_CU(launch_band_mode_fp64(u, A->JK[l], 1.0, v, A->JM[l], 1.0, vo, nl, inner, outer,
+                               std::max(bwM, bwK), st));
+    }
+    u = uo;
+    v = vo;
+    inner *= nl;
+  }
+  const int nt = A->n[d];
+  STFD_CU(launch_band_mode_fp64(u, A->JW, A->gamma, v, A->JMt, A->nu, y, nt, inner, 1,
+                           std::max(A->bwW, A->bwMt), st));
+  return STFD_OK;
+}
+
+}  // namespace
+
+extern "C" int stfd_st_matvec(const stfd_op* A, const double* x, double* y, int nrhs, void* stream) {
+  if (!A || nrhs < 0 || (nrhs > 0 && (!x || !y))) return STFD_ERR_ARG;
+  if (x == y) return STFD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int k = 0; k < nrhs; ++k) {
+    const int rc = matvec_one(A, x + (size_t)k * A->N, y + (size_t)k * A->N, st);
+    if (rc != STFD_OK) return rc;
+  }
+  return STFD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Flexible GMRES
+// ---------------------------------------------------------------------------
+
+extern "C" void stfd_gmres_default_opts(stfd_gmres_opts* o) {
+  if (!o) return;
+  o->tol = 1e-8;
+  o->restart = 100;
+  o->max_it = 1000;
+}
+
+namespace {
+
+// Pointer arrays (device) sized for `cap` vectors; vectors themselves are
+// allocated lazily by ensure_vec when an iteration first needs them.
+int ensure_ptr_array(std::vector<double*>& vec, double**& dptr, int& cap, int want) {
+  if (want <= cap) return STFD_OK;
+  dev_free(dptr);
+  dptr = nullptr;
+  if (cudaMalloc((void**)&dptr, (size_t)want * sizeof(double*)) != cudaSuccess) return STFD_ERR_ALLOC;
+  cap = want;
+  if (!vec.empty())
+    STFD_CU(cudaMemcpy(dptr, vec.data(), vec.size() * sizeof(double*), cudaMemcpyHostToDevice));
+  return STFD_OK;
+}
+
+int ensure_vec(std::vector<double*>& vec, double** dptr, int idx, long long N) {
+  while ((int)vec.size() <= idx) {
+    double* p = nullptr;
+    if (cudaMalloc((void**)&p, (size_t)N * sizeof(double)) != cudaSuccess) return STFD_ERR_ALLOC;
+    vec.push_back(p);
+    STFD_CU(cudaMemcpy(dptr + (vec.size() - 1), &p, sizeof(double*), cudaMemcpyHostToDevice));
+  }
+  return STFD_OK;
+}
+
+int ensure_work(GmresWork* w, int restart) {
+  int rc = ensure_ptr_array(w->V, w->dV, w->cap_v, restart + 1);
+  if (rc != STFD_OK) return rc;
+  rc = ensure_ptr_array(w->Z, w->dZ, w->cap_z, restart);
+  if (rc != STFD_OK) return rc;
+  const int need_partial = dot_blocks() * (restart + 1);
+  if (need_partial > w->partial_cap) {
+    dev_free(w->partial);
+    w->partial = nullptr;
+    if (cudaMalloc((void**)&w->partial, (size_t)need_partial * sizeof(double)) != cudaSuccess) return STFD_ERR_ALLOC;
+    w->partial_cap = need_partial;
+  }
+  if (restart + 3 > w->hcap) {
+    dev_free(w->h);
+    w->h = nullptr;
+    if (w->hostbuf) cudaFreeHost(w->hostbuf);
+    w->hostbuf = nullptr;
+    if (cudaMalloc((void**)&w->h, (size_t)(2 * restart + 6) * sizeof(double)) != cudaSuccess) return STFD_ERR_ALLOC;
+    if (cudaMallocHost((void**)&w->hostbuf, (size_t)(2 * restart + 6) * sizeof(double)) != cudaSuccess)
+      return STFD_ERR_ALLOC;
+    w->hcap = restart + 3;
+  }
+  return STFD_OK;
+}
+
+// out[0] = ||x||^2 (device) via the multi-dot kernel with m = 1.
+int device_dot(GmresWork* w, const double* const* dptr_of_x, const double* y, long long N, double* out,
+               cudaStream_t st) {
+  STFD_CU(launch_dot_multi(dptr_of_x, 1, y, N, w->partial, dot_blocks(), st));
+  STFD_CU(launch_reduce_partial(w->partial, 1, dot_blocks(), out, 0, st));
+  return STFD_OK;
+}
+
+}  // namespace
+
+extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const double* f, double* u,
+                                const stfd_gmres_opts* opts, stfd_gmres_info* info, void* stream) {
+  if (!Ac || !P || !f || !u || f == u) return STFD_ERR_ARG;
+  if (Ac->N != P->N || Ac->d != P->d) return STFD_ERR_ARG;
+  stfd_gmres_opts o;
+  stfd_gmres_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.restart < 1 || o.restart > 1000 || o.max_it < 1 || !(o.tol > 0.0)) return STFD_ERR_ARG;
+  stfd_op* A = const_cast<stfd_op*>(Ac);   // the Krylov workspace is cached in the op
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!A->gw) {
+    A->gw = new (std::nothrow) GmresWork;
+    if (!A->gw) return STFD_ERR_ALLOC;
+  }
+  GmresWork* w = A->gw;
+  int rc = ensure_work(w, o.restart);
+  if (rc != STFD_OK) return rc;
+  if ((rc = ensure_vec(w->V, w->dV, 1, A->N)) != STFD_OK) return rc;
+  const long long N = A->N;
+  const int m = o.restart;
+  const int nb = dot_blocks();
+  double* hb = w->hostbuf;        // pinned host mirror of dh
+  double* dh = w->h;              // [0..m] h, [m+1 .. 2m+1] h2, [2m+2] ||w||^2
+  double* dh2 = w->h + (m + 1);
+  double* dnrm = w->h + (2 * m + 2);
+  if (info) {
+    info->iters = 0;
+    info->converged = 0;
+    info->rel_res_est = 1.0;
+    info->rel_res_true = 1.0;
+    info->hist_len = 0;
+  }
+  // Residual of the current iterate into V[0] and its squared norm to the host.
+  auto residual = [&](bool u_is_zero, double* nrm2) -> int {
+    if (u_is_zero) {
+      STFD_CU(cudaMemcpyAsync(w->V[0], f, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      int r2 = matvec_one(A, u, w->V[1], st);
+      if (r2 != STFD_OK) return r2;
+      STFD_CU(launch_sub(w->V[0], f, w->V[1], N, st));
+    }
+    int r3 = device_dot(w, w->dV, w->V[0], N, dnrm, st);
+    if (r3 != STFD_OK) return r3;
+    STFD_CU(cudaMemcpyAsync(hb + 2 * m + 2, dnrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+    STFD_CU(cudaStreamSynchronize(st));
+    *nrm2 = hb[2 * m + 2];
+    return STFD_OK;
+  };
+  STFD_CU(cudaMemsetAsync(u, 0, (size_t)N * sizeof(double), st));
+  double nrm2 = 0.0;
+  if ((rc = residual(true, &nrm2)) != STFD_OK) return rc;
+  const double fnorm = std::sqrt(nrm2);
+  if (!std::isfinite(fnorm)) return STFD_ERR_NAN;
+  if (fnorm == 0.0) {
+    if (info) {
+      info->converged = 1;
+      info->rel_res_est = info->rel_res_true = 0.0;
+    }
+    return STFD_OK;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  int total = 0;
+  bool converged = false;
+  double est = 1.0, beta = fnorm;
+  while (true) {
+    // v_0 = r / beta  (dnrm still holds ||r||^2 on the device)
+    STFD_CU(launch_scale_by_inverse(w->V[0], w->V[0], dnrm, N, 1, st));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j_done = 0;
+    bool lucky = false;
+    for (int j = 0; j < m && total < o.max_it; ++j) {
+      if ((rc = ensure_vec(w->V, w->dV, j + 1, N)) != STFD_OK) return rc;
+      if ((rc = ensure_vec(w->Z, w->dZ, j, N)) != STFD_OK) return rc;
+      // z_j = P^{-1} v_j ;  w = A z_j  (built in V[j+1])
+      if ((rc = fd_apply_one(P, w->V[j], w->Z[j], P->work, st)) != STFD_OK) return rc;
+      if ((rc = matvec_one(A, w->Z[j], w->V[j + 1], st)) != STFD_OK) return rc;
+      // classical Gram-Schmidt twice: h = V^T w, w -= V h, h2 = V^T w, w -= V h2
+      STFD_CU(launch_dot_multi(w->dV, j + 1, w->V[j + 1], N, w->partial, nb, st));
+      STFD_CU(launch_reduce_partial(w->partial, j + 1, nb, dh, 0, st));
+      STFD_CU(launch_multi_axpy(w->V[j + 1], w->dV, dh, j + 1, N, -1.0, st));
+      STFD_CU(launch_dot_multi(w->dV, j + 1, w->V[j + 1], N, w->partial, nb, st));
+      STFD_CU(launch_reduce_partial(w->partial, j + 1, nb, dh2, 0, st));
+      STFD_CU(launch_multi_axpy(w->V[j + 1], w->dV, dh2, j + 1, N, -1.0, st));
+      if ((rc = device_dot(w, w->dV + (j + 1), w->V[j + 1], N, dnrm, st)) != STFD_OK) return rc;
+      STFD_CU(launch_scale_by_inverse(w->V[j + 1], w->V[j + 1], dnrm, N, 1, st));
+      STFD_CU(cudaMemcpyAsync(hb, dh, (size_t)(2 * m + 3) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      STFD_CU(cudaStreamSynchronize(st));
+      double* c = &H[(size_t)(m + 1) * j];
+      for (int i = 0; i <= j; ++i) c[i] = hb[i] + hb[m + 1 + i];
+      const double hn = std::sqrt(hb[2 * m + 2]);
+      c[j + 1] = hn;
+      for (int i = 0; i <= j + 1; ++i)
+        if (!std::isfinite(c[i])) return STFD_ERR_NAN;
+      for (int i = 0; i < j; ++i) {   // previous Givens rotations
+        const double t = cs[i] * c[i] + sn[i] * c[i + 1];
+        c[i + 1] = -sn[i] * c[i] + cs[i] * c[i + 1];
+        c[i] = t;
+      }
+      const double den = std::hypot(c[j], c[j + 1]);
+      if (den == 0.0) return STFD_ERR_BREAKDOWN;
+      cs[j] = c[j] / den;
+      sn[j] = c[j + 1] / den;
+      c[j] = den;
+      c[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++total;
+      j_done = j + 1;
+      est = std::fabs(g[j + 1]) / fnorm;
+      if (info && info->history && info->hist_len < info->hist_cap) info->history[info->hist_len++] = est;
+      if (est <= o.tol) {
+        converged = true;
+        break;
+      }
+      if (hn == 0.0) {   // invariant subspace reached: the update below is exact
+        lucky = true;
+        break;
+      }
+    }
+    // y = R^{-1} g (back substitution), u += Z y
+    for (int i = j_done - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int k = i + 1; k < j_done; ++k) t -= H[i + (size_t)(m + 1) * k] * y[k];
+      y[i] = t / H[i + (size_t)(m + 1) * i];
+    }
+    std::copy(y.begin(), y.begin() + j_done, hb);
+    STFD_CU(cudaMemcpyAsync(dh, hb, (size_t)j_done * sizeof(double), cudaMemcpyHostToDevice, st));
+    STFD_CU(launch_multi_axpy(u, w->dZ, dh, j_done, N, 1.0, st));
+    if (converged || lucky || total >= o.max_it) break;
+    // restart from the true residual
+    if ((rc = residual(false, &nrm2)) != STFD_OK) return rc;
+    beta = std::sqrt(nrm2);
+    if (!std::isfinite(beta)) return STFD_ERR_NAN;
+    if (beta <= o.tol * fnorm) {
+      converged = true;
+      est = beta / fnorm;
+      break;
+    }
+  }
+  // true residual ||f - A u|| / ||f||
+  if ((rc = residual(false, &nrm2)) != STFD_OK) return rc;
+  const double true_res = std::sqrt(nrm2) / fnorm;
+  if (info) {
+    info->iters = total;
+    info->converged = converged ? 1 : 0;
+    info->rel_res_est = est;
+    info->rel_res_true = true_res;
+  }
+  if (!std::isfinite(true_res)) return STFD_ERR_NAN;
+  return converged ? STFD_OK : STFD_NOT_CONVERGED;
+}

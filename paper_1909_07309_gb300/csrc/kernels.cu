@@ -1,0 +1,280 @@
+// FP64 device kernels: mode products (Steps 2 and 4 of Algorithm 1, and the
+// banded products of the system matvec), the arrowhead block-LU solve (Step
+// 3, eq. block_LU with the 2 x 2 blocks of the Remark in Sec. 4.5), and the
+// BLAS-1/2 pieces of GMRES.
+//
+// On GB300 the FP64 pipe delivers about 1 TFLOP/s (DFMA and DMMA alike), so
+// these kernels are bound by FP64 issue, not by HBM: they stage the data
+// tile in shared memory once and spend their time in DFMA.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "kernels.h"
+#include "profile.h"
+
+namespace stfd {
+namespace {
+
+constexpr int kTC = 32;        // tensor columns per block (one per lane)
+constexpr int kThreads = 256;  // 8 warps; warp w computes rows i = w, w+8, ...
+constexpr int kWarps = kThreads / 32;
+
+// Y[o, i, c] = s1 sum_a J1[i,a] X1[o,a,c] + s2 sum_a J2[i,a] X2[o,a,c], |a - i| <= bw.
+// Column q = o * inner + c; block b handles q in [32 b, 32 b + 32).
+// BAND selects the instantiation used by the system matvec (banded univariate
+// factors) versus the dense eigenvector products of Algorithm 1.
+template <bool BAND>
+__global__ void __launch_bounds__(kThreads)
+k_mode_fp64(const double* __restrict__ X1, const double* __restrict__ J1, double s1,
+            const double* __restrict__ X2, const double* __restrict__ J2, double s2,
+            double* __restrict__ Y, int n, long long inner, long long Q, int bw) {
+  extern __shared__ double smem[];
+  double* xs1 = smem;             // [n][kTC]
+  double* xs2 = smem + (size_t)n * kTC;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long q = (long long)blockIdx.x * kTC + lane;
+  const bool valid = q < Q;
+  long long base = 0;
+  if (valid) {
+    const long long o = q / inner;
+    base = o * (long long)n * inner + (q - o * inner);
+  }
+  for (int a = warp; a < n; a += kWarps) {
+    xs1[a * kTC + lane] = valid ? X1[base + (long long)a * inner] : 0.0;
+    if (X2) xs2[a * kTC + lane] = valid ? X2[base + (long long)a * inner] : 0.0;
+  }
+  __syncthreads();
+  for (int i = warp; i < n; i += kWarps) {
+    const int a0 = max(0, i - bw), a1 = min(n - 1, i + bw);
+    const double* j1 = J1 + (size_t)i * n;
+    double acc1 = 0.0, acc2 = 0.0;
+    for (int a = a0; a <= a1; ++a) acc1 = fma(__ldg(j1 + a), xs1[a * kTC + lane], acc1);
+    if (X2) {
+      const double* j2 = J2 + (size_t)i * n;
+      for (int a = a0; a <= a1; ++a) acc2 = fma(__ldg(j2 + a), xs2[a * kTC + lane], acc2);
+    }
+    if (valid) Y[base + (long long)i * inner] = X2 ? fma(s1, acc1, s2 * acc2) : s1 * acc1;
+  }
+}
+
+// Step 3 per spatial index k, with a = nu mu_k (mu_k = sum_l lambda_l[i_l]):
+//  pairs j:  H_j = [[a, b_j], [-b_j, a]], b_j = gamma lam_j, B_j = gamma [g_2j; g_2j+1]
+//  zero block (if any): H = a, B = gamma g_z;   last: H_n = gamma sigma + a
+//  y_n = x_n + sum_j B_j^T H_j^{-1} x_j,  q_n = y_n / S_k,  q_j = H_j^{-1} (x_j - B_j q_n).
+__global__ void k_arrowhead_fp64(double* __restrict__ X, ArrowParams p) {
+  const long long Ns = p.Ns;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < Ns;
+       k += (long long)gridDim.x * blockDim.x) {
+    long long rest = k;
+    const int i1 = (int)(rest % p.n1);
+    rest /= p.n1;
+    double mu = p.lam[0][i1];
+    if (p.d >= 2) {
+      const int i2 = (int)(rest % p.n2);
+      rest /= p.n2;
+      mu += p.lam[1][i2];
+    }
+    if (p.d >= 3) mu += p.lam[2][rest];
+    const double a = p.nu * mu;
+    const double gam = p.gamma;
+    double y = X[(long long)(p.nt - 1) * Ns + k];
+    for (int j = 0; j < p.n_pairs; ++j) {
+      const double x1 = X[(long long)(2 * j) * Ns + k], x2 = X[(long long)(2 * j + 1) * Ns + k];
+      const double b = gam * p.lamt[j];
+      const double inv = 1.0 / fma(a, a, b * b);
+      const double h1 = (a * x1 - b * x2) * inv, h2 = (b * x1 + a * x2) * inv;
+      y = fma(gam, fma(p.g[2 * j], h1, p.g[2 * j + 1] * h2), y);
+    }
+    const int z = 2 * p.n_pairs;
+    double x0 = 0.0;
+    if (p.has_zero) {
+      x0 = X[(long long)z * Ns + k];
+      y = fma(gam * p.g[z], x0 / a, y);
+    }
+    const double qn = y * p.Sinv[k];
+    X[(long long)(p.nt - 1) * Ns + k] = qn;
+    for (int j = 0; j < p.n_pairs; ++j) {
+      const long long o1 = (long long)(2 * j) * Ns + k, o2 = (long long)(2 * j + 1) * Ns + k;
+      const double b = gam * p.lamt[j];
+      const double inv = 1.0 / fma(a, a, b * b);
+      const double r1 = X[o1] - gam * p.g[2 * j] * qn, r2 = X[o2] - gam * p.g[2 * j + 1] * qn;
+      X[o1] = (a * r1 - b * r2) * inv;
+      X[o2] = (b * r1 + a * r2) * inv;
+    }
+    if (p.has_zero) X[(long long)z * Ns + k] = (x0 - gam * p.g[z] * qn) / a;
+  }
+}
+
+constexpr int kDotThreads = 256;
+constexpr int kDotGroup = 4;
+
+__device__ double block_sum(double v, double* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kDotThreads)
+k_dot_multi(const double* const* __restrict__ V, int m, const double* __restrict__ w, long long N,
+            double* __restrict__ partial) {
+  __shared__ double red[kDotThreads / 32];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int i0 = 0; i0 < m; i0 += kDotGroup) {
+    double acc[kDotGroup] = {0.0, 0.0, 0.0, 0.0};
+    const int cnt = min(kDotGroup, m - i0);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride) {
+      const double wk = w[k];
+#pragma unroll
+      for (int b = 0; b < kDotGroup; ++b)
+        if (b < cnt) acc[b] = fma(V[i0 + b][k], wk, acc[b]);
+    }
+    for (int b = 0; b < cnt; ++b) {
+      const double s = block_sum(acc[b], red);
+      if (threadIdx.x == 0) partial[(size_t)blockIdx.x * m + i0 + b] = s;
+    }
+  }
+}
+
+__global__ void k_reduce_partial(const double* __restrict__ partial, int m, int nblocks,
+                                 double* __restrict__ out, int accumulate) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * m + i];
+  out[i] = accumulate ? out[i] + s : s;
+}
+
+__global__ void k_multi_axpy(double* __restrict__ w, const double* const* __restrict__ V,
+                             const double* __restrict__ h, int m, long long N, double sign) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+       k += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s = fma(h[i], V[i][k], s);
+    w[k] = fma(sign, s, w[k]);
+  }
+}
+
+// y = x / den (or x / sqrt(den)); leaves x unscaled when the divisor is not positive.
+__global__ void k_scale_by_inverse(double* __restrict__ y, const double* __restrict__ x,
+                                   const double* __restrict__ den, long long N, int sqrt_den) {
+  const double dv = sqrt_den ? sqrt(den[0]) : den[0];
+  const double inv = dv > 0.0 ? 1.0 / dv : 1.0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+       k += (long long)gridDim.x * blockDim.x)
+    y[k] = x[k] * inv;
+}
+
+__global__ void k_sub(double* __restrict__ y, const double* __restrict__ a, const double* __restrict__ b,
+                      long long N) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+       k += (long long)gridDim.x * blockDim.x)
+    y[k] = a[k] - b[k];
+}
+
+int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+  }
+  return sms;
+}
+
+int grid_for(long long n, int threads) {
+  const long long want = (n + threads - 1) / threads;
+  const long long cap = (long long)sm_count() * 8;
+  return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+}  // namespace
+
+int dot_blocks() { return sm_count() * 2; }
+
+template <bool BAND>
+static cudaError_t launch_mode_impl(const char* name, const double* X1, const double* J1, double s1,
+                                   const double* X2, const double* J2, double s2, double* Y, int n,
+                                   long long inner, long long outer, int bw, cudaStream_t st) {
+  const long long Q = inner * outer;
+  if (Q <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(X2 ? 2 : 1) * n * kTC * sizeof(double);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k_mode_fp64<BAND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         2 * 256 * kTC * (int)sizeof(double));
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  // algorithmic work: 2 flops per stored band entry per column and input
+  double entries = 0.0;
+  for (int i = 0; i < n; ++i) entries += (double)(std::min(n - 1, i + bw) - std::max(0, i - bw) + 1);
+  const int nin = X2 ? 2 : 1;
+  const double flops = 2.0 * entries * (double)Q * nin;
+  const double bytes = 8.0 * (double)Q * n * (nin + 1);
+  ProfScope ps(name, flops, bytes, st);
+  const long long blocks = (Q + kTC - 1) / kTC;
+  k_mode_fp64<BAND><<<(unsigned)blocks, kThreads, smem, st>>>(X1, J1, s1, X2, J2, s2, Y, n, inner, Q, bw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fd_mode_fp64(const double* X, const double* J, double* Y, int n, long long inner,
+                                long long outer, cudaStream_t st) {
+  return launch_mode_impl<false>("fd_mode_fp64", X, J, 1.0, nullptr, nullptr, 0.0, Y, n, inner, outer, n, st);
+}
+
+cudaError_t launch_band_mode_fp64(const double* X1, const double* J1, double s1,
+                                  const double* X2, const double* J2, double s2,
+                                  double* Y, int n, long long inner, long long outer, int bw,
+                                  cudaStream_t st) {
+  return launch_mode_impl<true>("band_mode_fp64", X1, J1, s1, X2, J2, s2, Y, n, inner, outer, bw, st);
+}
+
+cudaError_t launch_arrowhead_fp64(double* X, const ArrowParams& p, cudaStream_t st) {
+  if (p.Ns <= 0) return cudaSuccess;
+  ProfScope ps("arrowhead_fp64", (double)p.Ns * (10.0 * p.n_pairs + 4.0), 16.0 * (double)p.Ns * p.nt, st);
+  k_arrowhead_fp64<<<grid_for(p.Ns, 256), 256, 0, st>>>(X, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot_multi(const double* const* V, int m, const double* w, long long N,
+                             double* partial, int nblocks, cudaStream_t st) {
+  ProfScope ps("gmres_dot_multi", 2.0 * N * m, 8.0 * N * (m + 1), st);
+  k_dot_multi<<<nblocks, kDotThreads, 0, st>>>(V, m, w, N, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partial(const double* partial, int m, int nblocks, double* out,
+                                  int accumulate, cudaStream_t st) {
+  ProfScope ps("gmres_reduce", (double)m * nblocks, 8.0 * m * nblocks, st);
+  k_reduce_partial<<<(m + 127) / 128, 128, 0, st>>>(partial, m, nblocks, out, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_axpy(double* w, const double* const* V, const double* h, int m,
+                              long long N, double sign, cudaStream_t st) {
+  ProfScope ps("gmres_multi_axpy", 2.0 * N * m, 8.0 * N * (m + 2), st);
+  k_multi_axpy<<<grid_for(N, 256), 256, 0, st>>>(w, V, h, m, N, sign);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_by_inverse(double* y, const double* x, const double* den, long long N,
+                                    int sqrt_den, cudaStream_t st) {
+  ProfScope ps("gmres_scale", (double)N, 16.0 * N, st);
+  k_scale_by_inverse<<<grid_for(N, 256), 256, 0, st>>>(y, x, den, N, sqrt_den);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub(double* y, const double* a, const double* b, long long N, cudaStream_t st) {
+  ProfScope ps("gmres_sub", (double)N, 24.0 * N, st);
+  k_sub<<<grid_for(N, 256), 256, 0, st>>>(y, a, b, N);
+  return cudaGetLastError();
+}
+
+}  // namespace stfd

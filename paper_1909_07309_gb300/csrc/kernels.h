@@ -1,0 +1,53 @@
+// Launchers of the device kernels (FP64 path). All are stream-ordered and
+// return the cudaError_t of the launch.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace stfd {
+
+// Mode product of Algorithm 1 (dense n x n factor):
+// Y[o, i, c] = sum_a J[i*n + a] X[o, a, c] for o < outer, i < n, c < inner,
+// with X[o, a, c] at o*n*inner + a*inner + c. Y must not alias X.
+cudaError_t launch_fd_mode_fp64(const double* X, const double* J, double* Y, int n, long long inner,
+                                long long outer, cudaStream_t st);
+
+// Banded mode products of the system matvec:
+// Y[o, i, c] = s1 sum_a J1[i,a] X1[o,a,c] (+ s2 sum_a J2[i,a] X2[o,a,c]), |a - i| <= bw.
+// X2/J2 may be NULL. Y must not alias X1 or X2.
+cudaError_t launch_band_mode_fp64(const double* X1, const double* J1, double s1,
+                                  const double* X2, const double* J2, double s2,
+                                  double* Y, int n, long long inner, long long outer, int bw,
+                                  cudaStream_t st);
+
+// In-place Step 3 of Algorithm 1 on the spectral tensor X[t][k] (time index
+// slowest): block LU of the real arrowhead system per spatial index k.
+struct ArrowParams {
+  int d, n1, n2, nt, n_pairs, has_zero;
+  long long Ns;
+  const double* lam[3];   // spatial eigenvalues per direction
+  const double* lamt;     // n_pairs
+  const double* g;        // nt - 1
+  const double* Sinv;     // Ns reciprocals of the Schur complement
+  double gamma, nu;
+};
+cudaError_t launch_arrowhead_fp64(double* X, const ArrowParams& p, cudaStream_t st);
+
+// GMRES BLAS: partial[b*m + i] = sum over block b's range of V_i[k] * w[k].
+cudaError_t launch_dot_multi(const double* const* V, int m, const double* w, long long N,
+                             double* partial, int nblocks, cudaStream_t st);
+// out[i] = sum_b partial[b*m + i]  (+ out[i] if accumulate)
+cudaError_t launch_reduce_partial(const double* partial, int m, int nblocks, double* out,
+                                  int accumulate, cudaStream_t st);
+// w[k] += sign * sum_i h[i] V_i[k]
+cudaError_t launch_multi_axpy(double* w, const double* const* V, const double* h, int m,
+                              long long N, double sign, cudaStream_t st);
+// y[k] = x[k] / *den, or x[k] / sqrt(*den) if sqrt_den (den on the device;
+// a non-positive divisor leaves x unscaled)
+cudaError_t launch_scale_by_inverse(double* y, const double* x, const double* den, long long N,
+                                    int sqrt_den, cudaStream_t st);
+// y[k] = a[k] - b[k]
+cudaError_t launch_sub(double* y, const double* a, const double* b, long long N, cudaStream_t st);
+
+int dot_blocks();
+
+}  // namespace stfd

@@ -1,0 +1,184 @@
+// Per-kernel CUDA-event timing, launch counting and the DFMA throughput probe
+// declared in stfd_profile.h.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "profile.h"
+#include "stfd.h"
+#include "stfd_profile.h"
+
+namespace stfd {
+namespace {
+
+struct Pending {
+  const char* name;
+  cudaEvent_t e0, e1;
+  double flops, bytes;
+};
+
+struct Total {
+  std::string name;
+  long long launches = 0;
+  double ms = 0.0, flops = 0.0, bytes = 0.0;
+};
+
+std::mutex g_mu;
+bool g_on = false;
+std::vector<Pending> g_pending;
+std::vector<Total> g_totals;
+std::vector<cudaEvent_t> g_free;
+std::atomic<long long> g_launches{0};
+
+cudaEvent_t take_event() {
+  if (!g_free.empty()) {
+    cudaEvent_t e = g_free.back();
+    g_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Fold pending records into totals (caller holds the lock).
+void drain() {
+  for (const Pending& p : g_pending) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(p.e1) == cudaSuccess && cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+      Total* t = nullptr;
+      for (Total& x : g_totals)
+        if (x.name == p.name) t = &x;
+      if (!t) {
+        g_totals.push_back(Total());
+        t = &g_totals.back();
+        t->name = p.name;
+      }
+      t->launches += 1;
+      t->ms += ms;
+      t->flops += p.flops;
+      t->bytes += p.bytes;
+    }
+    g_free.push_back(p.e0);
+    g_free.push_back(p.e1);
+  }
+  g_pending.clear();
+}
+
+}  // namespace
+
+ProfScope::ProfScope(const char* name, double flops, double bytes, cudaStream_t st)
+    : name_(name), flops_(flops), bytes_(bytes), st_(st) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_on) return;
+  e0_ = take_event();
+  e1_ = take_event();
+  if (e0_ && e1_) {
+    cudaEventRecord(e0_, st_);
+    active_ = true;
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (!active_) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaEventRecord(e1_, st_);
+  g_pending.push_back(Pending{name_, e0_, e1_, flops_, bytes_});
+}
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+// Eight independent FMA chains per thread keep the FP64 pipe saturated.
+__global__ void k_probe_dfma(double* out, int iters, double c) {
+  double a0 = threadIdx.x * 1e-3, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
+  double a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+  const double b = 0.999999;
+  for (int i = 0; i < iters; ++i) {
+    a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
+    a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
+  }
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+
+}  // namespace
+}  // namespace stfd
+
+using namespace stfd;
+
+extern "C" int stfd_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_on = on != 0;
+  return STFD_OK;
+}
+
+extern "C" int stfd_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  drain();
+  g_totals.clear();
+  return STFD_OK;
+}
+
+extern "C" int stfd_profile_count(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  drain();
+  return (int)g_totals.size();
+}
+
+extern "C" int stfd_profile_get(int idx, char* name, int name_cap, long long* launches, double* ms,
+                                double* flops, double* bytes) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  drain();
+  if (idx < 0 || idx >= (int)g_totals.size()) return STFD_ERR_ARG;
+  const Total& t = g_totals[idx];
+  if (name && name_cap > 0) {
+    std::strncpy(name, t.name.c_str(), (size_t)name_cap - 1);
+    name[name_cap - 1] = '\0';
+  }
+  if (launches) *launches = t.launches;
+  if (ms) *ms = t.ms;
+  if (flops) *flops = t.flops;
+  if (bytes) *bytes = t.bytes;
+  return STFD_OK;
+}
+
+extern "C" long long stfd_launch_count(void) { return g_launches.load(); }
+
+extern "C" int stfd_probe_fp64_peak(double* flops_per_s, void* stream) {
+  if (!flops_per_s) return STFD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return STFD_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return STFD_ERR_CUDA;
+  const int threads = 256, blocks = sms * 8, iters = 4000;
+  double* out = nullptr;
+  if (cudaMalloc((void**)&out, (size_t)threads * blocks * sizeof(double)) != cudaSuccess) return STFD_ERR_ALLOC;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = STFD_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = STFD_ERR_CUDA;
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && rc == STFD_OK; ++rep) {
+    cudaEventRecord(e0, st);
+    k_probe_dfma<<<blocks, threads, 0, st>>>(out, iters, 1e-7);
+    count_launch();
+    cudaEventRecord(e1, st);
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = STFD_ERR_CUDA;
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;   // first launch is a warm-up
+  }
+  if (rc == STFD_OK) *flops_per_s = 16.0 * iters * (double)threads * blocks / (best * 1e-3);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  return rc;
+}

@@ -1,0 +1,352 @@
+"""Python binding of the C ABI in ``include/stfd.h`` (ctypes; marshalling only).
+
+Every numerical step runs in ``lib/libstfd.so``: the host-side setup in its
+C++ code and the apply / matvec / GMRES path in its CUDA kernels. This module
+only converts arguments (numpy arrays for host data, torch CUDA tensors for
+device data, torch's current stream) and raises on error codes. There is no
+fallback: if the library is missing or fails to load, every call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+STFD_OK = 0
+STFD_NOT_CONVERGED = 1
+STFD_FP64 = 0
+STFD_BC_NONE, STFD_BC_INITIAL, STFD_BC_DIRICHLET = 0, 1, 2
+
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_dbl_p = ctypes.POINTER(ctypes.c_double)
+_c_dbl_pp = ctypes.POINTER(_c_dbl_p)
+_lib = None
+
+
+class StfdError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (what, _strerror(code), code))
+
+
+class GmresOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_it", ctypes.c_int)]
+
+
+class GmresInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("rel_res_est", ctypes.c_double), ("rel_res_true", ctypes.c_double),
+                ("history", _c_dbl_p), ("hist_cap", ctypes.c_int), ("hist_len", ctypes.c_int)]
+
+
+# Exported symbols and their signatures: (restype, argtypes).
+SIGNATURES = {
+    "stfd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "stfd_version": (ctypes.c_int, []),
+    "stfd_spline_matrices": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                            _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_int_p]),
+    "stfd_spline_load_trig": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double, _c_dbl_p]),
+    "stfd_fd_factors": (ctypes.c_int, [ctypes.c_int, _c_int_p, _c_dbl_pp, _c_dbl_pp, _c_dbl_p, _c_dbl_p,
+                                       _c_dbl_pp, _c_dbl_pp, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p,
+                                       _c_int_p, _c_int_p]),
+    "stfd_fd_setup": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _c_int_p, _c_dbl_pp,
+                                     _c_dbl_pp, _c_dbl_p, _c_dbl_p, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_void_p]),
+    "stfd_fd_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p]),
+    "stfd_fd_shape": (ctypes.c_int, [ctypes.c_void_p, _c_int_p, _c_int_p, ctypes.POINTER(ctypes.c_longlong)]),
+    "stfd_fd_destroy": (None, [ctypes.c_void_p]),
+    "stfd_op_create_kron": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _c_int_p, _c_dbl_pp,
+                                           _c_dbl_pp, _c_dbl_p, _c_dbl_p, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_void_p]),
+    "stfd_st_matvec": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                      ctypes.c_void_p]),
+    "stfd_op_destroy": (None, [ctypes.c_void_p]),
+    "stfd_gmres_default_opts": (None, [ctypes.POINTER(GmresOpts)]),
+    "stfd_gmres_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo), ctypes.c_void_p]),
+    # include/stfd_profile.h
+    "stfd_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "stfd_profile_reset": (ctypes.c_int, []),
+    "stfd_profile_count": (ctypes.c_int, []),
+    "stfd_profile_get": (ctypes.c_int, [ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_longlong), _c_dbl_p, _c_dbl_p, _c_dbl_p]),
+    "stfd_launch_count": (ctypes.c_longlong, []),
+    "stfd_probe_fp64_peak": (ctypes.c_int, [_c_dbl_p, ctypes.c_void_p]),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libstfd.so (building it first if it is absent and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libstfd.so is not built (%s); run paper_1909_07309_gb300.build" % path)
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _strerror(code):
+    try:
+        return load().stfd_strerror(int(code)).decode()
+    except Exception:   # the library itself is unavailable
+        return "status"
+
+
+def _check(rc, what, allow_not_converged=False):
+    if rc == STFD_OK or (allow_not_converged and rc == STFD_NOT_CONVERGED):
+        return rc
+    raise StfdError(rc, what)
+
+
+def _f64(a):
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_c_dbl_p)
+
+
+def _ptr_array(arrs):
+    return (_c_dbl_p * len(arrs))(*[_dptr(a) for a in arrs])
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, N, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous float64 CUDA tensor" % what)
+    if t.numel() % N != 0:
+        raise ValueError("%s has %d entries, not a multiple of N = %d" % (what, t.numel(), N))
+    return ctypes.c_void_p(t.data_ptr()), t.numel() // N
+
+
+# ---------------------------------------------------------------------------
+# host entry points
+# ---------------------------------------------------------------------------
+
+def stfd_spline_matrices(p, n_el, length=1.0, bc=STFD_BC_NONE):
+    """(M, K, W) dense n x n univariate matrices (eq. time_mat / space_mat factors)."""
+    lib = load()
+    n = ctypes.c_int(0)
+    _check(lib.stfd_spline_matrices(p, n_el, float(length), bc, None, None, None, ctypes.byref(n)),
+           "stfd_spline_matrices")
+    M, K, W = (np.zeros((n.value, n.value), order="F") for _ in range(3))
+    _check(lib.stfd_spline_matrices(p, n_el, float(length), bc, _dptr(M), _dptr(K), _dptr(W), ctypes.byref(n)),
+           "stfd_spline_matrices")
+    return M, K, W
+
+
+def stfd_spline_load_trig(p, n_el, length, bc, freq, c_sin, c_cos):
+    lib = load()
+    n = ctypes.c_int(0)
+    _check(lib.stfd_spline_matrices(p, n_el, float(length), bc, None, None, None, ctypes.byref(n)),
+           "stfd_spline_matrices")
+    out = np.zeros(n.value)
+    _check(lib.stfd_spline_load_trig(p, n_el, float(length), bc, float(freq), float(c_sin), float(c_cos),
+                                     _dptr(out)), "stfd_spline_load_trig")
+    return out
+
+
+def stfd_fd_factors(K, M, Wt, Mt):
+    """Host factors of Step 1 of Algorithm 1 (real arrowhead form), as a dict."""
+    lib = load()
+    d = len(K)
+    K = [_f64(k) for k in K]
+    M = [_f64(m) for m in M]
+    Wt, Mt = _f64(Wt), _f64(Mt)
+    n = [k.shape[0] for k in K] + [Wt.shape[0]]
+    nt = n[-1]
+    U = [np.zeros((nl, nl), order="F") for nl in n[:d]]
+    lam = [np.zeros(nl) for nl in n[:d]]
+    Ut = np.zeros((nt, nt), order="F")
+    lamt = np.zeros(max(1, nt // 2))
+    g = np.zeros(nt - 1)
+    sigma = ctypes.c_double(0.0)
+    npairs = ctypes.c_int(0)
+    hz = ctypes.c_int(0)
+    rc = lib.stfd_fd_factors(d, (ctypes.c_int * (d + 1))(*n), _ptr_array(K), _ptr_array(M), _dptr(Wt), _dptr(Mt),
+                             _ptr_array(U), _ptr_array(lam), _dptr(Ut), _dptr(lamt), _dptr(g),
+                             ctypes.byref(sigma), ctypes.byref(npairs), ctypes.byref(hz))
+    _check(rc, "stfd_fd_factors")
+    return {"U": U, "lam": lam, "Ut": Ut, "lamt": lamt[:npairs.value].copy(), "g": g,
+            "sigma": sigma.value, "n_pairs": npairs.value, "has_zero": hz.value}
+
+
+# ---------------------------------------------------------------------------
+# device handles
+# ---------------------------------------------------------------------------
+
+class FD:
+    """Preconditioner handle: ``stfd_fd_setup`` / ``stfd_fd_apply`` / ``stfd_fd_destroy``."""
+
+    def __init__(self, K, M, Wt, Mt, gamma=1.0, nu=1.0, precision=STFD_FP64, stream=None):
+        lib = load()
+        self._lib = lib
+        self.handle = ctypes.c_void_p()
+        K = [_f64(k) for k in K]
+        M = [_f64(m) for m in M]
+        Wt, Mt = _f64(Wt), _f64(Mt)
+        self.d = len(K)
+        self.n = [k.shape[0] for k in K] + [Wt.shape[0]]
+        self.N = int(np.prod(self.n))
+        rc = lib.stfd_fd_setup(ctypes.byref(self.handle), self.d, (ctypes.c_int * (self.d + 1))(*self.n),
+                               _ptr_array(K), _ptr_array(M), _dptr(Wt), _dptr(Mt), float(gamma), float(nu),
+                               int(precision), _stream(stream))
+        _check(rc, "stfd_fd_setup")
+
+    def apply(self, r, s=None, stream=None):
+        """s = P^{-1} r for r of shape (N,) or (nrhs, N); returns s."""
+        import torch
+        if s is None:
+            s = torch.empty_like(r)
+        rp, nrhs = _dev(r, self.N, "r")
+        sp, nrhs2 = _dev(s, self.N, "s")
+        if nrhs != nrhs2:
+            raise ValueError("r and s hold different numbers of right-hand sides")
+        _check(self._lib.stfd_fd_apply(self.handle, rp, sp, nrhs, _stream(stream)), "stfd_fd_apply")
+        return s
+
+    def close(self):
+        if self.handle:
+            self._lib.stfd_fd_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class KronOp:
+    """System operator handle: ``stfd_op_create_kron`` / ``stfd_st_matvec`` / ``stfd_gmres_solve``."""
+
+    def __init__(self, K, M, Wt, Mt, gamma=1.0, nu=1.0, stream=None):
+        lib = load()
+        self._lib = lib
+        self.handle = ctypes.c_void_p()
+        K = [_f64(k) for k in K]
+        M = [_f64(m) for m in M]
+        Wt, Mt = _f64(Wt), _f64(Mt)
+        self.d = len(K)
+        self.n = [k.shape[0] for k in K] + [Wt.shape[0]]
+        self.N = int(np.prod(self.n))
+        rc = lib.stfd_op_create_kron(ctypes.byref(self.handle), self.d, (ctypes.c_int * (self.d + 1))(*self.n),
+                                     _ptr_array(K), _ptr_array(M), _dptr(Wt), _dptr(Mt), float(gamma),
+                                     float(nu), _stream(stream))
+        _check(rc, "stfd_op_create_kron")
+
+    def matvec(self, x, y=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        xp, nrhs = _dev(x, self.N, "x")
+        yp, nrhs2 = _dev(y, self.N, "y")
+        if nrhs != nrhs2:
+            raise ValueError("x and y hold different numbers of vectors")
+        _check(self._lib.stfd_st_matvec(self.handle, xp, yp, nrhs, _stream(stream)), "stfd_st_matvec")
+        return y
+
+    def gmres(self, fd, f, u=None, tol=1e-8, restart=100, max_it=1000, hist_cap=1000, stream=None):
+        """Solve A u = f with FD-preconditioned flexible GMRES; returns (u, info dict)."""
+        import torch
+        if u is None:
+            u = torch.empty_like(f)
+        fp, k1 = _dev(f, self.N, "f")
+        up, k2 = _dev(u, self.N, "u")
+        if k1 != 1 or k2 != 1:
+            raise ValueError("gmres solves one right-hand side")
+        opts = GmresOpts(float(tol), int(restart), int(max_it))
+        hist = np.zeros(max(1, hist_cap))
+        info = GmresInfo(0, 0, 0.0, 0.0, _dptr(hist), int(hist_cap), 0)
+        rc = self._lib.stfd_gmres_solve(self.handle, fd.handle, fp, up, ctypes.byref(opts), ctypes.byref(info),
+                                        _stream(stream))
+        _check(rc, "stfd_gmres_solve", allow_not_converged=True)
+        return u, {"iters": info.iters, "converged": bool(info.converged), "rel_res_est": info.rel_res_est,
+                   "rel_res_true": info.rel_res_true, "history": hist[:info.hist_len].copy(), "status": rc}
+
+    def close(self):
+        if self.handle:
+            self._lib.stfd_op_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# diagnostics (include/stfd_profile.h)
+# ---------------------------------------------------------------------------
+
+def stfd_profile_enable(on=True):
+    _check(load().stfd_profile_enable(1 if on else 0), "stfd_profile_enable")
+
+
+def stfd_profile_reset():
+    _check(load().stfd_profile_reset(), "stfd_profile_reset")
+
+
+def stfd_profile_records():
+    """List of {name, launches, ms, flops, bytes} per kernel since the last reset."""
+    lib = load()
+    out = []
+    for i in range(lib.stfd_profile_count()):
+        name = ctypes.create_string_buffer(64)
+        n = ctypes.c_longlong(0)
+        ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib.stfd_profile_get(i, name, 64, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
+                                    ctypes.byref(by)), "stfd_profile_get")
+        out.append({"name": name.value.decode(), "launches": n.value, "ms": ms.value,
+                    "flops": fl.value, "bytes": by.value})
+    return out
+
+
+def stfd_launch_count():
+    return int(load().stfd_launch_count())
+
+
+def stfd_probe_fp64_peak(stream=None):
+    """Measured FP64 FMA throughput of the current device (FLOP/s)."""
+    v = ctypes.c_double(0.0)
+    _check(load().stfd_probe_fp64_peak(ctypes.byref(v), _stream(stream)), "stfd_probe_fp64_peak")
+    return v.value
+
+
+def heat_problem(d, p, n_el, T=1.0, lengths=None, p_t=None, n_el_t=None):
+    """Univariate factors of the heat problem on a box x (0, T) from the library's own
+    spline assembly: returns (K_list, M_list, W_t, M_t)."""
+    lengths = [1.0] * d if lengths is None else list(lengths)
+    p_t = p if p_t is None else p_t
+    n_el_t = n_el if n_el_t is None else n_el_t
+    K, M = [], []
+    for l in range(d):
+        Ml, Kl, _ = stfd_spline_matrices(p, n_el, lengths[l], STFD_BC_DIRICHLET)
+        K.append(Kl)
+        M.append(Ml)
+    Mt, _, Wt = stfd_spline_matrices(p_t, n_el_t, T, STFD_BC_INITIAL)
+    return K, M, Wt, Mt
