@@ -276,7 +276,7 @@ int fd_apply_one(const stfd_fd* h, const double* r, double* s, double* work, cud
 
 extern "C" int stfd_fd_apply(const stfd_fd* h, const double* r, double* s, int nrhs, void* stream) {
   if (!h || nrhs < 0 || (nrhs > 0 && (!r || !s))) return STFD_ERR_ARG;
-  if (r == s) return STFD_ERR_ARG;
+  if (nrhs > 0 && r == s) return STFD_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   for (int k = 0; k < nrhs; ++k) {
     const int rc = fd_apply_one(h, r + (size_t)k * h->N, s + (size_t)k * h->N, h->work, st);
@@ -403,7 +403,7 @@ int matvec_one(const stfd_op* A, const double* x, double* y, cudaStream_t st) {
 
 extern "C" int stfd_st_matvec(const stfd_op* A, const double* x, double* y, int nrhs, void* stream) {
   if (!A || nrhs < 0 || (nrhs > 0 && (!x || !y))) return STFD_ERR_ARG;
-  if (x == y) return STFD_ERR_ARG;
+  if (nrhs > 0 && x == y) return STFD_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   for (int k = 0; k < nrhs; ++k) {
     const int rc = matvec_one(A, x + (size_t)k * A->N, y + (size_t)k * A->N, st);

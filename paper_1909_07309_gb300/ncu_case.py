@@ -1,0 +1,39 @@
+"""Small fixed workloads for Nsight Compute captures of one kernel family.
+
+  python -m paper_1909_07309_gb300.ncu_case {fd,matvec,solve} D P N_EL [REPS]
+
+Builds the unit-cube problem (d = D, degree P, N_EL elements per direction),
+runs one warm-up and REPS applications of fd_apply, st_matvec or the
+preconditioned GMRES solve, synchronises and exits. Prints nothing else.
+"""
+import sys
+
+import numpy as np
+
+
+def main(argv):
+    import torch
+
+    from . import inputs, stfd
+    what, d, p, n_el = argv[0], int(argv[1]), int(argv[2]), int(argv[3])
+    reps = int(argv[4]) if len(argv) > 4 else 2
+    K, M, Wt, Mt = stfd.heat_problem(d, p, n_el)
+    P = stfd.FD(K, M, Wt, Mt)
+    A = stfd.KronOp(K, M, Wt, Mt)
+    r = torch.from_numpy(inputs.standard_normal(P.N, 1)).cuda()
+    out = torch.empty_like(r)
+    for _ in range(1 + reps):
+        if what == "fd":
+            P.apply(r, out)
+        elif what == "matvec":
+            A.matvec(r, out)
+        elif what == "solve":
+            A.gmres(P, r, out)
+        else:
+            raise SystemExit("unknown case %s" % what)
+    torch.cuda.synchronize()
+    print("ncu_case %s d=%d p=%d n_el=%d N=%d reps=%d ok" % (what, d, p, n_el, P.N, reps))
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])
