@@ -35,7 +35,7 @@ L2_BYTES = 129 * 2 ** 20
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture
 # (profiles/fd_mode_fp64_unit_cube_p3_nel64.txt); None until captured for the current kernel.
-NCU_TRAFFIC = {"kernel": "fd_mode_fp64", "bytes_per_launch": None}
+NCU_TRAFFIC = {"kernel": "fd_mode_fp64", "bytes_per_launch": 238.1e6}
 
 
 def measured_peaks():
@@ -47,7 +47,7 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -62,7 +62,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, FileNotFoundError):
@@ -173,7 +173,7 @@ def reference_main(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--restart", type=int, default=100)
@@ -288,13 +288,19 @@ def main():
     stfd.stfd_profile_reset()
     total_ms = sum(rc["ms"] for rc in recs) or 1.0
     top = max(recs, key=lambda rc: rc["ms"])
-    fp64_peak = stfd.stfd_probe_fp64_peak()
+    probe = stfd.stfd_probe_fp64_peak()
+    # FP64 peak from unit counts and clocks: 2 DFMA per clock per SM (the nominal
+    # 1.25 TFLOP/s at 152 SMs and 2070 MHz), at the median SM clock sampled in the timed region.
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    mhz = clocks.get("sm_mhz") or 2070.0
+    fp64_peak = 2 * 2 * sms * mhz * 1e6
     per_launch_s = top["ms"] * 1e-3 / top["launches"]
     achieved = top["flops"] / top["launches"] / per_launch_s
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["kernel"] == top["name"] else None
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / fp64_peak, "traffic": traffic, "kernel": top["name"],
-                "peak_source": "FP64 DFMA throughput measured in this run (stfd_probe_fp64_peak)",
+                "peak_source": "FP64: 2 DFMA/clk/SM x %d SMs x %.0f MHz (sampled); DFMA probe in this run %.3f TFLOP/s"
+                               % (sms, mhz, probe / 1e12),
                 "achieved_gbs": top["bytes"] / top["launches"] / per_launch_s / 1e9,
                 "share_of_step": top["ms"] / total_ms}
     kernels = {rc["name"]: {"launches": rc["launches"], "ms": round(rc["ms"], 3),
