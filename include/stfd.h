@@ -183,6 +183,38 @@ void stfd_gmres_default_opts(stfd_gmres_opts* opts);
 int stfd_gmres_solve(const stfd_op* A, const stfd_fd* P, const double* f_dev, double* u_dev,
                      const stfd_gmres_opts* opts, stfd_gmres_info* info, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free system matvec. The paper has no counterpart: this entry
+ * point serves callers that must not allocate device memory -- for example a
+ * host application that owns every byte of device memory through its own
+ * allocator and memory budget, or a latency-critical loop where cudaMalloc /
+ * cudaFree would synchronise the device and stall other streams.
+ *
+ * Computes y_dev = A x_dev exactly like stfd_st_matvec (same sum-factorised
+ * banded products), but takes the univariate matrices as caller-owned device
+ * arrays and keeps its scratch (four partial-sum tensors) in one static device
+ * array of 4 * STFD_NOALLOC_MAX_N doubles (16 MiB) that every GPU loading the
+ * library holds until the process exits. It calls no allocating routine.
+ *   n[0..d]   sizes as in stfd_op_create_kron; N = prod n must not exceed
+ *             STFD_NOALLOC_MAX_N (else STFD_ERR_ARG, nothing launched)
+ *   K_dev[l], M_dev[l]  device, column-major n[l] x n[l]; Wt_dev, Mt_dev n_t x n_t
+ *   bw        host array of d+1 half-bandwidths (space directions, then time:
+ *             max over the two matrices of that direction); NULL or a
+ *             negative entry treats that direction as dense
+ *   x_dev, y_dev        device N-vectors, must not overlap
+ * The first call on a device looks up the static array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture. All calls share the one array, which
+ * keeps the last call's contents; every scratch element is written before it is
+ * read within a call, so nothing needs clearing. Calls that overlap on the GPU
+ * (concurrent streams, or several host threads) race on the scratch: order them.
+ * ------------------------------------------------------------------------ */
+#define STFD_NOALLOC_MAX_N 524288
+
+int stfd_st_matvec_noalloc(int d, const int* n, const double* const* K_dev, const double* const* M_dev,
+                           const double* Wt_dev, const double* Mt_dev, const int* bw,
+                           double gamma, double nu, const double* x_dev, double* y_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

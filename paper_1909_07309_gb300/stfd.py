@@ -17,6 +17,7 @@ STFD_OK = 0
 STFD_NOT_CONVERGED = 1
 STFD_FP64 = 0
 STFD_BC_NONE, STFD_BC_INITIAL, STFD_BC_DIRICHLET = 0, 1, 2
+STFD_NOALLOC_MAX_N = 524288
 
 _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_dbl_p = ctypes.POINTER(ctypes.c_double)
@@ -67,6 +68,10 @@ SIGNATURES = {
     "stfd_gmres_default_opts": (None, [ctypes.POINTER(GmresOpts)]),
     "stfd_gmres_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo), ctypes.c_void_p]),
+    "stfd_st_matvec_noalloc": (ctypes.c_int, [ctypes.c_int, _c_int_p, ctypes.POINTER(ctypes.c_void_p),
+                                              ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p,
+                                              _c_int_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p]),
     # include/stfd_profile.h
     "stfd_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "stfd_profile_reset": (ctypes.c_int, []),
