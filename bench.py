@@ -277,6 +277,40 @@ def main():
     mv_ms = e0.elapsed_time(e1) / args.steps
     resid = float(torch.linalg.norm(y - r) / torch.linalg.norm(r))
 
+    # ---- mixed-precision preconditioners inside the same FP64 flexible GMRES
+    variants = {}
+    for name, prec in (("fp64", stfd.STFD_FP64), ("tf32", stfd.STFD_TF32), ("bf16", stfd.STFD_BF16)):
+        Pv = P if prec == stfd.STFD_FP64 else stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=prec)
+        for _ in range(3):
+            Pv.apply(r, s)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            Pv.apply(r, s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        v_fd = e0.elapsed_time(e1) / args.steps
+        s_v = s.clone()
+        for _ in range(args.warmup):
+            A.gmres(Pv, f, u, tol=1e-8, restart=args.restart)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, vinfo = A.gmres(Pv, f, u, tol=1e-8, restart=args.restart)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        v_gm = e0.elapsed_time(e1) / args.steps
+        variants[name] = {"fd_apply_ms": v_fd, "fd_apply_dofs_per_s": N / (v_fd * 1e-3), "gmres_ms": v_gm,
+                          "gmres_iters": vinfo["iters"], "rel_res_true": vinfo["rel_res_true"], "_s": s_v}
+        if Pv is not P:
+            Pv.close()
+    ref_s = variants["fp64"].pop("_s")
+    for name in ("tf32", "bf16"):
+        sv = variants[name].pop("_s")
+        variants[name]["fd_apply_rel_err_vs_fp64"] = float(torch.linalg.norm(sv - ref_s) / torch.linalg.norm(ref_s))
+    if stfd.load().stfd_device_status() != 0:
+        raise RuntimeError("a tensor-core kernel reported a timed-out wait")
+
     # ---- roofline of the dominant kernel: per-launch CUDA events inside the library
     stfd.stfd_profile_reset()
     stfd.stfd_profile_enable(True)
@@ -318,6 +352,7 @@ def main():
         "fd_apply": {"ms": fd_ms, "dofs_per_s": N / (fd_ms * 1e-3)},
         "st_matvec": {"ms": mv_ms, "dofs_per_s": N / (mv_ms * 1e-3), "residual_A_Pinv_r": resid},
         "gmres_time_to_1e-8_ms": ms / args.steps,
+        "precond_variants": variants,
         "roofline": roofline, "kernels": kernels, "gpu_launches": launches,
         "clocks": clocks, "e2e": e2e,
     }

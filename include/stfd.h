@@ -49,8 +49,13 @@ enum {
   STFD_NOT_CONVERGED = 1    /* solver stopped at max_it above the tolerance */
 };
 
-/* Arithmetic of the preconditioner's mode products. */
-enum { STFD_FP64 = 0 };
+/* Arithmetic of the preconditioner's mode products (Steps 2 and 4 of
+ * Algorithm 1). STFD_FP64: FP64 throughout. STFD_TF32 / STFD_BF16: operands
+ * rounded to TF32 / BF16 on the tcgen05 tensor cores with FP32 accumulation,
+ * FP32 intermediates and an FP32 Step 3; input and output vectors stay FP64.
+ * The low-precision preconditioner is meant for flexible GMRES, which keeps
+ * the outer iteration, the system matvec and the residual in FP64. */
+enum { STFD_FP64 = 0, STFD_TF32 = 1, STFD_BF16 = 2 };
 
 /* Boundary treatment of a univariate basis (Sec. 2.2). */
 enum {
@@ -61,6 +66,12 @@ enum {
 
 const char* stfd_strerror(int code);
 int stfd_version(void);
+
+/* Reads and clears the device flag that the tensor-core kernels set when a
+ * bounded wait on the tensor-core pipeline gives up (they then skip their
+ * remaining work, release tensor memory and return). Synchronises the device.
+ * Returns STFD_OK, STFD_ERR_TIMEOUT if the flag was set, or STFD_ERR_CUDA. */
+int stfd_device_status(void);
 
 /* ------------------------------------------------------------------------
  * Univariate spline matrices (host, CPU only).
@@ -107,7 +118,8 @@ int stfd_fd_factors(int d, const int* n, const double* const* K, const double* c
 
 /* ------------------------------------------------------------------------
  * Preconditioner handle (Algorithm 1). d in {1, 2, 3}, 1 <= n[l] <= 256,
- * 2 <= n_t <= 256, gamma > 0, nu > 0. The factorisation runs on the host;
+ * 2 <= n_t <= 256, gamma > 0, nu > 0, precision one of STFD_FP64 / STFD_TF32 /
+ * STFD_BF16 (low precision: n[l] <= 128). The factorisation runs on the host;
  * factors are uploaded on `stream` and the call synchronises that stream
  * before returning. Device memory held: the factors, one N-vector of
  * scratch and N_s Schur-complement reciprocals.

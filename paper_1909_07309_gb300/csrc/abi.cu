@@ -80,6 +80,13 @@ struct stfd_fd {
   double* work = nullptr;
   int n_pairs = 0, has_zero = 0;
   double sigma = 0.0;
+  // low-precision path (STFD_TF32 / STFD_BF16): operand images of U^T / U and FP32 copies
+  unsigned char* Bf[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};
+  unsigned char* Bb[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};
+  float* lam_f[kMaxDim] = {nullptr, nullptr, nullptr};
+  float* lamt_f = nullptr;
+  float* g_f = nullptr;
+  float* Sinv_f = nullptr;
 };
 
 struct GmresWork {
@@ -127,6 +134,13 @@ extern "C" const char* stfd_strerror(int code) {
 
 extern "C" int stfd_version(void) { return 1; }
 
+extern "C" int stfd_device_status(void) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return STFD_ERR_CUDA;
+  int flag = 0;
+  if (tc_status_read_and_clear(&flag) != 0) return STFD_ERR_CUDA;
+  return flag ? STFD_ERR_TIMEOUT : STFD_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Preconditioner
 // ---------------------------------------------------------------------------
@@ -142,6 +156,14 @@ extern "C" void stfd_fd_destroy(stfd_fd* h) {
   dev_free(h->g);
   dev_free(h->Sinv);
   dev_free(h->work);
+  for (int l = 0; l <= kMaxDim; ++l) {
+    dev_free(h->Bf[l]);
+    dev_free(h->Bb[l]);
+  }
+  for (int l = 0; l < kMaxDim; ++l) dev_free(h->lam_f[l]);
+  dev_free(h->lamt_f);
+  dev_free(h->g_f);
+  dev_free(h->Sinv_f);
   delete h;
 }
 
@@ -152,7 +174,10 @@ extern "C" int stfd_fd_setup(stfd_fd** out, int d, const int* n, const double* c
   *out = nullptr;
   if (!sizes_ok(d, n) || !K || !M || !Wt || !Mt) return STFD_ERR_ARG;
   if (!(gamma > 0.0) || !(nu > 0.0) || !std::isfinite(gamma) || !std::isfinite(nu)) return STFD_ERR_ARG;
-  if (precision != STFD_FP64) return STFD_ERR_ARG;
+  if (precision != STFD_FP64 && precision != STFD_TF32 && precision != STFD_BF16) return STFD_ERR_ARG;
+  if (precision != STFD_FP64)
+    for (int l = 0; l <= d; ++l)
+      if (n[l] > 128) return STFD_ERR_ARG;   // factor + tile + staging must fit in shared memory
   HostFactors f;
   int rc = factorize_host(d, n, K, M, Wt, Mt, f);
   if (rc != STFD_OK) return rc;
@@ -209,6 +234,36 @@ extern "C" int stfd_fd_setup(stfd_fd** out, int d, const int* n, const double* c
   if (rc == STFD_OK && f.n_pairs > 0) rc = dev_upload(&h->lamt, f.lamt.data(), f.lamt.size(), st);
   if (rc == STFD_OK) rc = dev_upload(&h->g, f.g.data(), f.g.size(), st);
   if (rc == STFD_OK) rc = dev_upload<double>(&h->work, nullptr, (size_t)h->N, st);
+  // low precision: operand images and FP32 copies (kept alive in `keep` until the sync)
+  std::vector<std::vector<float>> keepf;
+  std::vector<std::vector<unsigned char>> keepb;
+  if (rc == STFD_OK && precision != STFD_FP64) {
+    const int kind = precision == STFD_BF16 ? 0 : 1;
+    for (int l = 0; l <= d && rc == STFD_OK; ++l) {
+      // keep[2l] is row-major U^T (= column-major U), keep[2l+1] row-major U
+      keepb.push_back(tc_operand_image(keep[2 * l].data(), n[l], kind));
+      rc = dev_upload(&h->Bf[l], keepb.back().data(), keepb.back().size(), st);
+      if (rc != STFD_OK) break;
+      keepb.push_back(tc_operand_image(keep[2 * l + 1].data(), n[l], kind));
+      rc = dev_upload(&h->Bb[l], keepb.back().data(), keepb.back().size(), st);
+      if (rc == STFD_OK && l < d) {
+        keepf.emplace_back(f.lam[l].begin(), f.lam[l].end());
+        rc = dev_upload(&h->lam_f[l], keepf.back().data(), keepf.back().size(), st);
+      }
+    }
+    if (rc == STFD_OK && f.n_pairs > 0) {
+      keepf.emplace_back(f.lamt.begin(), f.lamt.end());
+      rc = dev_upload(&h->lamt_f, keepf.back().data(), keepf.back().size(), st);
+    }
+    if (rc == STFD_OK) {
+      keepf.emplace_back(f.g.begin(), f.g.end());
+      rc = dev_upload(&h->g_f, keepf.back().data(), keepf.back().size(), st);
+    }
+    if (rc == STFD_OK) {
+      keepf.emplace_back(Sinv.begin(), Sinv.end());
+      rc = dev_upload(&h->Sinv_f, keepf.back().data(), keepf.back().size(), st);
+    }
+  }
   if (rc == STFD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = STFD_ERR_CUDA;
   if (rc != STFD_OK) {
     stfd_fd_destroy(h);
@@ -229,8 +284,51 @@ extern "C" int stfd_fd_shape(const stfd_fd* h, int* d_out, int* n, long long* N_
 
 namespace {
 
+// Low-precision Algorithm 1: tensor-core mode products with FP32 intermediates
+// held in the handle's scratch (two FP32 N-vectors in the FP64 work buffer).
+int fd_apply_one_lowp(const stfd_fd* h, const double* r, double* s, double* work, cudaStream_t st) {
+  const int d = h->d;
+  const int kind = h->precision == STFD_BF16 ? 0 : 1;
+  float* buf[2] = {reinterpret_cast<float*>(work), reinterpret_cast<float*>(work) + h->N};
+  int cur = -1;   // -1: the FP64 input r
+  long long inner = 1;
+  for (int l = 0; l <= d; ++l) {
+    const long long outer = h->N / (inner * h->n[l]);
+    const int dst = (cur == 0) ? 1 : 0;
+    const void* X = cur < 0 ? static_cast<const void*>(r) : static_cast<const void*>(buf[cur]);
+    STFD_CU(launch_tc_mode(kind, X, cur < 0 ? 1 : 0, buf[dst], 0, h->Bf[l], h->n[l], inner, outer, st));
+    cur = dst;
+    inner *= h->n[l];
+  }
+  ArrowParamsT<float> ap;
+  ap.d = d;
+  ap.n1 = h->n[0];
+  ap.n2 = d >= 2 ? h->n[1] : 1;
+  ap.nt = h->n[d];
+  ap.n_pairs = h->n_pairs;
+  ap.has_zero = h->has_zero;
+  ap.Ns = h->Ns;
+  for (int l = 0; l < 3; ++l) ap.lam[l] = l < d ? h->lam_f[l] : nullptr;
+  ap.lamt = h->lamt_f;
+  ap.g = h->g_f;
+  ap.Sinv = h->Sinv_f;
+  ap.gamma = (float)h->gamma;
+  ap.nu = (float)h->nu;
+  STFD_CU(launch_arrowhead_fp32(buf[cur], ap, st));
+  for (int l = d; l >= 0; --l) {
+    inner /= h->n[l];
+    const long long outer = h->N / (inner * h->n[l]);
+    const int dst = (cur == 0) ? 1 : 0;
+    void* Y = (l == 0) ? static_cast<void*>(s) : static_cast<void*>(buf[dst]);
+    STFD_CU(launch_tc_mode(kind, buf[cur], 0, Y, l == 0 ? 1 : 0, h->Bb[l], h->n[l], inner, outer, st));
+    cur = dst;
+  }
+  return STFD_OK;
+}
+
 // One right-hand side: s = P^{-1} r through 2(d+1) mode products and Step 3.
 int fd_apply_one(const stfd_fd* h, const double* r, double* s, double* work, cudaStream_t st) {
+  if (h->precision != STFD_FP64) return fd_apply_one_lowp(h, r, s, work, st);
   const int d = h->d;
   const int P = 2 * (d + 1);
   auto buf = [&](int k) { return ((P - k) % 2 == 0) ? s : work; };   // pass k writes buf(k), buf(P) = s

@@ -62,43 +62,44 @@ k_mode_fp64(const double* __restrict__ X1, const double* __restrict__ J1, double
 //  pairs j:  H_j = [[a, b_j], [-b_j, a]], b_j = gamma lam_j, B_j = gamma [g_2j; g_2j+1]
 //  zero block (if any): H = a, B = gamma g_z;   last: H_n = gamma sigma + a
 //  y_n = x_n + sum_j B_j^T H_j^{-1} x_j,  q_n = y_n / S_k,  q_j = H_j^{-1} (x_j - B_j q_n).
-__global__ void k_arrowhead_fp64(double* __restrict__ X, ArrowParams p) {
+template <typename T>
+__global__ void k_arrowhead(T* __restrict__ X, ArrowParamsT<T> p) {
   const long long Ns = p.Ns;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < Ns;
        k += (long long)gridDim.x * blockDim.x) {
     long long rest = k;
     const int i1 = (int)(rest % p.n1);
     rest /= p.n1;
-    double mu = p.lam[0][i1];
+    T mu = p.lam[0][i1];
     if (p.d >= 2) {
       const int i2 = (int)(rest % p.n2);
       rest /= p.n2;
       mu += p.lam[1][i2];
     }
     if (p.d >= 3) mu += p.lam[2][rest];
-    const double a = p.nu * mu;
-    const double gam = p.gamma;
-    double y = X[(long long)(p.nt - 1) * Ns + k];
+    const T a = p.nu * mu;
+    const T gam = p.gamma;
+    T y = X[(long long)(p.nt - 1) * Ns + k];
     for (int j = 0; j < p.n_pairs; ++j) {
-      const double x1 = X[(long long)(2 * j) * Ns + k], x2 = X[(long long)(2 * j + 1) * Ns + k];
-      const double b = gam * p.lamt[j];
-      const double inv = 1.0 / fma(a, a, b * b);
-      const double h1 = (a * x1 - b * x2) * inv, h2 = (b * x1 + a * x2) * inv;
+      const T x1 = X[(long long)(2 * j) * Ns + k], x2 = X[(long long)(2 * j + 1) * Ns + k];
+      const T b = gam * p.lamt[j];
+      const T inv = T(1) / fma(a, a, b * b);
+      const T h1 = (a * x1 - b * x2) * inv, h2 = (b * x1 + a * x2) * inv;
       y = fma(gam, fma(p.g[2 * j], h1, p.g[2 * j + 1] * h2), y);
     }
     const int z = 2 * p.n_pairs;
-    double x0 = 0.0;
+    T x0 = 0.0;
     if (p.has_zero) {
       x0 = X[(long long)z * Ns + k];
       y = fma(gam * p.g[z], x0 / a, y);
     }
-    const double qn = y * p.Sinv[k];
+    const T qn = y * p.Sinv[k];
     X[(long long)(p.nt - 1) * Ns + k] = qn;
     for (int j = 0; j < p.n_pairs; ++j) {
       const long long o1 = (long long)(2 * j) * Ns + k, o2 = (long long)(2 * j + 1) * Ns + k;
-      const double b = gam * p.lamt[j];
-      const double inv = 1.0 / fma(a, a, b * b);
-      const double r1 = X[o1] - gam * p.g[2 * j] * qn, r2 = X[o2] - gam * p.g[2 * j + 1] * qn;
+      const T b = gam * p.lamt[j];
+      const T inv = T(1) / fma(a, a, b * b);
+      const T r1 = X[o1] - gam * p.g[2 * j] * qn, r2 = X[o2] - gam * p.g[2 * j + 1] * qn;
       X[o1] = (a * r1 - b * r2) * inv;
       X[o2] = (b * r1 + a * r2) * inv;
     }
@@ -239,7 +240,14 @@ cudaError_t launch_band_mode_fp64(const double* X1, const double* J1, double s1,
 cudaError_t launch_arrowhead_fp64(double* X, const ArrowParams& p, cudaStream_t st) {
   if (p.Ns <= 0) return cudaSuccess;
   ProfScope ps("arrowhead_fp64", (double)p.Ns * (10.0 * p.n_pairs + 4.0), 16.0 * (double)p.Ns * p.nt, st);
-  k_arrowhead_fp64<<<grid_for(p.Ns, 256), 256, 0, st>>>(X, p);
+  k_arrowhead<double><<<grid_for(p.Ns, 256), 256, 0, st>>>(X, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_arrowhead_fp32(float* X, const ArrowParamsT<float>& p, cudaStream_t st) {
+  if (p.Ns <= 0) return cudaSuccess;
+  ProfScope ps("arrowhead_fp32", (double)p.Ns * (10.0 * p.n_pairs + 4.0), 8.0 * (double)p.Ns * p.nt, st);
+  k_arrowhead<float><<<grid_for(p.Ns, 256), 256, 0, st>>>(X, p);
   return cudaGetLastError();
 }
 

@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 namespace stfd {
 
 // Mode product of Algorithm 1 (dense n x n factor):
@@ -21,16 +23,30 @@ cudaError_t launch_band_mode_fp64(const double* X1, const double* J1, double s1,
 
 // In-place Step 3 of Algorithm 1 on the spectral tensor X[t][k] (time index
 // slowest): block LU of the real arrowhead system per spatial index k.
-struct ArrowParams {
+template <typename T>
+struct ArrowParamsT {
   int d, n1, n2, nt, n_pairs, has_zero;
   long long Ns;
-  const double* lam[3];   // spatial eigenvalues per direction
-  const double* lamt;     // n_pairs
-  const double* g;        // nt - 1
-  const double* Sinv;     // Ns reciprocals of the Schur complement
-  double gamma, nu;
+  const T* lam[3];   // spatial eigenvalues per direction
+  const T* lamt;     // n_pairs
+  const T* g;        // nt - 1
+  const T* Sinv;     // Ns reciprocals of the Schur complement
+  T gamma, nu;
 };
+using ArrowParams = ArrowParamsT<double>;
 cudaError_t launch_arrowhead_fp64(double* X, const ArrowParams& p, cudaStream_t st);
+// FP32 variant for the mixed-precision preconditioner
+cudaError_t launch_arrowhead_fp32(float* X, const ArrowParamsT<float>& p, cudaStream_t st);
+
+// tcgen05 mode product with BF16 (kind 0) or TF32 (kind 1) operands and FP32
+// accumulation: Y[o, i, c] = sum_a J[i, a] X[o, a, c]. X is FP64 or FP32, Y FP32 or
+// FP64 (not both FP64). B is the factor image from tc_operand_image (device).
+cudaError_t launch_tc_mode(int kind, const void* X, int x_is_double, void* Y, int y_is_double,
+                           const unsigned char* B, int n, long long inner, long long outer, cudaStream_t st);
+// Host: factor J (row-major n x n, J[i*n + a]) as a K-major canonical operand image.
+std::vector<unsigned char> tc_operand_image(const double* J, int n, int kind);
+// Host: read and clear the device flag set when a bounded tensor-core wait gives up.
+int tc_status_read_and_clear(int* status);
 
 // GMRES BLAS: partial[b*m + i] = sum over block b's range of V_i[k] * w[k].
 cudaError_t launch_dot_multi(const double* const* V, int m, const double* w, long long N,

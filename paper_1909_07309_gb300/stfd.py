@@ -15,7 +15,7 @@ from . import build as _build
 
 STFD_OK = 0
 STFD_NOT_CONVERGED = 1
-STFD_FP64 = 0
+STFD_FP64, STFD_TF32, STFD_BF16 = 0, 1, 2
 STFD_BC_NONE, STFD_BC_INITIAL, STFD_BC_DIRICHLET = 0, 1, 2
 STFD_NOALLOC_MAX_N = 524288
 
@@ -45,6 +45,7 @@ class GmresInfo(ctypes.Structure):
 SIGNATURES = {
     "stfd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "stfd_version": (ctypes.c_int, []),
+    "stfd_device_status": (ctypes.c_int, []),
     "stfd_spline_matrices": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_int_p]),
     "stfd_spline_load_trig": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
