@@ -33,9 +33,9 @@ METRIC = "fd_apply dofs/s and GMRES time-to-1e-8 residual, FP64 vs TF32/BF16-pre
 UNIT = "dofs/s"
 L2_BYTES = 129 * 2 ** 20
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture
-# (profiles/fd_mode_fp64_unit_cube_p3_nel64.txt); None until captured for the current kernel.
-NCU_TRAFFIC = {"kernel": "fd_mode_fp64", "bytes_per_launch": 238.1e6}
+# DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/);
+# None until captured for the current kernel.
+NCU_TRAFFIC = {"kernel": "fd_mode_df", "bytes_per_launch": None}
 
 
 def measured_peaks():
@@ -197,8 +197,11 @@ def main():
 
     cfg = inputs.SCALE
     K, M, Wt, Mt, f_np = build_workload(cfg)
-    A = stfd.KronOp(K, M, Wt, Mt, cfg["gamma"], cfg["nu"])
-    P = stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"])
+    t_setup = time.perf_counter()
+    # FP64-accurate solve: double-float Algorithm 1 and double-float matvec (FP32 pipes)
+    A = stfd.KronOp(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], arith=stfd.STFD_OP_DF32)
+    P = stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=stfd.STFD_DF32)
+    setup_ms = (time.perf_counter() - t_setup) * 1e3
     N = P.N
     f = torch.from_numpy(f_np).cuda()
     u = torch.empty_like(f)
@@ -277,10 +280,12 @@ def main():
     mv_ms = e0.elapsed_time(e1) / args.steps
     resid = float(torch.linalg.norm(y - r) / torch.linalg.norm(r))
 
-    # ---- mixed-precision preconditioners inside the same FP64 flexible GMRES
+    # ---- preconditioner variants inside the same FP64 flexible GMRES
     variants = {}
-    for name, prec in (("fp64", stfd.STFD_FP64), ("tf32", stfd.STFD_TF32), ("bf16", stfd.STFD_BF16)):
-        Pv = P if prec == stfd.STFD_FP64 else stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=prec)
+    A64 = stfd.KronOp(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], arith=stfd.STFD_OP_FP64)
+    for name, prec, op in (("df32", stfd.STFD_DF32, A), ("fp64_ieee", stfd.STFD_FP64, A64),
+                           ("tf32", stfd.STFD_TF32, A), ("bf16", stfd.STFD_BF16, A)):
+        Pv = P if prec == stfd.STFD_DF32 else stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=prec)
         for _ in range(3):
             Pv.apply(r, s)
         torch.cuda.synchronize()
@@ -292,20 +297,22 @@ def main():
         v_fd = e0.elapsed_time(e1) / args.steps
         s_v = s.clone()
         for _ in range(args.warmup):
-            A.gmres(Pv, f, u, tol=1e-8, restart=args.restart)
+            op.gmres(Pv, f, u, tol=1e-8, restart=args.restart)
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
-            _, vinfo = A.gmres(Pv, f, u, tol=1e-8, restart=args.restart)
+            _, vinfo = op.gmres(Pv, f, u, tol=1e-8, restart=args.restart)
         e1.record(stream)
         torch.cuda.synchronize()
         v_gm = e0.elapsed_time(e1) / args.steps
-        variants[name] = {"fd_apply_ms": v_fd, "fd_apply_dofs_per_s": N / (v_fd * 1e-3), "gmres_ms": v_gm,
+        variants[name] = {"precond": name, "matvec": "fp64_ieee" if op is A64 else "df32",
+                          "fd_apply_ms": v_fd, "fd_apply_dofs_per_s": N / (v_fd * 1e-3), "gmres_ms": v_gm,
                           "gmres_iters": vinfo["iters"], "rel_res_true": vinfo["rel_res_true"], "_s": s_v}
         if Pv is not P:
             Pv.close()
-    ref_s = variants["fp64"].pop("_s")
-    for name in ("tf32", "bf16"):
+    A64.close()
+    ref_s = variants["fp64_ieee"]["_s"]
+    for name in variants:
         sv = variants[name].pop("_s")
         variants[name]["fd_apply_rel_err_vs_fp64"] = float(torch.linalg.norm(sv - ref_s) / torch.linalg.norm(ref_s))
     if stfd.load().stfd_device_status() != 0:
@@ -323,30 +330,37 @@ def main():
     total_ms = sum(rc["ms"] for rc in recs) or 1.0
     top = max(recs, key=lambda rc: rc["ms"])
     probe = stfd.stfd_probe_fp64_peak()
-    # FP64 peak from unit counts and clocks: 2 DFMA per clock per SM (the nominal
-    # 1.25 TFLOP/s at 152 SMs and 2070 MHz), at the median SM clock sampled in the timed region.
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
     mhz = clocks.get("sm_mhz") or 2070.0
-    fp64_peak = 2 * 2 * sms * mhz * 1e6
     per_launch_s = top["ms"] * 1e-3 / top["launches"]
     achieved = top["flops"] / top["launches"] / per_launch_s
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["kernel"] == top["name"] else None
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": traffic, "kernel": top["name"],
-                "peak_source": "FP64: 2 DFMA/clk/SM x %d SMs x %.0f MHz (sampled); DFMA probe in this run %.3f TFLOP/s"
-                               % (sms, mhz, probe / 1e12),
+    if top["name"].endswith("_df"):
+        # double-float kernels issue 12 FP32 instructions per FP64-equivalent FMA
+        # (2 flop): peak = 128 FP32 lanes x SMs x clock x 2 / 12
+        peak = 128 * sms * mhz * 1e6 * 2 / 12
+        src = "FP32 pipes: 128 lanes/SM x %d SMs x %.0f MHz (sampled) / 12 FP32 ops per double-float FMA" % (sms, mhz)
+    else:
+        peak = 2 * 2 * sms * mhz * 1e6
+        src = "FP64: 2 DFMA/clk/SM x %d SMs x %.0f MHz (sampled); DFMA probe in this run %.3f TFLOP/s" % (
+            sms, mhz, probe / 1e12)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": top["name"], "peak_source": src,
                 "achieved_gbs": top["bytes"] / top["launches"] / per_launch_s / 1e9,
-                "share_of_step": top["ms"] / total_ms}
+                "share_of_step": top["ms"] / total_ms, "fp64_probe_tflops": probe / 1e12}
     kernels = {rc["name"]: {"launches": rc["launches"], "ms": round(rc["ms"], 3),
                             "share": round(rc["ms"] / total_ms, 4)} for rc in recs}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "df32", "data": "synthetic",
         "config": {"workload": cfg["name"], "N": N, "solve": "FD-preconditioned flexible GMRES to 1e-8, x0 = 0",
                    "restart": args.restart, "gmres_iters": infos[-1]["iters"],
-                   "rel_res_true": infos[-1]["rel_res_true"], "precond": "FP64",
+                   "rel_res_true": infos[-1]["rel_res_true"],
+                   "precond": "Algorithm 1 in double-float (2 x FP32, ~48-bit) arithmetic, FP64 in/out",
+                   "matvec": "double-float (2 x FP32, ~48-bit), FP64 in/out", "gmres": "FP64",
+                   "setup_ms": setup_ms,
                    "l2": "inputs larger than L2 (working set %.2f GB > 129 MB)" % (10 * N * 8 / 1e9),
                    "parallelism": "replicas x%d" % world},
         "fd_apply": {"ms": fd_ms, "dofs_per_s": N / (fd_ms * 1e-3)},

@@ -55,7 +55,11 @@ enum {
  * FP32 intermediates and an FP32 Step 3; input and output vectors stay FP64.
  * The low-precision preconditioner is meant for flexible GMRES, which keeps
  * the outer iteration, the system matvec and the residual in FP64. */
-enum { STFD_FP64 = 0, STFD_TF32 = 1, STFD_BF16 = 2 };
+enum { STFD_FP64 = 0, STFD_TF32 = 1, STFD_BF16 = 2, STFD_DF32 = 3 };
+/* STFD_DF32: FP64-accurate Algorithm 1 in double-float arithmetic on the FP32
+ * pipes (every value an unevaluated pair hi + lo of floats, about 48
+ * significant bits; products split exactly by FMA, sums by error-free
+ * two-sum); FP64 input and output, agrees with STFD_FP64 to about 1e-13. */
 
 /* Boundary treatment of a univariate basis (Sec. 2.2). */
 enum {
@@ -147,13 +151,21 @@ void stfd_fd_destroy(stfd_fd* h);
  * banded univariate factors (bandwidth 2p+1 is detected from the entries;
  * any dense factor works, only slower). Same size limits as stfd_fd_setup.
  * The factors are uploaded on `stream`, which is synchronised.
+ * `arith` selects the arithmetic of the banded products:
+ *   STFD_OP_FP64  FP64 fused multiply-adds (IEEE double throughout);
+ *   STFD_OP_DF32  double-float on the FP32 pipes: every value is an unevaluated
+ *                 pair hi + lo of floats (about 48 significant bits), products
+ *                 split exactly by FMA, sums by error-free two-sum; FP64 input
+ *                 and output. Agrees with STFD_OP_FP64 to about 1e-14 relative
+ *                 and is several times faster on GPUs with low FP64 throughput.
  * ------------------------------------------------------------------------ */
 typedef struct stfd_op stfd_op;
+enum { STFD_OP_FP64 = 0, STFD_OP_DF32 = 1 };
 
 int stfd_op_create_kron(stfd_op** out, int d, const int* n,
                         const double* const* K, const double* const* M,
                         const double* Wt, const double* Mt,
-                        double gamma, double nu, void* stream);
+                        double gamma, double nu, int arith, void* stream);
 
 /* y_dev = A x_dev for nrhs vectors (matrix-free, sum-factorised through eq.
  * kron_vec_multi: 3d+1 banded mode products). x_dev and y_dev may not

@@ -87,6 +87,14 @@ struct stfd_fd {
   float* lamt_f = nullptr;
   float* g_f = nullptr;
   float* Sinv_f = nullptr;
+  // double-float path (STFD_DF32): (hi, lo) factors and arrowhead data
+  float2* Jf2[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};
+  float2* Jb2[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};
+  float2* lam2[kMaxDim] = {nullptr, nullptr, nullptr};
+  float2* B2 = nullptr;
+  float2* BB2 = nullptr;
+  float2* G2 = nullptr;
+  float2* Sinv2 = nullptr;
 };
 
 struct GmresWork {
@@ -114,6 +122,12 @@ struct stfd_op {
   int bwW = 0, bwMt = 0;
   double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
   GmresWork* gw = nullptr;
+  int arith = STFD_OP_FP64;
+  // double-float factors (hi, lo) for STFD_OP_DF32
+  float2* JM2[kMaxDim] = {nullptr, nullptr, nullptr};
+  float2* JK2[kMaxDim] = {nullptr, nullptr, nullptr};
+  float2* JW2 = nullptr;
+  float2* JMt2 = nullptr;
 };
 
 extern "C" const char* stfd_strerror(int code) {
@@ -164,6 +178,15 @@ extern "C" void stfd_fd_destroy(stfd_fd* h) {
   dev_free(h->lamt_f);
   dev_free(h->g_f);
   dev_free(h->Sinv_f);
+  for (int l = 0; l <= kMaxDim; ++l) {
+    dev_free(h->Jf2[l]);
+    dev_free(h->Jb2[l]);
+  }
+  for (int l = 0; l < kMaxDim; ++l) dev_free(h->lam2[l]);
+  dev_free(h->B2);
+  dev_free(h->BB2);
+  dev_free(h->G2);
+  dev_free(h->Sinv2);
   delete h;
 }
 
@@ -174,8 +197,9 @@ extern "C" int stfd_fd_setup(stfd_fd** out, int d, const int* n, const double* c
   *out = nullptr;
   if (!sizes_ok(d, n) || !K || !M || !Wt || !Mt) return STFD_ERR_ARG;
   if (!(gamma > 0.0) || !(nu > 0.0) || !std::isfinite(gamma) || !std::isfinite(nu)) return STFD_ERR_ARG;
-  if (precision != STFD_FP64 && precision != STFD_TF32 && precision != STFD_BF16) return STFD_ERR_ARG;
-  if (precision != STFD_FP64)
+  if (precision != STFD_FP64 && precision != STFD_TF32 && precision != STFD_BF16 && precision != STFD_DF32)
+    return STFD_ERR_ARG;
+  if (precision == STFD_TF32 || precision == STFD_BF16)
     for (int l = 0; l <= d; ++l)
       if (n[l] > 128) return STFD_ERR_ARG;   // factor + tile + staging must fit in shared memory
   HostFactors f;
@@ -237,7 +261,33 @@ extern "C" int stfd_fd_setup(stfd_fd** out, int d, const int* n, const double* c
   // low precision: operand images and FP32 copies (kept alive in `keep` until the sync)
   std::vector<std::vector<float>> keepf;
   std::vector<std::vector<unsigned char>> keepb;
-  if (rc == STFD_OK && precision != STFD_FP64) {
+  std::vector<std::vector<float2>> keep2;
+  auto up2 = [&](const double* v, size_t cnt, float2** dst) {
+    keep2.emplace_back(cnt);
+    for (size_t k = 0; k < cnt; ++k) {
+      const float hh = (float)v[k];
+      keep2.back()[k] = make_float2(hh, (float)(v[k] - (double)hh));
+    }
+    return dev_upload(dst, keep2.back().data(), cnt, st);
+  };
+  if (rc == STFD_OK && precision == STFD_DF32) {
+    for (int l = 0; l <= d && rc == STFD_OK; ++l) {
+      rc = up2(keep[2 * l].data(), keep[2 * l].size(), &h->Jf2[l]);
+      if (rc == STFD_OK) rc = up2(keep[2 * l + 1].data(), keep[2 * l + 1].size(), &h->Jb2[l]);
+      if (rc == STFD_OK && l < d) rc = up2(f.lam[l].data(), f.lam[l].size(), &h->lam2[l]);
+    }
+    std::vector<double> B(std::max(1, f.n_pairs)), BB(std::max(1, f.n_pairs)), G(f.g.size());
+    for (int j = 0; j < f.n_pairs; ++j) {
+      B[j] = gamma * f.lamt[j];
+      BB[j] = B[j] * B[j];
+    }
+    for (size_t j = 0; j < f.g.size(); ++j) G[j] = gamma * f.g[j];
+    if (rc == STFD_OK) rc = up2(B.data(), B.size(), &h->B2);
+    if (rc == STFD_OK) rc = up2(BB.data(), BB.size(), &h->BB2);
+    if (rc == STFD_OK) rc = up2(G.data(), G.size(), &h->G2);
+    if (rc == STFD_OK) rc = up2(Sinv.data(), Sinv.size(), &h->Sinv2);
+  }
+  if (rc == STFD_OK && (precision == STFD_TF32 || precision == STFD_BF16)) {
     const int kind = precision == STFD_BF16 ? 0 : 1;
     for (int l = 0; l <= d && rc == STFD_OK; ++l) {
       // keep[2l] is row-major U^T (= column-major U), keep[2l+1] row-major U
@@ -326,8 +376,39 @@ int fd_apply_one_lowp(const stfd_fd* h, const double* r, double* s, double* work
   return STFD_OK;
 }
 
+// Double-float Algorithm 1: same pass structure as the FP64 path, intermediates
+// stored as float2 in the scratch and output buffers.
+int fd_apply_one_df(const stfd_fd* h, const double* r, double* s, double* work, cudaStream_t st) {
+  const int d = h->d;
+  const int P = 2 * (d + 1);
+  auto buf = [&](int k) { return ((P - k) % 2 == 0) ? static_cast<void*>(s) : static_cast<void*>(work); };
+  const void* src = r;
+  int pass = 0;
+  long long inner = 1;
+  for (int l = 0; l <= d; ++l) {
+    const long long outer = h->N / (inner * h->n[l]);
+    void* dst = buf(++pass);
+    STFD_CU(launch_fd_mode_df(src, pass == 1 ? 1 : 0, h->Jf2[l], dst, 0, h->n[l], inner, outer, st));
+    src = dst;
+    inner *= h->n[l];
+  }
+  const float2* lam[3] = {h->lam2[0], h->lam2[1], h->lam2[2]};
+  STFD_CU(launch_arrowhead_df(static_cast<float2*>(const_cast<void*>(src)), d, h->n[0], d >= 2 ? h->n[1] : 1,
+                              h->n[d], h->n_pairs, h->has_zero, h->Ns, lam, h->B2, h->BB2, h->G2, h->Sinv2, h->nu,
+                              st));
+  for (int l = d; l >= 0; --l) {
+    inner /= h->n[l];
+    const long long outer = h->N / (inner * h->n[l]);
+    void* dst = buf(++pass);
+    STFD_CU(launch_fd_mode_df(src, 0, h->Jb2[l], dst, pass == P ? 1 : 0, h->n[l], inner, outer, st));
+    src = dst;
+  }
+  return STFD_OK;
+}
+
 // One right-hand side: s = P^{-1} r through 2(d+1) mode products and Step 3.
 int fd_apply_one(const stfd_fd* h, const double* r, double* s, double* work, cudaStream_t st) {
+  if (h->precision == STFD_DF32) return fd_apply_one_df(h, r, s, work, st);
   if (h->precision != STFD_FP64) return fd_apply_one_lowp(h, r, s, work, st);
   const int d = h->d;
   const int P = 2 * (d + 1);
@@ -407,6 +488,12 @@ extern "C" void stfd_op_destroy(stfd_op* A) {
   }
   dev_free(A->JW);
   dev_free(A->JMt);
+  for (int l = 0; l < kMaxDim; ++l) {
+    dev_free(A->JM2[l]);
+    dev_free(A->JK2[l]);
+  }
+  dev_free(A->JW2);
+  dev_free(A->JMt2);
   for (int k = 0; k < 4; ++k) dev_free(A->tmp[k]);
   gmres_free(A->gw);
   delete A;
@@ -414,13 +501,14 @@ extern "C" void stfd_op_destroy(stfd_op* A) {
 
 extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const double* const* K,
                                    const double* const* M, const double* Wt, const double* Mt,
-                                   double gamma, double nu, void* stream) {
+                                   double gamma, double nu, int arith, void* stream) {
   if (!out) return STFD_ERR_ARG;
   *out = nullptr;
   if (!sizes_ok(d, n) || !K || !M || !Wt || !Mt) return STFD_ERR_ARG;
   for (int l = 0; l < d; ++l)
     if (!K[l] || !M[l]) return STFD_ERR_ARG;
   if (!std::isfinite(gamma) || !std::isfinite(nu)) return STFD_ERR_ARG;
+  if (arith != STFD_OP_FP64 && arith != STFD_OP_DF32) return STFD_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   stfd_op* A = new (std::nothrow) stfd_op;
   if (!A) return STFD_ERR_ALLOC;
@@ -432,6 +520,7 @@ extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const dou
   }
   A->gamma = gamma;
   A->nu = nu;
+  A->arith = arith;
   int rc = STFD_OK;
   std::vector<std::vector<double>> keep;
   for (int l = 0; l < d && rc == STFD_OK; ++l) {
@@ -454,6 +543,24 @@ extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const dou
     A->bwMt = bandwidth(n[d], Mt);
   }
   for (int k = 0; k < 4 && rc == STFD_OK; ++k) rc = dev_upload<double>(&A->tmp[k], nullptr, (size_t)A->N, st);
+  // double-float copies (hi, lo) of the row-major factors: keep = [M_0, K_0, M_1, K_1, ..., W_t, M_t]
+  std::vector<std::vector<float2>> keep2;
+  if (rc == STFD_OK && arith == STFD_OP_DF32) {
+    auto split = [&](const std::vector<double>& J, float2** dst) {
+      keep2.emplace_back(J.size());
+      for (size_t k = 0; k < J.size(); ++k) {
+        const float h = (float)J[k];
+        keep2.back()[k] = make_float2(h, (float)(J[k] - (double)h));
+      }
+      return dev_upload(dst, keep2.back().data(), keep2.back().size(), st);
+    };
+    for (int l = 0; l < d && rc == STFD_OK; ++l) {
+      rc = split(keep[2 * l], &A->JM2[l]);
+      if (rc == STFD_OK) rc = split(keep[2 * l + 1], &A->JK2[l]);
+    }
+    if (rc == STFD_OK) rc = split(keep[2 * d], &A->JW2);
+    if (rc == STFD_OK) rc = split(keep[2 * d + 1], &A->JMt2);
+  }
   if (rc == STFD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = STFD_ERR_CUDA;
   if (rc != STFD_OK) {
     stfd_op_destroy(A);
@@ -468,7 +575,37 @@ namespace {
 // y = gamma (W_t x M_d x..x M_1) x + nu (M_t x sum_l M_d..K_l..M_1) x, sum-factorised:
 // direction 1: (u, v) = (x x_1 M_1, x x_1 K_1); direction l > 1:
 // (u, v) <- (u x_l M_l, u x_l K_l + v x_l M_l); time: y = gamma u x W_t + nu v x M_t.
+// Same sum-factorisation in double-float arithmetic, one pass per direction;
+// intermediates are float2 (hi, lo) pairs.
+int matvec_one_df(const stfd_op* A, const double* x, double* y, cudaStream_t st) {
+  const int d = A->d;
+  float2* T[4];
+  for (int k = 0; k < 4; ++k) T[k] = reinterpret_cast<float2*>(A->tmp[k]);
+  long long inner = 1;
+  const float2* u = nullptr;
+  const float2* v = nullptr;
+  for (int l = 0; l < d; ++l) {
+    const int nl = A->n[l];
+    const long long outer = A->N / (inner * nl);
+    float2* uo = (l % 2 == 0) ? T[0] : T[2];
+    float2* vo = (l % 2 == 0) ? T[1] : T[3];
+    const int bw = std::max(A->bwM[l], A->bwK[l]);
+    if (l == 0) {
+      STFD_CU(launch_band_first_df(x, A->JM2[l], A->JK2[l], uo, vo, nl, inner, outer, bw, st));
+    } else {
+      STFD_CU(launch_band_mid_df(u, v, A->JM2[l], A->JK2[l], uo, vo, nl, inner, outer, bw, st));
+    }
+    u = uo;
+    v = vo;
+    inner *= nl;
+  }
+  const int nt = A->n[d];
+  STFD_CU(launch_band_last_df(u, v, A->JW2, A->gamma, A->JMt2, A->nu, y, nt, inner, 1, std::max(A->bwW, A->bwMt), st));
+  return STFD_OK;
+}
+
 int matvec_one(const stfd_op* A, const double* x, double* y, cudaStream_t st) {
+  if (A->arith == STFD_OP_DF32) return matvec_one_df(A, x, y, st);
   const int d = A->d;
   double* const* T = A->tmp;
   long long inner = 1;

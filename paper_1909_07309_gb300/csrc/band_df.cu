@@ -1,0 +1,178 @@
+// Banded mode products of the system matvec (eq. syst_mat through eq.
+// kron_vec_multi) in double-float arithmetic on the FP32 pipes.
+//
+// GB300 issues FP64 at about 1/70 of its FP32 rate, so the FP64-accurate
+// matvec keeps every value as an unevaluated sum hi + lo of two floats
+// (about 48 significant bits): products are split exactly with an FMA
+// (two-product), sums are accumulated with Knuth's error-free two-sum, and
+// the low-order parts are summed separately. Intermediate tensors are stored
+// as float2 (8 bytes, the size of a double); the first pass reads FP64 and the
+// last writes FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "kernels.h"
+#include "profile.h"
+
+namespace stfd {
+namespace {
+
+constexpr int kTC = 32;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+struct df {
+  float h, l;
+};
+
+__device__ __forceinline__ df to_df(double x) {
+  const float h = __double2float_rn(x);
+  return df{h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ df to_df(float2 v) { return df{v.x, v.y}; }
+__device__ __forceinline__ double to_double(df a) { return (double)a.h + (double)a.l; }
+
+// acc += b * x, b and x double-floats; the b.l * x.l term (~2^-48 relative) is dropped.
+__device__ __forceinline__ void df_fma(df& acc, float2 b, df x) {
+  const float p = b.x * x.h;
+  const float e = fmaf(b.x, x.h, -p);                  // exact: b.h x.h = p + e
+  const float lo = fmaf(b.x, x.l, fmaf(b.y, x.h, e));
+  const float s = acc.h + p;                           // two-sum(acc.h, p)
+  const float bp = s - acc.h;
+  const float err = (acc.h - (s - bp)) + (p - bp);
+  acc.h = s;
+  acc.l += err + lo;
+}
+
+__device__ __forceinline__ df df_norm(df a) {
+  const float s = a.h + a.l;
+  return df{s, a.l - (s - a.h)};
+}
+
+// a * s with s a double-float scalar
+__device__ __forceinline__ df df_scale(df a, float2 s) {
+  const float p = a.h * s.x;
+  const float e = fmaf(a.h, s.x, -p);
+  const float lo = fmaf(a.h, s.y, fmaf(a.l, s.x, e));
+  return df_norm(df{p, lo});
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  const float s = a.h + b.h;
+  const float bp = s - a.h;
+  const float err = (a.h - (s - bp)) + (b.h - bp);
+  return df_norm(df{s, err + a.l + b.l});
+}
+
+template <typename T>
+__device__ __forceinline__ df load_df(const T* p, long long i);
+template <>
+__device__ __forceinline__ df load_df<double>(const double* p, long long i) { return to_df(p[i]); }
+template <>
+__device__ __forceinline__ df load_df<float2>(const float2* p, long long i) { return to_df(p[i]); }
+
+__device__ __forceinline__ void store_df(double* p, long long i, df v) { p[i] = to_double(v); }
+__device__ __forceinline__ void store_df(float2* p, long long i, df v) { p[i] = make_float2(v.h, v.l); }
+
+// One direction of the sum-factorised matvec in a single pass over the data:
+//   Uo = U x_m A1                         (if TWO_OUT)
+//   Vo = s2 (U x_m A2) + s3 (V x_m A3)    (V term if HAS_V)
+// with |a - i| <= bw. U is FP64 (first direction) or float2, V float2, Vo float2
+// or FP64 (time direction). The three accumulations are independent chains.
+template <typename TIn, typename TOut, bool HAS_V, bool TWO_OUT>
+__global__ void __launch_bounds__(kThreads)
+k_band_pair_df(const TIn* __restrict__ U, const float2* __restrict__ V, const float2* __restrict__ A1,
+               const float2* __restrict__ A2, const float2* __restrict__ A3, float2 s2, float2 s3,
+               float2* __restrict__ Uo, TOut* __restrict__ Vo, int n, long long inner, long long Q, int bw,
+               int scale) {
+  extern __shared__ float2 sm2[];
+  float2* xu = sm2;
+  float2* xv = sm2 + (size_t)n * kTC;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long q = (long long)blockIdx.x * kTC + lane;
+  const bool valid = q < Q;
+  long long base = 0;
+  if (valid) {
+    const long long o = q / inner;
+    base = o * (long long)n * inner + (q - o * inner);
+  }
+  for (int a = warp; a < n; a += kWarps) {
+    const df v = valid ? load_df<TIn>(U, base + (long long)a * inner) : df{0.f, 0.f};
+    xu[a * kTC + lane] = make_float2(v.h, v.l);
+    if (HAS_V) xv[a * kTC + lane] = valid ? V[base + (long long)a * inner] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int i = warp; i < n; i += kWarps) {
+    const int a0 = max(0, i - bw), a1 = min(n - 1, i + bw);
+    const float2* r1 = A1 + (size_t)i * n;
+    const float2* r2 = A2 + (size_t)i * n;
+    const float2* r3 = A3 + (size_t)i * n;
+    df c1{0.f, 0.f}, c2{0.f, 0.f}, c3{0.f, 0.f};
+    for (int a = a0; a <= a1; ++a) {
+      const df xa = to_df(xu[a * kTC + lane]);
+      if (TWO_OUT) df_fma(c1, __ldg(r1 + a), xa);
+      df_fma(c2, __ldg(r2 + a), xa);
+      if (HAS_V) df_fma(c3, __ldg(r3 + a), to_df(xv[a * kTC + lane]));
+    }
+    df vo = df_norm(c2);
+    if (scale) vo = df_scale(vo, s2);
+    if (HAS_V) {
+      df t = df_norm(c3);
+      if (scale) t = df_scale(t, s3);
+      vo = df_add(vo, t);
+    }
+    if (valid) {
+      if (TWO_OUT) store_df(Uo, base + (long long)i * inner, df_norm(c1));
+      store_df(Vo, base + (long long)i * inner, vo);
+    }
+  }
+}
+
+template <typename TIn, typename TOut, bool HAS_V, bool TWO_OUT>
+cudaError_t launch_pair(const TIn* U, const float2* V, const float2* A1, const float2* A2, const float2* A3,
+                        double s2, double s3, float2* Uo, TOut* Vo, int n, long long inner, long long outer, int bw,
+                        cudaStream_t st) {
+  const long long Q = inner * outer;
+  if (Q <= 0) return cudaSuccess;
+  static bool attr_done = false;
+  if (!attr_done) {
+    const cudaError_t e = cudaFuncSetAttribute(k_band_pair_df<TIn, TOut, HAS_V, TWO_OUT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               2 * 256 * kTC * (int)sizeof(float2));
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const size_t smem = (size_t)(HAS_V ? 2 : 1) * n * kTC * sizeof(float2);
+  double entries = 0.0;
+  for (int i = 0; i < n; ++i) entries += (double)(std::min(n - 1, i + bw) - std::max(0, i - bw) + 1);
+  const int nprod = (TWO_OUT ? 1 : 0) + 1 + (HAS_V ? 1 : 0);
+  const int nio = (HAS_V ? 2 : 1) + (TWO_OUT ? 2 : 1);
+  ProfScope ps("band_pair_df", 2.0 * entries * (double)Q * nprod, 8.0 * (double)Q * n * nio, st);
+  const float h2 = (float)s2, h3 = (float)s3;
+  const float2 c2 = make_float2(h2, (float)(s2 - (double)h2)), c3 = make_float2(h3, (float)(s3 - (double)h3));
+  const int scale = (s2 != 1.0 || s3 != 1.0) ? 1 : 0;
+  k_band_pair_df<TIn, TOut, HAS_V, TWO_OUT><<<(unsigned)((Q + kTC - 1) / kTC), kThreads, smem, st>>>(
+      U, V, A1, A2, A3, c2, c3, Uo, Vo, n, inner, Q, bw, scale);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_band_first_df(const double* x, const float2* M, const float2* K, float2* Uo, float2* Vo, int n,
+                                 long long inner, long long outer, int bw, cudaStream_t st) {
+  return launch_pair<double, float2, false, true>(x, nullptr, M, K, nullptr, 1.0, 1.0, Uo, Vo, n, inner, outer, bw, st);
+}
+
+cudaError_t launch_band_mid_df(const float2* u, const float2* v, const float2* M, const float2* K, float2* Uo,
+                               float2* Vo, int n, long long inner, long long outer, int bw, cudaStream_t st) {
+  return launch_pair<float2, float2, true, true>(u, v, M, K, M, 1.0, 1.0, Uo, Vo, n, inner, outer, bw, st);
+}
+
+cudaError_t launch_band_last_df(const float2* u, const float2* v, const float2* W, double gamma, const float2* Mt,
+                                double nu, double* y, int n, long long inner, long long outer, int bw,
+                                cudaStream_t st) {
+  return launch_pair<float2, double, true, false>(u, v, nullptr, W, Mt, gamma, nu, nullptr, y, n, inner, outer, bw, st);
+}
+
+}  // namespace stfd

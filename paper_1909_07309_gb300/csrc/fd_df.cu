@@ -1,0 +1,206 @@
+// Algorithm 1 (Steps 2-4) in double-float arithmetic on the FP32 pipes: the
+// FP64-accurate preconditioner for a GPU whose FP64 pipe is ~1/70 of its FP32
+// rate. Dense mode products (eq. kron_vec_multi with the eigenvector factors)
+// and the real arrowhead block LU (eq. block_LU, 2 x 2 blocks of the Remark in
+// Sec. 4.5) both carry every value as a (hi, lo) float pair.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "df.cuh"
+#include "kernels.h"
+#include "profile.h"
+
+namespace stfd {
+namespace {
+
+using dfa::df;
+
+constexpr int kTC = 32;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kIB = 4;   // output rows per thread and pass (register blocking)
+
+template <typename T>
+__device__ __forceinline__ df ld(const T* p, long long i);
+template <>
+__device__ __forceinline__ df ld<double>(const double* p, long long i) { return dfa::from_double(p[i]); }
+template <>
+__device__ __forceinline__ df ld<float2>(const float2* p, long long i) { return dfa::from_float2(p[i]); }
+__device__ __forceinline__ void st(double* p, long long i, df v) { p[i] = dfa::to_double(v); }
+__device__ __forceinline__ void st(float2* p, long long i, df v) { p[i] = make_float2(v.h, v.l); }
+
+// Y[o, i, c] = sum_a J[i, a] X[o, a, c]; J row-major (hi, lo) pairs.
+template <typename TIn, typename TOut>
+__global__ void __launch_bounds__(kThreads)
+k_mode_df(const TIn* __restrict__ X, const float2* __restrict__ J, TOut* __restrict__ Y, int n, long long inner,
+          long long Q) {
+  extern __shared__ float2 xs[];   // [n][kTC]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long q = (long long)blockIdx.x * kTC + lane;
+  const bool valid = q < Q;
+  long long base = 0;
+  if (valid) {
+    const long long o = q / inner;
+    base = o * (long long)n * inner + (q - o * inner);
+  }
+  for (int a = warp; a < n; a += kWarps) {
+    const df v = valid ? ld<TIn>(X, base + (long long)a * inner) : df{0.f, 0.f};
+    xs[a * kTC + lane] = make_float2(v.h, v.l);
+  }
+  __syncthreads();
+  for (int i0 = warp; i0 < n; i0 += kWarps * kIB) {
+    df acc[kIB];
+    const float2* row[kIB];
+#pragma unroll
+    for (int b = 0; b < kIB; ++b) {
+      acc[b] = df{0.f, 0.f};
+      const int i = min(i0 + b * kWarps, n - 1);
+      row[b] = J + (size_t)i * n;
+    }
+    for (int a = 0; a < n; ++a) {
+      const df x = dfa::from_float2(xs[a * kTC + lane]);
+#pragma unroll
+      for (int b = 0; b < kIB; ++b) dfa::fma_acc(acc[b], __ldg(row[b] + a), x);
+    }
+    if (valid) {
+#pragma unroll
+      for (int b = 0; b < kIB; ++b) {
+        const int i = i0 + b * kWarps;
+        if (i < n) st(Y, base + (long long)i * inner, dfa::norm(acc[b]));
+      }
+    }
+  }
+}
+
+struct ArrowDF {
+  int d, n1, n2, nt, n_pairs, has_zero;
+  long long Ns;
+  const float2* lam[3];   // spatial eigenvalues
+  const float2* B;        // gamma lam_j per pair
+  const float2* BB;       // (gamma lam_j)^2 per pair
+  const float2* G;        // gamma g, nt - 1 entries
+  const float2* Sinv;     // Ns
+  float2 nu;
+};
+
+// Step 3 per spatial index k (see k_arrowhead in kernels.cu for the algebra).
+__global__ void k_arrowhead_df(float2* __restrict__ X, ArrowDF p) {
+  const long long Ns = p.Ns;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < Ns;
+       k += (long long)gridDim.x * blockDim.x) {
+    long long rest = k;
+    const int i1 = (int)(rest % p.n1);
+    rest /= p.n1;
+    df mu = dfa::from_float2(p.lam[0][i1]);
+    if (p.d >= 2) {
+      const int i2 = (int)(rest % p.n2);
+      rest /= p.n2;
+      mu = dfa::add(mu, dfa::from_float2(p.lam[1][i2]));
+    }
+    if (p.d >= 3) mu = dfa::add(mu, dfa::from_float2(p.lam[2][rest]));
+    const df a = dfa::mul(dfa::from_float2(p.nu), mu);
+    const df a2 = dfa::mul(a, a);
+    df y = dfa::from_float2(X[(long long)(p.nt - 1) * Ns + k]);
+    for (int j = 0; j < p.n_pairs; ++j) {
+      const df x1 = dfa::from_float2(X[(long long)(2 * j) * Ns + k]);
+      const df x2 = dfa::from_float2(X[(long long)(2 * j + 1) * Ns + k]);
+      const df b = dfa::from_float2(p.B[j]);
+      const df inv = dfa::recip(dfa::add(a2, dfa::from_float2(p.BB[j])));
+      const df h1 = dfa::mul(dfa::sub(dfa::mul(a, x1), dfa::mul(b, x2)), inv);
+      const df h2 = dfa::mul(dfa::add(dfa::mul(b, x1), dfa::mul(a, x2)), inv);
+      y = dfa::add(y, dfa::add(dfa::mul(dfa::from_float2(p.G[2 * j]), h1), dfa::mul(dfa::from_float2(p.G[2 * j + 1]), h2)));
+    }
+    const int z = 2 * p.n_pairs;
+    df x0{0.f, 0.f}, inva{0.f, 0.f};
+    if (p.has_zero) {
+      x0 = dfa::from_float2(X[(long long)z * Ns + k]);
+      inva = dfa::recip(a);
+      y = dfa::add(y, dfa::mul(dfa::from_float2(p.G[z]), dfa::mul(x0, inva)));
+    }
+    const df qn = dfa::mul(y, dfa::from_float2(p.Sinv[k]));
+    X[(long long)(p.nt - 1) * Ns + k] = make_float2(qn.h, qn.l);
+    for (int j = 0; j < p.n_pairs; ++j) {
+      const long long o1 = (long long)(2 * j) * Ns + k, o2 = (long long)(2 * j + 1) * Ns + k;
+      const df b = dfa::from_float2(p.B[j]);
+      const df inv = dfa::recip(dfa::add(a2, dfa::from_float2(p.BB[j])));
+      const df r1 = dfa::sub(dfa::from_float2(X[o1]), dfa::mul(dfa::from_float2(p.G[2 * j]), qn));
+      const df r2 = dfa::sub(dfa::from_float2(X[o2]), dfa::mul(dfa::from_float2(p.G[2 * j + 1]), qn));
+      const df q1 = dfa::mul(dfa::sub(dfa::mul(a, r1), dfa::mul(b, r2)), inv);
+      const df q2 = dfa::mul(dfa::add(dfa::mul(b, r1), dfa::mul(a, r2)), inv);
+      X[o1] = make_float2(q1.h, q1.l);
+      X[o2] = make_float2(q2.h, q2.l);
+    }
+    if (p.has_zero) {
+      const df q0 = dfa::mul(dfa::sub(x0, dfa::mul(dfa::from_float2(p.G[z]), qn)), inva);
+      X[(long long)z * Ns + k] = make_float2(q0.h, q0.l);
+    }
+  }
+}
+
+int sms() {
+  static int s = 0;
+  if (s == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s <= 0) s = 148;
+  }
+  return s;
+}
+
+template <typename TIn, typename TOut>
+cudaError_t launch_mode(const TIn* X, const float2* J, TOut* Y, int n, long long inner, long long outer,
+                        cudaStream_t st) {
+  const long long Q = inner * outer;
+  if (Q <= 0) return cudaSuccess;
+  static bool attr_done = false;
+  if (!attr_done) {
+    const cudaError_t e = cudaFuncSetAttribute(k_mode_df<TIn, TOut>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               256 * kTC * (int)sizeof(float2));
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  ProfScope ps("fd_mode_df", 2.0 * (double)Q * n * n, 8.0 * (double)Q * n * 2, st);
+  k_mode_df<TIn, TOut><<<(unsigned)((Q + kTC - 1) / kTC), kThreads, (size_t)n * kTC * sizeof(float2), st>>>(
+      X, J, Y, n, inner, Q);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fd_mode_df(const void* X, int x_is_double, const float2* J, void* Y, int y_is_double, int n,
+                              long long inner, long long outer, cudaStream_t st) {
+  if (x_is_double)
+    return launch_mode<double, float2>((const double*)X, J, (float2*)Y, n, inner, outer, st);
+  if (y_is_double)
+    return launch_mode<float2, double>((const float2*)X, J, (double*)Y, n, inner, outer, st);
+  return launch_mode<float2, float2>((const float2*)X, J, (float2*)Y, n, inner, outer, st);
+}
+
+cudaError_t launch_arrowhead_df(float2* X, int d, int n1, int n2, int nt, int n_pairs, int has_zero, long long Ns,
+                                const float2* const* lam, const float2* B, const float2* BB, const float2* G,
+                                const float2* Sinv, double nu, cudaStream_t st) {
+  if (Ns <= 0) return cudaSuccess;
+  ArrowDF p;
+  p.d = d;
+  p.n1 = n1;
+  p.n2 = n2;
+  p.nt = nt;
+  p.n_pairs = n_pairs;
+  p.has_zero = has_zero;
+  p.Ns = Ns;
+  for (int l = 0; l < 3; ++l) p.lam[l] = l < d ? lam[l] : nullptr;
+  p.B = B;
+  p.BB = BB;
+  p.G = G;
+  p.Sinv = Sinv;
+  const float nh = (float)nu;
+  p.nu = make_float2(nh, (float)(nu - (double)nh));
+  ProfScope ps("arrowhead_df", (double)Ns * (10.0 * n_pairs + 4.0), 16.0 * (double)Ns * nt, st);
+  const long long want = (Ns + 255) / 256;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)sms() * 8));
+  k_arrowhead_df<<<grid, 256, 0, st>>>(X, p);
+  return cudaGetLastError();
+}
+
+}  // namespace stfd

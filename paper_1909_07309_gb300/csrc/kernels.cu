@@ -122,19 +122,40 @@ __device__ double block_sum(double v, double* red) {
   return t;   // valid in thread 0
 }
 
+// partial[b*m + i] = sum over block b's share of V_i . w. Vector pointers are
+// hoisted out of the element loop and the loop is unrolled so that every thread
+// keeps several independent loads in flight.
 __global__ void __launch_bounds__(kDotThreads)
 k_dot_multi(const double* const* __restrict__ V, int m, const double* __restrict__ w, long long N,
             double* __restrict__ partial) {
   __shared__ double red[kDotThreads / 32];
   const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   for (int i0 = 0; i0 < m; i0 += kDotGroup) {
-    double acc[kDotGroup] = {0.0, 0.0, 0.0, 0.0};
     const int cnt = min(kDotGroup, m - i0);
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride) {
-      const double wk = w[k];
+    const double* v[kDotGroup];
+#pragma unroll
+    for (int b = 0; b < kDotGroup; ++b) v[b] = V[i0 + (b < cnt ? b : 0)];
+    double acc[kDotGroup] = {0.0, 0.0, 0.0, 0.0};
+    long long k = k0;
+    for (; k + 3 * stride < N; k += 4 * stride) {
+      double wk[4], x[4][kDotGroup];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        wk[u] = __ldg(w + k + u * stride);
+#pragma unroll
+        for (int b = 0; b < kDotGroup; ++b) x[u][b] = b < cnt ? __ldg(v[b] + k + u * stride) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int b = 0; b < kDotGroup; ++b) acc[b] = fma(x[u][b], wk[u], acc[b]);
+    }
+    for (; k < N; k += stride) {
+      const double wk = __ldg(w + k);
 #pragma unroll
       for (int b = 0; b < kDotGroup; ++b)
-        if (b < cnt) acc[b] = fma(V[i0 + b][k], wk, acc[b]);
+        if (b < cnt) acc[b] = fma(__ldg(v[b] + k), wk, acc[b]);
     }
     for (int b = 0; b < cnt; ++b) {
       const double s = block_sum(acc[b], red);
@@ -152,13 +173,28 @@ __global__ void k_reduce_partial(const double* __restrict__ partial, int m, int 
   out[i] = accumulate ? out[i] + s : s;
 }
 
-__global__ void k_multi_axpy(double* __restrict__ w, const double* const* __restrict__ V,
-                             const double* __restrict__ h, int m, long long N, double sign) {
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N;
-       k += (long long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int i = 0; i < m; ++i) s = fma(h[i], V[i][k], s);
-    w[k] = fma(sign, s, w[k]);
+// w[k] += sign * sum_i h[i] V_i[k]: each thread owns 4 strided elements and
+// walks the vectors with the pointer and coefficient hoisted per vector.
+__global__ void __launch_bounds__(256)
+k_multi_axpy(double* __restrict__ w, const double* const* __restrict__ V, const double* __restrict__ h, int m,
+             long long N, double sign) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; k0 < N; k0 += 4 * stride) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < m; ++i) {
+      const double* vi = V[i];
+      const double hi = h[i];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long k = k0 + u * stride;
+        if (k < N) acc[u] = fma(hi, __ldg(vi + k), acc[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long k = k0 + u * stride;
+      if (k < N) w[k] = fma(sign, acc[u], w[k]);
+    }
   }
 }
 
@@ -197,7 +233,7 @@ int grid_for(long long n, int threads) {
 
 }  // namespace
 
-int dot_blocks() { return sm_count() * 2; }
+int dot_blocks() { return sm_count() * 4; }
 
 template <bool BAND>
 static cudaError_t launch_mode_impl(const char* name, const double* X1, const double* J1, double s1,
@@ -268,7 +304,7 @@ cudaError_t launch_reduce_partial(const double* partial, int m, int nblocks, dou
 cudaError_t launch_multi_axpy(double* w, const double* const* V, const double* h, int m,
                               long long N, double sign, cudaStream_t st) {
   ProfScope ps("gmres_multi_axpy", 2.0 * N * m, 8.0 * N * (m + 2), st);
-  k_multi_axpy<<<grid_for(N, 256), 256, 0, st>>>(w, V, h, m, N, sign);
+  k_multi_axpy<<<grid_for((N + 3) / 4, 256), 256, 0, st>>>(w, V, h, m, N, sign);
   return cudaGetLastError();
 }
 

@@ -64,6 +64,27 @@ cudaError_t launch_scale_by_inverse(double* y, const double* x, const double* de
 // y[k] = a[k] - b[k]
 cudaError_t launch_sub(double* y, const double* a, const double* b, long long N, cudaStream_t st);
 
+// Double-float banded passes of the matvec (band_df.cu); factors row-major (hi, lo):
+//   first direction:  (Uo, Vo) = (x x M, x x K), x FP64
+//   other directions: (Uo, Vo) = (u x M, u x K + v x M)
+//   time:             y = gamma u x W + nu v x M_t, y FP64
+cudaError_t launch_band_first_df(const double* x, const float2* M, const float2* K, float2* Uo, float2* Vo, int n,
+                                 long long inner, long long outer, int bw, cudaStream_t st);
+cudaError_t launch_band_mid_df(const float2* u, const float2* v, const float2* M, const float2* K, float2* Uo,
+                               float2* Vo, int n, long long inner, long long outer, int bw, cudaStream_t st);
+cudaError_t launch_band_last_df(const float2* u, const float2* v, const float2* W, double gamma, const float2* Mt,
+                                double nu, double* y, int n, long long inner, long long outer, int bw,
+                                cudaStream_t st);
+
+// Double-float Algorithm 1 (fd_df.cu): dense mode product with (hi, lo) row-major
+// factor J, X FP64 or float2, Y float2 or FP64 (not both FP64); Step 3 in place on
+// a float2 spectral tensor with per-pair B = gamma lam_j, BB = B^2, G = gamma g.
+cudaError_t launch_fd_mode_df(const void* X, int x_is_double, const float2* J, void* Y, int y_is_double, int n,
+                              long long inner, long long outer, cudaStream_t st);
+cudaError_t launch_arrowhead_df(float2* X, int d, int n1, int n2, int nt, int n_pairs, int has_zero, long long Ns,
+                                const float2* const* lam, const float2* B, const float2* BB, const float2* G,
+                                const float2* Sinv, double nu, cudaStream_t st);
+
 int dot_blocks();
 
 }  // namespace stfd

@@ -15,9 +15,10 @@ from . import build as _build
 
 STFD_OK = 0
 STFD_NOT_CONVERGED = 1
-STFD_FP64, STFD_TF32, STFD_BF16 = 0, 1, 2
+STFD_FP64, STFD_TF32, STFD_BF16, STFD_DF32 = 0, 1, 2, 3
 STFD_BC_NONE, STFD_BC_INITIAL, STFD_BC_DIRICHLET = 0, 1, 2
 STFD_NOALLOC_MAX_N = 524288
+STFD_OP_FP64, STFD_OP_DF32 = 0, 1
 
 _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_dbl_p = ctypes.POINTER(ctypes.c_double)
@@ -62,7 +63,7 @@ SIGNATURES = {
     "stfd_fd_destroy": (None, [ctypes.c_void_p]),
     "stfd_op_create_kron": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _c_int_p, _c_dbl_pp,
                                            _c_dbl_pp, _c_dbl_p, _c_dbl_p, ctypes.c_double, ctypes.c_double,
-                                           ctypes.c_void_p]),
+                                           ctypes.c_int, ctypes.c_void_p]),
     "stfd_st_matvec": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                       ctypes.c_void_p]),
     "stfd_op_destroy": (None, [ctypes.c_void_p]),
@@ -249,7 +250,7 @@ class FD:
 class KronOp:
     """System operator handle: ``stfd_op_create_kron`` / ``stfd_st_matvec`` / ``stfd_gmres_solve``."""
 
-    def __init__(self, K, M, Wt, Mt, gamma=1.0, nu=1.0, stream=None):
+    def __init__(self, K, M, Wt, Mt, gamma=1.0, nu=1.0, arith=STFD_OP_FP64, stream=None):
         lib = load()
         self._lib = lib
         self.handle = ctypes.c_void_p()
@@ -261,7 +262,7 @@ class KronOp:
         self.N = int(np.prod(self.n))
         rc = lib.stfd_op_create_kron(ctypes.byref(self.handle), self.d, (ctypes.c_int * (self.d + 1))(*self.n),
                                      _ptr_array(K), _ptr_array(M), _dptr(Wt), _dptr(Mt), float(gamma),
-                                     float(nu), _stream(stream))
+                                     float(nu), int(arith), _stream(stream))
         _check(rc, "stfd_op_create_kron")
 
     def matvec(self, x, y=None, stream=None):

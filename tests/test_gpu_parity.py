@@ -46,12 +46,14 @@ FD_CASES = [  # d, p, n_el, T, gamma, nu, nrhs  (n_t - 1 = n_el + p - 2 takes bo
 ]
 
 
+@pytest.mark.parametrize("prec", [stfd.STFD_FP64, stfd.STFD_DF32])
 @pytest.mark.parametrize("d,p,n_el,T,gamma,nu,nrhs", FD_CASES)
-def test_fd_apply_matches_oracle(d, p, n_el, T, gamma, nu, nrhs):
+def test_fd_apply_matches_oracle(d, p, n_el, T, gamma, nu, nrhs, prec):
+    """FP64 and double-float (FP64-accurate) Algorithm 1 against the oracle, 1e-11."""
     if n_el + p - 2 < 1:
         pytest.skip("no spatial dofs")
     K, M, Wt, Mt = stfd.heat_problem(d, p, n_el, T=T)
-    P = stfd.FD(K, M, Wt, Mt, gamma, nu)
+    P = stfd.FD(K, M, Wt, Mt, gamma, nu, precision=prec)
     r = inputs.standard_normal(P.N, seed=11 + d + p, batch=nrhs).reshape(nrhs, P.N)
     s = host(P.apply(dev(r)))
     oK, oM, oWt, oMt = oracle_factors(d, p, n_el, T)
@@ -79,10 +81,12 @@ MV_CASES = [(1, 3, 30, 1.0, 1.0, 1.0, 1), (2, 2, 16, 1.0, 1.0, 1.0, 2), (2, 4, 1
             (3, 3, 13, 1.0, 1.0, 1.0, 1), (3, 1, 17, 2.0, 1.1, 0.9, 1)]
 
 
+@pytest.mark.parametrize("arith", [stfd.STFD_OP_FP64, stfd.STFD_OP_DF32])
 @pytest.mark.parametrize("d,p,n_el,T,gamma,nu,nrhs", MV_CASES)
-def test_st_matvec_matches_oracle(d, p, n_el, T, gamma, nu, nrhs):
+def test_st_matvec_matches_oracle(d, p, n_el, T, gamma, nu, nrhs, arith):
+    """FP64 and double-float (about 48-bit) matvec both agree with the oracle to 1e-13."""
     K, M, Wt, Mt = stfd.heat_problem(d, p, n_el, T=T)
-    A = stfd.KronOp(K, M, Wt, Mt, gamma, nu)
+    A = stfd.KronOp(K, M, Wt, Mt, gamma, nu, arith=arith)
     x = inputs.standard_normal(A.N, seed=3, batch=nrhs).reshape(nrhs, A.N)
     y = host(A.matvec(dev(x)))
     oK, oM, oWt, oMt = oracle_factors(d, p, n_el, T)
@@ -91,12 +95,14 @@ def test_st_matvec_matches_oracle(d, p, n_el, T, gamma, nu, nrhs):
         assert np.max(np.abs(y[k] - ref)) <= 1e-13 * np.max(np.abs(ref))
 
 
-def test_gmres_unit_cube_single_iteration():
+@pytest.mark.parametrize("arith,prec", [(stfd.STFD_OP_FP64, stfd.STFD_FP64), (stfd.STFD_OP_DF32, stfd.STFD_FP64),
+                                        (stfd.STFD_OP_DF32, stfd.STFD_DF32)])
+def test_gmres_unit_cube_single_iteration(arith, prec):
     """Unit cube, T = 1, constant coefficients: P = A, one iteration (Sec. 4, F = id)."""
     d, p, n_el = 3, 3, 12
     K, M, Wt, Mt = stfd.heat_problem(d, p, n_el)
-    A = stfd.KronOp(K, M, Wt, Mt)
-    P = stfd.FD(K, M, Wt, Mt)
+    A = stfd.KronOp(K, M, Wt, Mt, arith=arith)
+    P = stfd.FD(K, M, Wt, Mt, precision=prec)
     f = inputs.standard_normal(A.N, seed=21)
     u, info = A.gmres(P, dev(f))
     assert info["converged"] and info["iters"] == 1
@@ -106,14 +112,14 @@ def test_gmres_unit_cube_single_iteration():
     assert np.linalg.norm(host(u) - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("restart", [100, 4])
-def test_gmres_mismatched_preconditioner(restart):
+@pytest.mark.parametrize("restart,arith", [(100, stfd.STFD_OP_FP64), (4, stfd.STFD_OP_FP64), (100, stfd.STFD_OP_DF32)])
+def test_gmres_mismatched_preconditioner(restart, arith):
     """nu_A = 2, nu_P = 1: several iterations; same count as the oracle's
     GMRES (same Krylov space; CGS2 vs MGS differ only by rounding), true
     residual <= 1e-8 and the solution of a direct solve."""
     d, p, n_el = 2, 3, 10
     K, M, Wt, Mt = stfd.heat_problem(d, p, n_el)
-    A = stfd.KronOp(K, M, Wt, Mt, 1.0, 2.0)
+    A = stfd.KronOp(K, M, Wt, Mt, 1.0, 2.0, arith=arith)
     P = stfd.FD(K, M, Wt, Mt, 1.0, 1.0)
     f = inputs.standard_normal(A.N, seed=8)
     u, info = A.gmres(P, dev(f), restart=restart)
@@ -166,14 +172,15 @@ def _row_of_A(S, idx, oK, oM, oWt, oMt, gamma, nu, p):
     return float(val)
 
 
-def test_fd_apply_full_size_residual_samples():
+@pytest.mark.parametrize("prec", [stfd.STFD_FP64, stfd.STFD_DF32])
+def test_fd_apply_full_size_residual_samples(prec):
     """Workload at scale (d = 3, p = 3, 64 elements, N = 18,125,250): P = A on
     the unit cube, so A (P^{-1} r) = r holds at every entry; checked on 400
     sampled entries with the oracle's univariate matrices."""
     cfg = inputs.SCALE
     d, p, n_el = cfg["d"], cfg["p"], cfg["n_el"]
     K, M, Wt, Mt = stfd.heat_problem(d, p, n_el)
-    P = stfd.FD(K, M, Wt, Mt)
+    P = stfd.FD(K, M, Wt, Mt, precision=prec)
     r = inputs.standard_normal(P.N, cfg["rhs_seed"])
     s = host(P.apply(dev(r)))
     oK, oM, oWt, oMt = oracle_factors(d, p, n_el)
