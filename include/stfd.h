@@ -55,7 +55,13 @@ enum {
  * FP32 intermediates and an FP32 Step 3; input and output vectors stay FP64.
  * The low-precision preconditioner is meant for flexible GMRES, which keeps
  * the outer iteration, the system matvec and the residual in FP64. */
-enum { STFD_FP64 = 0, STFD_TF32 = 1, STFD_BF16 = 2, STFD_DF32 = 3 };
+enum { STFD_FP64 = 0, STFD_TF32 = 1, STFD_BF16 = 2, STFD_DF32 = 3, STFD_FP64TC = 4 };
+/* STFD_FP64TC: FP64-accurate Algorithm 1 with the mode products on the tcgen05
+ * tensor cores: each row of the tensor and of the factor is split exactly into
+ * six signed 8-bit digits under its own power of two, digit products run as
+ * BF16 MMAs with FP32 accumulation (exact for the leading diagonals), and the
+ * partial sums are recombined in double-float arithmetic; Step 3 in double-float.
+ * Requires every n[l] <= 80. Agrees with STFD_FP64 to about 1e-13. */
 /* STFD_DF32: FP64-accurate Algorithm 1 in double-float arithmetic on the FP32
  * pipes (every value an unevaluated pair hi + lo of floats, about 48
  * significant bits; products split exactly by FMA, sums by error-free

@@ -95,6 +95,11 @@ struct stfd_fd {
   float2* BB2 = nullptr;
   float2* G2 = nullptr;
   float2* Sinv2 = nullptr;
+  // tensor-core FP64-accurate path (STFD_FP64TC): digit planes and row scales of U^T / U
+  unsigned char* Zf[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};
+  unsigned char* Zb[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};
+  int* zvf[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};
+  int* zvb[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 struct GmresWork {
@@ -187,6 +192,12 @@ extern "C" void stfd_fd_destroy(stfd_fd* h) {
   dev_free(h->BB2);
   dev_free(h->G2);
   dev_free(h->Sinv2);
+  for (int l = 0; l <= kMaxDim; ++l) {
+    dev_free(h->Zf[l]);
+    dev_free(h->Zb[l]);
+    dev_free(h->zvf[l]);
+    dev_free(h->zvb[l]);
+  }
   delete h;
 }
 
@@ -197,8 +208,12 @@ extern "C" int stfd_fd_setup(stfd_fd** out, int d, const int* n, const double* c
   *out = nullptr;
   if (!sizes_ok(d, n) || !K || !M || !Wt || !Mt) return STFD_ERR_ARG;
   if (!(gamma > 0.0) || !(nu > 0.0) || !std::isfinite(gamma) || !std::isfinite(nu)) return STFD_ERR_ARG;
-  if (precision != STFD_FP64 && precision != STFD_TF32 && precision != STFD_BF16 && precision != STFD_DF32)
+  if (precision != STFD_FP64 && precision != STFD_TF32 && precision != STFD_BF16 && precision != STFD_DF32 &&
+      precision != STFD_FP64TC)
     return STFD_ERR_ARG;
+  if (precision == STFD_FP64TC)
+    for (int l = 0; l <= d; ++l)
+      if (n[l] > ozaki_max_n()) return STFD_ERR_ARG;
   if (precision == STFD_TF32 || precision == STFD_BF16)
     for (int l = 0; l <= d; ++l)
       if (n[l] > 128) return STFD_ERR_ARG;   // factor + tile + staging must fit in shared memory
@@ -270,10 +285,24 @@ extern "C" int stfd_fd_setup(stfd_fd** out, int d, const int* n, const double* c
     }
     return dev_upload(dst, keep2.back().data(), cnt, st);
   };
-  if (rc == STFD_OK && precision == STFD_DF32) {
+  std::vector<std::vector<unsigned char>> keepz;
+  std::vector<std::vector<int>> keepv;
+  if (rc == STFD_OK && precision == STFD_FP64TC) {
     for (int l = 0; l <= d && rc == STFD_OK; ++l) {
-      rc = up2(keep[2 * l].data(), keep[2 * l].size(), &h->Jf2[l]);
-      if (rc == STFD_OK) rc = up2(keep[2 * l + 1].data(), keep[2 * l + 1].size(), &h->Jb2[l]);
+      for (int dir = 0; dir < 2 && rc == STFD_OK; ++dir) {
+        keepv.emplace_back();
+        keepz.push_back(ozaki_planes(keep[2 * l + dir].data(), n[l], keepv.back()));
+        rc = dev_upload(dir == 0 ? &h->Zf[l] : &h->Zb[l], keepz.back().data(), keepz.back().size(), st);
+        if (rc == STFD_OK) rc = dev_upload(dir == 0 ? &h->zvf[l] : &h->zvb[l], keepv.back().data(), keepv.back().size(), st);
+      }
+    }
+  }
+  if (rc == STFD_OK && (precision == STFD_DF32 || precision == STFD_FP64TC)) {
+    for (int l = 0; l <= d && rc == STFD_OK; ++l) {
+      if (precision == STFD_DF32) {
+        rc = up2(keep[2 * l].data(), keep[2 * l].size(), &h->Jf2[l]);
+        if (rc == STFD_OK) rc = up2(keep[2 * l + 1].data(), keep[2 * l + 1].size(), &h->Jb2[l]);
+      }
       if (rc == STFD_OK && l < d) rc = up2(f.lam[l].data(), f.lam[l].size(), &h->lam2[l]);
     }
     std::vector<double> B(std::max(1, f.n_pairs)), BB(std::max(1, f.n_pairs)), G(f.g.size());
@@ -376,9 +405,17 @@ int fd_apply_one_lowp(const stfd_fd* h, const double* r, double* s, double* work
   return STFD_OK;
 }
 
-// Double-float Algorithm 1: same pass structure as the FP64 path, intermediates
-// stored as float2 in the scratch and output buffers.
+// Double-float Algorithm 1 (mode products in double-float on the FP32 pipes,
+// or on the tensor cores by exact digit slices): same pass structure as the
+// FP64 path, intermediates stored as float2 in the scratch and output buffers.
 int fd_apply_one_df(const stfd_fd* h, const double* r, double* s, double* work, cudaStream_t st) {
+  const bool tc = h->precision == STFD_FP64TC;
+  auto mode = [&](const void* X, int xd, int l, bool fwd, void* Y, int yd, long long inner, long long outer) {
+    if (tc)
+      return launch_fd_mode_ozaki(X, xd, fwd ? h->Zf[l] : h->Zb[l], fwd ? h->zvf[l] : h->zvb[l], Y, yd, h->n[l],
+                                  inner, outer, st);
+    return launch_fd_mode_df(X, xd, fwd ? h->Jf2[l] : h->Jb2[l], Y, yd, h->n[l], inner, outer, st);
+  };
   const int d = h->d;
   const int P = 2 * (d + 1);
   auto buf = [&](int k) { return ((P - k) % 2 == 0) ? static_cast<void*>(s) : static_cast<void*>(work); };
@@ -388,7 +425,7 @@ int fd_apply_one_df(const stfd_fd* h, const double* r, double* s, double* work, 
   for (int l = 0; l <= d; ++l) {
     const long long outer = h->N / (inner * h->n[l]);
     void* dst = buf(++pass);
-    STFD_CU(launch_fd_mode_df(src, pass == 1 ? 1 : 0, h->Jf2[l], dst, 0, h->n[l], inner, outer, st));
+    STFD_CU(mode(src, pass == 1 ? 1 : 0, l, true, dst, 0, inner, outer));
     src = dst;
     inner *= h->n[l];
   }
@@ -400,7 +437,7 @@ int fd_apply_one_df(const stfd_fd* h, const double* r, double* s, double* work, 
     inner /= h->n[l];
     const long long outer = h->N / (inner * h->n[l]);
     void* dst = buf(++pass);
-    STFD_CU(launch_fd_mode_df(src, 0, h->Jb2[l], dst, pass == P ? 1 : 0, h->n[l], inner, outer, st));
+    STFD_CU(mode(src, 0, l, false, dst, pass == P ? 1 : 0, inner, outer));
     src = dst;
   }
   return STFD_OK;
@@ -408,7 +445,7 @@ int fd_apply_one_df(const stfd_fd* h, const double* r, double* s, double* work, 
 
 // One right-hand side: s = P^{-1} r through 2(d+1) mode products and Step 3.
 int fd_apply_one(const stfd_fd* h, const double* r, double* s, double* work, cudaStream_t st) {
-  if (h->precision == STFD_DF32) return fd_apply_one_df(h, r, s, work, st);
+  if (h->precision == STFD_DF32 || h->precision == STFD_FP64TC) return fd_apply_one_df(h, r, s, work, st);
   if (h->precision != STFD_FP64) return fd_apply_one_lowp(h, r, s, work, st);
   const int d = h->d;
   const int P = 2 * (d + 1);

@@ -85,6 +85,13 @@ cudaError_t launch_arrowhead_df(float2* X, int d, int n1, int n2, int nt, int n_
                                 const float2* const* lam, const float2* B, const float2* BB, const float2* G,
                                 const float2* Sinv, double nu, cudaStream_t st);
 
+// FP64-accurate mode product on tcgen05 by exact BF16 digit slices (tc_ozaki.cu):
+// X FP64 or float2, Y float2 or FP64 (not both FP64); B / v from ozaki_planes.
+cudaError_t launch_fd_mode_ozaki(const void* X, int x_is_double, const unsigned char* B, const int* v, void* Y,
+                                 int y_is_double, int n, long long inner, long long outer, cudaStream_t st);
+std::vector<unsigned char> ozaki_planes(const double* J, int n, std::vector<int>& v);
+int ozaki_max_n();
+
 int dot_blocks();
 
 }  // namespace stfd

@@ -1,0 +1,388 @@
+// FP64-accurate mode products of Algorithm 1 on the tcgen05 tensor cores by
+// exact digit slicing (the error-free splitting of Ozaki, Ogita, Oishi and
+// Rump): Y[q][i] = sum_a X[q][a] J[i][a] with
+//
+//   X[q][a] = 2^{u_q} F[q][a],  F = sum_{k<6} dx_k 2^{40-8k},  |dx_k| <= 255,
+//   J[i][a] = 2^{v_i} G[i][a],  G = sum_{l<6} dj_l 2^{40-8l},  |dj_l| <= 255,
+//
+// one power of two per row (the row's largest exponent), so that every digit
+// is an integer that BF16 holds exactly and every digit product is exact.
+// Then Y[q][i] = 2^{u_q + v_i + 80} sum_{c<6} 2^{-8c} T_c[q][i] with
+// T_c = sum_{k+l=c} sum_a dx_k[q][a] dj_l[i][a]. Each T_c is accumulated in its
+// own FP32 TMEM accumulator by BF16 tcgen05 MMAs: for c <= 2 every partial sum
+// is an integer below 2^24 (n <= 80), hence exact; for c >= 3 the FP32 rounding
+// sits below 2^-44 of the result scale. Pairs with k + l >= 6 are dropped
+// (< 2^-47 relative). The six T_c are combined in double-float arithmetic.
+//
+// One persistent CTA per SM (the six accumulators take 480 of the 512 TMEM
+// columns). Per 128-column tile: stage X in shared memory, convert each row to
+// 48-bit fixed point, then for k = 0..5 write digit plane dx_k (double
+// buffered) and issue the MMAs of pairs (k, l <= 5 - k) against the resident
+// planes of J.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "df.cuh"
+#include "kernels.h"
+#include "profile.h"
+#include "tc_common.cuh"
+
+namespace stfd {
+
+extern __device__ int g_tc_status;
+
+namespace {
+
+constexpr int kTile = 128;
+constexpr int kDig = 6;
+constexpr long kWaitIters = 1L << 22;
+
+__host__ __device__ inline size_t canon_off16(int r, int k, int kcores) {
+  return (size_t)(r >> 3) * (kcores * 128) + (size_t)(k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+struct OzArgs {
+  const void* X;
+  void* Y;
+  const unsigned char* B;   // kDig digit planes of J (npad x npad BF16 each)
+  const int* v;             // per output row i: 2^{v_i} scale of J
+  int n, npad;
+  long long inner, Q, ntiles;
+};
+
+// Row of doubles -> 48-bit fixed point: returns u with x = F 2^u.
+__device__ __forceinline__ int row_fixed_double(long long* F, int n) {
+  int E = 0;
+  for (int a = 0; a < n; ++a) E = max(E, (int)((F[a] >> 52) & 0x7FF));
+  for (int a = 0; a < n; ++a) {
+    const long long bits = F[a];
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    long long f = 0;
+    if (ex != 0) {
+      const unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      const int sh = E - ex + 5;
+      f = sh < 64 ? (long long)(m >> sh) : 0;
+    }
+    F[a] = bits < 0 ? -f : f;
+  }
+  return E - 1070;   // |x| = m 2^{ex-1075} = F 2^{E-1070}
+}
+
+// Row of double-floats (stored as float2 bits) -> 48-bit fixed point.
+__device__ __forceinline__ int row_fixed_df(long long* F, int n) {
+  int E = 0;
+  for (int a = 0; a < n; ++a) {
+    const unsigned int hb = (unsigned int)((unsigned long long)F[a] & 0xFFFFFFFFull);
+    E = max(E, (int)((hb >> 23) & 0xFF));
+  }
+  for (int a = 0; a < n; ++a) {
+    const unsigned long long w = (unsigned long long)F[a];
+    const unsigned int hb = (unsigned int)(w & 0xFFFFFFFFull), lb = (unsigned int)(w >> 32);
+    long long fh = 0, fl = 0;
+    const int eh = (hb >> 23) & 0xFF, el = (lb >> 23) & 0xFF;
+    if (eh != 0) {
+      const long long mh = (long long)((hb & 0x7FFFFF) | 0x800000);
+      const int sh = 24 + eh - E;        // |h| = mh 2^{eh-150} = F 2^{E-174}
+      fh = sh >= 0 ? (mh << sh) : (sh > -64 ? (mh >> -sh) : 0);
+      if (hb >> 31) fh = -fh;
+    }
+    if (el != 0) {
+      const long long ml = (long long)((lb & 0x7FFFFF) | 0x800000);
+      const int sh = 24 + el - E;
+      fl = sh >= 0 ? (ml << sh) : (sh > -64 ? (ml >> -sh) : 0);
+      if (lb >> 31) fl = -fl;
+    }
+    F[a] = fh + fl;
+  }
+  return E - 174;
+}
+
+__device__ __forceinline__ float pow2f(int e) {   // 2^e for e in [-126, 127]
+  return __int_as_float((e + 127) << 23);
+}
+
+template <typename T>
+struct IsDouble {
+  static constexpr bool value = false;
+};
+template <>
+struct IsDouble<double> {
+  static constexpr bool value = true;
+};
+
+template <typename T>
+struct StoreOut;
+template <>
+struct StoreOut<double> {
+  __device__ static void put(double* p, long long i, dfa::df v) { p[i] = dfa::to_double(v); }
+};
+template <>
+struct StoreOut<float2> {
+  __device__ static void put(float2* p, long long i, dfa::df v) { p[i] = make_float2(v.h, v.l); }
+};
+
+template <typename TIn, typename TOut>
+__global__ void __launch_bounds__(kTile, 1) k_tc_ozaki(OzArgs args) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int n = args.n, npad = args.npad;
+  const int kcores = npad / 8;                  // 16-byte core matrices along K (8 BF16 each)
+  const uint32_t sbo = (uint32_t)kcores * 128u;
+  const size_t plane = (size_t)npad * npad * 2;
+  const size_t abytes = (size_t)kTile * npad * 2;
+  const int ld = n + 1;                         // staging row stride (8-byte words)
+  const long long inner = args.inner, Q = args.Q;
+  unsigned char* sB = smem;                                  // kDig planes
+  long long* sF = reinterpret_cast<long long*>(sB + kDig * plane);   // kTile x ld
+  unsigned char* sA = reinterpret_cast<unsigned char*>(sF + (size_t)kTile * ld);   // 2 buffers
+  int* sv = reinterpret_cast<int*>(sA + 2 * abytes);        // npad
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sv + ((npad + 3) & ~3));  // 2 barriers
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  int* sflag = reinterpret_cast<int*>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(args.B);
+    uint4* dst = reinterpret_cast<uint4*>(sB);
+    const int nv = (int)(kDig * plane / 16);
+    for (int e = tid; e < nv; e += kTile) dst[e] = src[e];
+    uint4* za = reinterpret_cast<uint4*>(sA);
+    const int na = (int)(2 * abytes / 16);
+    for (int e = tid; e < na; e += kTile) za[e] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < npad; i += kTile) sv[i] = i < n ? args.v[i] : 0;
+  }
+  if (tid == 0) {
+    tc::mbar_init(tc::smem_u32(&mbar[0]), 1);
+    tc::mbar_init(tc::smem_u32(&mbar[1]), 1);
+    *sflag = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 512);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = tc::instr_desc(1u, kTile, npad);
+  const uint32_t a_addr = tc::smem_u32(sA), b_addr = tc::smem_u32(sB);
+  const int ksteps = npad / 16;
+  uint32_t ph[2] = {0u, 0u};
+  bool failed = false;
+
+  auto wait_buf = [&](int b) {
+    if (!tc::mbar_wait(tc::smem_u32(&mbar[b]), ph[b], kWaitIters)) *sflag = 1;
+    ph[b] ^= 1u;
+  };
+
+  for (long long tile = blockIdx.x; tile < args.ntiles && !failed; tile += gridDim.x) {
+    const long long q0 = tile * kTile;
+    const int rows = (int)min((long long)kTile, Q - q0);
+    const long long q = q0 + tid;
+    long long base = 0;
+    if (q < Q) {
+      const long long o = q / inner;
+      base = o * (long long)n * inner + (q - o * inner);
+    }
+    // ---- stage the tile's raw 8-byte values (row = tile column q)
+    const long long* Xw = static_cast<const long long*>(args.X);
+    if (inner == 1) {
+      const long long* src = Xw + q0 * n;
+      const int cnt = rows * n;
+      for (int e = tid; e < cnt; e += kTile) {
+        const int r = e / n;
+        sF[r * ld + (e - r * n)] = __ldg(src + e);
+      }
+    } else if (q < Q) {
+      for (int a = 0; a < n; ++a) sF[tid * ld + a] = __ldg(Xw + base + (long long)a * inner);
+    }
+    __syncthreads();
+    // ---- own row -> fixed point and its power-of-two scale
+    long long* Frow = sF + tid * ld;
+    int urow = 0;
+    if (tid < rows) urow = IsDouble<TIn>::value ? row_fixed_double(Frow, n) : row_fixed_df(Frow, n);
+    else
+      for (int a = 0; a < n; ++a) Frow[a] = 0;
+    // ---- digit planes k = 0..5 (double buffered) and their MMAs
+    for (int k = 0; k < kDig; ++k) {
+      const int b = k & 1;
+      if (k >= 2) wait_buf(b);
+      unsigned char* A = sA + b * abytes;
+      const int shift = 40 - 8 * k;
+      // one core-matrix row (8 consecutive K entries, 16 bytes) per store
+      for (int a0 = 0; a0 < n; a0 += 8) {
+        uint32_t w[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          float v2[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int a = a0 + 2 * t + h;
+            const long long f = a < n ? Frow[a] : 0;
+            const int dg = (int)(((f < 0 ? -f : f) >> shift) & 0xFF);
+            v2[h] = (float)(f < 0 ? -dg : dg);
+          }
+          const __nv_bfloat162 pr = __floats2bfloat162_rn(v2[0], v2[1]);
+          w[t] = *reinterpret_cast<const uint32_t*>(&pr);
+        }
+        *reinterpret_cast<uint4*>(A + canon_off16(tid, a0, kcores)) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      if (tid == 0) {
+        for (int l = 0; l + k < kDig; ++l) {
+          const uint32_t dcol = tmem + (uint32_t)((k + l) * npad);
+          for (int s = 0; s < ksteps; ++s) {
+            const uint64_t da = tc::smem_desc(a_addr + (uint32_t)(b * abytes) + s * 256, 128u, sbo);
+            const uint64_t db = tc::smem_desc(b_addr + (uint32_t)(l * plane) + s * 256, 128u, sbo);
+            tc::mma<0>(dcol, da, db, idesc, (k > 0 || s > 0) ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(tc::smem_u32(&mbar[b]));
+      }
+    }
+    wait_buf(0);   // commit of k = 4
+    wait_buf(1);   // commit of k = 5 (covers every MMA of the tile)
+    __syncthreads();
+    if (*sflag) {
+      if (tid == 0) atomicExch(&g_tc_status, 1);
+      failed = true;
+      break;
+    }
+    tc::fence_after_sync();
+    // ---- epilogue: combine the six diagonals of row tid
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < npad; c0 += 16) {
+      float T[kDig][16];
+#pragma unroll
+      for (int c = 0; c < kDig; ++c) tc::tmem_ld16(lane_base + (uint32_t)(c * npad + c0), T[c]);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int i = c0 + j;
+        if (i >= n) continue;
+        dfa::df s{0.f, 0.f};
+#pragma unroll
+        for (int c = kDig - 1; c >= 0; --c) s = dfa::add(s, dfa::df{T[c][j] * pow2f(-8 * c), 0.f});
+        int sc = urow + sv[i] + 80;
+        sc = max(-250, min(250, sc));
+        const float f1 = pow2f(sc / 2), f2 = pow2f(sc - sc / 2);
+        const dfa::df y{s.h * f1 * f2, s.l * f1 * f2};
+        if (tid < rows) {
+          if (inner == 1) {
+            float2* st = reinterpret_cast<float2*>(sF);
+            st[tid * ld + i] = make_float2(y.h, y.l);
+          } else {
+            StoreOut<TOut>::put(static_cast<TOut*>(args.Y), base + (long long)i * inner, y);
+          }
+        }
+      }
+    }
+    if (inner == 1) {
+      __syncthreads();
+      const float2* st = reinterpret_cast<const float2*>(sF);
+      TOut* dst = static_cast<TOut*>(args.Y) + q0 * n;
+      const int cnt = rows * n;
+      for (int e = tid; e < cnt; e += kTile) {
+        const int r = e / n;
+        const float2 v = st[r * ld + (e - r * n)];
+        StoreOut<TOut>::put(dst, e, dfa::df{v.x, v.y});
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+int sm_count_oz() {
+  static int s = 0;
+  if (s == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s <= 0) s = 148;
+  }
+  return s;
+}
+
+size_t oz_smem_bytes(int n) {
+  const int npad = (n + 15) / 16 * 16;
+  return (size_t)kDig * npad * npad * 2 + (size_t)kTile * (n + 1) * 8 + 2 * (size_t)kTile * npad * 2 +
+         (size_t)((npad + 3) & ~3) * 4 + 32;
+}
+
+template <typename TIn, typename TOut>
+cudaError_t launch_oz(const TIn* X, TOut* Y, const unsigned char* B, const int* v, int n, long long inner,
+                      long long outer, cudaStream_t st) {
+  const long long Q = inner * outer;
+  if (Q <= 0) return cudaSuccess;
+  const size_t smem = oz_smem_bytes(n);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  static bool attr_done = false;
+  if (!attr_done) {
+    const cudaError_t e = cudaFuncSetAttribute(k_tc_ozaki<TIn, TOut>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               227 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const long long ntiles = (Q + kTile - 1) / kTile;
+  const long long grid = std::min<long long>(ntiles, sm_count_oz());
+  OzArgs a{X, Y, B, v, n, (n + 15) / 16 * 16, inner, Q, ntiles};
+  ProfScope ps("fd_mode_ozaki", 2.0 * (double)Q * n * n, 8.0 * (double)Q * n * 2, st);
+  // 227 KB requested so that exactly one CTA (which owns all 512 TMEM columns) fits per SM
+  k_tc_ozaki<TIn, TOut><<<(unsigned)grid, kTile, 227 * 1024, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int ozaki_max_n() { return 80; }
+
+// Host: digit planes of a row-major n x n factor J (J[i*n + a]) and the
+// per-row scale exponents v_i (J[i][a] ~= 2^{v_i} sum_l dj_l 2^{40-8l}).
+std::vector<unsigned char> ozaki_planes(const double* J, int n, std::vector<int>& v) {
+  const int npad = (n + 15) / 16 * 16;
+  const int kcores = npad / 8;
+  const size_t plane = (size_t)npad * npad * 2;
+  std::vector<unsigned char> img(kDig * plane, 0);
+  v.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    int E = 0;
+    for (int a = 0; a < n; ++a) {
+      unsigned long long bits;
+      std::memcpy(&bits, &J[(size_t)i * n + a], 8);
+      E = std::max(E, (int)((bits >> 52) & 0x7FF));
+    }
+    v[i] = E - 1070;
+    for (int a = 0; a < n; ++a) {
+      unsigned long long bits;
+      std::memcpy(&bits, &J[(size_t)i * n + a], 8);
+      const int ex = (int)((bits >> 52) & 0x7FF);
+      unsigned long long f = 0;
+      if (ex != 0) {
+        const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const int sh = E - ex + 5;
+        f = sh < 64 ? (m >> sh) : 0;
+      }
+      const bool neg = (bits >> 63) != 0;
+      for (int l = 0; l < kDig; ++l) {
+        const int dg = (int)((f >> (40 - 8 * l)) & 0xFF);
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)(neg ? -dg : dg));
+        std::memcpy(&img[l * plane + canon_off16(i, a, kcores)], &h, 2);
+      }
+    }
+  }
+  return img;
+}
+
+cudaError_t launch_fd_mode_ozaki(const void* X, int x_is_double, const unsigned char* B, const int* v, void* Y,
+                                 int y_is_double, int n, long long inner, long long outer, cudaStream_t st) {
+  if (x_is_double) return launch_oz<double, float2>((const double*)X, (float2*)Y, B, v, n, inner, outer, st);
+  if (y_is_double) return launch_oz<float2, double>((const float2*)X, (double*)Y, B, v, n, inner, outer, st);
+  return launch_oz<float2, float2>((const float2*)X, (float2*)Y, B, v, n, inner, outer, st);
+}
+
+}  // namespace stfd
