@@ -35,7 +35,7 @@ L2_BYTES = 129 * 2 ** 20
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/);
 # None until captured for the current kernel.
-NCU_TRAFFIC = {"kernel": "fd_mode_df", "bytes_per_launch": None}
+NCU_TRAFFIC = {"kernel": "fd_mode_ozaki", "bytes_per_launch": None}
 
 
 def measured_peaks():
@@ -198,9 +198,10 @@ def main():
     cfg = inputs.SCALE
     K, M, Wt, Mt, f_np = build_workload(cfg)
     t_setup = time.perf_counter()
-    # FP64-accurate solve: double-float Algorithm 1 and double-float matvec (FP32 pipes)
+    # FP64-accurate solve: Algorithm 1 with tensor-core digit-sliced mode products
+    # (STFD_FP64TC) and the double-float matvec on the FP32 pipes
     A = stfd.KronOp(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], arith=stfd.STFD_OP_DF32)
-    P = stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=stfd.STFD_DF32)
+    P = stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=stfd.STFD_FP64TC)
     setup_ms = (time.perf_counter() - t_setup) * 1e3
     N = P.N
     f = torch.from_numpy(f_np).cuda()
@@ -283,9 +284,9 @@ def main():
     # ---- preconditioner variants inside the same FP64 flexible GMRES
     variants = {}
     A64 = stfd.KronOp(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], arith=stfd.STFD_OP_FP64)
-    for name, prec, op in (("df32", stfd.STFD_DF32, A), ("fp64_ieee", stfd.STFD_FP64, A64),
-                           ("tf32", stfd.STFD_TF32, A), ("bf16", stfd.STFD_BF16, A)):
-        Pv = P if prec == stfd.STFD_DF32 else stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=prec)
+    for name, prec, op in (("fp64tc", stfd.STFD_FP64TC, A), ("df32", stfd.STFD_DF32, A),
+                           ("fp64_ieee", stfd.STFD_FP64, A64), ("tf32", stfd.STFD_TF32, A), ("bf16", stfd.STFD_BF16, A)):
+        Pv = P if prec == stfd.STFD_FP64TC else stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=prec)
         for _ in range(3):
             Pv.apply(r, s)
         torch.cuda.synchronize()
@@ -335,7 +336,14 @@ def main():
     per_launch_s = top["ms"] * 1e-3 / top["launches"]
     achieved = top["flops"] / top["launches"] / per_launch_s
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["kernel"] == top["name"] else None
-    if top["name"].endswith("_df"):
+    if top["name"] == "fd_mode_ozaki":
+        # BF16 tensor MMAs actually issued: 21 digit pairs x 2 x Q x npad x npad per launch
+        tc_flops = top["flops"] * 21.0 * (80.0 / 66.0) ** 2     # padded 66 -> 80 (K and N)
+        peaks, _src = measured_peaks()
+        peak = peaks.get("bf16_tflops", 1900.0) * 1e12
+        achieved_tc = tc_flops / top["launches"] / (top["ms"] * 1e-3 / top["launches"])
+        src = "BF16 dense tensor peak (MEASURED_PEAKS.json, %s); achieved counts the BF16 MMAs issued" % _src
+    elif top["name"].endswith("_df"):
         # double-float kernels issue 12 FP32 instructions per FP64-equivalent FMA
         # (2 flop): peak = 128 FP32 lanes x SMs x clock x 2 / 12
         peak = 128 * sms * mhz * 1e6 * 2 / 12
@@ -344,8 +352,13 @@ def main():
         peak = 2 * 2 * sms * mhz * 1e6
         src = "FP64: 2 DFMA/clk/SM x %d SMs x %.0f MHz (sampled); DFMA probe in this run %.3f TFLOP/s" % (
             sms, mhz, probe / 1e12)
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+    bound = "alu"
+    if top["name"] == "fd_mode_ozaki":
+        bound = "tensor"
+        achieved = achieved_tc
+    roofline = {"bound": bound, "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": top["name"], "peak_source": src,
+                "fp64_equivalent_tflops": top["flops"] / top["launches"] / per_launch_s / 1e12,
                 "achieved_gbs": top["bytes"] / top["launches"] / per_launch_s / 1e9,
                 "share_of_step": top["ms"] / total_ms, "fp64_probe_tflops": probe / 1e12}
     kernels = {rc["name"]: {"launches": rc["launches"], "ms": round(rc["ms"], 3),
@@ -358,7 +371,8 @@ def main():
         "config": {"workload": cfg["name"], "N": N, "solve": "FD-preconditioned flexible GMRES to 1e-8, x0 = 0",
                    "restart": args.restart, "gmres_iters": infos[-1]["iters"],
                    "rel_res_true": infos[-1]["rel_res_true"],
-                   "precond": "Algorithm 1 in double-float (2 x FP32, ~48-bit) arithmetic, FP64 in/out",
+                   "precond": "Algorithm 1, FP64-accurate: mode products on tcgen05 via exact BF16 digit slices "
+                              "(6 x 8-bit, FP32 accumulate, double-float recombination), Step 3 double-float",
                    "matvec": "double-float (2 x FP32, ~48-bit), FP64 in/out", "gmres": "FP64",
                    "setup_ms": setup_ms,
                    "l2": "inputs larger than L2 (working set %.2f GB > 129 MB)" % (10 * N * 8 / 1e9),

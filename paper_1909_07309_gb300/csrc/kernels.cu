@@ -122,9 +122,36 @@ __device__ double block_sum(double v, double* red) {
   return t;   // valid in thread 0
 }
 
-// partial[b*m + i] = sum over block b's share of V_i . w. Vector pointers are
-// hoisted out of the element loop and the loop is unrolled so that every thread
-// keeps several independent loads in flight.
+// Sum over this block's share of C vectors dotted with w (C is a compile-time
+// group size, so no vector is loaded twice), unrolled 4x along the vectors.
+template <int C>
+__device__ __forceinline__ void dot_group(const double* const* __restrict__ V, int i0, const double* __restrict__ w,
+                                          long long N, long long k0, long long stride, double* acc) {
+  const double* v[C];
+#pragma unroll
+  for (int b = 0; b < C; ++b) v[b] = V[i0 + b];
+  long long k = k0;
+  for (; k + 3 * stride < N; k += 4 * stride) {
+    double wk[4], x[4][C];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      wk[u] = __ldg(w + k + u * stride);
+#pragma unroll
+      for (int b = 0; b < C; ++b) x[u][b] = __ldg(v[b] + k + u * stride);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int b = 0; b < C; ++b) acc[b] = fma(x[u][b], wk[u], acc[b]);
+  }
+  for (; k < N; k += stride) {
+    const double wk = __ldg(w + k);
+#pragma unroll
+    for (int b = 0; b < C; ++b) acc[b] = fma(__ldg(v[b] + k), wk, acc[b]);
+  }
+}
+
+// partial[b*m + i] = sum over block b's share of V_i . w
 __global__ void __launch_bounds__(kDotThreads)
 k_dot_multi(const double* const* __restrict__ V, int m, const double* __restrict__ w, long long N,
             double* __restrict__ partial) {
@@ -133,29 +160,12 @@ k_dot_multi(const double* const* __restrict__ V, int m, const double* __restrict
   const long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   for (int i0 = 0; i0 < m; i0 += kDotGroup) {
     const int cnt = min(kDotGroup, m - i0);
-    const double* v[kDotGroup];
-#pragma unroll
-    for (int b = 0; b < kDotGroup; ++b) v[b] = V[i0 + (b < cnt ? b : 0)];
     double acc[kDotGroup] = {0.0, 0.0, 0.0, 0.0};
-    long long k = k0;
-    for (; k + 3 * stride < N; k += 4 * stride) {
-      double wk[4], x[4][kDotGroup];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        wk[u] = __ldg(w + k + u * stride);
-#pragma unroll
-        for (int b = 0; b < kDotGroup; ++b) x[u][b] = b < cnt ? __ldg(v[b] + k + u * stride) : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int b = 0; b < kDotGroup; ++b) acc[b] = fma(x[u][b], wk[u], acc[b]);
-    }
-    for (; k < N; k += stride) {
-      const double wk = __ldg(w + k);
-#pragma unroll
-      for (int b = 0; b < kDotGroup; ++b)
-        if (b < cnt) acc[b] = fma(__ldg(v[b] + k), wk, acc[b]);
+    switch (cnt) {
+      case 1: dot_group<1>(V, i0, w, N, k0, stride, acc); break;
+      case 2: dot_group<2>(V, i0, w, N, k0, stride, acc); break;
+      case 3: dot_group<3>(V, i0, w, N, k0, stride, acc); break;
+      default: dot_group<4>(V, i0, w, N, k0, stride, acc); break;
     }
     for (int b = 0; b < cnt; ++b) {
       const double s = block_sum(acc[b], red);
@@ -164,13 +174,16 @@ k_dot_multi(const double* const* __restrict__ V, int m, const double* __restrict
   }
 }
 
+// out[i] = sum_b partial[b*m + i]: one warp per entry, lanes stride over blocks.
 __global__ void k_reduce_partial(const double* __restrict__ partial, int m, int nblocks,
                                  double* __restrict__ out, int accumulate) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (i >= m) return;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * m + i];
-  out[i] = accumulate ? out[i] + s : s;
+  for (int b = lane; b < nblocks; b += 32) s += partial[(size_t)b * m + i];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0) out[i] = accumulate ? out[i] + s : s;
 }
 
 // w[k] += sign * sum_i h[i] V_i[k]: each thread owns 4 strided elements and
@@ -297,7 +310,7 @@ cudaError_t launch_dot_multi(const double* const* V, int m, const double* w, lon
 cudaError_t launch_reduce_partial(const double* partial, int m, int nblocks, double* out,
                                   int accumulate, cudaStream_t st) {
   ProfScope ps("gmres_reduce", (double)m * nblocks, 8.0 * m * nblocks, st);
-  k_reduce_partial<<<(m + 127) / 128, 128, 0, st>>>(partial, m, nblocks, out, accumulate);
+  k_reduce_partial<<<(m + 3) / 4, 128, 0, st>>>(partial, m, nblocks, out, accumulate);
   return cudaGetLastError();
 }
 

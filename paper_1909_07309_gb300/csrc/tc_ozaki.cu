@@ -54,51 +54,47 @@ struct OzArgs {
   long long inner, Q, ntiles;
 };
 
-// Row of doubles -> 48-bit fixed point: returns u with x = F 2^u.
-__device__ __forceinline__ int row_fixed_double(long long* F, int n) {
+// Largest biased exponent over the entries a = a0, a0 + step, ... < n of a
+// staged row (FP64 words or double-float words).
+template <bool DBL>
+__device__ __forceinline__ int row_max_exp(const long long* F, int n, int a0, int step) {
   int E = 0;
-  for (int a = 0; a < n; ++a) E = max(E, (int)((F[a] >> 52) & 0x7FF));
-  for (int a = 0; a < n; ++a) {
-    const long long bits = F[a];
-    const int ex = (int)((bits >> 52) & 0x7FF);
-    long long f = 0;
-    if (ex != 0) {
-      const unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-      const int sh = E - ex + 5;
-      f = sh < 64 ? (long long)(m >> sh) : 0;
-    }
-    F[a] = bits < 0 ? -f : f;
+  for (int a = a0; a < n; a += step) {
+    const unsigned long long w = (unsigned long long)F[a];
+    E = max(E, DBL ? (int)((w >> 52) & 0x7FF) : (int)((w >> 23) & 0xFF));
   }
-  return E - 1070;   // |x| = m 2^{ex-1075} = F 2^{E-1070}
+  return E;
 }
 
-// Row of double-floats (stored as float2 bits) -> 48-bit fixed point.
-__device__ __forceinline__ int row_fixed_df(long long* F, int n) {
-  int E = 0;
-  for (int a = 0; a < n; ++a) {
-    const unsigned int hb = (unsigned int)((unsigned long long)F[a] & 0xFFFFFFFFull);
-    E = max(E, (int)((hb >> 23) & 0xFF));
+// Staged entry -> signed 48-bit fixed point under the row exponent E:
+// FP64:         x = F 2^{E-1070};   double-float: x = F 2^{E-174}.
+template <bool DBL>
+__device__ __forceinline__ long long to_fixed(long long word, int E) {
+  if (DBL) {
+    const int ex = (int)(((unsigned long long)word >> 52) & 0x7FF);
+    if (ex == 0) return 0;
+    const unsigned long long m = ((unsigned long long)word & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = E - ex + 5;
+    const long long f = sh < 64 ? (long long)(m >> sh) : 0;
+    return word < 0 ? -f : f;
   }
-  for (int a = 0; a < n; ++a) {
-    const unsigned long long w = (unsigned long long)F[a];
-    const unsigned int hb = (unsigned int)(w & 0xFFFFFFFFull), lb = (unsigned int)(w >> 32);
-    long long fh = 0, fl = 0;
-    const int eh = (hb >> 23) & 0xFF, el = (lb >> 23) & 0xFF;
-    if (eh != 0) {
-      const long long mh = (long long)((hb & 0x7FFFFF) | 0x800000);
-      const int sh = 24 + eh - E;        // |h| = mh 2^{eh-150} = F 2^{E-174}
-      fh = sh >= 0 ? (mh << sh) : (sh > -64 ? (mh >> -sh) : 0);
-      if (hb >> 31) fh = -fh;
-    }
-    if (el != 0) {
-      const long long ml = (long long)((lb & 0x7FFFFF) | 0x800000);
-      const int sh = 24 + el - E;
-      fl = sh >= 0 ? (ml << sh) : (sh > -64 ? (ml >> -sh) : 0);
-      if (lb >> 31) fl = -fl;
-    }
-    F[a] = fh + fl;
+  const unsigned long long w = (unsigned long long)word;
+  const unsigned int hb = (unsigned int)(w & 0xFFFFFFFFull), lb = (unsigned int)(w >> 32);
+  long long fh = 0, fl = 0;
+  const int eh = (hb >> 23) & 0xFF, el = (lb >> 23) & 0xFF;
+  if (eh != 0) {
+    const long long mh = (long long)((hb & 0x7FFFFF) | 0x800000);
+    const int sh = 24 + eh - E;          // |h| = mh 2^{eh-150}
+    fh = sh >= 0 ? (mh << sh) : (sh > -64 ? (mh >> -sh) : 0);
+    if (hb >> 31) fh = -fh;
   }
-  return E - 174;
+  if (el != 0) {
+    const long long ml = (long long)((lb & 0x7FFFFF) | 0x800000);
+    const int sh = 24 + el - E;
+    fl = sh >= 0 ? (ml << sh) : (sh > -64 ? (ml >> -sh) : 0);
+    if (lb >> 31) fl = -fl;
+  }
+  return fh + fl;
 }
 
 __device__ __forceinline__ float pow2f(int e) {   // 2^e for e in [-126, 127]
@@ -125,8 +121,14 @@ struct StoreOut<float2> {
   __device__ static void put(float2* p, long long i, dfa::df v) { p[i] = make_float2(v.h, v.l); }
 };
 
+// 512 threads: thread t owns tile row r = t % 128 (its TMEM lane) together with
+// three other threads (parts p = t / 128) that split the row's columns.
+constexpr int kParts = 4;
+constexpr int kThreads = kTile * kParts;
+
 template <typename TIn, typename TOut>
-__global__ void __launch_bounds__(kTile, 1) k_tc_ozaki(OzArgs args) {
+__global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
+  constexpr bool DBL = IsDouble<TIn>::value;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int n = args.n, npad = args.npad;
   const int kcores = npad / 8;                  // 16-byte core matrices along K (8 BF16 each)
@@ -135,26 +137,29 @@ __global__ void __launch_bounds__(kTile, 1) k_tc_ozaki(OzArgs args) {
   const size_t abytes = (size_t)kTile * npad * 2;
   const int ld = n + 1;                         // staging row stride (8-byte words)
   const long long inner = args.inner, Q = args.Q;
-  unsigned char* sB = smem;                                  // kDig planes
-  long long* sF = reinterpret_cast<long long*>(sB + kDig * plane);   // kTile x ld
+  unsigned char* sB = smem;                                            // kDig planes
+  long long* sF = reinterpret_cast<long long*>(sB + kDig * plane);     // kTile x ld
   unsigned char* sA = reinterpret_cast<unsigned char*>(sF + (size_t)kTile * ld);   // 2 buffers
-  int* sv = reinterpret_cast<int*>(sA + 2 * abytes);        // npad
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sv + ((npad + 3) & ~3));  // 2 barriers
+  int* sv = reinterpret_cast<int*>(sA + 2 * abytes);                  // npad
+  int* sE = sv + ((npad + 3) & ~3);                                    // kParts x kTile
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sE + kParts * kTile);   // 2 barriers
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   int* sflag = reinterpret_cast<int*>(tslot + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int t = threadIdx.x, warp = t >> 5, r = t & (kTile - 1), part = t >> 7;
+  const int nchunk = (n + 7) / 8;               // 8-column chunks holding data
+  const int nchunk_pad = npad / 8;
 
   {
     const uint4* src = reinterpret_cast<const uint4*>(args.B);
     uint4* dst = reinterpret_cast<uint4*>(sB);
     const int nv = (int)(kDig * plane / 16);
-    for (int e = tid; e < nv; e += kTile) dst[e] = src[e];
+    for (int e = t; e < nv; e += kThreads) dst[e] = src[e];
     uint4* za = reinterpret_cast<uint4*>(sA);
     const int na = (int)(2 * abytes / 16);
-    for (int e = tid; e < na; e += kTile) za[e] = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < npad; i += kTile) sv[i] = i < n ? args.v[i] : 0;
+    for (int e = t; e < na; e += kThreads) za[e] = make_uint4(0, 0, 0, 0);
+    for (int i = t; i < npad; i += kThreads) sv[i] = i < n ? args.v[i] : 0;
   }
-  if (tid == 0) {
+  if (t == 0) {
     tc::mbar_init(tc::smem_u32(&mbar[0]), 1);
     tc::mbar_init(tc::smem_u32(&mbar[1]), 1);
     *sflag = 0;
@@ -169,70 +174,74 @@ __global__ void __launch_bounds__(kTile, 1) k_tc_ozaki(OzArgs args) {
   const uint32_t a_addr = tc::smem_u32(sA), b_addr = tc::smem_u32(sB);
   const int ksteps = npad / 16;
   uint32_t ph[2] = {0u, 0u};
-  bool failed = false;
 
   auto wait_buf = [&](int b) {
     if (!tc::mbar_wait(tc::smem_u32(&mbar[b]), ph[b], kWaitIters)) *sflag = 1;
     ph[b] ^= 1u;
   };
 
-  for (long long tile = blockIdx.x; tile < args.ntiles && !failed; tile += gridDim.x) {
+  for (long long tile = blockIdx.x; tile < args.ntiles; tile += gridDim.x) {
     const long long q0 = tile * kTile;
     const int rows = (int)min((long long)kTile, Q - q0);
-    const long long q = q0 + tid;
+    const long long q = q0 + r;
     long long base = 0;
     if (q < Q) {
       const long long o = q / inner;
       base = o * (long long)n * inner + (q - o * inner);
     }
-    // ---- stage the tile's raw 8-byte values (row = tile column q)
+    // ---- stage the tile's raw 8-byte words (row r = tile column q), all copies in flight
     const long long* Xw = static_cast<const long long*>(args.X);
     if (inner == 1) {
       const long long* src = Xw + q0 * n;
       const int cnt = rows * n;
-      for (int e = tid; e < cnt; e += kTile) {
-        const int r = e / n;
-        sF[r * ld + (e - r * n)] = __ldg(src + e);
+      for (int e = t; e < cnt; e += kThreads) {
+        const int rr = e / n;
+        tc::cp_async8(&sF[rr * ld + (e - rr * n)], src + e);
       }
     } else if (q < Q) {
-      for (int a = 0; a < n; ++a) sF[tid * ld + a] = __ldg(Xw + base + (long long)a * inner);
+      for (int a = part; a < n; a += kParts) tc::cp_async8(&sF[r * ld + a], Xw + base + (long long)a * inner);
     }
+    tc::cp_async_wait_all();
     __syncthreads();
-    // ---- own row -> fixed point and its power-of-two scale
-    long long* Frow = sF + tid * ld;
-    int urow = 0;
-    if (tid < rows) urow = IsDouble<TIn>::value ? row_fixed_double(Frow, n) : row_fixed_df(Frow, n);
-    else
-      for (int a = 0; a < n; ++a) Frow[a] = 0;
+    // ---- row exponent (max over the four parts) and fixed-point conversion
+    long long* Frow = sF + r * ld;
+    sE[part * kTile + r] = (r < rows) ? row_max_exp<DBL>(Frow, n, part, kParts) : 0;
+    __syncthreads();
+    int E = 0;
+#pragma unroll
+    for (int pp = 0; pp < kParts; ++pp) E = max(E, sE[pp * kTile + r]);
+    const int urow = DBL ? E - 1070 : E - 174;
+    for (int a = part; a < n; a += kParts) Frow[a] = (r < rows) ? to_fixed<DBL>(Frow[a], E) : 0;
+    __syncthreads();
     // ---- digit planes k = 0..5 (double buffered) and their MMAs
     for (int k = 0; k < kDig; ++k) {
       const int b = k & 1;
       if (k >= 2) wait_buf(b);
       unsigned char* A = sA + b * abytes;
       const int shift = 40 - 8 * k;
-      // one core-matrix row (8 consecutive K entries, 16 bytes) per store
-      for (int a0 = 0; a0 < n; a0 += 8) {
+      for (int c8 = part; c8 < nchunk; c8 += kParts) {
+        const int a0 = 8 * c8;
         uint32_t w[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int tt = 0; tt < 4; ++tt) {
           float v2[2];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const int a = a0 + 2 * t + h;
+            const int a = a0 + 2 * tt + h;
             const long long f = a < n ? Frow[a] : 0;
             const int dg = (int)(((f < 0 ? -f : f) >> shift) & 0xFF);
             v2[h] = (float)(f < 0 ? -dg : dg);
           }
           const __nv_bfloat162 pr = __floats2bfloat162_rn(v2[0], v2[1]);
-          w[t] = *reinterpret_cast<const uint32_t*>(&pr);
+          w[tt] = *reinterpret_cast<const uint32_t*>(&pr);
         }
-        *reinterpret_cast<uint4*>(A + canon_off16(tid, a0, kcores)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(A + canon_off16(r, a0, kcores)) = make_uint4(w[0], w[1], w[2], w[3]);
       }
       tc::fence_async_smem();
       tc::fence_before_sync();
       __syncthreads();
       tc::fence_after_sync();
-      if (tid == 0) {
+      if (t == 0) {
         for (int l = 0; l + k < kDig; ++l) {
           const uint32_t dcol = tmem + (uint32_t)((k + l) * npad);
           for (int s = 0; s < ksteps; ++s) {
@@ -248,21 +257,20 @@ __global__ void __launch_bounds__(kTile, 1) k_tc_ozaki(OzArgs args) {
     wait_buf(1);   // commit of k = 5 (covers every MMA of the tile)
     __syncthreads();
     if (*sflag) {
-      if (tid == 0) atomicExch(&g_tc_status, 1);
-      failed = true;
+      if (t == 0) atomicExch(&g_tc_status, 1);
       break;
     }
     tc::fence_after_sync();
-    // ---- epilogue: combine the six diagonals of row tid
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < npad; c0 += 16) {
-      float T[kDig][16];
+    // ---- epilogue: part p combines the six diagonals of row r on chunks p, p+4, ...
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    for (int c8 = part; c8 < nchunk_pad; c8 += kParts) {
+      float T[kDig][8];
 #pragma unroll
-      for (int c = 0; c < kDig; ++c) tc::tmem_ld16(lane_base + (uint32_t)(c * npad + c0), T[c]);
+      for (int c = 0; c < kDig; ++c) tc::tmem_ld8(lane_base + (uint32_t)(c * npad + 8 * c8), T[c]);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int i = c0 + j;
-        if (i >= n) continue;
+      for (int j = 0; j < 8; ++j) {
+        const int i = 8 * c8 + j;
+        if (i >= n || r >= rows) continue;
         dfa::df s{0.f, 0.f};
 #pragma unroll
         for (int c = kDig - 1; c >= 0; --c) s = dfa::add(s, dfa::df{T[c][j] * pow2f(-8 * c), 0.f});
@@ -270,13 +278,10 @@ __global__ void __launch_bounds__(kTile, 1) k_tc_ozaki(OzArgs args) {
         sc = max(-250, min(250, sc));
         const float f1 = pow2f(sc / 2), f2 = pow2f(sc - sc / 2);
         const dfa::df y{s.h * f1 * f2, s.l * f1 * f2};
-        if (tid < rows) {
-          if (inner == 1) {
-            float2* st = reinterpret_cast<float2*>(sF);
-            st[tid * ld + i] = make_float2(y.h, y.l);
-          } else {
-            StoreOut<TOut>::put(static_cast<TOut*>(args.Y), base + (long long)i * inner, y);
-          }
+        if (inner == 1) {
+          reinterpret_cast<float2*>(sF)[r * ld + i] = make_float2(y.h, y.l);
+        } else {
+          StoreOut<TOut>::put(static_cast<TOut*>(args.Y), base + (long long)i * inner, y);
         }
       }
     }
@@ -285,9 +290,9 @@ __global__ void __launch_bounds__(kTile, 1) k_tc_ozaki(OzArgs args) {
       const float2* st = reinterpret_cast<const float2*>(sF);
       TOut* dst = static_cast<TOut*>(args.Y) + q0 * n;
       const int cnt = rows * n;
-      for (int e = tid; e < cnt; e += kTile) {
-        const int r = e / n;
-        const float2 v = st[r * ld + (e - r * n)];
+      for (int e = t; e < cnt; e += kThreads) {
+        const int rr = e / n;
+        const float2 v = st[rr * ld + (e - rr * n)];
         StoreOut<TOut>::put(dst, e, dfa::df{v.x, v.y});
       }
     }
@@ -311,7 +316,7 @@ int sm_count_oz() {
 size_t oz_smem_bytes(int n) {
   const int npad = (n + 15) / 16 * 16;
   return (size_t)kDig * npad * npad * 2 + (size_t)kTile * (n + 1) * 8 + 2 * (size_t)kTile * npad * 2 +
-         (size_t)((npad + 3) & ~3) * 4 + 32;
+         (size_t)((npad + 3) & ~3) * 4 + (size_t)kParts * kTile * 4 + 32;
 }
 
 template <typename TIn, typename TOut>
@@ -333,7 +338,7 @@ cudaError_t launch_oz(const TIn* X, TOut* Y, const unsigned char* B, const int* 
   OzArgs a{X, Y, B, v, n, (n + 15) / 16 * 16, inner, Q, ntiles};
   ProfScope ps("fd_mode_ozaki", 2.0 * (double)Q * n * n, 8.0 * (double)Q * n * 2, st);
   // 227 KB requested so that exactly one CTA (which owns all 512 TMEM columns) fits per SM
-  k_tc_ozaki<TIn, TOut><<<(unsigned)grid, kTile, 227 * 1024, st>>>(a);
+  k_tc_ozaki<TIn, TOut><<<(unsigned)grid, kThreads, 227 * 1024, st>>>(a);
   return cudaGetLastError();
 }
 
