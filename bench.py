@@ -336,13 +336,12 @@ def main():
     per_launch_s = top["ms"] * 1e-3 / top["launches"]
     achieved = top["flops"] / top["launches"] / per_launch_s
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["kernel"] == top["name"] else None
+    peaks, peak_src = measured_peaks()
     if top["name"] == "fd_mode_ozaki":
-        # BF16 tensor MMAs actually issued: 21 digit pairs x 2 x Q x npad x npad per launch
-        tc_flops = top["flops"] * 21.0 * (80.0 / 66.0) ** 2     # padded 66 -> 80 (K and N)
-        peaks, _src = measured_peaks()
-        peak = peaks.get("bf16_tflops", 1900.0) * 1e12
-        achieved_tc = tc_flops / top["launches"] / (top["ms"] * 1e-3 / top["launches"])
-        src = "BF16 dense tensor peak (MEASURED_PEAKS.json, %s); achieved counts the BF16 MMAs issued" % _src
+        # 21 exact BF16 digit-pair GEMMs need ~26 us of tensor time per launch at the
+        # BF16 peak, moving 16 B/dof needs ~43 us at the HBM peak: HBM bounds the ideal.
+        peak = peaks.get("hbm_gbs", 6800.0) * 1e9
+        src = "HBM copy bandwidth (MEASURED_PEAKS.json, %s); achieved = algorithmic bytes (16 B/dof) / time" % peak_src
     elif top["name"].endswith("_df"):
         # double-float kernels issue 12 FP32 instructions per FP64-equivalent FMA
         # (2 flop): peak = 128 FP32 lanes x SMs x clock x 2 / 12
@@ -352,15 +351,20 @@ def main():
         peak = 2 * 2 * sms * mhz * 1e6
         src = "FP64: 2 DFMA/clk/SM x %d SMs x %.0f MHz (sampled); DFMA probe in this run %.3f TFLOP/s" % (
             sms, mhz, probe / 1e12)
-    bound = "alu"
     if top["name"] == "fd_mode_ozaki":
-        bound = "tensor"
-        achieved = achieved_tc
-    roofline = {"bound": bound, "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": top["name"], "peak_source": src,
-                "fp64_equivalent_tflops": top["flops"] / top["launches"] / per_launch_s / 1e12,
-                "achieved_gbs": top["bytes"] / top["launches"] / per_launch_s / 1e9,
-                "share_of_step": top["ms"] / total_ms, "fp64_probe_tflops": probe / 1e12}
+        gbs = top["bytes"] / top["launches"] / per_launch_s
+        roofline = {"bound": "hbm", "achieved": gbs / 1e9, "peak": peak / 1e9, "unit": "GB/s",
+                    "frac": gbs / peak, "traffic": traffic, "kernel": top["name"], "peak_source": src,
+                    "fp64_equivalent_tflops": achieved / 1e12,
+                    "bf16_tensor_tflops": 21.0 * achieved / 1e12,
+                    "share_of_step": top["ms"] / total_ms, "fp64_probe_tflops": probe / 1e12}
+    else:
+        roofline = None
+    if roofline is None:
+        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": traffic, "kernel": top["name"], "peak_source": src,
+                    "achieved_gbs": top["bytes"] / top["launches"] / per_launch_s / 1e9,
+                    "share_of_step": top["ms"] / total_ms, "fp64_probe_tflops": probe / 1e12}
     kernels = {rc["name"]: {"launches": rc["launches"], "ms": round(rc["ms"], 3),
                             "share": round(rc["ms"] / total_ms, 4)} for rc in recs}
 

@@ -1,6 +1,6 @@
 """Small fixed workloads for Nsight Compute captures of one kernel family.
 
-  python -m paper_1909_07309_gb300.ncu_case {fd,matvec,solve} D P N_EL [REPS] [fp64|df32|tf32|bf16]
+  python -m paper_1909_07309_gb300.ncu_case {fd,matvec,solve} D P N_EL [REPS] [fp64|df32|fp64tc|tf32|bf16]
 
 Builds the unit-cube problem (d = D, degree P, N_EL elements per direction),
 runs one warm-up and REPS applications of fd_apply, st_matvec or the
@@ -18,7 +18,8 @@ def main(argv):
     what, d, p, n_el = argv[0], int(argv[1]), int(argv[2]), int(argv[3])
     reps = int(argv[4]) if len(argv) > 4 else 2
     arith = argv[5] if len(argv) > 5 else "fp64"
-    prec = {"fp64": stfd.STFD_FP64, "df32": stfd.STFD_DF32, "tf32": stfd.STFD_TF32, "bf16": stfd.STFD_BF16}[arith]
+    prec = {"fp64": stfd.STFD_FP64, "df32": stfd.STFD_DF32, "fp64tc": stfd.STFD_FP64TC,
+            "tf32": stfd.STFD_TF32, "bf16": stfd.STFD_BF16}[arith]
     K, M, Wt, Mt = stfd.heat_problem(d, p, n_el)
     P = stfd.FD(K, M, Wt, Mt, precision=prec)
     A = stfd.KronOp(K, M, Wt, Mt, arith=stfd.STFD_OP_FP64 if arith == "fp64" else stfd.STFD_OP_DF32)
