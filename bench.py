@@ -98,6 +98,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, world, device):
+    """Largest value over all ranks (the job's wall time is the slowest replica's)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(N, steps, world, ms):
+    """Whole-job dofs/s: every rank solved `steps` independent problems of N dofs."""
+    return N * steps * world / (ms * 1e-3)
+
+
 def build_workload(cfg):
     """Univariate factors from the library's own spline assembly and the RHS load."""
     from paper_1909_07309_gb300 import stfd
@@ -173,7 +188,7 @@ def reference_main(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--restart", type=int, default=100)
@@ -236,12 +251,8 @@ def main():
     barrier()
     clocks = sampler.stop()
     launches = stfd.stfd_launch_count() - launches0
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(t.item())
-    value = N * args.steps * world / (ms * 1e-3)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    value = job_throughput(N, args.steps, world, ms)
 
     # ---- end to end through the public API: pinned host f -> solve -> host u
     f_host = torch.from_numpy(f_np).pin_memory()

@@ -40,6 +40,15 @@ long long stfd_launch_count(void);
  * result is the denominator of an FP64-ALU roofline. Synchronous. */
 int stfd_probe_fp64_peak(double* flops_per_s, void* stream);
 
+/* Failure-detection self-test of the bounded device waits used by the
+ * tensor-core kernels: one thread initialises an mbarrier that nothing ever
+ * arrives on and waits on it for at most `max_iters` polls; when the wait gives
+ * up it sets the same device status flag the tensor-core kernels set and
+ * returns (no tensor core, tensor memory or other thread is involved). Read
+ * the flag with stfd_device_status(), which then reports STFD_ERR_TIMEOUT and
+ * clears it. 1 <= max_iters <= 1e6. Synchronous. */
+int stfd_probe_bounded_wait(int max_iters, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,6 +45,8 @@ cudaError_t launch_tc_mode(int kind, const void* X, int x_is_double, void* Y, in
                            const unsigned char* B, int n, long long inner, long long outer, cudaStream_t st);
 // Host: factor J (row-major n x n, J[i*n + a]) as a K-major canonical operand image.
 std::vector<unsigned char> tc_operand_image(const double* J, int n, int kind);
+// Self-test of the bounded mbarrier wait (never satisfied): sets the status flag.
+cudaError_t launch_probe_bounded_wait(int max_iters, cudaStream_t st);
 // Host: read and clear the device flag set when a bounded tensor-core wait gives up.
 int tc_status_read_and_clear(int* status);
 

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "kernels.h"
 #include "profile.h"
 #include "stfd.h"
 #include "stfd_profile.h"
@@ -149,6 +150,15 @@ extern "C" int stfd_profile_get(int idx, char* name, int name_cap, long long* la
 }
 
 extern "C" long long stfd_launch_count(void) { return g_launches.load(); }
+
+extern "C" int stfd_probe_bounded_wait(int max_iters, void* stream) {
+  if (max_iters < 1 || max_iters > 1000000) return STFD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  count_launch();
+  if (stfd::launch_probe_bounded_wait(max_iters, st) != cudaSuccess) return STFD_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return STFD_ERR_CUDA;
+  return STFD_OK;
+}
 
 extern "C" int stfd_probe_fp64_peak(double* flops_per_s, void* stream) {
   if (!flops_per_s) return STFD_ERR_ARG;

@@ -257,6 +257,22 @@ cudaError_t launch_tc_mode(int kind, const void* X, int x_is_double, void* Y, in
   return launch_impl<1, float, float>((const float*)X, (float*)Y, B, n, inner, outer, st);
 }
 
+namespace {
+// An mbarrier that expects one arrival which never comes: the bounded wait must
+// give up and raise the status flag.
+__global__ void k_probe_bounded_wait(int max_iters) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  tc::mbar_init(tc::smem_u32(&bar), 1);
+  if (!tc::mbar_wait(tc::smem_u32(&bar), 0, max_iters)) atomicExch(&g_tc_status, 1);
+}
+}  // namespace
+
+cudaError_t launch_probe_bounded_wait(int max_iters, cudaStream_t st) {
+  k_probe_bounded_wait<<<1, 32, 0, st>>>(max_iters);
+  return cudaGetLastError();
+}
+
 int tc_status_read_and_clear(int* status) {
   int zero = 0;
   if (cudaMemcpyFromSymbol(status, g_tc_status, sizeof(int)) != cudaSuccess) return -1;

@@ -82,6 +82,7 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_longlong), _c_dbl_p, _c_dbl_p, _c_dbl_p]),
     "stfd_launch_count": (ctypes.c_longlong, []),
     "stfd_probe_fp64_peak": (ctypes.c_int, [_c_dbl_p, ctypes.c_void_p]),
+    "stfd_probe_bounded_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p]),
 }
 
 
