@@ -173,7 +173,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   const uint32_t idesc = tc::instr_desc(1u, kTile, npad);
   const uint32_t a_addr = tc::smem_u32(sA), b_addr = tc::smem_u32(sB);
   const int ksteps = npad / 16;
+  // descriptor of the start of each operand; a byte offset o adds o >> 4 to the address field
+  const uint64_t da0 = tc::smem_desc(a_addr, 128u, sbo), db0 = tc::smem_desc(b_addr, 128u, sbo);
   uint32_t ph[2] = {0u, 0u};
+  const int nitems = kTile * nchunk;            // (row, 8-column chunk) digit items per plane
+  bool staged = false;                          // next tile already in flight (strided modes)
 
   auto wait_buf = [&](int b) {
     if (!tc::mbar_wait(tc::smem_u32(&mbar[b]), ph[b], kWaitIters)) *sflag = 1;
@@ -189,18 +193,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
       const long long o = q / inner;
       base = o * (long long)n * inner + (q - o * inner);
     }
-    // ---- stage the tile's raw 8-byte words (row r = tile column q), all copies in flight
+    // ---- stage the tile's raw 8-byte words (row r = tile column q), all copies in flight;
+    // in the strided modes the copies were issued during the previous tile's epilogue
     const long long* Xw = static_cast<const long long*>(args.X);
-    if (inner == 1) {
-      const long long* src = Xw + q0 * n;
-      const int cnt = rows * n;
-      for (int e = t; e < cnt; e += kThreads) {
-        const int rr = e / n;
-        tc::cp_async8(&sF[rr * ld + (e - rr * n)], src + e);
+    if (!staged) {
+      if (inner == 1) {
+        const long long* src = Xw + q0 * n;
+        const int cnt = rows * n;
+        for (int e = t; e < cnt; e += kThreads) {
+          const int rr = e / n;
+          tc::cp_async8(&sF[rr * ld + (e - rr * n)], src + e);
+        }
+      } else if (q < Q) {
+        for (int a = part; a < n; a += kParts) tc::cp_async8(&sF[r * ld + a], Xw + base + (long long)a * inner);
       }
-    } else if (q < Q) {
-      for (int a = part; a < n; a += kParts) tc::cp_async8(&sF[r * ld + a], Xw + base + (long long)a * inner);
     }
+    staged = false;
     tc::cp_async_wait_all();
     __syncthreads();
     // ---- row exponent (max over the four parts) and fixed-point conversion
@@ -211,31 +219,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
 #pragma unroll
     for (int pp = 0; pp < kParts; ++pp) E = max(E, sE[pp * kTile + r]);
     const int urow = DBL ? E - 1070 : E - 174;
-    for (int a = part; a < n; a += kParts) Frow[a] = (r < rows) ? to_fixed<DBL>(Frow[a], E) : 0;
+    // packed digit source: word0 = sign << 31 | bits 24..47 of |F|, word1 = bits 0..23
+    for (int a = part; a < n; a += kParts) {
+      const long long f = (r < rows) ? to_fixed<DBL>(Frow[a], E) : 0;
+      const unsigned long long m = (unsigned long long)(f < 0 ? -f : f);
+      const unsigned int w0 = (unsigned int)(m >> 24) | (f < 0 ? 0x80000000u : 0u);
+      const unsigned int w1 = (unsigned int)(m & 0xFFFFFFull);
+      Frow[a] = (long long)(((unsigned long long)w1 << 32) | w0);
+    }
     __syncthreads();
     // ---- digit planes k = 0..5 (double buffered) and their MMAs
+#pragma unroll
     for (int k = 0; k < kDig; ++k) {
       const int b = k & 1;
       if (k >= 2) wait_buf(b);
       unsigned char* A = sA + b * abytes;
-      const int shift = 40 - 8 * k;
-      for (int c8 = part; c8 < nchunk; c8 += kParts) {
+      const int sh = 16 - 8 * (k % 3);
+      // warp 0 issues the MMAs; the other 15 warps write the plane
+      for (int it = t - 32; it >= 0 && it < nitems; it += kThreads - 32) {
+        const int rr = it & (kTile - 1), c8 = it >> 7;
+        const long long* Fr = sF + rr * ld;
         const int a0 = 8 * c8;
         uint32_t w[4];
 #pragma unroll
         for (int tt = 0; tt < 4; ++tt) {
-          float v2[2];
+          uint32_t bits2[2];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int a = a0 + 2 * tt + h;
-            const long long f = a < n ? Frow[a] : 0;
-            const int dg = (int)(((f < 0 ? -f : f) >> shift) & 0xFF);
-            v2[h] = (float)(f < 0 ? -dg : dg);
+            const unsigned long long pw = a < n ? (unsigned long long)Fr[a] : 0ull;
+            const uint32_t w0 = (uint32_t)pw, w1 = (uint32_t)(pw >> 32);
+            const uint32_t dg = ((k < 3 ? w0 : w1) >> sh) & 0xFFu;
+            // exact float of the digit (0x4B000000 | d is 2^23 + d), signed; its top 16 bits are its BF16
+            const float fv = __int_as_float(0x4B000000u | dg) - 8388608.0f;
+            bits2[h] = (uint32_t)__float_as_int(fv) | (w0 & 0x80000000u);
           }
-          const __nv_bfloat162 pr = __floats2bfloat162_rn(v2[0], v2[1]);
-          w[tt] = *reinterpret_cast<const uint32_t*>(&pr);
+          w[tt] = __byte_perm(bits2[0], bits2[1], 0x7632);
         }
-        *reinterpret_cast<uint4*>(A + canon_off16(r, a0, kcores)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(A + canon_off16(rr, a0, kcores)) = make_uint4(w[0], w[1], w[2], w[3]);
       }
       tc::fence_async_smem();
       tc::fence_before_sync();
@@ -245,12 +266,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
         for (int l = 0; l + k < kDig; ++l) {
           const uint32_t dcol = tmem + (uint32_t)((k + l) * npad);
           for (int s = 0; s < ksteps; ++s) {
-            const uint64_t da = tc::smem_desc(a_addr + (uint32_t)(b * abytes) + s * 256, 128u, sbo);
-            const uint64_t db = tc::smem_desc(b_addr + (uint32_t)(l * plane) + s * 256, 128u, sbo);
+            const uint64_t da = da0 + (uint64_t)((b * abytes + s * 256) >> 4);
+            const uint64_t db = db0 + (uint64_t)((l * plane + s * 256) >> 4);
             tc::mma<0>(dcol, da, db, idesc, (k > 0 || s > 0) ? 1u : 0u);
           }
         }
         tc::mma_commit(tc::smem_u32(&mbar[b]));
+      }
+    }
+    // ---- strided modes: the staging buffer is free now, start the next tile's copies
+    {
+      const long long nt = tile + gridDim.x;
+      if (inner != 1 && nt < args.ntiles) {
+        const long long nq = nt * kTile + r;
+        if (nq < Q) {
+          const long long o = nq / inner;
+          const long long nbase = o * (long long)n * inner + (nq - o * inner);
+          for (int a = part; a < n; a += kParts) tc::cp_async8(&sF[r * ld + a], Xw + nbase + (long long)a * inner);
+        }
+        staged = true;
       }
     }
     wait_buf(0);   // commit of k = 4
@@ -271,9 +305,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
       for (int j = 0; j < 8; ++j) {
         const int i = 8 * c8 + j;
         if (i >= n || r >= rows) continue;
-        dfa::df s{0.f, 0.f};
+        // exact two-sums for the three leading diagonals; the trailing three sit
+        // below 2^-22 of the total and are summed in plain FP32 (error < 2^-46 of it)
+        float hi = T[0][j], lo = 0.f;
 #pragma unroll
-        for (int c = kDig - 1; c >= 0; --c) s = dfa::add(s, dfa::df{T[c][j] * pow2f(-8 * c), 0.f});
+        for (int c = 1; c < 3; ++c) {
+          const float v = T[c][j] * pow2f(-8 * c);
+          const float sm = hi + v, bp = sm - hi;
+          lo += (hi - (sm - bp)) + (v - bp);
+          hi = sm;
+        }
+        lo += fmaf(T[5][j], pow2f(-40), fmaf(T[4][j], pow2f(-32), T[3][j] * pow2f(-24)));
+        const dfa::df s = dfa::norm(dfa::df{hi, lo});
         int sc = urow + sv[i] + 80;
         sc = max(-250, min(250, sc));
         const float f1 = pow2f(sc / 2), f2 = pow2f(sc - sc / 2);
@@ -299,6 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
     tc::fence_before_sync();
     __syncthreads();
   }
+  tc::cp_async_wait_all();   // no copy may still target this CTA's shared memory at exit
   tc::fence_after_sync();
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
