@@ -133,6 +133,13 @@ struct stfd_op {
   float2* JK2[kMaxDim] = {nullptr, nullptr, nullptr};
   float2* JW2 = nullptr;
   float2* JMt2 = nullptr;
+  // band-compressed double-float factors Ab[i][t] = A[i][i-p+t] (when every p <= 4)
+  int pb[kMaxDim + 1] = {0, 0, 0, 0};
+  bool banded = false;
+  float2* Mb[kMaxDim] = {nullptr, nullptr, nullptr};
+  float2* Kb[kMaxDim] = {nullptr, nullptr, nullptr};
+  float2* Wb = nullptr;
+  float2* Mtb = nullptr;
 };
 
 extern "C" const char* stfd_strerror(int code) {
@@ -531,6 +538,12 @@ extern "C" void stfd_op_destroy(stfd_op* A) {
   }
   dev_free(A->JW2);
   dev_free(A->JMt2);
+  for (int l = 0; l < kMaxDim; ++l) {
+    dev_free(A->Mb[l]);
+    dev_free(A->Kb[l]);
+  }
+  dev_free(A->Wb);
+  dev_free(A->Mtb);
   for (int k = 0; k < 4; ++k) dev_free(A->tmp[k]);
   gmres_free(A->gw);
   delete A;
@@ -597,6 +610,30 @@ extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const dou
     }
     if (rc == STFD_OK) rc = split(keep[2 * d], &A->JW2);
     if (rc == STFD_OK) rc = split(keep[2 * d + 1], &A->JMt2);
+    // band-compressed copies for the unrolled kernels (half-bandwidth 1..4 in every direction)
+    A->banded = true;
+    for (int l = 0; l <= d; ++l) {
+      A->pb[l] = l < d ? std::max(A->bwM[l], A->bwK[l]) : std::max(A->bwW, A->bwMt);
+      if (A->pb[l] < 1 || A->pb[l] > 4) A->banded = false;
+    }
+    auto compress = [&](const std::vector<double>& J, int nl, int p, float2** dst) {
+      const int W = 2 * p + 1;
+      std::vector<double> band((size_t)nl * W, 0.0);
+      for (int i = 0; i < nl; ++i)
+        for (int t = 0; t < W; ++t) {
+          const int a = i - p + t;
+          if (a >= 0 && a < nl) band[(size_t)i * W + t] = J[(size_t)i * nl + a];
+        }
+      return split(band, dst);
+    };
+    if (A->banded) {
+      for (int l = 0; l < d && rc == STFD_OK; ++l) {
+        rc = compress(keep[2 * l], n[l], A->pb[l], &A->Mb[l]);
+        if (rc == STFD_OK) rc = compress(keep[2 * l + 1], n[l], A->pb[l], &A->Kb[l]);
+      }
+      if (rc == STFD_OK) rc = compress(keep[2 * d], n[d], A->pb[d], &A->Wb);
+      if (rc == STFD_OK) rc = compress(keep[2 * d + 1], n[d], A->pb[d], &A->Mtb);
+    }
   }
   if (rc == STFD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = STFD_ERR_CUDA;
   if (rc != STFD_OK) {
@@ -627,7 +664,13 @@ int matvec_one_df(const stfd_op* A, const double* x, double* y, cudaStream_t st)
     float2* uo = (l % 2 == 0) ? T[0] : T[2];
     float2* vo = (l % 2 == 0) ? T[1] : T[3];
     const int bw = std::max(A->bwM[l], A->bwK[l]);
-    if (l == 0) {
+    if (A->banded) {
+      if (l == 0) {
+        STFD_CU(launch_band_first_dfc(x, A->Mb[l], A->Kb[l], uo, vo, nl, inner, outer, A->pb[l], st));
+      } else {
+        STFD_CU(launch_band_mid_dfc(u, v, A->Mb[l], A->Kb[l], uo, vo, nl, inner, outer, A->pb[l], st));
+      }
+    } else if (l == 0) {
       STFD_CU(launch_band_first_df(x, A->JM2[l], A->JK2[l], uo, vo, nl, inner, outer, bw, st));
     } else {
       STFD_CU(launch_band_mid_df(u, v, A->JM2[l], A->JK2[l], uo, vo, nl, inner, outer, bw, st));
@@ -637,7 +680,11 @@ int matvec_one_df(const stfd_op* A, const double* x, double* y, cudaStream_t st)
     inner *= nl;
   }
   const int nt = A->n[d];
-  STFD_CU(launch_band_last_df(u, v, A->JW2, A->gamma, A->JMt2, A->nu, y, nt, inner, 1, std::max(A->bwW, A->bwMt), st));
+  if (A->banded) {
+    STFD_CU(launch_band_last_dfc(u, v, A->Wb, A->gamma, A->Mtb, A->nu, y, nt, inner, 1, A->pb[d], st));
+  } else {
+    STFD_CU(launch_band_last_df(u, v, A->JW2, A->gamma, A->JMt2, A->nu, y, nt, inner, 1, std::max(A->bwW, A->bwMt), st));
+  }
   return STFD_OK;
 }
 

@@ -77,6 +77,15 @@ cudaError_t launch_band_mid_df(const float2* u, const float2* v, const float2* M
 cudaError_t launch_band_last_df(const float2* u, const float2* v, const float2* W, double gamma, const float2* Mt,
                                 double nu, double* y, int n, long long inner, long long outer, int bw,
                                 cudaStream_t st);
+// Same passes with band-compressed factors Ab[i][t] = A[i][i-p+t], t < 2p+1, and a
+// compile-time half-bandwidth p in 1..4 (cudaErrorInvalidValue otherwise).
+cudaError_t launch_band_first_dfc(const double* x, const float2* Mb, const float2* Kb, float2* Uo, float2* Vo, int n,
+                                  long long inner, long long outer, int p, cudaStream_t st);
+cudaError_t launch_band_mid_dfc(const float2* u, const float2* v, const float2* Mb, const float2* Kb, float2* Uo,
+                                float2* Vo, int n, long long inner, long long outer, int p, cudaStream_t st);
+cudaError_t launch_band_last_dfc(const float2* u, const float2* v, const float2* Wb, double gamma, const float2* Mtb,
+                                 double nu, double* y, int n, long long inner, long long outer, int p,
+                                 cudaStream_t st);
 
 // Double-float Algorithm 1 (fd_df.cu): dense mode product with (hi, lo) row-major
 // factor J, X FP64 or float2, Y float2 or FP64 (not both FP64); Step 3 in place on
