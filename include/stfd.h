@@ -147,6 +147,14 @@ int stfd_fd_setup(stfd_fd** out, int d, const int* n,
  * not overlap. Calls on one handle must not overlap in time (shared scratch). */
 int stfd_fd_apply(const stfd_fd* h, const double* r_dev, double* s_dev, int nrhs, void* stream);
 
+/* s_dev = P^{-T} r_dev, the transposed preconditioner, as used by the adjoint
+ * solve. Not in the paper; it follows from its factorisation (Sec. 4.2-4.5):
+ * P^{-T} = (U_t (x) U_s) (gamma Delta_t^T (x) I + nu I (x) Lambda_s)^{-1}
+ * (U_t^T (x) U_s^T) with the same factors, and Delta_t^T is the arrowhead of
+ * the Remark in Sec. 4.5 with lambda_j and g negated (the Schur complement is
+ * unchanged). Arguments, precision and errors as stfd_fd_apply. */
+int stfd_fd_apply_transpose(const stfd_fd* h, const double* r_dev, double* s_dev, int nrhs, void* stream);
+
 /* Problem sizes of a handle: n[0..d] (array of d+1 ints) and *N_out. */
 int stfd_fd_shape(const stfd_fd* h, int* d_out, int* n, long long* N_out);
 
@@ -178,6 +186,11 @@ int stfd_op_create_kron(stfd_op** out, int d, const int* n,
  * overlap. Calls on one op must not overlap in time (shared scratch). */
 int stfd_st_matvec(const stfd_op* A, const double* x_dev, double* y_dev, int nrhs, void* stream);
 
+/* y_dev = A^T x_dev = (gamma W_t^T (x) M_s + nu M_t (x) K_s) x_dev (W_t is the
+ * only non-symmetric factor, eq. time_mat). Used by the adjoint solve; not in
+ * the paper. Arguments and errors as stfd_st_matvec. */
+int stfd_st_matvec_transpose(const stfd_op* A, const double* x_dev, double* y_dev, int nrhs, void* stream);
+
 void stfd_op_destroy(stfd_op* A);
 
 /* ------------------------------------------------------------------------
@@ -196,6 +209,8 @@ typedef struct {
   double tol;        /* relative residual target, default 1e-8 */
   int restart;       /* Krylov dimension per cycle, default 100 */
   int max_it;        /* total iterations, default 1000 */
+  int transpose;     /* 0: solve A u = f with P^{-1};  1: solve the adjoint
+                        A^T u = f with P^{-T} (default 0) */
 } stfd_gmres_opts;
 
 typedef struct {

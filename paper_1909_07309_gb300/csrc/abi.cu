@@ -123,6 +123,7 @@ struct stfd_op {
   double* JK[kMaxDim] = {nullptr, nullptr, nullptr};
   int bwM[kMaxDim] = {0, 0, 0}, bwK[kMaxDim] = {0, 0, 0};
   double* JW = nullptr;
+  double* JWT = nullptr;   // W_t^T, for A^T
   double* JMt = nullptr;
   int bwW = 0, bwMt = 0;
   double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -132,6 +133,7 @@ struct stfd_op {
   float2* JM2[kMaxDim] = {nullptr, nullptr, nullptr};
   float2* JK2[kMaxDim] = {nullptr, nullptr, nullptr};
   float2* JW2 = nullptr;
+  float2* JWT2 = nullptr;
   float2* JMt2 = nullptr;
   // band-compressed double-float factors Ab[i][t] = A[i][i-p+t] (when every p <= 4)
   int pb[kMaxDim + 1] = {0, 0, 0, 0};
@@ -139,6 +141,7 @@ struct stfd_op {
   float2* Mb[kMaxDim] = {nullptr, nullptr, nullptr};
   float2* Kb[kMaxDim] = {nullptr, nullptr, nullptr};
   float2* Wb = nullptr;
+  float2* WbT = nullptr;
   float2* Mtb = nullptr;
 };
 
@@ -372,7 +375,7 @@ namespace {
 
 // Low-precision Algorithm 1: tensor-core mode products with FP32 intermediates
 // held in the handle's scratch (two FP32 N-vectors in the FP64 work buffer).
-int fd_apply_one_lowp(const stfd_fd* h, const double* r, double* s, double* work, cudaStream_t st) {
+int fd_apply_one_lowp(const stfd_fd* h, const double* r, double* s, double* work, int trans, cudaStream_t st) {
   const int d = h->d;
   const int kind = h->precision == STFD_BF16 ? 0 : 1;
   float* buf[2] = {reinterpret_cast<float*>(work), reinterpret_cast<float*>(work) + h->N};
@@ -400,6 +403,7 @@ int fd_apply_one_lowp(const stfd_fd* h, const double* r, double* s, double* work
   ap.Sinv = h->Sinv_f;
   ap.gamma = (float)h->gamma;
   ap.nu = (float)h->nu;
+  ap.sgn = trans ? -1.0f : 1.0f;
   STFD_CU(launch_arrowhead_fp32(buf[cur], ap, st));
   for (int l = d; l >= 0; --l) {
     inner /= h->n[l];
@@ -415,7 +419,7 @@ int fd_apply_one_lowp(const stfd_fd* h, const double* r, double* s, double* work
 // Double-float Algorithm 1 (mode products in double-float on the FP32 pipes,
 // or on the tensor cores by exact digit slices): same pass structure as the
 // FP64 path, intermediates stored as float2 in the scratch and output buffers.
-int fd_apply_one_df(const stfd_fd* h, const double* r, double* s, double* work, cudaStream_t st) {
+int fd_apply_one_df(const stfd_fd* h, const double* r, double* s, double* work, int trans, cudaStream_t st) {
   const bool tc = h->precision == STFD_FP64TC;
   auto mode = [&](const void* X, int xd, int l, bool fwd, void* Y, int yd, long long inner, long long outer) {
     if (tc)
@@ -439,7 +443,7 @@ int fd_apply_one_df(const stfd_fd* h, const double* r, double* s, double* work, 
   const float2* lam[3] = {h->lam2[0], h->lam2[1], h->lam2[2]};
   STFD_CU(launch_arrowhead_df(static_cast<float2*>(const_cast<void*>(src)), d, h->n[0], d >= 2 ? h->n[1] : 1,
                               h->n[d], h->n_pairs, h->has_zero, h->Ns, lam, h->B2, h->BB2, h->G2, h->Sinv2, h->nu,
-                              st));
+                              trans ? -1 : 1, st));
   for (int l = d; l >= 0; --l) {
     inner /= h->n[l];
     const long long outer = h->N / (inner * h->n[l]);
@@ -450,10 +454,13 @@ int fd_apply_one_df(const stfd_fd* h, const double* r, double* s, double* work, 
   return STFD_OK;
 }
 
-// One right-hand side: s = P^{-1} r through 2(d+1) mode products and Step 3.
-int fd_apply_one(const stfd_fd* h, const double* r, double* s, double* work, cudaStream_t st) {
-  if (h->precision == STFD_DF32 || h->precision == STFD_FP64TC) return fd_apply_one_df(h, r, s, work, st);
-  if (h->precision != STFD_FP64) return fd_apply_one_lowp(h, r, s, work, st);
+// One right-hand side: s = P^{-1} r (trans = 0) or s = P^{-T} r (trans = 1)
+// through 2(d+1) mode products and Step 3. P^{-T} = (U_t x U_s) Delta^{-T}
+// (U_t x U_s)^T uses the same factors; only the arrowhead core is transposed,
+// which in the real 2 x 2-block form flips the signs of lambda_j and g.
+int fd_apply_one(const stfd_fd* h, const double* r, double* s, double* work, int trans, cudaStream_t st) {
+  if (h->precision == STFD_DF32 || h->precision == STFD_FP64TC) return fd_apply_one_df(h, r, s, work, trans, st);
+  if (h->precision != STFD_FP64) return fd_apply_one_lowp(h, r, s, work, trans, st);
   const int d = h->d;
   const int P = 2 * (d + 1);
   auto buf = [&](int k) { return ((P - k) % 2 == 0) ? s : work; };   // pass k writes buf(k), buf(P) = s
@@ -483,6 +490,7 @@ int fd_apply_one(const stfd_fd* h, const double* r, double* s, double* work, cud
   ap.Sinv = h->Sinv;
   ap.gamma = h->gamma;
   ap.nu = h->nu;
+  ap.sgn = trans ? -1.0 : 1.0;
   STFD_CU(launch_arrowhead_fp64(const_cast<double*>(src), ap, st));
   // Step 4: x_{d+1} U_t, then x_d U_d ... x_1 U_1
   for (int l = d; l >= 0; --l) {
@@ -497,15 +505,25 @@ int fd_apply_one(const stfd_fd* h, const double* r, double* s, double* work, cud
 
 }  // namespace
 
-extern "C" int stfd_fd_apply(const stfd_fd* h, const double* r, double* s, int nrhs, void* stream) {
+namespace {
+int fd_apply_batch(const stfd_fd* h, const double* r, double* s, int nrhs, int trans, void* stream) {
   if (!h || nrhs < 0 || (nrhs > 0 && (!r || !s))) return STFD_ERR_ARG;
   if (nrhs > 0 && r == s) return STFD_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   for (int k = 0; k < nrhs; ++k) {
-    const int rc = fd_apply_one(h, r + (size_t)k * h->N, s + (size_t)k * h->N, h->work, st);
+    const int rc = fd_apply_one(h, r + (size_t)k * h->N, s + (size_t)k * h->N, h->work, trans, st);
     if (rc != STFD_OK) return rc;
   }
   return STFD_OK;
+}
+}  // namespace
+
+extern "C" int stfd_fd_apply(const stfd_fd* h, const double* r, double* s, int nrhs, void* stream) {
+  return fd_apply_batch(h, r, s, nrhs, 0, stream);
+}
+
+extern "C" int stfd_fd_apply_transpose(const stfd_fd* h, const double* r, double* s, int nrhs, void* stream) {
+  return fd_apply_batch(h, r, s, nrhs, 1, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -531,18 +549,21 @@ extern "C" void stfd_op_destroy(stfd_op* A) {
     dev_free(A->JK[l]);
   }
   dev_free(A->JW);
+  dev_free(A->JWT);
   dev_free(A->JMt);
   for (int l = 0; l < kMaxDim; ++l) {
     dev_free(A->JM2[l]);
     dev_free(A->JK2[l]);
   }
   dev_free(A->JW2);
+  dev_free(A->JWT2);
   dev_free(A->JMt2);
   for (int l = 0; l < kMaxDim; ++l) {
     dev_free(A->Mb[l]);
     dev_free(A->Kb[l]);
   }
   dev_free(A->Wb);
+  dev_free(A->WbT);
   dev_free(A->Mtb);
   for (int k = 0; k < 4; ++k) dev_free(A->tmp[k]);
   gmres_free(A->gw);
@@ -592,6 +613,11 @@ extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const dou
     rc = dev_upload(&A->JMt, keep.back().data(), keep.back().size(), st);
     A->bwMt = bandwidth(n[d], Mt);
   }
+  // W_t^T row-major is W_t column-major read as rows: keep[2d + 2]
+  if (rc == STFD_OK) {
+    keep.emplace_back(Wt, Wt + (size_t)n[d] * n[d]);
+    rc = dev_upload(&A->JWT, keep.back().data(), keep.back().size(), st);
+  }
   for (int k = 0; k < 4 && rc == STFD_OK; ++k) rc = dev_upload<double>(&A->tmp[k], nullptr, (size_t)A->N, st);
   // double-float copies (hi, lo) of the row-major factors: keep = [M_0, K_0, M_1, K_1, ..., W_t, M_t]
   std::vector<std::vector<float2>> keep2;
@@ -610,6 +636,7 @@ extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const dou
     }
     if (rc == STFD_OK) rc = split(keep[2 * d], &A->JW2);
     if (rc == STFD_OK) rc = split(keep[2 * d + 1], &A->JMt2);
+    if (rc == STFD_OK) rc = split(keep[2 * d + 2], &A->JWT2);
     // band-compressed copies for the unrolled kernels (half-bandwidth 1..4 in every direction)
     A->banded = true;
     for (int l = 0; l <= d; ++l) {
@@ -632,6 +659,7 @@ extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const dou
         if (rc == STFD_OK) rc = compress(keep[2 * l + 1], n[l], A->pb[l], &A->Kb[l]);
       }
       if (rc == STFD_OK) rc = compress(keep[2 * d], n[d], A->pb[d], &A->Wb);
+      if (rc == STFD_OK) rc = compress(keep[2 * d + 2], n[d], A->pb[d], &A->WbT);
       if (rc == STFD_OK) rc = compress(keep[2 * d + 1], n[d], A->pb[d], &A->Mtb);
     }
   }
@@ -651,7 +679,7 @@ namespace {
 // (u, v) <- (u x_l M_l, u x_l K_l + v x_l M_l); time: y = gamma u x W_t + nu v x M_t.
 // Same sum-factorisation in double-float arithmetic, one pass per direction;
 // intermediates are float2 (hi, lo) pairs.
-int matvec_one_df(const stfd_op* A, const double* x, double* y, cudaStream_t st) {
+int matvec_one_df(const stfd_op* A, const double* x, double* y, int trans, cudaStream_t st) {
   const int d = A->d;
   float2* T[4];
   for (int k = 0; k < 4; ++k) T[k] = reinterpret_cast<float2*>(A->tmp[k]);
@@ -681,15 +709,18 @@ int matvec_one_df(const stfd_op* A, const double* x, double* y, cudaStream_t st)
   }
   const int nt = A->n[d];
   if (A->banded) {
-    STFD_CU(launch_band_last_dfc(u, v, A->Wb, A->gamma, A->Mtb, A->nu, y, nt, inner, 1, A->pb[d], st));
+    STFD_CU(launch_band_last_dfc(u, v, trans ? A->WbT : A->Wb, A->gamma, A->Mtb, A->nu, y, nt, inner, 1, A->pb[d],
+                                 st));
   } else {
-    STFD_CU(launch_band_last_df(u, v, A->JW2, A->gamma, A->JMt2, A->nu, y, nt, inner, 1, std::max(A->bwW, A->bwMt), st));
+    STFD_CU(launch_band_last_df(u, v, trans ? A->JWT2 : A->JW2, A->gamma, A->JMt2, A->nu, y, nt, inner, 1, std::max(A->bwW, A->bwMt), st));
   }
   return STFD_OK;
 }
 
-int matvec_one(const stfd_op* A, const double* x, double* y, cudaStream_t st) {
-  if (A->arith == STFD_OP_DF32) return matvec_one_df(A, x, y, st);
+// y = A x (trans = 0) or y = A^T x (trans = 1); A^T = gamma W_t^T x M_s + nu M_t x K_s
+// since every factor but W_t is symmetric.
+int matvec_one(const stfd_op* A, const double* x, double* y, int trans, cudaStream_t st) {
+  if (A->arith == STFD_OP_DF32) return matvec_one_df(A, x, y, trans, st);
   const int d = A->d;
   double* const* T = A->tmp;
   long long inner = 1;
@@ -713,22 +744,32 @@ int matvec_one(const stfd_op* A, const double* x, double* y, cudaStream_t st) {
     inner *= nl;
   }
   const int nt = A->n[d];
-  STFD_CU(launch_band_mode_fp64(u, A->JW, A->gamma, v, A->JMt, A->nu, y, nt, inner, 1,
+  STFD_CU(launch_band_mode_fp64(u, trans ? A->JWT : A->JW, A->gamma, v, A->JMt, A->nu, y, nt, inner, 1,
                            std::max(A->bwW, A->bwMt), st));
   return STFD_OK;
 }
 
 }  // namespace
 
-extern "C" int stfd_st_matvec(const stfd_op* A, const double* x, double* y, int nrhs, void* stream) {
+namespace {
+int matvec_batch(const stfd_op* A, const double* x, double* y, int nrhs, int trans, void* stream) {
   if (!A || nrhs < 0 || (nrhs > 0 && (!x || !y))) return STFD_ERR_ARG;
   if (nrhs > 0 && x == y) return STFD_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   for (int k = 0; k < nrhs; ++k) {
-    const int rc = matvec_one(A, x + (size_t)k * A->N, y + (size_t)k * A->N, st);
+    const int rc = matvec_one(A, x + (size_t)k * A->N, y + (size_t)k * A->N, trans, st);
     if (rc != STFD_OK) return rc;
   }
   return STFD_OK;
+}
+}  // namespace
+
+extern "C" int stfd_st_matvec(const stfd_op* A, const double* x, double* y, int nrhs, void* stream) {
+  return matvec_batch(A, x, y, nrhs, 0, stream);
+}
+
+extern "C" int stfd_st_matvec_transpose(const stfd_op* A, const double* x, double* y, int nrhs, void* stream) {
+  return matvec_batch(A, x, y, nrhs, 1, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -740,6 +781,7 @@ extern "C" void stfd_gmres_default_opts(stfd_gmres_opts* o) {
   o->tol = 1e-8;
   o->restart = 100;
   o->max_it = 1000;
+  o->transpose = 0;
 }
 
 namespace {
@@ -810,6 +852,8 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
   stfd_gmres_default_opts(&o);
   if (opts) o = *opts;
   if (o.restart < 1 || o.restart > 1000 || o.max_it < 1 || !(o.tol > 0.0)) return STFD_ERR_ARG;
+  if (o.transpose != 0 && o.transpose != 1) return STFD_ERR_ARG;
+  const int tr = o.transpose;
   stfd_op* A = const_cast<stfd_op*>(Ac);   // the Krylov workspace is cached in the op
   cudaStream_t st = (cudaStream_t)stream;
   if (!A->gw) {
@@ -839,7 +883,7 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
     if (u_is_zero) {
       STFD_CU(cudaMemcpyAsync(w->V[0], f, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     } else {
-      int r2 = matvec_one(A, u, w->V[1], st);
+      int r2 = matvec_one(A, u, w->V[1], tr, st);
       if (r2 != STFD_OK) return r2;
       STFD_CU(launch_sub(w->V[0], f, w->V[1], N, st));
     }
@@ -876,9 +920,9 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
     for (int j = 0; j < m && total < o.max_it; ++j) {
       if ((rc = ensure_vec(w->V, w->dV, j + 1, N)) != STFD_OK) return rc;
       if ((rc = ensure_vec(w->Z, w->dZ, j, N)) != STFD_OK) return rc;
-      // z_j = P^{-1} v_j ;  w = A z_j  (built in V[j+1])
-      if ((rc = fd_apply_one(P, w->V[j], w->Z[j], P->work, st)) != STFD_OK) return rc;
-      if ((rc = matvec_one(A, w->Z[j], w->V[j + 1], st)) != STFD_OK) return rc;
+      // z_j = P^{-1} v_j ;  w = A z_j  (built in V[j+1]); P^{-T}, A^T when transposed
+      if ((rc = fd_apply_one(P, w->V[j], w->Z[j], P->work, tr, st)) != STFD_OK) return rc;
+      if ((rc = matvec_one(A, w->Z[j], w->V[j + 1], tr, st)) != STFD_OK) return rc;
       // classical Gram-Schmidt twice: h = V^T w, w -= V h, h2 = V^T w, w -= V h2
       STFD_CU(launch_dot_multi(w->dV, j + 1, w->V[j + 1], N, w->partial, nb, st));
       STFD_CU(launch_reduce_partial(w->partial, j + 1, nb, dh, 0, st));

@@ -78,7 +78,7 @@ __global__ void k_arrowhead(T* __restrict__ X, ArrowParamsT<T> p) {
     }
     if (p.d >= 3) mu += p.lam[2][rest];
     const T a = p.nu * mu;
-    const T gam = p.gamma;
+    const T gam = p.gamma * p.sgn;   // transposed system: b_j -> -b_j, B_j -> -B_j
     T y = X[(long long)(p.nt - 1) * Ns + k];
     for (int j = 0; j < p.n_pairs; ++j) {
       const T x1 = X[(long long)(2 * j) * Ns + k], x2 = X[(long long)(2 * j + 1) * Ns + k];

@@ -32,6 +32,7 @@ struct ArrowParamsT {
   const T* g;        // nt - 1
   const T* Sinv;     // Ns reciprocals of the Schur complement
   T gamma, nu;
+  T sgn;             // +1: Delta_t;  -1: Delta_t^T (lam_j and g change sign)
 };
 using ArrowParams = ArrowParamsT<double>;
 cudaError_t launch_arrowhead_fp64(double* X, const ArrowParams& p, cudaStream_t st);
@@ -94,7 +95,7 @@ cudaError_t launch_fd_mode_df(const void* X, int x_is_double, const float2* J, v
                               long long inner, long long outer, cudaStream_t st);
 cudaError_t launch_arrowhead_df(float2* X, int d, int n1, int n2, int nt, int n_pairs, int has_zero, long long Ns,
                                 const float2* const* lam, const float2* B, const float2* BB, const float2* G,
-                                const float2* Sinv, double nu, cudaStream_t st);
+                                const float2* Sinv, double nu, int sgn, cudaStream_t st);
 
 // FP64-accurate mode product on tcgen05 by exact BF16 digit slices (tc_ozaki.cu):
 // X FP64 or float2, Y float2 or FP64 (not both FP64); B / v from ozaki_planes.

@@ -33,7 +33,8 @@ class StfdError(RuntimeError):
 
 
 class GmresOpts(ctypes.Structure):
-    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_it", ctypes.c_int)]
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_it", ctypes.c_int),
+                ("transpose", ctypes.c_int)]
 
 
 class GmresInfo(ctypes.Structure):
@@ -59,6 +60,8 @@ SIGNATURES = {
                                      ctypes.c_int, ctypes.c_void_p]),
     "stfd_fd_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.c_void_p]),
+    "stfd_fd_apply_transpose": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                               ctypes.c_void_p]),
     "stfd_fd_shape": (ctypes.c_int, [ctypes.c_void_p, _c_int_p, _c_int_p, ctypes.POINTER(ctypes.c_longlong)]),
     "stfd_fd_destroy": (None, [ctypes.c_void_p]),
     "stfd_op_create_kron": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _c_int_p, _c_dbl_pp,
@@ -66,6 +69,8 @@ SIGNATURES = {
                                            ctypes.c_int, ctypes.c_void_p]),
     "stfd_st_matvec": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                       ctypes.c_void_p]),
+    "stfd_st_matvec_transpose": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                ctypes.c_void_p]),
     "stfd_op_destroy": (None, [ctypes.c_void_p]),
     "stfd_gmres_default_opts": (None, [ctypes.POINTER(GmresOpts)]),
     "stfd_gmres_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -224,8 +229,8 @@ class FD:
                                int(precision), _stream(stream))
         _check(rc, "stfd_fd_setup")
 
-    def apply(self, r, s=None, stream=None):
-        """s = P^{-1} r for r of shape (N,) or (nrhs, N); returns s."""
+    def apply(self, r, s=None, stream=None, transpose=False):
+        """s = P^{-1} r (or P^{-T} r) for r of shape (N,) or (nrhs, N); returns s."""
         import torch
         if s is None:
             s = torch.empty_like(r)
@@ -233,7 +238,8 @@ class FD:
         sp, nrhs2 = _dev(s, self.N, "s")
         if nrhs != nrhs2:
             raise ValueError("r and s hold different numbers of right-hand sides")
-        _check(self._lib.stfd_fd_apply(self.handle, rp, sp, nrhs, _stream(stream)), "stfd_fd_apply")
+        name = "stfd_fd_apply_transpose" if transpose else "stfd_fd_apply"
+        _check(getattr(self._lib, name)(self.handle, rp, sp, nrhs, _stream(stream)), name)
         return s
 
     def close(self):
@@ -266,7 +272,8 @@ class KronOp:
                                      float(nu), int(arith), _stream(stream))
         _check(rc, "stfd_op_create_kron")
 
-    def matvec(self, x, y=None, stream=None):
+    def matvec(self, x, y=None, stream=None, transpose=False):
+        """y = A x (or A^T x) for x of shape (N,) or (nrhs, N); returns y."""
         import torch
         if y is None:
             y = torch.empty_like(x)
@@ -274,11 +281,14 @@ class KronOp:
         yp, nrhs2 = _dev(y, self.N, "y")
         if nrhs != nrhs2:
             raise ValueError("x and y hold different numbers of vectors")
-        _check(self._lib.stfd_st_matvec(self.handle, xp, yp, nrhs, _stream(stream)), "stfd_st_matvec")
+        name = "stfd_st_matvec_transpose" if transpose else "stfd_st_matvec"
+        _check(getattr(self._lib, name)(self.handle, xp, yp, nrhs, _stream(stream)), name)
         return y
 
-    def gmres(self, fd, f, u=None, tol=1e-8, restart=100, max_it=1000, hist_cap=1000, stream=None):
-        """Solve A u = f with FD-preconditioned flexible GMRES; returns (u, info dict)."""
+    def gmres(self, fd, f, u=None, tol=1e-8, restart=100, max_it=1000, hist_cap=1000, stream=None,
+              transpose=False):
+        """Solve A u = f (or the adjoint A^T u = f with P^{-T}) with FD-preconditioned
+        flexible GMRES; returns (u, info dict)."""
         import torch
         if u is None:
             u = torch.empty_like(f)
@@ -286,7 +296,7 @@ class KronOp:
         up, k2 = _dev(u, self.N, "u")
         if k1 != 1 or k2 != 1:
             raise ValueError("gmres solves one right-hand side")
-        opts = GmresOpts(float(tol), int(restart), int(max_it))
+        opts = GmresOpts(float(tol), int(restart), int(max_it), 1 if transpose else 0)
         hist = np.zeros(max(1, hist_cap))
         info = GmresInfo(0, 0, 0.0, 0.0, _dptr(hist), int(hist_cap), 0)
         rc = self._lib.stfd_gmres_solve(self.handle, fd.handle, fp, up, ctypes.byref(opts), ctypes.byref(info),
