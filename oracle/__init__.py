@@ -24,11 +24,19 @@ Sangalli, Tani) and cites the section / equation it restates:
   Givens rotations, zero initial guess (Sec. 4.5 and Sec. 5 set-up).
 * ``loads``    -- load vectors and point evaluation of discrete solutions for
   manufactured solutions (Sec. 3.1 linear form F).
+* ``geometry`` -- the exact NURBS quarter-annulus map and its Jacobian (the
+  domain of Sec. 5, extruded in 3D).
+* ``mapped``   -- spatial mass / stiffness matrices on a mapped domain with
+  variable coefficients (Sec. 4.6 and 4.6.1), the geometry-aware
+  preconditioner (eqs. separation, over_A, prec_geo) and the adjoint gradient
+  of a solution misfit (built from the paper's algebra; not in the paper).
 
 Pins (tests marked ``not gpu``) tie each function to facts the paper and the
 mathematics fix: partition of unity, closed-form uniform B-spline matrices,
 W_t + W_t^T = e_n e_n^T (eq. integral_W), Tables 1 and 3, the arrowhead
-identities of eq. time_eig_2, direct sparse solves, and a manufactured
-polynomial solution that lies in the spline space. No function here is
-"parity unpinned".
+identities of eq. time_eig_2, direct sparse solves, a manufactured
+polynomial solution that lies in the spline space, the area of the quarter
+annulus, the optimal L2 convergence rate of a manufactured solution on it,
+exact recovery of separable coefficient data, and central finite differences
+of the loss. No function here is "parity unpinned".
 """

@@ -1,0 +1,139 @@
+"""Pins of the oracle's mapped-domain matrices, geometry-aware preconditioner
+and adjoint gradient against the mathematics (Sec. 4.6, Sec. 5)."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import fd as ofd, geometry, mapped, matrices as omat
+from paper_1909_07309_gb300 import inputs
+
+
+def test_quarter_circle_is_exact():
+    t = np.linspace(0.0, 1.0, 101)
+    C, dC = geometry.quarter_circle(t)
+    assert np.max(np.abs(np.linalg.norm(C, axis=1) - 1.0)) <= 1e-15
+    ang = np.arctan2(C[:, 1], C[:, 0])
+    assert abs(ang[0]) <= 1e-15 and abs(ang[50] - np.pi / 4) <= 1e-15 and abs(ang[-1] - np.pi / 2) <= 1e-15
+    h = 1e-6
+    fd = (geometry.quarter_circle(t + h)[0] - geometry.quarter_circle(t - h)[0]) / (2 * h)
+    assert np.max(np.abs(fd - dC)) <= 1e-8
+    assert np.all(np.abs(np.sum(C * dC, axis=1)) <= 1e-14)          # C' is tangent
+
+
+@pytest.mark.parametrize("d,p,n_el", [(2, 2, 8), (2, 4, 3), (3, 2, 3)])
+def test_full_basis_area_and_constants(d, p, n_el):
+    """Partition of unity: sum of the full mass matrix = |Omega| = 3 pi / 4
+    (height 1 in 3D); stiffness annihilates constants."""
+    M, K = mapped.full_spatial_matrices(d, p, n_el, nq=p + 3)
+    assert abs(M.sum() - 0.75 * np.pi) <= 1e-12
+    assert np.max(np.abs(K.sum(axis=1))) <= 1e-12
+    assert np.max(np.abs(K - K.T)) <= 1e-13 and np.max(np.abs(M - M.T)) <= 1e-13
+
+
+@pytest.mark.parametrize("d,p,n_el", [(2, 3, 5), (3, 2, 3)])
+def test_box_geometry_reduces_to_kronecker(d, p, n_el):
+    """F = identity: M_s = M_d (x) .. (x) M_1 and K_s = sum_l M_d .. K_l .. M_1
+    from the (independently pinned) univariate matrices, eq. space_univ_par_mat."""
+    Ms, Ks = mapped.spatial_matrices(d, p, n_el, geom="box")
+    K1, M1 = omat.space_matrices(p, n_el)
+    Kk, Mk = mapped.kron_spatial([K1] * d, [M1] * d)
+    assert abs(Ms - Mk).max() <= 1e-15 and abs(Ks - Kk).max() <= 1e-14
+
+
+def test_manufactured_solution_converges_at_optimal_rate():
+    """u = t (r^2 - 1)(4 - r^2) x y on the quarter annulus with kappa = 1 + 0.5
+    sin(2 pi x) cos(2 pi y), c = 1 + 0.3 x y, f = c u_t - div(kappa grad u):
+    the L2(L2) error falls like h^{p+1} (Sec. 5.1, Fig. err_L2)."""
+    s = pytest.importorskip("sympy")
+    x, y, t = s.symbols("x y t")
+    kap = 1 + s.Rational(1, 2) * s.sin(2 * s.pi * x) * s.cos(2 * s.pi * y)
+    cc = 1 + s.Rational(3, 10) * x * y
+    u = t * (x ** 2 + y ** 2 - 1) * (4 - x ** 2 - y ** 2) * x * y
+    f = cc * s.diff(u, t) - s.diff(kap * s.diff(u, x), x) - s.diff(kap * s.diff(u, y), y)
+    fl, ul = s.lambdify((x, y, t), f, "numpy"), s.lambdify((x, y, t), u, "numpy")
+    kl, cl = s.lambdify((x, y), kap, "numpy"), s.lambdify((x, y), cc, "numpy")
+    F = lambda X, T: fl(X[..., 0], X[..., 1], T)
+    U = lambda X, T: ul(X[..., 0], X[..., 1], T) * np.ones_like(T)
+    p, errs = 2, []
+    for ne in (4, 8, 16):
+        Ms, Ks = mapped.spatial_matrices(2, p, ne, c=lambda X: cl(X[..., 0], X[..., 1]),
+                                         kappa=lambda X: kl(X[..., 0], X[..., 1]), nq=p + 3)
+        Wt, Mt = omat.time_matrices(p, ne, 1.0)
+        uh = spla.spsolve(mapped.space_time(Ms, Ks, Wt, Mt).tocsc(), mapped.load(2, p, ne, p, ne, F))
+        errs.append(mapped.l2_error(uh, 2, p, ne, p, ne, U))
+    rates = [errs[k] / errs[k + 1] for k in range(2)]
+    assert all(6.5 <= r <= 10.0 for r in rates), rates
+
+
+def test_separation_reproduces_separable_data():
+    """If diag(C) is exactly of the form of eq. separation, the fit returns it."""
+    d, n_el = 3, 5
+    g = np.random.default_rng(0)
+    phi = g.uniform(0.5, 2.0, (d, n_el))
+    Phi = g.uniform(0.5, 2.0, (d, n_el))
+    ids = mapped.element_ids(d, n_el)
+    C = np.zeros((d + 1, len(ids)))
+    for k, e in enumerate(ids):
+        pm = np.prod([phi[l, e[l]] for l in range(d)])
+        C[d, k] = pm
+        for l in range(d):
+            C[l, k] = pm / phi[l, e[l]] * Phi[l, e[l]]
+    ph, Ph = mapped.separate(C, d, n_el)
+    for k, e in enumerate(ids):
+        pm = np.prod([ph[l, e[l]] for l in range(d)])
+        assert abs(pm - C[d, k]) <= 1e-13 * C[d, k]
+        for l in range(d):
+            assert abs(pm / ph[l, e[l]] * Ph[l, e[l]] - C[l, k]) <= 1e-13 * C[l, k]
+
+
+def test_geometry_preconditioner_box_is_exact_and_diagonal_matches():
+    """Box, constant coefficients: A~ = A and D = I. Quarter annulus: diag of
+    D^{1/2} A~ D^{1/2} equals diag(A) (eq. prec_geo) and the oracle's FD
+    applied to the weighted factors inverts it (direct solve)."""
+    d, p, n_el = 2, 2, 5
+    Wt, Mt = omat.time_matrices(p, n_el, 1.0)
+    for geom in ("box", "quarter_annulus"):
+        kappa = (lambda X: 1 + 0.5 * np.sin(2 * np.pi * X[..., 0]) * np.cos(2 * np.pi * X[..., 1])) \
+            if geom != "box" else None
+        Ms, Ks = mapped.spatial_matrices(d, p, n_el, geom, kappa=kappa)
+        A = mapped.space_time(Ms, Ks, Wt, Mt)
+        Cd = mapped.coefficient_diagonal(d, n_el, geom, kappa=kappa)
+        phi, Phi = mapped.separate(Cd, d, n_el)
+        KM = [mapped.weighted_matrices(p, n_el, phi[l], Phi[l]) for l in range(d)]
+        Kl, Ml = [k for k, _ in KM], [m for _, m in KM]
+        Kt, Mtl = mapped.kron_spatial(Kl, Ml)
+        At = mapped.space_time(Mtl, Kt, Wt, Mt)
+        Dg = mapped.diag_scaling(A, At)
+        if geom == "box":
+            assert abs(At - A).max() <= 1e-13 and np.max(np.abs(Dg - 1)) <= 1e-13
+        PG = (np.sqrt(Dg)[:, None] * At.toarray()) * np.sqrt(Dg)[None, :]
+        assert np.max(np.abs(np.diag(PG) - A.diagonal())) <= 1e-13 * np.max(A.diagonal())
+        r = inputs.standard_normal(A.shape[0], seed=4)
+        s, _ = ofd.apply(ofd.setup(Kl, Ml, Wt, Mt), r / np.sqrt(Dg))
+        s = s / np.sqrt(Dg)
+        ref = np.linalg.solve(PG, r)
+        assert np.linalg.norm(s - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_adjoint_gradient_matches_central_differences():
+    """dL/dkappa_e and dL/df of the direct-solve loss against central
+    differences (h = 1e-6) on random directions."""
+    d, p, n_el = 2, 2, 4
+    g = np.random.default_rng(5)
+    n_e = n_el ** d
+    kap = g.uniform(0.5, 2.0, n_e)
+    n_s, n_t = n_el + p - 2, n_el + p - 1
+    f = g.standard_normal(n_s ** d * n_t)
+    _, u_obs, _, _ = mapped.loss_and_grads(kap * (1 + 0.1 * g.standard_normal(n_e)), f, np.zeros_like(f),
+                                           d, p, n_el, p, n_el)
+    L0, _, lam, dk = mapped.loss_and_grads(kap, f, u_obs, d, p, n_el, p, n_el)
+    h = 1e-6
+    for _ in range(4):
+        v = g.standard_normal(n_e)
+        Lp = mapped.loss_and_grads(kap + h * v, f, u_obs, d, p, n_el, p, n_el)[0]
+        Lm = mapped.loss_and_grads(kap - h * v, f, u_obs, d, p, n_el, p, n_el)[0]
+        assert abs((Lp - Lm) / (2 * h) - dk @ v) <= 1e-6 * max(abs(dk @ v), 1e-3 * np.linalg.norm(dk))
+        w = g.standard_normal(f.size)
+        Lp = mapped.loss_and_grads(kap, f + h * w, u_obs, d, p, n_el, p, n_el)[0]
+        Lm = mapped.loss_and_grads(kap, f - h * w, u_obs, d, p, n_el, p, n_el)[0]
+        assert abs((Lp - Lm) / (2 * h) - lam @ w) <= 1e-6 * max(abs(lam @ w), 1e-3 * np.linalg.norm(lam))
