@@ -229,6 +229,114 @@ int stfd_gmres_solve(const stfd_op* A, const stfd_fd* P, const double* f_dev, do
                      const stfd_gmres_opts* opts, stfd_gmres_info* info, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Mapped domains and variable coefficients (Sec. 4.6 and 4.6.1).
+ *
+ * With a geometry map F of the parametric box (0,1)^d and time-independent
+ * coefficients c(x) (heat capacity, gamma_s) and kappa(x) (conductivity,
+ * nu_s), the system is A = gamma W_t (x) M_s + nu M_t (x) K_s with general
+ * sparse spatial matrices (the parametric form of [A]_{ij} in Sec. 4.6):
+ *     [M_s]_{ij} = int c(F) B^_i B^_j |det J|,
+ *     [K_s]_{ij} = int kappa(F) grad^B^_i . J^{-1} J^{-T} grad^B^_j |det J|.
+ *
+ * Geometries (d = spatial dimension):
+ *   STFD_GEOM_BOX              F = identity on (0,1)^d.
+ *   STFD_GEOM_QUARTER_ANNULUS  F(eta) = (1 + eta_1) C(eta_2) [, eta_3], d in {2, 3}:
+ *                              the quarter of the annulus with radii 1 and 2
+ *                              (Sec. 5), C the exact rational quadratic (NURBS)
+ *                              quarter circle with control points (1,0), (1,1),
+ *                              (0,1) and weights 1, 1/sqrt(2), 1; extruded over
+ *                              (0,1) in the third direction when d = 3.
+ * The discrete space is the push-forward of the parametric splines (eq.
+ * disc_space): degree p, n_el uniform elements and maximal smoothness per
+ * direction, Dirichlet reduction in every direction (n_s = n_el + p - 2).
+ *
+ * Tensor-product stencil layout of a spatial matrix S (N_s x N_s with
+ * N_s = n_s^d): in a tensor-product spline space S[i][j] = 0 unless
+ * |i_l - j_l| <= p in every direction, so S is stored as (2p+1)^d arrays of
+ * N_s values,  st[o * N_s + i] = S[i][i + sum_l (o_l - p) n_s^(l-1)]  with
+ * o = sum_l o_l (2p+1)^(l-1), o_l in 0..2p (direction 1 fastest), and 0
+ * wherever that column lies outside the box.
+ *
+ * Quadrature: nq Gauss points per element and direction (nq >= p + 1).
+ * Points, elements and local functions are numbered colexicographically
+ * (direction 1 fastest); point k of element e is entry e * nq^d + k.
+ * ------------------------------------------------------------------------ */
+enum { STFD_GEOM_BOX = 0, STFD_GEOM_QUARTER_ANNULUS = 1 };
+
+/* Physical coordinates of the quadrature points (host): x[a * Q + k] for
+ * coordinate a < d and point k < Q = n_el^d nq^d. The caller evaluates c and
+ * kappa there for stfd_spatial_assemble. */
+int stfd_spatial_quadrature_points(int d, int p, int n_el, int geom, int nq, double* x);
+
+/* Physical coordinates of the element midpoints F((e + 1/2) / n_el) (host):
+ * x[a * n_el^d + e]. Coefficient values there feed stfd_geo_separate. */
+int stfd_spatial_element_midpoints(int d, int n_el, int geom, double* x);
+
+/* Assemble M_s and K_s (host, multi-threaded) in the stencil layout; c_q and
+ * kappa_q hold the coefficients at the Q quadrature points (NULL = 1). Ms and
+ * Ks (either may be NULL) receive (2p+1)^d * N_s doubles each. */
+int stfd_spatial_assemble(int d, int p, int n_el, int geom, int nq, const double* c_q, const double* kappa_q,
+                          double* Ms, double* Ks);
+
+/* Element stiffness matrices of unit conductivity (host): Ke receives n_el^d
+ * blocks of (p+1)^d x (p+1)^d doubles, block e holding K_e[a][b] at
+ * e * (p+1)^(2d) + a * (p+1)^d + b over the element's local functions
+ * (including those removed by the Dirichlet reduction), so that
+ * K_s = sum_e kappa_e K_e for a piecewise-constant conductivity. */
+int stfd_spatial_element_stiffness(int d, int p, int n_el, int geom, int nq, double* Ke);
+
+/* Separation of variables of eq. separation (host): the diagonal of the
+ * coefficient matrix frak{C} -- kappa |det J| [J^{-1} J^{-T}]_{ll} for l <= d
+ * and c |det J| -- is interpolated by its value at each element midpoint
+ * (c_mid, kappa_mid: coefficient values there, NULL = 1) and fitted by
+ *     C_{d+1} ~ phi_1 .. phi_d,   C_l ~ phi_1 .. Phi_l .. phi_d,
+ * by least squares in log space on the element grid (univariate factors from
+ * marginal means; the paper cites another work for its algorithm, this is the
+ * reading used here). phi, Phi receive d x n_el values (phi[l * n_el + k]).
+ * Returns STFD_ERR_ARG for non-positive data. */
+int stfd_geo_separate(int d, int n_el, int geom, const double* c_mid, const double* kappa_mid, double* phi,
+                      double* Phi);
+
+/* Weighted univariate matrices of eq. over_A (host):
+ * M[i,j] = int w_mass b_i b_j, K[i,j] = int w_stiff b'_i b'_j with weights
+ * constant per element (n_el values each, NULL = 1); otherwise as
+ * stfd_spline_matrices. */
+int stfd_spline_matrices_weighted(int p, int n_el, double length, int bc, const double* w_mass,
+                                  const double* w_stiff, double* M, double* K, int* n_out);
+
+/* System operator with general spatial matrices: Ms, Ks host arrays in the
+ * stencil layout with half-bandwidth p_s ((2p_s+1)^d * N_s doubles each),
+ * n[0..d-1] = n_s per direction, n[d] = n_t, Wt and Mt the column-major time
+ * factors. arith as stfd_op_create_kron (STFD_OP_DF32 keeps the coefficients
+ * and intermediates as double-float pairs). The op works with
+ * stfd_st_matvec, stfd_st_matvec_transpose (A^T: M_s and K_s are symmetric)
+ * and stfd_gmres_solve. Device memory: the two coefficient arrays and two
+ * N-vectors of scratch. */
+int stfd_op_create_stencil(stfd_op** out, int d, const int* n, int p_s, const double* Ms, const double* Ks,
+                           const double* Wt, const double* Mt, double gamma, double nu, int arith, void* stream);
+
+/* Diagonal scaling of the geometry-aware preconditioner (eq. prec_geo):
+ * after this call the handle applies P = D^{1/2} A~ D^{1/2}, where A~ is the
+ * operator of its univariate factors and D = diag(A) / diag(A~) per dof, from
+ * Ms_diag and Ks_diag (host, N_s each): the diagonals of the true spatial
+ * matrices of A. Both NULL removes the scaling. Part of the set-up: not to be
+ * called while an apply on the handle is in flight. Device memory: two
+ * N-vectors. Synchronises `stream`. */
+int stfd_fd_set_scaling(stfd_fd* h, const double* Ms_diag, const double* Ks_diag, void* stream);
+
+/* Gradient of a loss with respect to a piecewise-constant conductivity
+ * kappa_e (K_s = sum_e kappa_e K_e), not in the paper: with A u = f and the
+ * adjoint solution lam of A^T lam = dL/du,
+ *     g_e = dL/dkappa_e = -nu lam^T (M_t (x) K_e) u.
+ * Ke_dev: device copy of stfd_spatial_element_stiffness's output for the
+ * same (d, p, n_el); lam_dev, u_dev: device N-vectors; g_dev: device, n_el^d
+ * values. Requires n_s = n_el + p - 2 in every direction of A and
+ * (p+1)^(2d) doubles of shared memory per element (about 200 KiB at most).
+ * Uses the op's scratch: not concurrent with other calls on A. */
+int stfd_grad_kappa_elements(const stfd_op* A, int p, int n_el, const double* Ke_dev, const double* lam_dev,
+                             const double* u_dev, double* g_dev, void* stream);
+
+/* ------------------------------------------------------------------------
  * Allocation-free system matvec. The paper has no counterpart: this entry
  * point serves callers that must not allocate device memory -- for example a
  * host application that owns every byte of device memory through its own

@@ -304,20 +304,50 @@ def diag_scaling(A, Atil):
 # Adjoint gradient
 # ---------------------------------------------------------------------------
 
+def geometry_preconditioner(A, d, p, n_el, Wt, Mt, geom="quarter_annulus", c=None, kappa=None, kappa_elem=None,
+                            transpose=False):
+    """v -> (A^G)^{-1} v (or (A^G)^{-T} v) with A^G = D^{1/2} A~ D^{1/2} (eq. prec_geo),
+    A~^{-1} by the oracle's Algorithm 1 on the weighted univariate factors."""
+    from . import fd as ofd
+    Cd = coefficient_diagonal(d, n_el, geom, c=c, kappa=kappa, kappa_elem=kappa_elem)
+    phi, Phi = separate(Cd, d, n_el)
+    KM = [weighted_matrices(p, n_el, phi[l], Phi[l]) for l in range(d)]
+    Kl, Ml = [k for k, _ in KM], [m for _, m in KM]
+    Kt, Mtl = kron_spatial(Kl, Ml)
+    sq = np.sqrt(diag_scaling(A, space_time(Mtl, Kt, Wt, Mt)))
+    fac = ofd.setup(Kl, Ml, Wt.T.copy() if transpose else Wt, Mt)
+    return lambda v: ofd.apply(fac, v / sq)[0] / sq
+
+
 def loss_and_grads(kappa_elem, f, u_obs, d, p, n_el, p_t, n_el_t, geom="quarter_annulus", T=1.0, c=None,
-                   gamma=1.0, nu=1.0):
-    """L = 1/2 (u - u_obs)^T (M_t (x) M_s) (u - u_obs) with A(kappa) u = f, by
-    direct solves; returns (L, u, dL/df, dL/dkappa)."""
+                   gamma=1.0, nu=1.0, solver="direct", tol=1e-13):
+    """L = 1/2 (u - u_obs)^T (M_t (x) M_s) (u - u_obs) with A(kappa) u = f;
+    returns (L, u, dL/df, dL/dkappa). solver="direct": SuperLU; "gmres": the
+    oracle's GMRES with the geometry-aware preconditioner (for sizes where a
+    direct solve is too slow), to relative residual tol."""
     from .matrices import time_matrices
+    from . import gmres as ogm
     Ms, Ks, elems = spatial_matrices(d, p, n_el, geom, c=c, kappa_elem=kappa_elem, element_stiffness=True)
     Wt, Mt = time_matrices(p_t, n_el_t, T)
     A = space_time(Ms, Ks, Wt, Mt, gamma, nu)
-    u = spla.spsolve(A.tocsc(), f)
+    if solver == "direct":
+        lu = spla.splu(A.tocsc())
+        solve = lambda b, tr: lu.solve(b, trans="T" if tr else "N")
+    else:
+        pre = {tr: geometry_preconditioner(A, d, p, n_el, Wt, Mt, geom, c=c, kappa_elem=kappa_elem, transpose=tr)
+               for tr in (False, True)}
+        AT = A.T.tocsr()
+
+        def solve(b, tr):
+            x, info = ogm.gmres((lambda v: AT @ v) if tr else (lambda v: A @ v), pre[tr], b, tol=tol)
+            assert info["converged"]
+            return x
+    u = solve(f, False)
     Mst = sp.kron(sp.csr_matrix(Mt), Ms).tocsr()
     r = u - u_obs
     gu = Mst @ r
     L = 0.5 * float(r @ gu)
-    lam = spla.spsolve(A.T.tocsc(), gu)
+    lam = solve(gu, True)
     n_s = n_el + p - 2
     U = u.reshape(-1, n_s ** d)            # [time][space]
     Lm = lam.reshape(-1, n_s ** d)

@@ -100,6 +100,10 @@ struct stfd_fd {
   unsigned char* Zb[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};
   int* zvf[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};
   int* zvb[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};
+  // diagonals of the univariate factors (host), for the scaling of eq. prec_geo
+  std::vector<double> diagM[kMaxDim], diagK[kMaxDim], diagWt, diagMt;
+  double* dscale = nullptr;   // D^{-1/2} per dof (device), or nullptr
+  double* work2 = nullptr;    // scaled right-hand side
 };
 
 struct GmresWork {
@@ -143,6 +147,12 @@ struct stfd_op {
   float2* Wb = nullptr;
   float2* WbT = nullptr;
   float2* Mtb = nullptr;
+  // general spatial matrices (stfd_op_create_stencil)
+  int kind = 0;                                   // 0: Kronecker factors, 1: stencil
+  StencilOpDev sop;
+  void* sbuf[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* MtbU = nullptr;                         // band rows of M_t (unscaled, FP64) for gradients
+  int pt = 0;
 };
 
 extern "C" const char* stfd_strerror(int code) {
@@ -208,6 +218,8 @@ extern "C" void stfd_fd_destroy(stfd_fd* h) {
     dev_free(h->zvf[l]);
     dev_free(h->zvb[l]);
   }
+  dev_free(h->dscale);
+  dev_free(h->work2);
   delete h;
 }
 
@@ -244,6 +256,15 @@ extern "C" int stfd_fd_setup(stfd_fd** out, int d, const int* n, const double* c
   h->n_pairs = f.n_pairs;
   h->has_zero = f.has_zero;
   h->sigma = f.sigma;
+  for (int l = 0; l < d; ++l)
+    for (int i = 0; i < n[l]; ++i) {
+      h->diagM[l].push_back(M[l][i + (size_t)n[l] * i]);
+      h->diagK[l].push_back(K[l][i + (size_t)n[l] * i]);
+    }
+  for (int i = 0; i < n[d]; ++i) {
+    h->diagWt.push_back(Wt[i + (size_t)n[d] * i]);
+    h->diagMt.push_back(Mt[i + (size_t)n[d] * i]);
+  }
   // Step 2 uses J = U^T (row-major J[i][a] = U[a][i] = column-major U as is),
   // Step 4 uses J = U.
   std::vector<std::vector<double>> keep;
@@ -458,7 +479,7 @@ int fd_apply_one_df(const stfd_fd* h, const double* r, double* s, double* work, 
 // through 2(d+1) mode products and Step 3. P^{-T} = (U_t x U_s) Delta^{-T}
 // (U_t x U_s)^T uses the same factors; only the arrowhead core is transposed,
 // which in the real 2 x 2-block form flips the signs of lambda_j and g.
-int fd_apply_one(const stfd_fd* h, const double* r, double* s, double* work, int trans, cudaStream_t st) {
+int fd_apply_core(const stfd_fd* h, const double* r, double* s, double* work, int trans, cudaStream_t st) {
   if (h->precision == STFD_DF32 || h->precision == STFD_FP64TC) return fd_apply_one_df(h, r, s, work, trans, st);
   if (h->precision != STFD_FP64) return fd_apply_one_lowp(h, r, s, work, trans, st);
   const int d = h->d;
@@ -503,7 +524,70 @@ int fd_apply_one(const stfd_fd* h, const double* r, double* s, double* work, int
   return STFD_OK;
 }
 
+// With the diagonal scaling of eq. prec_geo, P = D^{1/2} A~ D^{1/2}, so
+// P^{-1} r = D^{-1/2} A~^{-1} (D^{-1/2} r) (and the same with A~^{-T}).
+int fd_apply_one(const stfd_fd* h, const double* r, double* s, double* work, int trans, cudaStream_t st) {
+  if (!h->dscale) return fd_apply_core(h, r, s, work, trans, st);
+  STFD_CU(launch_scale(r, h->dscale, h->work2, h->N, st));
+  const int rc = fd_apply_core(h, h->work2, s, work, trans, st);
+  if (rc != STFD_OK) return rc;
+  STFD_CU(launch_scale(s, h->dscale, s, h->N, st));
+  return STFD_OK;
+}
+
 }  // namespace
+
+extern "C" int stfd_fd_set_scaling(stfd_fd* h, const double* Ms_diag, const double* Ks_diag, void* stream) {
+  if (!h) return STFD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!Ms_diag && !Ks_diag) {
+    if (cudaStreamSynchronize(st) != cudaSuccess) return STFD_ERR_CUDA;
+    dev_free(h->dscale);
+    dev_free(h->work2);
+    h->dscale = h->work2 = nullptr;
+    return STFD_OK;
+  }
+  if (!Ms_diag || !Ks_diag) return STFD_ERR_ARG;
+  // D_(k,t) = (gamma w_t a_k + nu m_t b_k) / (gamma w_t a~_k + nu m_t b~_k) with a, b the
+  // diagonals of M_s, K_s and a~, b~ those of the Kronecker factors of the handle.
+  const int d = h->d;
+  std::vector<double> at((size_t)h->Ns), bt((size_t)h->Ns);
+  for (long long k = 0; k < h->Ns; ++k) {
+    long long rest = k;
+    int idx[kMaxDim];
+    for (int l = 0; l < d; ++l) {
+      idx[l] = (int)(rest % h->n[l]);
+      rest /= h->n[l];
+    }
+    double m = 1.0, kk = 0.0;
+    for (int l = 0; l < d; ++l) m *= h->diagM[l][idx[l]];
+    for (int l = 0; l < d; ++l) {
+      double t = h->diagK[l][idx[l]];
+      for (int q = 0; q < d; ++q)
+        if (q != l) t *= h->diagM[q][idx[q]];
+      kk += t;
+    }
+    at[k] = m;
+    bt[k] = kk;
+  }
+  std::vector<double> ds((size_t)h->N);
+  const int nt = h->n[d];
+  for (int t = 0; t < nt; ++t) {
+    const double w = h->gamma * h->diagWt[t], mt = h->nu * h->diagMt[t];
+    for (long long k = 0; k < h->Ns; ++k) {
+      const double num = w * Ms_diag[k] + mt * Ks_diag[k];
+      const double den = w * at[k] + mt * bt[k];
+      const double D = num / den;
+      if (!(D > 0.0) || !std::isfinite(D)) return STFD_ERR_ARG;
+      ds[(size_t)t * h->Ns + k] = 1.0 / std::sqrt(D);
+    }
+  }
+  if (!h->work2 && dev_upload<double>(&h->work2, nullptr, (size_t)h->N, st) != STFD_OK) return STFD_ERR_ALLOC;
+  if (!h->dscale && dev_upload<double>(&h->dscale, nullptr, (size_t)h->N, st) != STFD_OK) return STFD_ERR_ALLOC;
+  STFD_CU(cudaMemcpyAsync(h->dscale, ds.data(), ds.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (cudaStreamSynchronize(st) != cudaSuccess) return STFD_ERR_CUDA;
+  return STFD_OK;
+}
 
 namespace {
 int fd_apply_batch(const stfd_fd* h, const double* r, double* s, int nrhs, int trans, void* stream) {
@@ -566,6 +650,8 @@ extern "C" void stfd_op_destroy(stfd_op* A) {
   dev_free(A->WbT);
   dev_free(A->Mtb);
   for (int k = 0; k < 4; ++k) dev_free(A->tmp[k]);
+  for (int k = 0; k < 7; ++k) dev_free(A->sbuf[k]);
+  dev_free(A->MtbU);
   gmres_free(A->gw);
   delete A;
 }
@@ -619,6 +705,16 @@ extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const dou
     rc = dev_upload(&A->JWT, keep.back().data(), keep.back().size(), st);
   }
   for (int k = 0; k < 4 && rc == STFD_OK; ++k) rc = dev_upload<double>(&A->tmp[k], nullptr, (size_t)A->N, st);
+  if (rc == STFD_OK) {
+    A->pt = A->bwMt;
+    std::vector<double> MbU((size_t)n[d] * (2 * A->pt + 1), 0.0);
+    for (int t = 0; t < n[d]; ++t)
+      for (int k = 0; k <= 2 * A->pt; ++k) {
+        const int a = t - A->pt + k;
+        if (a >= 0 && a < n[d]) MbU[(size_t)t * (2 * A->pt + 1) + k] = Mt[t + (size_t)n[d] * a];
+      }
+    rc = dev_upload(&A->MtbU, MbU.data(), MbU.size(), st);
+  }
   // double-float copies (hi, lo) of the row-major factors: keep = [M_0, K_0, M_1, K_1, ..., W_t, M_t]
   std::vector<std::vector<float2>> keep2;
   if (rc == STFD_OK && arith == STFD_OP_DF32) {
@@ -674,6 +770,120 @@ extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const dou
 
 namespace {
 
+// Band rows B[t][k] = s * A[t][t - pb + k] of a column-major n x n matrix
+// (transposed if `trans`).
+std::vector<double> band_rows(int n, const double* A, int pb, double s, bool trans) {
+  const int W = 2 * pb + 1;
+  std::vector<double> B((size_t)n * W, 0.0);
+  for (int t = 0; t < n; ++t)
+    for (int k = 0; k < W; ++k) {
+      const int a = t - pb + k;
+      if (a < 0 || a >= n) continue;
+      B[(size_t)t * W + k] = s * (trans ? A[a + (size_t)n * t] : A[t + (size_t)n * a]);
+    }
+  return B;
+}
+
+}  // namespace
+
+extern "C" int stfd_op_create_stencil(stfd_op** out, int d, const int* n, int p_s, const double* Ms,
+                                      const double* Ks, const double* Wt, const double* Mt, double gamma, double nu,
+                                      int arith, void* stream) {
+  if (!out) return STFD_ERR_ARG;
+  *out = nullptr;
+  if (!sizes_ok(d, n) || !Ms || !Ks || !Wt || !Mt || p_s < 0 || p_s > 10) return STFD_ERR_ARG;
+  if (!std::isfinite(gamma) || !std::isfinite(nu)) return STFD_ERR_ARG;
+  if (arith != STFD_OP_FP64 && arith != STFD_OP_DF32) return STFD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  stfd_op* A = new (std::nothrow) stfd_op;
+  if (!A) return STFD_ERR_ALLOC;
+  A->kind = 1;
+  A->d = d;
+  A->arith = arith;
+  A->gamma = gamma;
+  A->nu = nu;
+  long long Ns = 1;
+  for (int l = 0; l < d; ++l) Ns *= n[l];
+  for (int l = 0; l <= d; ++l) A->n[l] = n[l];
+  const int nt = n[d];
+  A->N = Ns * nt;
+  int S = 1;
+  for (int l = 0; l < d; ++l) S *= 2 * p_s + 1;
+  const int pt = std::max(bandwidth(nt, Wt), bandwidth(nt, Mt));
+  A->pt = pt;
+  StencilOpDev& o = A->sop;
+  o.d = d;
+  o.p = p_s;
+  o.pt = pt;
+  o.nt = nt;
+  for (int l = 0; l < d; ++l) o.n[l] = n[l];
+  o.Ns = Ns;
+  o.df = arith == STFD_OP_DF32;
+  std::vector<double> Wb = band_rows(nt, Wt, pt, gamma, false), WbT = band_rows(nt, Wt, pt, gamma, true),
+                      Mb = band_rows(nt, Mt, pt, nu, false), MbU = band_rows(nt, Mt, pt, 1.0, false);
+  int rc = dev_upload(&A->MtbU, MbU.data(), MbU.size(), st);
+  const double* srcs[5] = {Ms, Ks, Wb.data(), WbT.data(), Mb.data()};
+  const size_t cnt[5] = {(size_t)S * Ns, (size_t)S * Ns, Wb.size(), WbT.size(), Mb.size()};
+  std::vector<std::vector<float2>> keep2;
+  for (int k = 0; k < 5 && rc == STFD_OK; ++k) {
+    if (o.df) {
+      keep2.emplace_back(cnt[k]);
+      for (size_t i = 0; i < cnt[k]; ++i) {
+        const float h = (float)srcs[k][i];
+        keep2.back()[i] = make_float2(h, (float)(srcs[k][i] - (double)h));
+      }
+      float2* dst = nullptr;
+      rc = dev_upload(&dst, keep2.back().data(), cnt[k], st);
+      A->sbuf[k] = dst;
+    } else {
+      double* dst = nullptr;
+      rc = dev_upload(&dst, srcs[k], cnt[k], st);
+      A->sbuf[k] = dst;
+    }
+  }
+  for (int k = 5; k < 7 && rc == STFD_OK; ++k) {
+    double* dst = nullptr;   // float2 and double have the same size
+    rc = dev_upload<double>(&dst, nullptr, (size_t)A->N, st);
+    A->sbuf[k] = dst;
+  }
+  if (rc == STFD_OK) {
+    o.Ms = A->sbuf[0];
+    o.Ks = A->sbuf[1];
+    o.Wb = A->sbuf[2];
+    o.WbT = A->sbuf[3];
+    o.Mtb = A->sbuf[4];
+    o.Z1 = A->sbuf[5];
+    o.Z2 = A->sbuf[6];
+  }
+  if (rc == STFD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = STFD_ERR_CUDA;
+  if (rc != STFD_OK) {
+    stfd_op_destroy(A);
+    return rc;
+  }
+  *out = A;
+  return STFD_OK;
+}
+
+extern "C" int stfd_grad_kappa_elements(const stfd_op* A, int p, int n_el, const double* Ke_dev,
+                                        const double* lam_dev, const double* u_dev, double* g_dev, void* stream) {
+  if (!A || !Ke_dev || !lam_dev || !u_dev || !g_dev || p < 1 || n_el < 1) return STFD_ERR_ARG;
+  const int d = A->d;
+  for (int l = 0; l < d; ++l)
+    if (A->n[l] != n_el + p - 2) return STFD_ERR_ARG;
+  if (grad_elements_smem(d, p) > 200 * 1024) return STFD_ERR_ARG;
+  if (!A->MtbU) return STFD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  long long Ns = A->N / A->n[d];
+  // ubar = (M_t (x) I) u in the op's scratch (two N-vectors of 8-byte entries)
+  double* ubar = A->kind == 1 ? static_cast<double*>(A->sbuf[5]) : A->tmp[0];
+  double* dup = A->kind == 1 ? static_cast<double*>(A->sbuf[6]) : A->tmp[1];
+  STFD_CU(launch_time_mass_fp64(u_dev, A->MtbU, ubar, dup, Ns, A->n[d], A->pt, st));
+  STFD_CU(launch_grad_elements(Ke_dev, lam_dev, ubar, g_dev, d, p, n_el, n_el + p - 2, Ns, A->n[d], A->nu, st));
+  return STFD_OK;
+}
+
+namespace {
+
 // y = gamma (W_t x M_d x..x M_1) x + nu (M_t x sum_l M_d..K_l..M_1) x, sum-factorised:
 // direction 1: (u, v) = (x x_1 M_1, x x_1 K_1); direction l > 1:
 // (u, v) <- (u x_l M_l, u x_l K_l + v x_l M_l); time: y = gamma u x W_t + nu v x M_t.
@@ -720,6 +930,10 @@ int matvec_one_df(const stfd_op* A, const double* x, double* y, int trans, cudaS
 // y = A x (trans = 0) or y = A^T x (trans = 1); A^T = gamma W_t^T x M_s + nu M_t x K_s
 // since every factor but W_t is symmetric.
 int matvec_one(const stfd_op* A, const double* x, double* y, int trans, cudaStream_t st) {
+  if (A->kind == 1) {
+    STFD_CU(launch_stencil_matvec(A->sop, x, y, trans, st));
+    return STFD_OK;
+  }
   if (A->arith == STFD_OP_DF32) return matvec_one_df(A, x, y, trans, st);
   const int d = A->d;
   double* const* T = A->tmp;

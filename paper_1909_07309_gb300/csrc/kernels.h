@@ -106,4 +106,27 @@ int ozaki_max_n();
 
 int dot_blocks();
 
+// General spatial matrices in the tensor-product stencil layout (stencil.cu).
+struct StencilOpDev {
+  int d = 0, p = 0, pt = 0, nt = 0;
+  int n[3] = {1, 1, 1};
+  long long Ns = 0;
+  bool df = false;                    // coefficients and intermediates as (hi, lo) float pairs
+  const void* Ms = nullptr;           // [(2p+1)^d][Ns] double or float2
+  const void* Ks = nullptr;
+  const void* Wb = nullptr;           // gamma W_t, band rows [nt][2pt+1]
+  const void* WbT = nullptr;          // gamma W_t^T
+  const void* Mtb = nullptr;          // nu M_t
+  void* Z1 = nullptr;                 // scratch nt * Ns
+  void* Z2 = nullptr;
+};
+cudaError_t launch_stencil_matvec(const StencilOpDev& op, const double* x, double* y, int trans, cudaStream_t st);
+size_t grad_elements_smem(int d, int p);
+cudaError_t launch_grad_elements(const double* Ke, const double* lam, const double* ubar, double* g, int d, int p,
+                                 int n_el, int n_s, long long Ns, int nt, double nu, cudaStream_t st);
+cudaError_t launch_scale(const double* x, const double* s, double* y, long long N, cudaStream_t st);
+// y = (M_t (x) I) x with the band rows Mb [nt][2pt+1] (FP64); `scratch` receives a copy.
+cudaError_t launch_time_mass_fp64(const double* x, const double* Mb, double* y, double* scratch, long long Ns, int nt,
+                                  int pt, cudaStream_t st);
+
 }  // namespace stfd

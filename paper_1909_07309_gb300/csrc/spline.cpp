@@ -82,7 +82,7 @@ static void span_values(const std::vector<double>& kv, int k, int deg, double x,
 }
 
 // Values and first derivatives of b_{k-p..k} at x in span k.
-static void span_values_derivs(const std::vector<double>& kv, int k, int p, double x,
+void span_values_derivs(const std::vector<double>& kv, int k, int p, double x,
                                double* N, double* dN) {
   span_values(kv, k, p, x, N);
   if (p == 0) { dN[0] = 0.0; return; }

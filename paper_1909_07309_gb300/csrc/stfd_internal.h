@@ -10,6 +10,8 @@ constexpr int kMaxN = 256;       // largest univariate size n_l / n_t
 
 std::vector<double> open_knots(int p, int n_el, double L);
 void gauss_legendre(int nq, std::vector<double>& x, std::vector<double>& w);
+// Values N[0..p] and derivatives dN[0..p] of b_{k-p..k} at x in knot span k.
+void span_values_derivs(const std::vector<double>& kv, int k, int p, double x, double* N, double* dN);
 
 // Host factorisation of Step 1 of Algorithm 1 (real form). Column-major.
 struct HostFactors {

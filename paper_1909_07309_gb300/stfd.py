@@ -19,6 +19,7 @@ STFD_FP64, STFD_TF32, STFD_BF16, STFD_DF32, STFD_FP64TC = 0, 1, 2, 3, 4
 STFD_BC_NONE, STFD_BC_INITIAL, STFD_BC_DIRICHLET = 0, 1, 2
 STFD_NOALLOC_MAX_N = 524288
 STFD_OP_FP64, STFD_OP_DF32 = 0, 1
+STFD_GEOM_BOX, STFD_GEOM_QUARTER_ANNULUS = 0, 1
 
 _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_dbl_p = ctypes.POINTER(ctypes.c_double)
@@ -79,6 +80,23 @@ SIGNATURES = {
                                               ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p,
                                               _c_int_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p]),
+    "stfd_spatial_quadrature_points": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                      ctypes.c_int, _c_dbl_p]),
+    "stfd_spatial_element_midpoints": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_dbl_p]),
+    "stfd_spatial_assemble": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p]),
+    "stfd_spatial_element_stiffness": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                      ctypes.c_int, _c_dbl_p]),
+    "stfd_geo_separate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_dbl_p, _c_dbl_p, _c_dbl_p,
+                                         _c_dbl_p]),
+    "stfd_spline_matrices_weighted": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                                     _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_int_p]),
+    "stfd_op_create_stencil": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _c_int_p, ctypes.c_int,
+                                              _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
+    "stfd_fd_set_scaling": (ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, _c_dbl_p, ctypes.c_void_p]),
+    "stfd_grad_kappa_elements": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     # include/stfd_profile.h
     "stfd_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "stfd_profile_reset": (ctypes.c_int, []),
@@ -242,6 +260,19 @@ class FD:
         _check(getattr(self._lib, name)(self.handle, rp, sp, nrhs, _stream(stream)), name)
         return s
 
+    def set_scaling(self, Ms_diag, Ks_diag, stream=None):
+        """Diagonal scaling of eq. prec_geo from the diagonals of the true M_s, K_s
+        (host arrays of N_s); None, None removes it."""
+        if Ms_diag is None and Ks_diag is None:
+            rc = self._lib.stfd_fd_set_scaling(self.handle, None, None, _stream(stream))
+        else:
+            a = np.ascontiguousarray(Ms_diag, dtype=np.float64)
+            b = np.ascontiguousarray(Ks_diag, dtype=np.float64)
+            if a.size * self.n[-1] != self.N or b.size != a.size:
+                raise ValueError("diagonals must hold N_s entries")
+            rc = self._lib.stfd_fd_set_scaling(self.handle, _dptr(a), _dptr(b), _stream(stream))
+        _check(rc, "stfd_fd_set_scaling")
+
     def close(self):
         if self.handle:
             self._lib.stfd_fd_destroy(self.handle)
@@ -254,7 +285,29 @@ class FD:
             pass
 
 
-class KronOp:
+class _Op:
+    """Common part of the system operator handles: matvec, GMRES, gradient."""
+
+    def grad_kappa_elements(self, p, n_el, Ke_dev, lam, u, g=None, stream=None):
+        """g_e = -nu lam^T (M_t kron K_e) u per element (``stfd_grad_kappa_elements``)."""
+        import torch
+        if g is None:
+            g = torch.empty(n_el ** self.d, dtype=torch.float64, device=u.device)
+        lp, k1 = _dev(lam, self.N, "lam")
+        up, k2 = _dev(u, self.N, "u")
+        if k1 != 1 or k2 != 1 or g.numel() != n_el ** self.d or not g.is_contiguous():
+            raise ValueError("one adjoint / state vector and n_el^d outputs")
+        if Ke_dev.dtype != torch.float64 or not Ke_dev.is_cuda or not Ke_dev.is_contiguous():
+            raise TypeError("Ke must be a contiguous float64 CUDA tensor")
+        if Ke_dev.numel() != n_el ** self.d * (p + 1) ** (2 * self.d):
+            raise ValueError("Ke must hold n_el^d blocks of (p+1)^d x (p+1)^d values")
+        _check(self._lib.stfd_grad_kappa_elements(self.handle, int(p), int(n_el), ctypes.c_void_p(Ke_dev.data_ptr()),
+                                                  lp, up, ctypes.c_void_p(g.data_ptr()), _stream(stream)),
+               "stfd_grad_kappa_elements")
+        return g
+
+
+class KronOp(_Op):
     """System operator handle: ``stfd_op_create_kron`` / ``stfd_st_matvec`` / ``stfd_gmres_solve``."""
 
     def __init__(self, K, M, Wt, Mt, gamma=1.0, nu=1.0, arith=STFD_OP_FP64, stream=None):
@@ -315,6 +368,156 @@ class KronOp:
             self.close()
         except Exception:
             pass
+
+
+class StencilOp(KronOp):
+    """System operator with general spatial matrices in the stencil layout
+    (``stfd_op_create_stencil``); matvec / transpose / GMRES as KronOp."""
+
+    def __init__(self, n, p_s, Ms, Ks, Wt, Mt, gamma=1.0, nu=1.0, arith=STFD_OP_DF32, stream=None):
+        lib = load()
+        self._lib = lib
+        self.handle = ctypes.c_void_p()
+        Wt, Mt = _f64(Wt), _f64(Mt)
+        self.n = [int(v) for v in n]
+        self.d = len(self.n) - 1
+        self.N = int(np.prod(self.n))
+        Ns = self.N // self.n[-1]
+        Ms = np.ascontiguousarray(Ms, dtype=np.float64)
+        Ks = np.ascontiguousarray(Ks, dtype=np.float64)
+        if Ms.size != (2 * p_s + 1) ** self.d * Ns or Ks.size != Ms.size:
+            raise ValueError("stencil arrays must hold (2p+1)^d * N_s values")
+        rc = lib.stfd_op_create_stencil(ctypes.byref(self.handle), self.d, (ctypes.c_int * (self.d + 1))(*self.n),
+                                        int(p_s), _dptr(Ms), _dptr(Ks), _dptr(Wt), _dptr(Mt), float(gamma),
+                                        float(nu), int(arith), _stream(stream))
+        _check(rc, "stfd_op_create_stencil")
+
+
+# ---------------------------------------------------------------------------
+# mapped domains (Sec. 4.6): host assembly and separation
+# ---------------------------------------------------------------------------
+
+def spatial_quadrature_points(d, p, n_el, geom, nq):
+    """Physical quadrature points, shape (d, n_el^d nq^d)."""
+    x = np.zeros((d, (n_el * nq) ** d))
+    _check(load().stfd_spatial_quadrature_points(d, p, n_el, geom, nq, _dptr(x)), "stfd_spatial_quadrature_points")
+    return x
+
+
+def spatial_element_midpoints(d, n_el, geom):
+    x = np.zeros((d, n_el ** d))
+    _check(load().stfd_spatial_element_midpoints(d, n_el, geom, _dptr(x)), "stfd_spatial_element_midpoints")
+    return x
+
+
+def _opt(a, size, what):
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != size:
+        raise ValueError("%s must hold %d values" % (what, size))
+    return a, _dptr(a)
+
+
+def spatial_assemble(d, p, n_el, geom, nq, c_q=None, kappa_q=None):
+    """(M_s, K_s) in the stencil layout, shape ((2p+1)^d, N_s) each."""
+    Q = (n_el * nq) ** d
+    c_keep, cp = _opt(c_q, Q, "c_q")
+    k_keep, kp = _opt(kappa_q, Q, "kappa_q")
+    Ns = (n_el + p - 2) ** d
+    S = (2 * p + 1) ** d
+    Ms = np.zeros((S, Ns))
+    Ks = np.zeros((S, Ns))
+    _check(load().stfd_spatial_assemble(d, p, n_el, geom, nq, cp, kp, _dptr(Ms), _dptr(Ks)), "stfd_spatial_assemble")
+    return Ms, Ks
+
+
+def spatial_element_stiffness(d, p, n_el, geom, nq):
+    """Unit-conductivity element stiffness, shape (n_el^d, (p+1)^d, (p+1)^d)."""
+    L = (p + 1) ** d
+    Ke = np.zeros((n_el ** d, L, L))
+    _check(load().stfd_spatial_element_stiffness(d, p, n_el, geom, nq, _dptr(Ke)), "stfd_spatial_element_stiffness")
+    return Ke
+
+
+def geo_separate(d, n_el, geom, c_mid=None, kappa_mid=None):
+    """(phi, Phi), each (d, n_el): eq. separation on the element grid."""
+    c_keep, cp = _opt(c_mid, n_el ** d, "c_mid")
+    k_keep, kp = _opt(kappa_mid, n_el ** d, "kappa_mid")
+    phi = np.zeros((d, n_el))
+    Phi = np.zeros((d, n_el))
+    _check(load().stfd_geo_separate(d, n_el, geom, cp, kp, _dptr(phi), _dptr(Phi)), "stfd_geo_separate")
+    return phi, Phi
+
+
+def spline_matrices_weighted(p, n_el, length, bc, w_mass=None, w_stiff=None):
+    """(M, K) with per-element weights (eq. over_A), column-major n x n."""
+    lib = load()
+    n = ctypes.c_int(0)
+    _check(lib.stfd_spline_matrices_weighted(p, n_el, float(length), bc, None, None, None, None, ctypes.byref(n)),
+           "stfd_spline_matrices_weighted")
+    wm_keep, wm = _opt(w_mass, n_el, "w_mass")
+    ws_keep, ws = _opt(w_stiff, n_el, "w_stiff")
+    M = np.zeros((n.value, n.value), order="F")
+    K = np.zeros((n.value, n.value), order="F")
+    _check(lib.stfd_spline_matrices_weighted(p, n_el, float(length), bc, wm, ws, _dptr(M), _dptr(K),
+                                             ctypes.byref(n)), "stfd_spline_matrices_weighted")
+    return M, K
+
+
+def stencil_center(p, d):
+    """Offset index of the diagonal in the stencil layout."""
+    return sum(p * (2 * p + 1) ** l for l in range(d))
+
+
+def _eval_coef(f, x, size):
+    if f is None:
+        return None
+    if callable(f):
+        return np.asarray(f(x), dtype=np.float64).reshape(size)
+    return np.asarray(f, dtype=np.float64).reshape(size)
+
+
+def mapped_problem(d, p, n_el, geom=STFD_GEOM_QUARTER_ANNULUS, c=None, kappa=None, kappa_elem=None, nq=None,
+                   T=1.0):
+    """Host data of the heat problem on a mapped domain (Sec. 4.6.1): stencil
+    M_s, K_s, time factors, and the univariate factors of the geometry-aware
+    preconditioner. c, kappa: callables of physical points x with x.shape ==
+    (d, m) returning m values (None = 1); kappa_elem: per-element conductivity
+    (overrides kappa)."""
+    nq = p + 1 if nq is None else nq
+    Q = (n_el * nq) ** d
+    xq = spatial_quadrature_points(d, p, n_el, geom, nq) if (c is not None or kappa is not None) else None
+    xm = spatial_element_midpoints(d, n_el, geom)
+    c_q = _eval_coef(c, xq, Q) if c is not None else None
+    if kappa_elem is not None:
+        kappa_elem = np.asarray(kappa_elem, dtype=np.float64).reshape(n_el ** d)
+        kappa_q = np.repeat(kappa_elem, nq ** d)
+        kappa_mid = kappa_elem
+    else:
+        kappa_q = _eval_coef(kappa, xq, Q) if kappa is not None else None
+        kappa_mid = _eval_coef(kappa, xm, n_el ** d) if kappa is not None else None
+    c_mid = _eval_coef(c, xm, n_el ** d) if c is not None else None
+    Ms, Ks = spatial_assemble(d, p, n_el, geom, nq, c_q, kappa_q)
+    phi, Phi = geo_separate(d, n_el, geom, c_mid, kappa_mid)
+    Kl, Ml = [], []
+    for l in range(d):
+        M_, K_ = spline_matrices_weighted(p, n_el, 1.0, STFD_BC_DIRICHLET, phi[l], Phi[l])
+        Kl.append(K_)
+        Ml.append(M_)
+    Mt, _, Wt = stfd_spline_matrices(p, n_el, T, STFD_BC_INITIAL)
+    ctr = stencil_center(p, d)
+    n = [n_el + p - 2] * d + [Wt.shape[0]]
+    return {"d": d, "p": p, "n_el": n_el, "geom": geom, "nq": nq, "n": n, "Ms": Ms, "Ks": Ks, "Wt": Wt, "Mt": Mt,
+            "K_tilde": Kl, "M_tilde": Ml, "Ms_diag": Ms[ctr].copy(), "Ks_diag": Ks[ctr].copy()}
+
+
+def geometry_preconditioner(prob, gamma=1.0, nu=1.0, precision=STFD_FP64, scaled=True, stream=None):
+    """FD handle of A^G = D^{1/2} A~ D^{1/2} (eq. prec_geo), or of A~ alone."""
+    P = FD(prob["K_tilde"], prob["M_tilde"], prob["Wt"], prob["Mt"], gamma, nu, precision=precision, stream=stream)
+    if scaled:
+        P.set_scaling(prob["Ms_diag"], prob["Ks_diag"], stream=stream)
+    return P
 
 
 # ---------------------------------------------------------------------------

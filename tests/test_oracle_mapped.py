@@ -137,3 +137,19 @@ def test_adjoint_gradient_matches_central_differences():
         Lp = mapped.loss_and_grads(kap, f + h * w, u_obs, d, p, n_el, p, n_el)[0]
         Lm = mapped.loss_and_grads(kap, f - h * w, u_obs, d, p, n_el, p, n_el)[0]
         assert abs((Lp - Lm) / (2 * h) - lam @ w) <= 1e-6 * max(abs(lam @ w), 1e-3 * np.linalg.norm(lam))
+
+
+def test_gradient_by_oracle_gmres_matches_direct():
+    """The GMRES route of the oracle's gradient (for sizes where SuperLU is too
+    slow) agrees with its direct-solve route."""
+    d, p, n_el = 2, 3, 6
+    g = np.random.default_rng(7)
+    kap = g.uniform(0.5, 2.0, n_el ** d)
+    n = (n_el + p - 2) ** d * (n_el + p - 1)
+    f = g.standard_normal(n)
+    u_obs = 0.1 * g.standard_normal(n)
+    L1, u1, l1, k1 = mapped.loss_and_grads(kap, f, u_obs, d, p, n_el, p, n_el)
+    L2, u2, l2, k2 = mapped.loss_and_grads(kap, f, u_obs, d, p, n_el, p, n_el, solver="gmres", tol=1e-13)
+    assert abs(L1 - L2) <= 1e-11 * abs(L1)
+    assert np.linalg.norm(l1 - l2) <= 1e-10 * np.linalg.norm(l1)
+    assert np.max(np.abs(k1 - k2)) <= 1e-10 * np.max(np.abs(k1))
