@@ -147,6 +147,127 @@ def run_oracle_solve(cfg):
     return t2 - t1, t1 - t0, info["iters"], f.size, res
 
 
+def cuda_time(fn, reps, stream):
+    """Average milliseconds of fn() over reps calls (CUDA events on `stream`)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def mapped_section(args, stream):
+    """Mixed-precision workload on the mapped domain: FP64-accurate vs TF32 /
+    BF16 geometry-aware preconditioner inside FP64 flexible GMRES (and the
+    plain parametric preconditioner for the iteration count)."""
+    import torch
+    from paper_1909_07309_gb300 import stfd
+    cfg = dict(inputs.MAPPED)
+    if args.mapped_n_el:
+        cfg["n_el"] = args.mapped_n_el
+    d, p, n_el = cfg["d"], cfg["p"], cfg["n_el"]
+    t0 = time.perf_counter()
+    prob = stfd.mapped_problem(d, p, n_el, stfd.STFD_GEOM_QUARTER_ANNULUS, c=inputs.c_bilinear,
+                               kappa=inputs.kappa_trig, T=cfg["T"])
+    host_setup_s = time.perf_counter() - t0
+    n = prob["n"]
+    N = int(np.prod(n))
+    mass = stfd.StencilOp(n, p, prob["Ms"], prob["Ms"], prob["Mt"], prob["Mt"], 1.0, 0.0, arith=stfd.STFD_OP_DF32)
+    f = mass.matvec(torch.from_numpy(inputs.standard_normal(N, cfg["rhs_seed"])).cuda())
+    mass.close()
+    A = stfd.StencilOp(n, p, prob["Ms"], prob["Ks"], prob["Wt"], prob["Mt"], cfg["gamma"], cfg["nu"],
+                       arith=stfd.STFD_OP_DF32)
+    y = torch.empty_like(f)
+    mv_ms, _ = cuda_time(lambda: A.matvec(f, y), 3, stream)
+    # preconditioner accuracy is stated on an N(0,1) input: on the right-hand side
+    # f = (M_t x M_s) c the rounding noise of a low-precision input is of the size
+    # of f's own smooth content, which P^{-1} amplifies most
+    r = torch.from_numpy(inputs.standard_normal(N, cfg["rhs_seed"] + 1)).cuda()
+    steps = args.mapped_steps
+    out = {"workload": cfg["name"], "N": N, "host_setup_s": host_setup_s, "steps": steps,
+           "matvec": "stencil, double-float", "st_matvec_ms": mv_ms, "variants": {}}
+    s_ref = None
+    K, M, Wt, Mt = stfd.heat_problem(d, p, n_el, T=cfg["T"])
+    for name, prec, geo in (("fp64_accurate", stfd.STFD_DF32, True), ("tf32", stfd.STFD_TF32, True),
+                            ("bf16", stfd.STFD_BF16, True), ("plain_fp64_accurate", stfd.STFD_DF32, False)):
+        P = stfd.geometry_preconditioner(prob, cfg["gamma"], cfg["nu"], precision=prec) if geo else \
+            stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=prec)
+        s = torch.empty_like(f)
+        P.apply(r, s)
+        fd_ms, _ = cuda_time(lambda: P.apply(r, s), 3, stream)
+        if s_ref is None:
+            s_ref = s.clone()
+        err = float(torch.linalg.norm(s - s_ref) / torch.linalg.norm(s_ref)) if geo else None
+        reps = steps if geo else 1
+        if geo:
+            A.gmres(P, f, y, tol=1e-8)      # warm-up (allocates the Krylov vectors)
+        gm_ms, (_, info) = cuda_time(lambda: A.gmres(P, f, y, tol=1e-8), reps, stream)
+        out["variants"][name] = {"precond": ("A^G " if geo else "A^ ") + name.replace("plain_", ""),
+                                 "fd_apply_ms": fd_ms, "fd_apply_rel_err_vs_fp64_accurate_on_N01_input": err,
+                                 "gmres_ms": gm_ms,
+                                 "gmres_iters": info["iters"], "rel_res_true": info["rel_res_true"]}
+        P.close()
+    base = out["variants"]["fp64_accurate"]["gmres_ms"]
+    for v in out["variants"].values():
+        v["speedup_vs_fp64_accurate"] = base / v["gmres_ms"]
+    A.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def adjoint_section(args, stream):
+    """Gradient of the L2 misfit w.r.t. the per-element conductivity and the
+    source: forward FGMRES + adjoint FGMRES (transposed FD) + device contraction."""
+    import torch
+    from paper_1909_07309_gb300 import autograd as ag, stfd
+    cfg = inputs.ADJOINT
+    d, p, n_el = cfg["d"], cfg["p"], cfg["n_el"]
+    kap, kap_obs, c = inputs.adjoint_draws(cfg)
+    model = ag.MappedHeatModel(d, p, n_el, stfd.STFD_GEOM_QUARTER_ANNULUS, kappa_ref=kap, T=cfg["T"], tol=1e-10)
+    f = model.mass.matvec(torch.from_numpy(c).cuda())
+    u_obs = ag.solve(torch.as_tensor(kap_obs), f, model).detach()
+
+    def grad_eval():
+        kt = torch.tensor(kap, requires_grad=True)
+        ft = f.clone().requires_grad_(True)
+        L = ag.l2_misfit(ag.solve(kt, ft, model), u_obs, model)
+        L.backward()
+        return float(L.detach()), kt.grad, ft.grad
+
+    for _ in range(2):
+        grad_eval()
+    model.iters.clear()
+    steps = max(1, args.mapped_steps)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        L, gk, gf = grad_eval()
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / steps
+    its = model.iters[:2]
+    # central differences (h = 1e-6) on two random directions, tight solves
+    model.tol = 1e-13
+    L, gk, gf = grad_eval()
+    g = np.random.default_rng(20)
+    worst = 0.0
+    for _ in range(2):
+        v = g.standard_normal(kap.size)
+        with torch.no_grad():
+            lp = float(ag.l2_misfit(ag.solve(torch.as_tensor(kap + 1e-6 * v), f, model), u_obs, model))
+            lm = float(ag.l2_misfit(ag.solve(torch.as_tensor(kap - 1e-6 * v), f, model), u_obs, model))
+        fd = (lp - lm) / 2e-6
+        worst = max(worst, abs(fd - float(gk.numpy() @ v)) / (np.linalg.norm(gk.numpy()) * np.linalg.norm(v)))
+    N = model.N
+    return {"workload": cfg["name"], "N": N, "loss": L, "gradient_ms": wall * 1e3,
+            "includes": "host assembly of K_s(kappa), forward FGMRES, adjoint FGMRES with P^-T, element contraction",
+            "forward_iters": its[0] if its else None, "adjoint_iters": its[1] if len(its) > 1 else None,
+            "fd_check_max_rel_dev": worst, "fd_check": "central differences h=1e-6, 2 directions, tol 1e-13"}
+
+
 def blas_threads():
     for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
         if os.environ.get(var):
@@ -193,6 +314,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--restart", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mapped", action="store_true", help="skip the mapped-domain mixed-precision workload")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint gradient workload")
+    ap.add_argument("--mapped-n-el", type=int, default=0, help="elements per direction of the mapped workload")
+    ap.add_argument("--mapped-steps", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -401,6 +526,13 @@ def main():
     }
     peaks, src = measured_peaks()
     line["hbm_peak_gbs"] = {"value": peaks.get("hbm_gbs"), "source": src}
+    A.close()
+    P.close()
+    torch.cuda.empty_cache()
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_section(args, stream)
+    if not args.no_mapped:
+        line["mapped_mixed_precision"] = mapped_section(args, stream)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         secs, _, iters, Nc, res = run_oracle_solve(cfg)

@@ -8,7 +8,8 @@
 // R consecutive rows and TC time slices: for every pair of outer offsets it
 // stages the R + 2p needed entries of Z1 and Z2 per time slice in shared
 // memory, then every thread applies the 2p+1 innermost offsets of its row to
-// all TC slices, so each coefficient is read once per TC slices.
+// all TC slices. The time chunks of one row block are consecutive block
+// indices, so they run together and share that block's coefficients in L2.
 //
 // Also: the per-element conductivity gradient -nu lam^T (M_t (x) K_e) u and
 // the diagonal scaling of the geometry-aware preconditioner (eq. prec_geo).
@@ -27,7 +28,6 @@ namespace {
 using dfa::df;
 
 constexpr int kRows = 256;   // rows per CTA (threads)
-constexpr int kTC = 8;       // time slices per CTA
 
 template <typename T>
 struct Num;
@@ -56,53 +56,65 @@ struct StencilDims {
   int nt;
 };
 
-// Pass 2. Grid: x = row blocks, y = time chunks.
-template <typename T>
+// Pass 2. Block b handles time chunk b % n_chunks of row block b / n_chunks.
+// PP > 0 fixes the half-bandwidth p at compile time (unrolled offsets,
+// immediate shared-memory offsets); PP = 0 reads it from g.
+template <typename T, int kTC, int PP>
 __global__ void __launch_bounds__(kRows)
 k_stencil(const T* __restrict__ Ms, const T* __restrict__ Ks, const T* __restrict__ Z1, const T* __restrict__ Z2,
           double* __restrict__ y, StencilDims g) {
   extern __shared__ unsigned char smem_raw[];
-  const int p = g.p, W = 2 * p + 1, span = kRows + 2 * p;
+  const int p = PP > 0 ? PP : g.p;
+  const int W = 2 * p + 1, span = kRows + 2 * p;
   T* z1s = reinterpret_cast<T*>(smem_raw);            // [kTC][span]
   T* z2s = z1s + kTC * span;
-  const long long i0 = (long long)blockIdx.x * kRows;
+  const int n_chunks = (g.nt + kTC - 1) / kTC;
+  const long long i0 = (long long)(blockIdx.x / n_chunks) * kRows;
+  const int t0 = (int)(blockIdx.x % n_chunks) * kTC;
   const long long i = i0 + threadIdx.x;
   const bool valid = i < g.Ns;
-  const int t0 = blockIdx.y * kTC;
   const int ntc = min(kTC, g.nt - t0);
   const int S23 = g.d >= 3 ? W * W : (g.d == 2 ? W : 1);
+  const T* mrow = Ms + (valid ? i : 0);
+  const T* krow = Ks + (valid ? i : 0);
   typename Num<T>::acc acc[kTC];
 #pragma unroll
   for (int tt = 0; tt < kTC; ++tt) acc[tt] = Num<T>::zero();
   for (int o23 = 0; o23 < S23; ++o23) {
     const int o2 = g.d >= 2 ? o23 % W : p, o3 = g.d >= 3 ? o23 / W : p;
-    const long long base = (long long)(o2 - p) * g.n1 + (long long)(o3 - p) * g.n1 * g.n2;
+    const long long base = i0 - p + (long long)(o2 - p) * g.n1 + (long long)(o3 - p) * g.n1 * g.n2;
     __syncthreads();
-    for (int k = threadIdx.x; k < kTC * span; k += kRows) {
-      const int tt = k / span, c = k - tt * span;
-      long long j = i0 + base - p + c;
+    // stage Z1, Z2 at columns base .. base + span - 1 for the kTC slices
+    for (int c = threadIdx.x; c < span; c += kRows) {
+      long long j = base + c;
       j = j < 0 ? 0 : (j >= g.Ns ? g.Ns - 1 : j);   // the coefficient is 0 for columns outside the box
-      T v1{}, v2{};
-      if (tt < ntc) {
-        v1 = Z1[(long long)(t0 + tt) * g.Ns + j];
-        v2 = Z2[(long long)(t0 + tt) * g.Ns + j];
+#pragma unroll
+      for (int tt = 0; tt < kTC; ++tt) {
+        T v1{}, v2{};
+        if (tt < ntc) {
+          v1 = Z1[(long long)(t0 + tt) * g.Ns + j];
+          v2 = Z2[(long long)(t0 + tt) * g.Ns + j];
+        }
+        z1s[tt * span + c] = v1;
+        z2s[tt * span + c] = v2;
       }
-      z1s[k] = v1;
-      z2s[k] = v2;
     }
     __syncthreads();
-    if (valid) {
-      for (int o1 = 0; o1 < W; ++o1) {
-        const long long o = o1 + (long long)W * o23;
-        const T m = Ms[o * g.Ns + i], kk = Ks[o * g.Ns + i];
+    const long long ob = (long long)W * o23 * g.Ns;
 #pragma unroll
-        for (int tt = 0; tt < kTC; ++tt)
-          Num<T>::fma2(acc[tt], m, z1s[tt * span + threadIdx.x + o1], kk, z2s[tt * span + threadIdx.x + o1]);
-      }
+    for (int o1 = 0; o1 < (PP > 0 ? 2 * PP + 1 : W); ++o1) {
+      if (PP == 0 && o1 >= W) break;
+      const T m = mrow[ob + (long long)o1 * g.Ns], kk = krow[ob + (long long)o1 * g.Ns];
+#pragma unroll
+      for (int tt = 0; tt < kTC; ++tt)
+        Num<T>::fma2(acc[tt], m, z1s[tt * span + threadIdx.x + o1], kk, z2s[tt * span + threadIdx.x + o1]);
     }
   }
-  if (valid)
-    for (int tt = 0; tt < ntc; ++tt) y[(long long)(t0 + tt) * g.Ns + i] = Num<T>::out(acc[tt]);
+  if (valid) {
+#pragma unroll
+    for (int tt = 0; tt < kTC; ++tt)   // static indices keep acc[] in registers
+      if (tt < ntc) y[(long long)(t0 + tt) * g.Ns + i] = Num<T>::out(acc[tt]);
+  }
 }
 
 // Pass 1: Z1[t] = gamma sum_tau W[t, tau] x[tau], Z2[t] = nu sum_tau Mt[t, tau] x[tau]
@@ -149,6 +161,22 @@ int sm_count() {
   return s;
 }
 
+template <typename T, int kTC, int PP>
+cudaError_t run_stencil(const StencilOpDev& op, T* Z1, T* Z2, double* y, const StencilDims& g, cudaStream_t st) {
+  const size_t smem = (size_t)2 * kTC * (kRows + 2 * op.p) * sizeof(T);
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_stencil<T, kTC, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               96 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const long long blocks = ((g.Ns + kRows - 1) / kRows) * ((g.nt + kTC - 1) / kTC);
+  k_stencil<T, kTC, PP><<<(unsigned)blocks, kRows, smem, st>>>(static_cast<const T*>(op.Ms),
+                                                                static_cast<const T*>(op.Ks), Z1, Z2, y, g);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t stencil_matvec(const StencilOpDev& op, const double* x, double* y, int trans, cudaStream_t st) {
   const T* Wb = static_cast<const T*>(trans ? op.WbT : op.Wb);
@@ -174,18 +202,15 @@ cudaError_t stencil_matvec(const StencilOpDev& op, const double* x, double* y, i
   g.nt = nt;
   int S = 1;
   for (int l = 0; l < op.d; ++l) S *= 2 * op.p + 1;
-  const size_t smem = (size_t)2 * kTC * (kRows + 2 * op.p) * sizeof(T);
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_stencil<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   ProfScope ps("stencil_space", 4.0 * S * (double)Ns * nt,
                (2.0 * S * sizeof(T)) * (double)Ns + 2.0 * sizeof(T) * (double)Ns * nt + 8.0 * (double)Ns * nt, st);
-  dim3 grid((unsigned)((Ns + kRows - 1) / kRows), (unsigned)((nt + kTC - 1) / kTC));
-  k_stencil<T><<<grid, kRows, smem, st>>>(static_cast<const T*>(op.Ms), static_cast<const T*>(op.Ks), Z1, Z2, y, g);
-  return cudaGetLastError();
+  switch (op.p) {
+    case 1: return run_stencil<T, 8, 1>(op, Z1, Z2, y, g, st);
+    case 2: return run_stencil<T, 8, 2>(op, Z1, Z2, y, g, st);
+    case 3: return run_stencil<T, 8, 3>(op, Z1, Z2, y, g, st);
+    case 4: return run_stencil<T, 8, 4>(op, Z1, Z2, y, g, st);
+    default: return run_stencil<T, 8, 0>(op, Z1, Z2, y, g, st);
+  }
 }
 
 // g[e] = -nu sum_t lam_t^T K_e ubar_t over the element's reduced rows, with

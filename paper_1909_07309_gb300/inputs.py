@@ -20,6 +20,42 @@ SCALE = dict(name="unit cube x (0,1), d=3, p=3, n_el=64", d=3, p=3, n_el=64,
              T=1.0, gamma=1.0, nu=1.0, rhs_seed=1)
 
 
+# Mixed-precision workload on a mapped domain: quarter annulus with radii 1
+# and 2 (exact NURBS map) extruded over (0, 1), d = 3, p = 4, 96 elements per
+# direction (n_s = 98, n_t = 99, N = 93,178,008), conductivity kappa and heat
+# capacity c below, right-hand side f = (M_t kron M_s) c_rhs with c_rhs ~ N(0, 1)
+# from seed 3.
+MAPPED = dict(name="quarter annulus (NURBS, extruded) x (0,1), d=3, p=4, n_el=96, variable kappa, c",
+              d=3, p=4, n_el=96, T=1.0, gamma=1.0, nu=1.0, rhs_seed=3)
+
+# Adjoint workload: planar quarter annulus x (0, 1), d = 2, p = 3, 32 elements
+# per direction (N = 37,026), piecewise-constant conductivity kappa_e ~ U[0.5, 2]
+# per element (seed 5); observations from kappa_e * exp(0.1 xi_e), xi ~ N(0, 1)
+# (same generator); f = (M_t kron M_s) c_rhs with c_rhs ~ N(0, 1) (same generator).
+ADJOINT = dict(name="quarter annulus x (0,1), d=2, p=3, n_el=32, kappa_e ~ U[0.5,2]", d=2, p=3, n_el=32,
+               T=1.0, gamma=1.0, nu=1.0, seed=5)
+
+
+def kappa_trig(x):
+    """kappa(x) = 1 + 0.5 sin(2 pi x_1) cos(2 pi x_2); x has shape (d, m)."""
+    return 1.0 + 0.5 * np.sin(2 * np.pi * x[0]) * np.cos(2 * np.pi * x[1])
+
+
+def c_bilinear(x):
+    """c(x) = 1 + 0.3 x_1 x_2; x has shape (d, m)."""
+    return 1.0 + 0.3 * x[0] * x[1]
+
+
+def adjoint_draws(cfg):
+    """(kappa_e, kappa_obs_e, c_rhs) of the adjoint workload."""
+    g = np.random.default_rng(cfg["seed"])
+    n_e = cfg["n_el"] ** cfg["d"]
+    kap = g.uniform(0.5, 2.0, n_e)
+    kap_obs = kap * np.exp(0.1 * g.standard_normal(n_e))
+    _, _, N = sizes(cfg)
+    return kap, kap_obs, g.standard_normal(N)
+
+
 def sizes(cfg):
     """(n_s, n_t, N) for uniform maximal-smoothness knots: n_s = n_el + p - 2, n_t = n_el + p - 1."""
     n_s = cfg["n_el"] + cfg["p"] - 2

@@ -1,10 +1,13 @@
 """Small fixed workloads for Nsight Compute captures of one kernel family.
 
   python -m paper_1909_07309_gb300.ncu_case {fd,matvec,solve} D P N_EL [REPS] [fp64|df32|fp64tc|tf32|bf16]
+  python -m paper_1909_07309_gb300.ncu_case {stencil,mapped_solve} D P N_EL [REPS] [fp64|df32|tf32|bf16]
 
 Builds the unit-cube problem (d = D, degree P, N_EL elements per direction),
 runs one warm-up and REPS applications of fd_apply, st_matvec or the
-preconditioned GMRES solve, synchronises and exits. Prints nothing else.
+preconditioned GMRES solve, synchronises and exits. `stencil` and
+`mapped_solve` use the quarter-annulus problem with variable coefficients
+(stencil matvec; GMRES with the geometry-aware preconditioner).
 """
 import sys
 
@@ -20,6 +23,22 @@ def main(argv):
     arith = argv[5] if len(argv) > 5 else "fp64"
     prec = {"fp64": stfd.STFD_FP64, "df32": stfd.STFD_DF32, "fp64tc": stfd.STFD_FP64TC,
             "tf32": stfd.STFD_TF32, "bf16": stfd.STFD_BF16}[arith]
+    if what in ("stencil", "mapped_solve"):
+        prob = stfd.mapped_problem(d, p, n_el, stfd.STFD_GEOM_QUARTER_ANNULUS, c=inputs.c_bilinear,
+                                   kappa=inputs.kappa_trig)
+        A = stfd.StencilOp(prob["n"], p, prob["Ms"], prob["Ks"], prob["Wt"], prob["Mt"],
+                           arith=stfd.STFD_OP_FP64 if arith == "fp64" else stfd.STFD_OP_DF32)
+        P = stfd.geometry_preconditioner(prob, precision=stfd.STFD_DF32 if prec == stfd.STFD_FP64TC else prec)
+        r = torch.from_numpy(inputs.standard_normal(A.N, 1)).cuda()
+        out = torch.empty_like(r)
+        for _ in range(1 + reps):
+            if what == "stencil":
+                A.matvec(r, out)
+            else:
+                A.gmres(P, r, out)
+        torch.cuda.synchronize()
+        print("ncu_case %s d=%d p=%d n_el=%d N=%d reps=%d ok" % (what, d, p, n_el, A.N, reps))
+        return
     K, M, Wt, Mt = stfd.heat_problem(d, p, n_el)
     P = stfd.FD(K, M, Wt, Mt, precision=prec)
     A = stfd.KronOp(K, M, Wt, Mt, arith=stfd.STFD_OP_FP64 if arith == "fp64" else stfd.STFD_OP_DF32)
