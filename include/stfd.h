@@ -337,6 +337,64 @@ int stfd_grad_kappa_elements(const stfd_op* A, int p, int n_el, const double* Ke
                              const double* u_dev, double* g_dev, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Batched solver: many independent small heat problems on the unit box
+ * (0,1)^d x (0,T), constant coefficients gamma, nu, each with its own number
+ * of elements n_el[k], degree p[k] (space and time) and number of right-hand
+ * sides nrhs[k]. Not a section of the paper: it batches its method. On the
+ * unit box the preconditioner of eq. prec_definition equals A, so FD-
+ * preconditioned GMRES converges in one iteration (Sec. 4); the batched
+ * solve performs exactly that iteration, u = P^{-1} f by Algorithm 1, and the
+ * true relative residual ||f - A u|| / ||f|| (eq. syst_mat, sum-factorised)
+ * per right-hand side, all in FP64-accurate double-float arithmetic.
+ *
+ * The work runs as ONE persistent kernel launch: every CTA repeatedly takes
+ * the next (problem, right-hand side) item from a list sorted by size
+ * (largest first) and solves it alone. stfd_batch_solve captures the launch
+ * (with the reset of the work counter) into a CUDA graph bound to the given
+ * pointers and replays it on later calls with the same pointers.
+ *
+ * Limits: d in {1,2,3}; 1 <= p[k] <= 10; n_s = n_el + p - 2 >= 1;
+ * n_s, n_t <= 256; at most 2^20 dofs per problem; count >= 1.
+ * autotune != 0 times every candidate CTA configuration (threads per CTA x
+ * CTAs per SM, see stfd_batch_stats) on the batch with synthetic right-hand
+ * sides and keeps the fastest; otherwise 256 threads x 4 CTAs per SM.
+ * Device memory: factors, 4 * max_N float pairs of scratch per CTA slot
+ * (SMs x 8 slots) and the work list.
+ * ------------------------------------------------------------------------ */
+typedef struct stfd_batch stfd_batch;
+
+int stfd_batch_create(stfd_batch** out, int count, int d, const int* n_el, const int* p, const int* nrhs,
+                      double T, double gamma, double nu, int autotune, void* stream);
+
+/* Packed vector layout: problem k's nrhs[k] right-hand sides (each of
+ * N_k = n_s^d n_t dofs, vec order) start at offsets[k] (count + 1 entries,
+ * offsets[count] = total). *n_items = sum of nrhs. Any output may be NULL. */
+int stfd_batch_layout(const stfd_batch* b, long long* offsets, int* n_items, long long* total);
+
+/* u_dev = P_k^{-1} f_dev per problem and right-hand side (packed layout);
+ * relres_dev (optional, n_items doubles, problem-major then right-hand side)
+ * receives ||f - A u|| / ||f||. f_dev and u_dev must not overlap. Calls on one
+ * batch must not overlap in time (shared work counter and scratch). The first
+ * call with a new (f, u, relres) pointer triple captures and instantiates the
+ * graph. */
+int stfd_batch_solve(stfd_batch* b, const double* f_dev, double* u_dev, double* relres_dev, void* stream);
+
+/* After a solve has completed: per-problem solve time in microseconds (first
+ * start to last end of its right-hand sides, device global timer) in
+ * problem_us (count entries), the chosen configuration, and the autotuning
+ * times in milliseconds per candidate (NaN if not run or infeasible; the 8
+ * candidates are 128x2, 128x4, 128x8, 256x1, 256x2, 256x4, 512x1, 512x2
+ * threads x CTAs per SM). Any output may be NULL. Synchronous. */
+int stfd_batch_stats(const stfd_batch* b, double* problem_us, int* threads, int* ctas_per_sm, double* tune_ms,
+                     int tune_cap);
+
+/* Work-list order: item idx (0 <= idx < n_items) solves right-hand side *rhs
+ * of problem *problem. */
+int stfd_batch_item(const stfd_batch* b, int idx, int* problem, int* rhs);
+
+void stfd_batch_destroy(stfd_batch* b);
+
+/* ------------------------------------------------------------------------
  * Allocation-free system matvec. The paper has no counterpart: this entry
  * point serves callers that must not allocate device memory -- for example a
  * host application that owns every byte of device memory through its own

@@ -281,24 +281,7 @@ extern "C" int stfd_fd_setup(stfd_fd** out, int d, const int* n, const double* c
   // S_k = gamma sigma + a + sum_j gamma^2 a |g_j|^2 / (a^2 + gamma^2 lam_j^2) [+ gamma^2 g_z^2 / a]
   std::vector<double> Sinv;
   if (rc == STFD_OK) {
-    Sinv.resize((size_t)h->Ns);
-    for (long long k = 0; k < h->Ns; ++k) {
-      long long rest = k;
-      double mu = 0.0;
-      for (int l = 0; l < d; ++l) {
-        mu += f.lam[l][rest % n[l]];
-        rest /= n[l];
-      }
-      const double a = nu * mu;
-      double S = gamma * f.sigma + a;
-      for (int j = 0; j < f.n_pairs; ++j) {
-        const double b = gamma * f.lamt[j];
-        const double g2 = f.g[2 * j] * f.g[2 * j] + f.g[2 * j + 1] * f.g[2 * j + 1];
-        S += gamma * gamma * a * g2 / (a * a + b * b);
-      }
-      if (f.has_zero) S += gamma * gamma * f.g[2 * f.n_pairs] * f.g[2 * f.n_pairs] / a;
-      Sinv[k] = 1.0 / S;
-    }
+    Sinv = schur_reciprocals(f, gamma, nu);
     rc = dev_upload(&h->Sinv, Sinv.data(), Sinv.size(), st);
   }
   if (rc == STFD_OK && f.n_pairs > 0) rc = dev_upload(&h->lamt, f.lamt.data(), f.lamt.size(), st);

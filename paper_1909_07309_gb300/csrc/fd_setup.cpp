@@ -364,3 +364,34 @@ extern "C" int stfd_fd_factors(int d, const int* n, const double* const* K, cons
   if (has_zero) *has_zero = f.has_zero;
   return STFD_OK;
 }
+
+namespace stfd {
+
+// Reciprocals of the Schur complement of the arrowhead per spatial index
+// (eq. block_LU): with a = nu mu_k,
+// S_k = gamma sigma + a + sum_j gamma^2 a |g_j|^2 / (a^2 + gamma^2 lam_j^2) [+ gamma^2 g_z^2 / a].
+std::vector<double> schur_reciprocals(const HostFactors& f, double gamma, double nu) {
+  long long Ns = 1;
+  for (int l = 0; l < f.d; ++l) Ns *= f.n[l];
+  std::vector<double> Sinv((size_t)Ns);
+  for (long long k = 0; k < Ns; ++k) {
+    long long rest = k;
+    double mu = 0.0;
+    for (int l = 0; l < f.d; ++l) {
+      mu += f.lam[l][rest % f.n[l]];
+      rest /= f.n[l];
+    }
+    const double a = nu * mu;
+    double S = gamma * f.sigma + a;
+    for (int j = 0; j < f.n_pairs; ++j) {
+      const double b = gamma * f.lamt[j];
+      const double g2 = f.g[2 * j] * f.g[2 * j] + f.g[2 * j + 1] * f.g[2 * j + 1];
+      S += gamma * gamma * a * g2 / (a * a + b * b);
+    }
+    if (f.has_zero) S += gamma * gamma * f.g[2 * f.n_pairs] * f.g[2 * f.n_pairs] / a;
+    Sinv[k] = 1.0 / S;
+  }
+  return Sinv;
+}
+
+}  // namespace stfd

@@ -30,4 +30,7 @@ struct HostFactors {
 int factorize_host(int d, const int* n, const double* const* K, const double* const* M,
                    const double* Wt, const double* Mt, HostFactors& f);
 
+// S_k^{-1} of eq. block_LU for every spatial index k.
+std::vector<double> schur_reciprocals(const HostFactors& f, double gamma, double nu);
+
 }  // namespace stfd

@@ -36,6 +36,21 @@ ADJOINT = dict(name="quarter annulus x (0,1), d=2, p=3, n_el=32, kappa_e ~ U[0.5
                T=1.0, gamma=1.0, nu=1.0, seed=5)
 
 
+# Batched workload: 512 independent problems on the unit square x (0, 1),
+# d = 2, n_el ~ U{8..48}, p ~ U{1..4}, nrhs ~ U{1..8} per problem, constant
+# coefficients, right-hand sides with i.i.d. N(0, 1) entries; all draws from
+# default_rng(4) in this order.
+BATCH = dict(name="512 problems, unit square x (0,1), d=2, n_el~U{8..48}, p~U{1..4}, nrhs~U{1..8}",
+             count=512, d=2, T=1.0, gamma=1.0, nu=1.0, seed=4)
+
+
+def batch_draws(cfg):
+    """(n_el, p, nrhs) arrays of the batched workload and a generator for its right-hand sides."""
+    g = np.random.default_rng(cfg["seed"])
+    n = cfg["count"]
+    return g.integers(8, 49, n), g.integers(1, 5, n), g.integers(1, 9, n), g
+
+
 def kappa_trig(x):
     """kappa(x) = 1 + 0.5 sin(2 pi x_1) cos(2 pi x_2); x has shape (d, m)."""
     return 1.0 + 0.5 * np.sin(2 * np.pi * x[0]) * np.cos(2 * np.pi * x[1])

@@ -97,6 +97,16 @@ SIGNATURES = {
     "stfd_fd_set_scaling": (ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, _c_dbl_p, ctypes.c_void_p]),
     "stfd_grad_kappa_elements": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "stfd_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _c_int_p,
+                                         _c_int_p, _c_int_p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_int, ctypes.c_void_p]),
+    "stfd_batch_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), _c_int_p,
+                                         ctypes.POINTER(ctypes.c_longlong)]),
+    "stfd_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "stfd_batch_stats": (ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, _c_int_p, _c_int_p, _c_dbl_p, ctypes.c_int]),
+    "stfd_batch_item": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_int_p, _c_int_p]),
+    "stfd_batch_destroy": (None, [ctypes.c_void_p]),
     # include/stfd_profile.h
     "stfd_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "stfd_profile_reset": (ctypes.c_int, []),
@@ -391,6 +401,76 @@ class StencilOp(KronOp):
                                         int(p_s), _dptr(Ms), _dptr(Ks), _dptr(Wt), _dptr(Mt), float(gamma),
                                         float(nu), int(arith), _stream(stream))
         _check(rc, "stfd_op_create_stencil")
+
+
+class Batch:
+    """Batched solver handle (``stfd_batch_*``): many small unit-box problems,
+    one persistent graph-captured launch per solve."""
+
+    CANDIDATES = [(128, 2), (128, 4), (128, 8), (256, 1), (256, 2), (256, 4), (512, 1), (512, 2)]
+
+    def __init__(self, n_el, p, nrhs, d=2, T=1.0, gamma=1.0, nu=1.0, autotune=True, stream=None):
+        lib = load()
+        self._lib = lib
+        self.handle = ctypes.c_void_p()
+        n_el, p, nrhs = (np.ascontiguousarray(a, dtype=np.int32) for a in (n_el, p, nrhs))
+        if not (n_el.size == p.size == nrhs.size):
+            raise ValueError("n_el, p and nrhs must have one entry per problem")
+        self.count, self.d = int(n_el.size), int(d)
+        self.n_el, self.p, self.nrhs = n_el, p, nrhs
+        ip = ctypes.POINTER(ctypes.c_int)
+        rc = lib.stfd_batch_create(ctypes.byref(self.handle), self.count, self.d, n_el.ctypes.data_as(ip),
+                                   p.ctypes.data_as(ip), nrhs.ctypes.data_as(ip), float(T), float(gamma), float(nu),
+                                   1 if autotune else 0, _stream(stream))
+        _check(rc, "stfd_batch_create")
+        off = (ctypes.c_longlong * (self.count + 1))()
+        ni = ctypes.c_int(0)
+        tot = ctypes.c_longlong(0)
+        _check(lib.stfd_batch_layout(self.handle, off, ctypes.byref(ni), ctypes.byref(tot)), "stfd_batch_layout")
+        self.offsets = np.array(off[:], dtype=np.int64)
+        self.n_items = ni.value
+        self.total = tot.value
+
+    def sizes(self, k):
+        """(n_s, n_t, N) of problem k."""
+        ns = int(self.n_el[k] + self.p[k] - 2)
+        nt = int(self.n_el[k] + self.p[k] - 1)
+        return ns, nt, ns ** self.d * nt
+
+    def solve(self, f, u=None, relres=None, stream=None):
+        """u = P^{-1} f per problem / right-hand side (packed); returns (u, relres)."""
+        import torch
+        if u is None:
+            u = torch.empty_like(f)
+        if relres is None:
+            relres = torch.empty(self.n_items, dtype=torch.float64, device=f.device)
+        for t, n in ((f, self.total), (u, self.total), (relres, self.n_items)):
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+                raise ValueError("packed float64 CUDA vectors of the batch layout expected")
+        _check(self._lib.stfd_batch_solve(self.handle, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                          ctypes.c_void_p(relres.data_ptr()), _stream(stream)), "stfd_batch_solve")
+        return u, relres
+
+    def stats(self):
+        """Per-problem solve time (us) of the last solve, chosen (threads, CTAs/SM), tuning table."""
+        us = np.zeros(self.count)
+        th, ct = ctypes.c_int(0), ctypes.c_int(0)
+        tune = np.zeros(len(self.CANDIDATES))
+        _check(self._lib.stfd_batch_stats(self.handle, _dptr(us), ctypes.byref(th), ctypes.byref(ct), _dptr(tune),
+                                          len(self.CANDIDATES)), "stfd_batch_stats")
+        return us, (th.value, ct.value), {"%dx%d" % c: (None if np.isnan(v) else float(v))
+                                          for c, v in zip(self.CANDIDATES, tune)}
+
+    def close(self):
+        if self.handle:
+            self._lib.stfd_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------------------

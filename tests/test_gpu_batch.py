@@ -1,0 +1,96 @@
+"""GPU: the batched solver (one persistent graph-captured launch over many
+small unit-box problems of uneven size, degree and right-hand-side count)
+against the oracle's Algorithm 1 per problem (1e-11), with the per-item true
+residual, autotuning, graph replay and argument checks."""
+import numpy as np
+import pytest
+
+from oracle import fd as ofd, matrices as omat
+from paper_1909_07309_gb300 import inputs, stfd
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def oracle_solve(d, p, n_el, f, T=1.0, gamma=1.0, nu=1.0):
+    K, M = omat.space_matrices(p, n_el)
+    Wt, Mt = omat.time_matrices(p, n_el, T)
+    return ofd.fd_solve([K] * d, [M] * d, Wt, Mt, f, gamma, nu)
+
+
+def check_against_oracle(B, f, u, rel, items, d, T=1.0, gamma=1.0, nu=1.0):
+    f, u, rel = f.cpu().numpy(), u.cpu().numpy(), rel.cpu().numpy()
+    item = 0
+    for k in range(B.count):
+        ns, nt, N = B.sizes(k)
+        for r in range(int(B.nrhs[k])):
+            if items is None or k in items:
+                o = B.offsets[k] + r * N
+                ref = oracle_solve(d, int(B.p[k]), int(B.n_el[k]), f[o:o + N], T, gamma, nu)
+                assert np.linalg.norm(u[o:o + N] - ref) <= 1e-11 * np.linalg.norm(ref), (k, r)
+            # forward error 1e-11 of P^{-1} = A^{-1}; the residual carries the
+            # conditioning of A on top (2e-11 seen at p = 4): bound 1e-10
+            assert rel[item] <= 1e-10, (k, r, rel[item])
+            item += 1
+
+
+@pytest.mark.parametrize("d,T,gamma,nu", [(2, 1.0, 1.0, 1.0), (1, 0.5, 2.0, 0.3), (3, 1.0, 1.0, 1.0)])
+def test_batch_small_matches_oracle(d, T, gamma, nu):
+    g = np.random.default_rng(d)
+    n_el = np.array([3, 4, 7, 5, 12, 2, 9, 6] if d < 3 else [3, 4, 5, 2, 6])
+    p = np.array([1, 2, 3, 4, 2, 3, 1, 4] if d < 3 else [1, 2, 3, 4, 2])
+    nrhs = g.integers(1, 4, n_el.size)
+    B = stfd.Batch(n_el, p, nrhs, d=d, T=T, gamma=gamma, nu=nu, autotune=False)
+    f = torch.from_numpy(g.standard_normal(B.total)).cuda()
+    u, rel = B.solve(f)
+    torch.cuda.synchronize()
+    check_against_oracle(B, f, u, rel, None, d, T, gamma, nu)
+
+
+def test_batch_autotune_graph_replay_and_determinism():
+    """Every configuration gives the same solution bits (one thread owns each
+    output); the graph replays on the same pointers and re-captures on new ones."""
+    g = np.random.default_rng(9)
+    n_el, p, nrhs = g.integers(3, 20, 24), g.integers(1, 5, 24), g.integers(1, 5, 24)
+    A = stfd.Batch(n_el, p, nrhs, autotune=True)
+    Bf = stfd.Batch(n_el, p, nrhs, autotune=False)
+    us, (th, ct), tune = A.stats()
+    assert (th, ct) in stfd.Batch.CANDIDATES and any(v is not None for v in tune.values())
+    f = torch.from_numpy(g.standard_normal(A.total)).cuda()
+    u1, r1 = A.solve(f)
+    u2, r2 = A.solve(f)                       # replay
+    u3 = torch.empty_like(f)
+    A.solve(f, u3)                            # new pointers: re-capture
+    u4, _ = Bf.solve(f)
+    torch.cuda.synchronize()
+    assert torch.equal(u1, u2) and torch.equal(u1, u3) and torch.equal(u1, u4)
+    assert float(r1.max()) <= 1e-10
+    us, _, _ = A.stats()
+    assert np.all(us > 0)
+
+
+def test_batch_workload_residuals_and_samples():
+    """The batched workload (512 problems, n_el ~ U{8..48}, p ~ U{1..4}, nrhs ~
+    U{1..8}): every true residual <= 1e-10, eight problems equal the oracle."""
+    cfg = inputs.BATCH
+    n_el, p, nrhs, g = inputs.batch_draws(cfg)
+    B = stfd.Batch(n_el, p, nrhs, d=cfg["d"], autotune=False)
+    f = torch.from_numpy(g.standard_normal(B.total)).cuda()
+    u, rel = B.solve(f)
+    torch.cuda.synchronize()
+    assert float(rel.max()) <= 1e-10
+    sample = set(np.random.default_rng(1).choice(B.count, 8, replace=False).tolist())
+    check_against_oracle(B, f, u, torch.zeros(B.n_items, dtype=torch.float64), sample, cfg["d"])
+
+
+def test_batch_argument_checks():
+    with pytest.raises(stfd.StfdError):
+        stfd.Batch([1], [1], [1])                 # n_s = 0
+    with pytest.raises(stfd.StfdError):
+        stfd.Batch([5], [2], [0])                 # no right-hand side
+    with pytest.raises(stfd.StfdError):
+        stfd.Batch([120], [4], [1], d=3)          # more than 2^20 dofs
+    B = stfd.Batch([4], [2], [1], autotune=False)
+    f = torch.zeros(B.total, dtype=torch.float64, device="cuda")
+    with pytest.raises(stfd.StfdError):
+        B.solve(f, f)                             # aliasing
