@@ -33,9 +33,10 @@ METRIC = "fd_apply dofs/s and GMRES time-to-1e-8 residual, FP64 vs TF32/BF16-pre
 UNIT = "dofs/s"
 L2_BYTES = 129 * 2 ** 20
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/);
-# None until captured for the current kernel.
-NCU_TRAFFIC = {"kernel": "fd_mode_ozaki", "bytes_per_launch": None}
+# DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/,
+# mean over the 8 launches of one fd_apply at the workload); None once the
+# kernel changes until it is captured again.
+NCU_TRAFFIC = {"kernel": "fd_mode_ozaki", "bytes_per_launch": 237728640}
 
 
 def measured_peaks():
