@@ -195,7 +195,8 @@ def mapped_section(args, stream):
     s_ref = None
     K, M, Wt, Mt = stfd.heat_problem(d, p, n_el, T=cfg["T"])
     for name, prec, geo in (("fp64_accurate", stfd.STFD_DF32, True), ("tf32", stfd.STFD_TF32, True),
-                            ("bf16", stfd.STFD_BF16, True), ("plain_fp64_accurate", stfd.STFD_DF32, False)):
+                            ("bf16", stfd.STFD_BF16, True), ("fp64_ieee", stfd.STFD_FP64, True),
+                            ("plain_fp64_accurate", stfd.STFD_DF32, False)):
         P = stfd.geometry_preconditioner(prob, cfg["gamma"], cfg["nu"], precision=prec) if geo else \
             stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=prec)
         s = torch.empty_like(f)
@@ -204,7 +205,7 @@ def mapped_section(args, stream):
         if s_ref is None:
             s_ref = s.clone()
         err = float(torch.linalg.norm(s - s_ref) / torch.linalg.norm(s_ref)) if geo else None
-        reps = steps if geo else 1
+        reps = steps if (geo and prec != stfd.STFD_FP64) else 1
         if geo:
             A.gmres(P, f, y, tol=1e-8)      # warm-up (allocates the Krylov vectors)
         gm_ms, (_, info) = cuda_time(lambda: A.gmres(P, f, y, tol=1e-8), reps, stream)
@@ -214,8 +215,10 @@ def mapped_section(args, stream):
                                  "gmres_iters": info["iters"], "rel_res_true": info["rel_res_true"]}
         P.close()
     base = out["variants"]["fp64_accurate"]["gmres_ms"]
+    ieee = out["variants"]["fp64_ieee"]["gmres_ms"]
     for v in out["variants"].values():
         v["speedup_vs_fp64_accurate"] = base / v["gmres_ms"]
+        v["speedup_vs_fp64_ieee"] = ieee / v["gmres_ms"]
     A.close()
     torch.cuda.empty_cache()
     return out

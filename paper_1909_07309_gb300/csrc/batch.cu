@@ -48,26 +48,58 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Y = X x_m J over a tensor [outer][n][inner] (J row-major n x n, df pairs).
+// Y = X x_m J over a tensor [outer][n][inner] (J row-major n x n, df pairs),
+// all threads of the CTA: blocks of 32 tensor columns are staged in shared
+// memory (xs[n][32]); warp w accumulates rows i = w + W (b + 4 m), four rows at
+// a time in registers, for the 32 columns of its lanes.
 template <int THREADS>
 __device__ void mode_pass(const double* Xd, const float2* Xf, const float2* __restrict__ J, float2* Yf, double* Yd,
-                          int n, int inner, int N) {
-  for (int e = threadIdx.x; e < N; e += THREADS) {
-    const int c = e % inner, r = e / inner;
-    const int i = r % n, o = r / n;
-    const int base = o * n * inner + c;
-    const float2* Jr = J + i * n;
-    df acc{0.f, 0.f};
-    for (int a = 0; a < n; ++a) {
-      const int idx = base + a * inner;
-      const df x = Xd ? dfa::from_double(Xd[idx]) : dfa::from_float2(Xf[idx]);
-      dfa::fma_acc(acc, Jr[a], x);
+                          int n, int inner, int N, float2* xs) {
+  constexpr int kW = THREADS / 32;
+  constexpr int kIB = 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int Q = N / n;
+  for (int q0 = 0; q0 < Q; q0 += 32) {
+    const int q = q0 + lane;
+    const bool valid = q < Q;
+    int base = 0;
+    if (valid) {
+      const int o = q / inner;
+      base = o * n * inner + (q - o * inner);
     }
-    acc = dfa::norm(acc);
-    if (Yd)
-      Yd[e] = dfa::to_double(acc);
-    else
-      Yf[e] = make_float2(acc.h, acc.l);
+    for (int a = warp; a < n; a += kW) {
+      df v{0.f, 0.f};
+      if (valid) v = Xd ? dfa::from_double(Xd[base + a * inner]) : dfa::from_float2(Xf[base + a * inner]);
+      xs[a * 32 + lane] = make_float2(v.h, v.l);
+    }
+    __syncthreads();
+    for (int i0 = warp; i0 < n; i0 += kW * kIB) {
+      df acc[kIB];
+      const float2* row[kIB];
+#pragma unroll
+      for (int b = 0; b < kIB; ++b) {
+        acc[b] = df{0.f, 0.f};
+        row[b] = J + min(i0 + b * kW, n - 1) * n;
+      }
+      for (int a = 0; a < n; ++a) {
+        const df x = dfa::from_float2(xs[a * 32 + lane]);
+#pragma unroll
+        for (int b = 0; b < kIB; ++b) dfa::fma_acc(acc[b], __ldg(row[b] + a), x);
+      }
+      if (valid) {
+#pragma unroll
+        for (int b = 0; b < kIB; ++b) {
+          const int i = i0 + b * kW;
+          if (i >= n) continue;
+          const df y = dfa::norm(acc[b]);
+          if (Yd)
+            Yd[base + i * inner] = dfa::to_double(y);
+          else
+            Yf[base + i * inner] = make_float2(y.h, y.l);
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -114,6 +146,7 @@ k_batch(const BProb* __restrict__ probs, const BItem* __restrict__ items, int n_
         const double* __restrict__ f, double* __restrict__ u, double* __restrict__ relres,
         unsigned long long* __restrict__ times, int* __restrict__ counter, float2* __restrict__ scratch,
         int max_N) {
+  extern __shared__ float2 xs[];   // [max n][32] staging of mode_pass
   __shared__ int item_s;
   __shared__ double red[THREADS / 32];
   float2* buf[4];
@@ -134,12 +167,12 @@ k_batch(const BProb* __restrict__ probs, const BItem* __restrict__ items, int n_
     int cur = 0, inner = 1;
     for (int l = 0; l < d; ++l) {
       mode_pass<THREADS>(l == 0 ? fx : nullptr, l == 0 ? nullptr : buf[cur ^ 1], pool + P.Uf, buf[cur], nullptr,
-                         P.ns, inner, N);
+                         P.ns, inner, N, xs);
       __syncthreads();
       cur ^= 1;
       inner *= P.ns;
     }
-    mode_pass<THREADS>(nullptr, buf[cur ^ 1], pool + P.Utf, buf[cur], nullptr, P.nt, inner, N);
+    mode_pass<THREADS>(nullptr, buf[cur ^ 1], pool + P.Utf, buf[cur], nullptr, P.nt, inner, N, xs);
     __syncthreads();
     // Step 3 in place on buf[cur]
     {
@@ -162,13 +195,13 @@ k_batch(const BProb* __restrict__ probs, const BItem* __restrict__ items, int n_
     }
     __syncthreads();
     // Step 4: s = (U_t x U ... x U) q~, the last pass writes the FP64 solution
-    mode_pass<THREADS>(nullptr, buf[cur], pool + P.Utb, buf[cur ^ 1], nullptr, P.nt, inner, N);
+    mode_pass<THREADS>(nullptr, buf[cur], pool + P.Utb, buf[cur ^ 1], nullptr, P.nt, inner, N, xs);
     __syncthreads();
     cur ^= 1;
     for (int l = d - 1; l >= 0; --l) {
       inner /= P.ns;
       mode_pass<THREADS>(nullptr, buf[cur], pool + P.Ub, l == 0 ? nullptr : buf[cur ^ 1], l == 0 ? ux : nullptr,
-                         P.ns, inner, N);
+                         P.ns, inner, N, xs);
       __syncthreads();
       cur ^= 1;
     }
@@ -244,7 +277,7 @@ int sm_count() {
 using namespace stfd;
 
 struct stfd_batch {
-  int count = 0, d = 0, n_items = 0, max_N = 0, sms = 0;
+  int count = 0, d = 0, n_items = 0, max_N = 0, max_n = 0, sms = 0;
   std::vector<long long> offsets;       // count + 1
   std::vector<BItem> items;             // host copy (sorted)
   BProb* probs = nullptr;
@@ -273,32 +306,40 @@ cudaError_t launch_batch(const stfd_batch* b, int threads, int ctas, const doubl
   cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   const int grid = b->sms * ctas;
+  const size_t smem = (size_t)b->max_n * 32 * sizeof(float2);
   count_launch();
   switch (threads) {
     case 128:
-      k_batch<128><<<grid, 128, 0, st>>>(b->probs, b->ditems, b->n_items, b->pool, f, u, relres, b->times,
+      k_batch<128><<<grid, 128, smem, st>>>(b->probs, b->ditems, b->n_items, b->pool, f, u, relres, b->times,
                                          b->counter, b->scratch, b->max_N);
       break;
     case 512:
-      k_batch<512><<<grid, 512, 0, st>>>(b->probs, b->ditems, b->n_items, b->pool, f, u, relres, b->times,
+      k_batch<512><<<grid, 512, smem, st>>>(b->probs, b->ditems, b->n_items, b->pool, f, u, relres, b->times,
                                          b->counter, b->scratch, b->max_N);
       break;
     default:
-      k_batch<256><<<grid, 256, 0, st>>>(b->probs, b->ditems, b->n_items, b->pool, f, u, relres, b->times,
+      k_batch<256><<<grid, 256, smem, st>>>(b->probs, b->ditems, b->n_items, b->pool, f, u, relres, b->times,
                                          b->counter, b->scratch, b->max_N);
   }
   return cudaGetLastError();
 }
 
-bool feasible(int threads, int ctas) {
+template <int THREADS>
+cudaError_t set_smem(size_t smem) {
+  return smem > 48 * 1024
+             ? cudaFuncSetAttribute(k_batch<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+             : cudaSuccess;
+}
+
+bool feasible(int threads, int ctas, size_t smem) {
   int blocks = 0;
   cudaError_t e;
   if (threads == 128)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch<128>, 128, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch<128>, 128, smem);
   else if (threads == 512)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch<512>, 512, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch<512>, 512, smem);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch<256>, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch<256>, 256, smem);
   return e == cudaSuccess && blocks >= ctas;
 }
 
@@ -397,6 +438,7 @@ extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* 
     P.item_base = (int)b->items.size();
     b->offsets[k + 1] = b->offsets[k] + N * nrhs[k];
     b->max_N = std::max(b->max_N, (int)N);
+    b->max_n = std::max(b->max_n, std::max(ns, nt));
     // row-major U^T is the column-major U read by rows; row-major U is its transpose
     auto row_major = [](int n, const std::vector<double>& A) {
       std::vector<double> J((size_t)n * n);
@@ -453,6 +495,10 @@ extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* 
   if (rc == STFD_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) rc = STFD_ERR_CUDA;
   // autotune: time every feasible candidate on this batch with synthetic right-hand sides
   b->tune_ms.assign(kNumCandidates, NAN);
+  const size_t smem = (size_t)b->max_n * 32 * sizeof(float2);
+  if (rc == STFD_OK && (set_smem<128>(smem) != cudaSuccess || set_smem<256>(smem) != cudaSuccess ||
+                        set_smem<512>(smem) != cudaSuccess))
+    rc = STFD_ERR_CUDA;
   if (rc == STFD_OK && autotune) {
     const long long total = b->offsets[count];
     double *ft = nullptr, *ut = nullptr;
@@ -468,7 +514,7 @@ extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* 
       double best = 1e30;
       for (int c = 0; c < kNumCandidates && rc == STFD_OK; ++c) {
         const Candidate cd = kCandidates[c];
-        if (!feasible(cd.threads, cd.ctas)) continue;
+        if (!feasible(cd.threads, cd.ctas, smem)) continue;
         if (launch_batch(b, cd.threads, cd.ctas, ft, ut, nullptr, st) != cudaSuccess) rc = STFD_ERR_CUDA;
         cudaEventRecord(e0, st);
         for (int r = 0; r < 2 && rc == STFD_OK; ++r)
@@ -489,7 +535,7 @@ extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* 
     }
     cudaFree(ft);
     cudaFree(ut);
-  } else if (rc == STFD_OK && !feasible(b->threads, b->ctas_per_sm)) {
+  } else if (rc == STFD_OK && !feasible(b->threads, b->ctas_per_sm, smem)) {
     b->ctas_per_sm = 1;
   }
   if (rc != STFD_OK) {
