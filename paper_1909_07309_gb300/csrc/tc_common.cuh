@@ -113,6 +113,29 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// 32 lanes x 32 bits, 8 consecutive columns per thread, without the wait:
+// the registers are valid only after tmem_wait_ld8x6 below.
+__device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+
+// One wait for the tcgen05.ld issued before it, then six empty statements
+// that take the 6 x 8 loaded registers as read-write operands, so that no use
+// of them can be scheduled above the wait.
+__device__ __forceinline__ void tmem_wait_ld8x6(uint32_t (&r)[6][8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+    asm volatile(""
+                 : "+r"(r[c][0]), "+r"(r[c][1]), "+r"(r[c][2]), "+r"(r[c][3]), "+r"(r[c][4]), "+r"(r[c][5]),
+                   "+r"(r[c][6]), "+r"(r[c][7])
+                 :
+                 : "memory");
+}
+
 // Asynchronous 8-byte global -> shared copy (no register staging), and the wait
 // for every copy this thread has issued.
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {

@@ -298,9 +298,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
     // ---- epilogue: part p combines the six diagonals of row r on chunks p, p+4, ...
     const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     for (int c8 = part; c8 < nchunk_pad; c8 += kParts) {
+      uint32_t Tr[kDig][8];
+#pragma unroll
+      for (int c = 0; c < kDig; ++c) tc::tmem_ld8_async(lane_base + (uint32_t)(c * npad + 8 * c8), Tr[c]);
+      tc::tmem_wait_ld8x6(Tr);
       float T[kDig][8];
 #pragma unroll
-      for (int c = 0; c < kDig; ++c) tc::tmem_ld8(lane_base + (uint32_t)(c * npad + 8 * c8), T[c]);
+      for (int c = 0; c < kDig; ++c)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) T[c][j] = __uint_as_float(Tr[c][j]);
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int i = 8 * c8 + j;
