@@ -58,12 +58,18 @@ struct OzArgs {
 // staged row (FP64 words or double-float words).
 template <bool DBL>
 __device__ __forceinline__ int row_max_exp(const long long* F, int n, int a0, int step) {
-  int E = 0;
-  for (int a = a0; a < n; a += step) {
-    const unsigned long long w = (unsigned long long)F[a];
-    E = max(E, DBL ? (int)((w >> 52) & 0x7FF) : (int)((w >> 23) & 0xFF));
+  int E0 = 0, E1 = 0;   // two independent maxima for instruction-level parallelism
+  int a = a0;
+  for (; a + step < n; a += 2 * step) {
+    const unsigned long long w0 = (unsigned long long)F[a], w1 = (unsigned long long)F[a + step];
+    E0 = max(E0, DBL ? (int)((w0 >> 52) & 0x7FF) : (int)((w0 >> 23) & 0xFF));
+    E1 = max(E1, DBL ? (int)((w1 >> 52) & 0x7FF) : (int)((w1 >> 23) & 0xFF));
   }
-  return E;
+  if (a < n) {
+    const unsigned long long w = (unsigned long long)F[a];
+    E0 = max(E0, DBL ? (int)((w >> 52) & 0x7FF) : (int)((w >> 23) & 0xFF));
+  }
+  return max(E0, E1);
 }
 
 // Staged entry -> signed 48-bit fixed point under the row exponent E:
@@ -220,6 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
     for (int pp = 0; pp < kParts; ++pp) E = max(E, sE[pp * kTile + r]);
     const int urow = DBL ? E - 1070 : E - 174;
     // packed digit source: word0 = sign << 31 | bits 24..47 of |F|, word1 = bits 0..23
+#pragma unroll 4
     for (int a = part; a < n; a += kParts) {
       const long long f = (r < rows) ? to_fixed<DBL>(Frow[a], E) : 0;
       const unsigned long long m = (unsigned long long)(f < 0 ? -f : f);
