@@ -563,11 +563,12 @@ def main():
     A.close()
     P.close()
     torch.cuda.empty_cache()
-    if not args.no_batch:
+    # the other workloads are reported once, at N = 1 (replicas add nothing to them)
+    if world == 1 and not args.no_batch:
         line["batched"] = batch_section(args, stream)
-    if not args.no_adjoint:
+    if world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_section(args, stream)
-    if not args.no_mapped:
+    if world == 1 and not args.no_mapped:
         line["mapped_mixed_precision"] = mapped_section(args, stream)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
