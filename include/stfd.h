@@ -246,6 +246,10 @@ int stfd_gmres_solve(const stfd_op* A, const stfd_fd* P, const double* f_dev, do
  *                              quarter circle with control points (1,0), (1,1),
  *                              (0,1) and weights 1, 1/sqrt(2), 1; extruded over
  *                              (0,1) in the third direction when d = 3.
+ *   STFD_GEOM_REVOLVED_QUARTER_ANNULUS  d = 3: the planar quarter annulus
+ *                              (a, b) = (1 + eta_1) C(eta_2) turned by a right
+ *                              angle about the axis {(x_1, -1, 0)} (Sec. 5.1):
+ *                              F = (a, -1 + (b+1) C_x(eta_3), (b+1) C_y(eta_3)).
  * The discrete space is the push-forward of the parametric splines (eq.
  * disc_space): degree p, n_el uniform elements and maximal smoothness per
  * direction, Dirichlet reduction in every direction (n_s = n_el + p - 2).
@@ -261,7 +265,7 @@ int stfd_gmres_solve(const stfd_op* A, const stfd_fd* P, const double* f_dev, do
  * Points, elements and local functions are numbered colexicographically
  * (direction 1 fastest); point k of element e is entry e * nq^d + k.
  * ------------------------------------------------------------------------ */
-enum { STFD_GEOM_BOX = 0, STFD_GEOM_QUARTER_ANNULUS = 1 };
+enum { STFD_GEOM_BOX = 0, STFD_GEOM_QUARTER_ANNULUS = 1, STFD_GEOM_REVOLVED_QUARTER_ANNULUS = 2 };
 
 /* Physical coordinates of the quadrature points (host): x[a * Q + k] for
  * coordinate a < d and point k < Q = n_el^d nq^d. The caller evaluates c and

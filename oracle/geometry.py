@@ -7,6 +7,9 @@ The quarter annulus with radii 1 and 2 is the exact NURBS map: radial
 direction eta_1 linear, angular direction eta_2 the rational quadratic
 quarter circle with control points (1,0), (1,1), (0,1) and weights 1,
 1/sqrt(2), 1. For d = 3 the annulus is extruded in eta_3 over (0, 1).
+The revolved quarter annulus of Sec. 5.1 turns that planar annulus by a
+right angle about the axis {(x_1, -1, 0)}, the angle following the same
+rational quarter circle in eta_3.
 
 Each map returns the physical points and the Jacobian J[..., a, b] =
 d x_a / d eta_b computed from the closed form below (quotient rule for the
@@ -64,4 +67,23 @@ def quarter_annulus(eta):
     return x, J
 
 
-MAPS = {"box": box, "quarter_annulus": quarter_annulus}
+def revolved_quarter_annulus(eta):
+    """(a, b) = (1 + eta_1) C(eta_2);  F = (a, -1 + (b + 1) C_x(eta_3), (b + 1) C_y(eta_3))."""
+    eta = np.asarray(eta, dtype=np.float64)
+    r = 1.0 + eta[..., 0]
+    C2, dC2 = quarter_circle(eta[..., 1])
+    C3, dC3 = quarter_circle(eta[..., 2])
+    a, b = r * C2[..., 0], r * C2[..., 1]
+    da = np.stack([C2[..., 0], r * dC2[..., 0], np.zeros_like(r)], axis=-1)     # d a / d eta
+    db = np.stack([C2[..., 1], r * dC2[..., 1], np.zeros_like(r)], axis=-1)     # d b / d eta
+    x = np.stack([a, -1.0 + (b + 1.0) * C3[..., 0], (b + 1.0) * C3[..., 1]], axis=-1)
+    J = np.zeros(eta.shape + (3,))
+    J[..., 0, :] = da
+    J[..., 1, :] = db * C3[..., 0, None]
+    J[..., 2, :] = db * C3[..., 1, None]
+    J[..., 1, 2] += (b + 1.0) * dC3[..., 0]
+    J[..., 2, 2] += (b + 1.0) * dC3[..., 1]
+    return x, J
+
+
+MAPS = {"box": box, "quarter_annulus": quarter_annulus, "revolved_quarter_annulus": revolved_quarter_annulus}

@@ -66,12 +66,40 @@ bool geom_eval(int geom, int d, const double* eta, double* x, double* J) {
     }
     return true;
   }
+  if (geom == STFD_GEOM_REVOLVED_QUARTER_ANNULUS && d == 3) {
+    // planar annulus (a, b) = (1 + eta_1) C(eta_2), turned about {(x_1, -1, 0)} by the angle of C(eta_3)
+    const double r = 1.0 + eta[0];
+    double C2[2], dC2[2], C3[2], dC3[2];
+    quarter_circle(eta[1], C2, dC2);
+    quarter_circle(eta[2], C3, dC3);
+    const double a = r * C2[0], b = r * C2[1];
+    const double da[3] = {C2[0], r * dC2[0], 0.0}, db[3] = {C2[1], r * dC2[1], 0.0};
+    x[0] = a;
+    x[1] = -1.0 + (b + 1.0) * C3[0];
+    x[2] = (b + 1.0) * C3[1];
+    for (int k = 0; k < 3; ++k) {
+      J[0 * 3 + k] = da[k];
+      J[1 * 3 + k] = db[k] * C3[0];
+      J[2 * 3 + k] = db[k] * C3[1];
+    }
+    J[1 * 3 + 2] += (b + 1.0) * dC3[0];
+    J[2 * 3 + 2] += (b + 1.0) * dC3[1];
+    return true;
+  }
   return false;
 }
 
-// Both geometries have J^T J diagonal (C' is orthogonal to C), so only the
-// diagonal entries of G carry stiffness terms.
-bool diagonal_metric(int geom) { return geom == STFD_GEOM_BOX || geom == STFD_GEOM_QUARTER_ANNULUS; }
+bool geom_ok(int geom, int d) {
+  return geom == STFD_GEOM_BOX || (geom == STFD_GEOM_QUARTER_ANNULUS && d >= 2) ||
+         (geom == STFD_GEOM_REVOLVED_QUARTER_ANNULUS && d == 3);
+}
+
+// All three geometries have J^T J diagonal (C' is orthogonal to C, and the
+// turn is orthogonal to the plane of the annulus), so only the diagonal
+// entries of G carry stiffness terms.
+bool diagonal_metric(int geom) {
+  return geom == STFD_GEOM_BOX || geom == STFD_GEOM_QUARTER_ANNULUS || geom == STFD_GEOM_REVOLVED_QUARTER_ANNULUS;
+}
 
 // G = |det J| J^{-1} J^{-T}; returns |det J| (0 if J is singular).
 double metric(int d, const double* J, double* G) {
@@ -159,7 +187,7 @@ struct Problem {
 
 bool problem_init(Problem& P, int d, int p, int n_el, int geom, int nq) {
   if (d < 1 || d > kMaxDim || p < 1 || p > 10 || n_el < 1 || nq < 1 || nq > 32) return false;
-  if (geom != STFD_GEOM_BOX && !(geom == STFD_GEOM_QUARTER_ANNULUS && d >= 2)) return false;
+  if (!geom_ok(geom, d)) return false;
   if (n_el + p - 2 < 1) return false;
   P.d = d;
   P.p = p;
@@ -339,7 +367,7 @@ extern "C" int stfd_spatial_quadrature_points(int d, int p, int n_el, int geom, 
 
 extern "C" int stfd_spatial_element_midpoints(int d, int n_el, int geom, double* x) {
   if (d < 1 || d > kMaxDim || n_el < 1 || !x) return STFD_ERR_ARG;
-  if (geom != STFD_GEOM_BOX && !(geom == STFD_GEOM_QUARTER_ANNULUS && d >= 2)) return STFD_ERR_ARG;
+  if (!geom_ok(geom, d)) return STFD_ERR_ARG;
   long long n_elem = 1;
   for (int l = 0; l < d; ++l) n_elem *= n_el;
   double eta[3], xe[3], J[9];
@@ -447,7 +475,7 @@ extern "C" int stfd_spatial_element_stiffness(int d, int p, int n_el, int geom, 
 extern "C" int stfd_geo_separate(int d, int n_el, int geom, const double* c_mid, const double* kappa_mid,
                                  double* phi, double* Phi) {
   if (d < 1 || d > kMaxDim || n_el < 1 || !phi || !Phi) return STFD_ERR_ARG;
-  if (geom != STFD_GEOM_BOX && !(geom == STFD_GEOM_QUARTER_ANNULUS && d >= 2)) return STFD_ERR_ARG;
+  if (!geom_ok(geom, d)) return STFD_ERR_ARG;
   long long n_elem = 1;
   for (int l = 0; l < d; ++l) n_elem *= n_el;
   // log of the diagonal of frak{C} at the element midpoints: rows 0..d-1

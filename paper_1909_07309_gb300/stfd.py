@@ -19,7 +19,7 @@ STFD_FP64, STFD_TF32, STFD_BF16, STFD_DF32, STFD_FP64TC = 0, 1, 2, 3, 4
 STFD_BC_NONE, STFD_BC_INITIAL, STFD_BC_DIRICHLET = 0, 1, 2
 STFD_NOALLOC_MAX_N = 524288
 STFD_OP_FP64, STFD_OP_DF32 = 0, 1
-STFD_GEOM_BOX, STFD_GEOM_QUARTER_ANNULUS = 0, 1
+STFD_GEOM_BOX, STFD_GEOM_QUARTER_ANNULUS, STFD_GEOM_REVOLVED_QUARTER_ANNULUS = 0, 1, 2
 
 _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_dbl_p = ctypes.POINTER(ctypes.c_double)

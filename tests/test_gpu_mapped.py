@@ -189,3 +189,37 @@ def test_adjoint_gradient_workload_finite_differences_and_oracle():
         assert abs(fd - gk @ v) <= 1e-6 * np.linalg.norm(gk) * np.linalg.norm(v), (fd, gk @ v)
     _, _, _, dk = mapped.loss_and_grads(kap, host(f), host(u_obs), d, p, n_el, p, n_el, solver="gmres", tol=1e-13)
     assert np.max(np.abs(gk - dk)) <= 1e-7 * np.max(np.abs(dk))
+
+
+def _rev_quarter_table():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table_rev_quarter_iters.txt")
+    tab = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            k, ne, p, it = line.split()
+            tab[(k, int(ne), int(p))] = int(it)
+    return tab
+
+
+@pytest.mark.parametrize("n_el,p", [(8, 1), (8, 2), (8, 3), (8, 4), (16, 1), (16, 2), (16, 3), (16, 4)])
+def test_iterations_revolved_quarter_annulus_vs_table(n_el, p):
+    """Sec. 5.2, Table rev_quarter: GMRES iterations with A^ and A^G on the
+    revolved quarter annulus (gamma = nu = 1, T = 1, Krylov dimension 100) from
+    the CUDA path, right-hand side (M_t x M_s) 1. A^G within 3 of the printed
+    count (stable in p and n_el), A^ within -5..+10, A^G below half of A^."""
+    tab = _rev_quarter_table()
+    G = stfd.STFD_GEOM_REVOLVED_QUARTER_ANNULUS
+    prob = stfd.mapped_problem(3, p, n_el, G)
+    n = prob["n"]
+    N = int(np.prod(n))
+    A = stfd.StencilOp(n, p, prob["Ms"], prob["Ks"], prob["Wt"], prob["Mt"])
+    mass = stfd.StencilOp(n, p, prob["Ms"], prob["Ms"], prob["Mt"], prob["Mt"], 1.0, 0.0)
+    f = mass.matvec(torch.ones(N, dtype=torch.float64, device="cuda"))
+    K, M, Wt, Mt = stfd.heat_problem(3, p, n_el)
+    _, ih = A.gmres(stfd.FD(K, M, Wt, Mt, precision=stfd.STFD_FP64TC), f)
+    _, ig = A.gmres(stfd.geometry_preconditioner(prob, precision=stfd.STFD_FP64TC), f)
+    assert ih["converged"] and ig["converged"] and ig["rel_res_true"] <= 1e-8
+    assert abs(ig["iters"] - tab[("AG", n_el, p)]) <= 3, ig["iters"]
+    assert -5 <= ih["iters"] - tab[("Ahat", n_el, p)] <= 10, ih["iters"]
+    assert 2 * ig["iters"] < ih["iters"]

@@ -8,7 +8,8 @@ import scipy.sparse as sp
 from oracle import geometry, mapped, matrices as omat
 from paper_1909_07309_gb300 import stfd
 
-GEOMS = {"box": stfd.STFD_GEOM_BOX, "quarter_annulus": stfd.STFD_GEOM_QUARTER_ANNULUS}
+GEOMS = {"box": stfd.STFD_GEOM_BOX, "quarter_annulus": stfd.STFD_GEOM_QUARTER_ANNULUS,
+         "revolved_quarter_annulus": stfd.STFD_GEOM_REVOLVED_QUARTER_ANNULUS}
 
 
 def kappa_lib(x):          # x: (d, m)
@@ -51,7 +52,7 @@ def stencil_to_csr(st, d, p, n_s):
 
 @pytest.mark.parametrize("d,p,n_el,geom,nq", [(2, 3, 5, "quarter_annulus", 4), (2, 2, 6, "box", 3),
                                               (3, 2, 3, "quarter_annulus", 3), (2, 4, 4, "quarter_annulus", 6),
-                                              (1, 2, 7, "box", 3)])
+                                              (1, 2, 7, "box", 3), (3, 3, 3, "revolved_quarter_annulus", 4)])
 def test_spatial_assembly_matches_oracle(d, p, n_el, geom, nq):
     var = geom != "box"
     xq = stfd.spatial_quadrature_points(d, p, n_el, GEOMS[geom], nq)
