@@ -352,7 +352,12 @@ def main():
     ap.add_argument("--mapped-n-el", type=int, default=0, help="elements per direction of the mapped workload")
     ap.add_argument("--mapped-steps", type=int, default=2)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--oracle-once", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_once:   # child of the cpu_baseline leg: one oracle solve, one JSON line
+        secs, _, iters, Nc, _ = run_oracle_solve(inputs.SCALE)
+        print(json.dumps({"value": Nc / secs, "seconds": secs, "iters": iters}), flush=True)
+        return 0
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -576,6 +581,17 @@ def main():
         line["cpu_baseline"] = {"value": Nc / secs, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
                                 "sample": "one full oracle solve of the same workload (setup excluded), "
                                           "%d GMRES iteration(s), %.1f s" % (iters, secs)}
+        # the paper's setting is serial: the same solve with one BLAS thread, in a child
+        # process (the thread count is fixed when numpy loads)
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        try:
+            out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-once"], env=env,
+                                 capture_output=True, text=True, timeout=600)
+            one = json.loads(out.stdout.strip().splitlines()[-1])
+            line["cpu_baseline"]["single_thread_value"] = one["value"]
+            line["cpu_baseline"]["single_thread_sample"] = "the same solve, 1 BLAS thread (%.1f s)" % one["seconds"]
+        except (subprocess.SubprocessError, ValueError, IndexError, KeyError):
+            line["cpu_baseline"]["single_thread_value"] = None
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -477,7 +477,27 @@ extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* 
   std::stable_sort(b->items.begin(), b->items.end(),
                    [&](const BItem& x, const BItem& y) { return probs[x.prob].N > probs[y.prob].N; });
   b->n_items = (int)b->items.size();
-  b->max_ctas = 8;
+  // shared memory of the mode products, then the configurations that fit; the
+  // scratch holds one slot per CTA of the largest grid that will be launched
+  const size_t smem = (size_t)b->max_n * 32 * sizeof(float2);
+  if (set_smem<128>(smem) != cudaSuccess || set_smem<256>(smem) != cudaSuccess || set_smem<512>(smem) != cudaSuccess) {
+    stfd_batch_destroy(b);
+    return STFD_ERR_CUDA;
+  }
+  bool fits[kNumCandidates];
+  b->max_ctas = 0;
+  for (int c = 0; c < kNumCandidates; ++c) {
+    fits[c] = feasible(kCandidates[c].threads, kCandidates[c].ctas, smem);
+    if (fits[c] && autotune) b->max_ctas = std::max(b->max_ctas, kCandidates[c].ctas);
+  }
+  if (!autotune) {
+    if (!feasible(b->threads, b->ctas_per_sm, smem)) b->ctas_per_sm = 1;
+    b->max_ctas = b->ctas_per_sm;
+  }
+  if (b->max_ctas == 0) {
+    stfd_batch_destroy(b);
+    return STFD_ERR_ARG;   // no configuration fits (too large a factor for shared memory)
+  }
   auto up = [&](auto** dst, const auto* src, size_t cnt) -> int {
     if (cudaMalloc((void**)dst, cnt * sizeof(**dst)) != cudaSuccess) return STFD_ERR_ALLOC;
     if (src && cudaMemcpyAsync(*dst, src, cnt * sizeof(**dst), cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -495,10 +515,6 @@ extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* 
   if (rc == STFD_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) rc = STFD_ERR_CUDA;
   // autotune: time every feasible candidate on this batch with synthetic right-hand sides
   b->tune_ms.assign(kNumCandidates, NAN);
-  const size_t smem = (size_t)b->max_n * 32 * sizeof(float2);
-  if (rc == STFD_OK && (set_smem<128>(smem) != cudaSuccess || set_smem<256>(smem) != cudaSuccess ||
-                        set_smem<512>(smem) != cudaSuccess))
-    rc = STFD_ERR_CUDA;
   if (rc == STFD_OK && autotune) {
     const long long total = b->offsets[count];
     double *ft = nullptr, *ut = nullptr;
@@ -514,7 +530,7 @@ extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* 
       double best = 1e30;
       for (int c = 0; c < kNumCandidates && rc == STFD_OK; ++c) {
         const Candidate cd = kCandidates[c];
-        if (!feasible(cd.threads, cd.ctas, smem)) continue;
+        if (!fits[c]) continue;
         if (launch_batch(b, cd.threads, cd.ctas, ft, ut, nullptr, st) != cudaSuccess) rc = STFD_ERR_CUDA;
         cudaEventRecord(e0, st);
         for (int r = 0; r < 2 && rc == STFD_OK; ++r)
@@ -535,8 +551,6 @@ extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* 
     }
     cudaFree(ft);
     cudaFree(ut);
-  } else if (rc == STFD_OK && !feasible(b->threads, b->ctas_per_sm, smem)) {
-    b->ctas_per_sm = 1;
   }
   if (rc != STFD_OK) {
     stfd_batch_destroy(b);
