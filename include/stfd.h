@@ -361,9 +361,10 @@ int stfd_grad_kappa_elements(const stfd_op* A, int p, int n_el, const double* Ke
  * n_s, n_t <= 256; at most 2^20 dofs per problem; count >= 1.
  * autotune != 0 times every candidate CTA configuration (threads per CTA x
  * CTAs per SM, see stfd_batch_stats) on the batch with synthetic right-hand
- * sides and keeps the fastest; otherwise 256 threads x 4 CTAs per SM.
+ * sides and keeps the fastest; otherwise 256 threads x the largest of 4, 2, 1
+ * CTAs per SM that fits.
  * Device memory: factors, 4 * max_N float pairs of scratch per CTA slot
- * (SMs x 8 slots) and the work list.
+ * (SMs x the largest CTAs-per-SM count that can be launched) and the work list.
  * ------------------------------------------------------------------------ */
 typedef struct stfd_batch stfd_batch;
 

@@ -490,8 +490,9 @@ extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* 
     fits[c] = feasible(kCandidates[c].threads, kCandidates[c].ctas, smem);
     if (fits[c] && autotune) b->max_ctas = std::max(b->max_ctas, kCandidates[c].ctas);
   }
-  if (!autotune) {
-    if (!feasible(b->threads, b->ctas_per_sm, smem)) b->ctas_per_sm = 1;
+  if (!autotune) {   // 256 threads, as many CTAs per SM (4, 2 or 1) as fit
+    b->threads = 256;
+    b->ctas_per_sm = feasible(256, 4, smem) ? 4 : (feasible(256, 2, smem) ? 2 : 1);
     b->max_ctas = b->ctas_per_sm;
   }
   if (b->max_ctas == 0) {
