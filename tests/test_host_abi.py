@@ -122,3 +122,40 @@ def test_argument_errors():
     with pytest.raises(stfd.StfdError) as e:
         stfd.stfd_fd_factors([big], [big], Wt, Mt)
     assert e.value.code == -1
+
+
+def test_argument_errors_of_the_device_entry_points():
+    """Invalid arguments are rejected before any CUDA call (so this runs on a
+    host without a GPU): NULL handles and pointers, bad sizes and options."""
+    lib = stfd.load()
+    vp = ctypes.c_void_p()
+    n3 = (ctypes.c_int * 3)(4, 4, 5)
+    z = np.zeros(25 * 16)
+    dp = stfd._dptr(z)
+    # stencil op: NULL out, NULL matrices, bad half-bandwidth, bad arithmetic
+    assert lib.stfd_op_create_stencil(None, 2, n3, 1, dp, dp, dp, dp, 1.0, 1.0, 1, None) == -1
+    assert lib.stfd_op_create_stencil(ctypes.byref(vp), 2, n3, 1, None, dp, dp, dp, 1.0, 1.0, 1, None) == -1
+    assert lib.stfd_op_create_stencil(ctypes.byref(vp), 2, n3, -1, dp, dp, dp, dp, 1.0, 1.0, 1, None) == -1
+    assert lib.stfd_op_create_stencil(ctypes.byref(vp), 2, n3, 1, dp, dp, dp, dp, 1.0, 1.0, 7, None) == -1
+    assert lib.stfd_op_create_stencil(ctypes.byref(vp), 4, n3, 1, dp, dp, dp, dp, 1.0, 1.0, 1, None) == -1
+    assert not vp.value
+    # transposed applies / matvecs and gradients on NULL handles
+    assert lib.stfd_fd_apply_transpose(None, None, None, 1, None) == -1
+    assert lib.stfd_st_matvec_transpose(None, None, None, 1, None) == -1
+    assert lib.stfd_fd_set_scaling(None, dp, dp, None) == -1
+    assert lib.stfd_grad_kappa_elements(None, 2, 4, None, None, None, None, None) == -1
+    # GMRES options: transpose must be 0 or 1 (checked with NULL vectors first -> -1 either way)
+    assert lib.stfd_gmres_solve(None, None, None, None, None, None, None) == -1
+    # batch: empty, bad sizes, unsupported dimension
+    ints = (ctypes.c_int * 2)(4, 5)
+    one = (ctypes.c_int * 2)(1, 1)
+    assert lib.stfd_batch_create(ctypes.byref(vp), 0, 2, ints, ints, one, 1.0, 1.0, 1.0, 0, None) == -1
+    assert lib.stfd_batch_create(ctypes.byref(vp), 2, 4, ints, ints, one, 1.0, 1.0, 1.0, 0, None) == -1
+    assert lib.stfd_batch_create(ctypes.byref(vp), 2, 2, ints, ints, one, -1.0, 1.0, 1.0, 0, None) == -1
+    assert lib.stfd_batch_solve(None, None, None, None, None) == -1
+    assert lib.stfd_batch_item(None, 0, None, None) == -1
+    # mapped-domain host entry points
+    assert lib.stfd_spatial_assemble(2, 2, 3, 1, 0, None, None, dp, dp) == -1          # nq = 0
+    assert lib.stfd_spatial_assemble(2, 2, 3, 2, 3, None, None, dp, dp) == -1          # revolved needs d = 3
+    assert lib.stfd_spatial_element_midpoints(2, 3, 9, dp) == -1
+    assert lib.stfd_spline_matrices_weighted(2, 3, 1.0, 5, None, None, None, None, None) == -1
