@@ -567,8 +567,13 @@ def main():
                     "frac": achieved / peak, "traffic": traffic, "kernel": top["name"], "peak_source": src,
                     "achieved_gbs": top["bytes"] / top["launches"] / per_launch_s / 1e9,
                     "share_of_step": top["ms"] / total_ms, "fp64_probe_tflops": probe / 1e12}
+    # per kernel family: time share and the achieved rates of its algorithmic work
+    # (FP64-equivalent flops, minimum HBM bytes: each input read once, each output written once)
     kernels = {rc["name"]: {"launches": rc["launches"], "ms": round(rc["ms"], 3),
-                            "share": round(rc["ms"] / total_ms, 4)} for rc in recs}
+                            "share": round(rc["ms"] / total_ms, 4),
+                            "fp64_eq_tflops": round(rc["flops"] / (rc["ms"] * 1e-3) / 1e12, 3) if rc["ms"] > 0 else None,
+                            "algorithmic_gbs": round(rc["bytes"] / (rc["ms"] * 1e-3) / 1e9, 1) if rc["ms"] > 0 else None}
+               for rc in recs}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
