@@ -136,6 +136,42 @@ def spatial_matrices(d, p, n_el, geom="quarter_annulus", c=None, kappa=None, kap
     return Ms, Ks
 
 
+def spatial_rows(d, p, n_el, rows, geom="quarter_annulus", c=None, kappa=None, nq=None):
+    """Rows of the reduced M_s and K_s for the given reduced row indices, each
+    by quadrature over the (at most (p+1)^d) elements in the row's support:
+    returns {row: (columns, M values, K values)}. For sizes where the whole
+    matrix is too large to assemble here."""
+    nq = p + 1 if nq is None else nq
+    tabs = _tables(p, n_el, nq)
+    n_s = n_el + p - 2
+    out = {}
+    for row in rows:
+        idx = [(row // n_s ** l) % n_s for l in range(d)]
+        full = [i + 1 for i in idx]                      # full 1D index (the first function was dropped)
+        ranges = [range(max(0, f - p), min(n_el, f + 1)) for f in full]   # elements where b_f is non-zero
+        acc_m, acc_k = {}, {}
+        for e_rev in itertools.product(*reversed(ranges)):
+            e = tuple(reversed(e_rev))
+            eta, wq, V, G, act, x, J = _element_data(d, p, n_el, nq, geom, e, tabs)
+            detJ = np.linalg.det(J)
+            Jinv = np.linalg.inv(J)
+            Cmat = np.abs(detJ)[:, None, None] * np.einsum("qab,qcb->qac", Jinv, Jinv)
+            cval = np.ones(len(wq)) if c is None else c(x)
+            kval = np.ones(len(wq)) if kappa is None else kappa(x)
+            # local index of the row's function in this element (colexicographic)
+            a_loc = sum((full[l] - e[l]) * (p + 1) ** l for l in range(d))
+            g = _global_reduced(d, p, n_el, act)
+            mrow = V[:, a_loc] @ ((wq * cval * np.abs(detJ))[:, None] * V)
+            krow = np.einsum("q,qa,qab,qjb->j", wq * kval, G[:, a_loc, :], Cmat, G)
+            for j, gj in enumerate(g):
+                if gj >= 0:
+                    acc_m[gj] = acc_m.get(gj, 0.0) + mrow[j]
+                    acc_k[gj] = acc_k.get(gj, 0.0) + krow[j]
+        cols = np.array(sorted(acc_m))
+        out[row] = (cols, np.array([acc_m[j] for j in cols]), np.array([acc_k[j] for j in cols]))
+    return out
+
+
 def full_spatial_matrices(d, p, n_el, geom="quarter_annulus", nq=None):
     """Unreduced (M, K) over all (n_el + p)^d functions, unit coefficients (for pins)."""
     nq = p + 1 if nq is None else nq
@@ -226,19 +262,21 @@ def l2_error(u, d, p, n_el, p_t, n_el_t, exact, geom="quarter_annulus", T=1.0, n
 def coefficient_diagonal(d, n_el, geom="quarter_annulus", c=None, kappa=None, kappa_elem=None):
     """Per element (colexicographic), the diagonal of frak{C} at the element
     midpoint: rows l < d: kappa |det J| [J^{-1} J^{-T}]_{ll}; row d: c |det J|."""
-    out = np.zeros((d + 1, n_el ** d))
-    for eid, e in enumerate(element_ids(d, n_el)):
-        eta = (np.array(e, dtype=np.float64) + 0.5) / n_el
-        x, J = geometry.MAPS[geom](eta[None, :])
-        J = J[0]
-        det = abs(np.linalg.det(J))
-        Jinv = np.linalg.inv(J)
-        Cm = det * (Jinv @ Jinv.T)
-        kv = float(kappa_elem[eid]) if kappa_elem is not None else (1.0 if kappa is None else float(kappa(x)[0]))
-        cv = 1.0 if c is None else float(c(x)[0])
-        for l in range(d):
-            out[l, eid] = kv * Cm[l, l]
-        out[d, eid] = cv * det
+    ids = element_ids(d, n_el)
+    eta = (np.array(ids, dtype=np.float64) + 0.5) / n_el          # (n_elem, d)
+    x, J = geometry.MAPS[geom](eta)
+    det = np.abs(np.linalg.det(J))
+    Jinv = np.linalg.inv(J)
+    Cm = det[:, None, None] * np.einsum("eab,ecb->eac", Jinv, Jinv)
+    if kappa_elem is not None:
+        kv = np.asarray(kappa_elem, dtype=np.float64)
+    else:
+        kv = np.ones(len(ids)) if kappa is None else kappa(x)
+    cv = np.ones(len(ids)) if c is None else c(x)
+    out = np.zeros((d + 1, len(ids)))
+    for l in range(d):
+        out[l] = kv * Cm[:, l, l]
+    out[d] = cv * det
     return out
 
 

@@ -223,3 +223,64 @@ def test_iterations_revolved_quarter_annulus_vs_table(n_el, p):
     assert abs(ig["iters"] - tab[("AG", n_el, p)]) <= 3, ig["iters"]
     assert -5 <= ih["iters"] - tab[("Ahat", n_el, p)] <= 10, ih["iters"]
     assert 2 * ig["iters"] < ih["iters"]
+
+
+def test_mapped_workload_full_size_sampled_rows():
+    """The mixed-precision workload at full size (quarter annulus extruded, d = 3,
+    p = 4, 96 elements, N = 93,178,008), in the arithmetic bench.py times:
+    (1) sampled rows of the double-float stencil matvec against rows the oracle
+    assembles one by one (rounding bound 1e-12 of the absolute-value sum);
+    (2) sampled rows of A~ (A~^{-1} r) = r for the FP64-accurate preconditioner
+    on the weighted factors, with the oracle's own separation and univariate
+    matrices (1e-10 of max |r|, as the unit-cube full-size check)."""
+    cfg = inputs.MAPPED
+    d, p, n_el = cfg["d"], cfg["p"], cfg["n_el"]
+    prob = stfd.mapped_problem(d, p, n_el, QA, c=inputs.c_bilinear, kappa=inputs.kappa_trig)
+    n = prob["n"]
+    ns, nt = n[0], n[-1]
+    Ns = ns ** d
+    N = Ns * nt
+    A = stfd.StencilOp(n, p, prob["Ms"], prob["Ks"], prob["Wt"], prob["Mt"], arith=stfd.STFD_OP_DF32)
+    x = inputs.standard_normal(N, 61)
+    y = host(A.matvec(dev(x)))
+    A.close()
+    torch.cuda.empty_cache()
+    g = np.random.default_rng(62)
+    samples = [(int(g.integers(Ns)), int(g.integers(nt))) for _ in range(24)]
+    rows = mapped.spatial_rows(d, p, n_el, sorted({i for i, _ in samples}), "quarter_annulus", c=c_or, kappa=kappa_or)
+    Wt, Mt = omat.time_matrices(p, n_el, 1.0)
+    X = x.reshape(nt, Ns)
+    for i, t in samples:
+        cols, mv, kv = rows[i]
+        val = bound = 0.0
+        for tau in range(max(0, t - p), min(nt, t + p + 1)):
+            xs = X[tau, cols]
+            val += Wt[t, tau] * (mv @ xs) + Mt[t, tau] * (kv @ xs)
+            bound += abs(Wt[t, tau]) * (np.abs(mv) @ np.abs(xs)) + abs(Mt[t, tau]) * (np.abs(kv) @ np.abs(xs))
+        assert abs(y[i + Ns * t] - val) <= 1e-12 * bound, (i, t)
+    del y
+    P = stfd.geometry_preconditioner(prob, precision=stfd.STFD_DF32, scaled=False)
+    r = inputs.standard_normal(N, 63)
+    s = host(P.apply(dev(r))).reshape(nt, ns, ns, ns)          # [t][i3][i2][i1]
+    P.close()
+    Cd = mapped.coefficient_diagonal(d, n_el, "quarter_annulus", c=c_or, kappa=kappa_or)
+    phi, Phi = mapped.separate(Cd, d, n_el)
+    KM = [mapped.weighted_matrices(p, n_el, phi[l], Phi[l]) for l in range(d)]
+    Kl, Ml = [k for k, _ in KM], [m for _, m in KM]
+    worst = 0.0
+    for i, t in samples:
+        i1, i2, i3 = i % ns, (i // ns) % ns, i // ns ** 2
+        r3 = slice(max(0, i3 - p), i3 + p + 1)
+        r2 = slice(max(0, i2 - p), i2 + p + 1)
+        r1 = slice(max(0, i1 - p), i1 + p + 1)
+        val = 0.0
+        for tau in range(max(0, t - p), min(nt, t + p + 1)):
+            blk = s[tau, r3, r2, r1]
+            m3, m2, m1 = Ml[2][i3, r3], Ml[1][i2, r2], Ml[0][i1, r1]
+            k3, k2, k1 = Kl[2][i3, r3], Kl[1][i2, r2], Kl[0][i1, r1]
+            mass = np.einsum("c,b,a,cba->", m3, m2, m1, blk)
+            stiff = (np.einsum("c,b,a,cba->", m3, m2, k1, blk) + np.einsum("c,b,a,cba->", m3, k2, m1, blk) +
+                     np.einsum("c,b,a,cba->", k3, m2, m1, blk))
+            val += Wt[t, tau] * mass + Mt[t, tau] * stiff
+        worst = max(worst, abs(val - r[i + Ns * t]))
+    assert worst <= 1e-10 * np.max(np.abs(r)), worst

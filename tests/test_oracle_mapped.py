@@ -212,3 +212,19 @@ def test_oracle_iterations_match_table_rev_quarter(p):
     assert abs(i_g["iters"] - tab[("AG", n_el, p)]) <= 3, i_g["iters"]
     assert -5 <= i_hat["iters"] - tab[("Ahat", n_el, p)] <= 8, i_hat["iters"]
     assert 2 * i_g["iters"] < i_hat["iters"]
+
+
+def test_spatial_rows_equal_assembled_rows():
+    """The row-by-row assembly used for full-size samples equals the rows of
+    the whole assembled matrices."""
+    d, p, n_el = 3, 3, 4
+    kap = lambda X: 1 + 0.5 * np.sin(2 * np.pi * X[..., 0]) * np.cos(2 * np.pi * X[..., 1])
+    cc = lambda X: 1 + 0.3 * X[..., 0] * X[..., 1]
+    Ms, Ks = mapped.spatial_matrices(d, p, n_el, c=cc, kappa=kap)
+    rows = [0, 7, 31, Ms.shape[0] - 1]
+    got = mapped.spatial_rows(d, p, n_el, rows, c=cc, kappa=kap)
+    for r in rows:
+        cols, mv, kv = got[r]
+        assert np.array_equal(cols, Ms[r].indices[np.argsort(Ms[r].indices)])
+        assert np.max(np.abs(mv - Ms[r].toarray()[0, cols])) <= 1e-15
+        assert np.max(np.abs(kv - Ks[r].toarray()[0, cols])) <= 1e-14
