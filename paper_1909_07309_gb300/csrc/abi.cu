@@ -1031,13 +1031,6 @@ int ensure_work(GmresWork* w, int restart) {
   return STFD_OK;
 }
 
-// out[0] = ||x||^2 (device) via the multi-dot kernel with m = 1.
-int device_dot(GmresWork* w, const double* const* dptr_of_x, const double* y, long long N, double* out,
-               cudaStream_t st) {
-  STFD_CU(launch_dot_multi(dptr_of_x, 1, y, N, w->partial, dot_blocks(), st));
-  STFD_CU(launch_reduce_partial(w->partial, 1, dot_blocks(), out, 0, st));
-  return STFD_OK;
-}
 
 }  // namespace
 
@@ -1075,41 +1068,43 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
     info->rel_res_true = 1.0;
     info->hist_len = 0;
   }
-  // Residual of the current iterate into V[0] and its squared norm to the host.
-  auto residual = [&](bool u_is_zero, double* nrm2) -> int {
-    if (u_is_zero) {
-      STFD_CU(cudaMemcpyAsync(w->V[0], f, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    } else {
+  // Residual r = f - A u (r = f while u is zero) and ||r||^2 to the host in one
+  // fused pass; r is stored in V[0] only when a new cycle starts from it.
+  auto residual = [&](bool u_is_zero, bool write_v0, double* nrm2) -> int {
+    const double* Au = nullptr;
+    if (!u_is_zero) {
       int r2 = matvec_one(A, u, w->V[1], tr, st);
       if (r2 != STFD_OK) return r2;
-      STFD_CU(launch_sub(w->V[0], f, w->V[1], N, st));
+      Au = w->V[1];
     }
-    int r3 = device_dot(w, w->dV, w->V[0], N, dnrm, st);
-    if (r3 != STFD_OK) return r3;
+    STFD_CU(launch_sub_norm(write_v0 ? w->V[0] : nullptr, f, Au, N, w->partial, nb, st));
+    STFD_CU(launch_reduce_partial(w->partial, 1, nb, dnrm, 0, st));
     STFD_CU(cudaMemcpyAsync(hb + 2 * m + 2, dnrm, sizeof(double), cudaMemcpyDeviceToHost, st));
     STFD_CU(cudaStreamSynchronize(st));
     *nrm2 = hb[2 * m + 2];
     return STFD_OK;
   };
-  STFD_CU(cudaMemsetAsync(u, 0, (size_t)N * sizeof(double), st));
   double nrm2 = 0.0;
-  if ((rc = residual(true, &nrm2)) != STFD_OK) return rc;
+  if ((rc = residual(true, false, &nrm2)) != STFD_OK) return rc;
   const double fnorm = std::sqrt(nrm2);
   if (!std::isfinite(fnorm)) return STFD_ERR_NAN;
   if (fnorm == 0.0) {
+    STFD_CU(cudaMemsetAsync(u, 0, (size_t)N * sizeof(double), st));
     if (info) {
       info->converged = 1;
       info->rel_res_est = info->rel_res_true = 0.0;
     }
     return STFD_OK;
   }
+  const double* v0_src = f;   // the first cycle starts from r = f (u = 0)
+  bool first_cycle = true;    // u is written (not accumulated) by the first update
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   int total = 0;
   bool converged = false;
   double est = 1.0, beta = fnorm;
   while (true) {
     // v_0 = r / beta  (dnrm still holds ||r||^2 on the device)
-    STFD_CU(launch_scale_by_inverse(w->V[0], w->V[0], dnrm, N, 1, st));
+    STFD_CU(launch_scale_by_inverse(w->V[0], v0_src, dnrm, N, 1, st));
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int j_done = 0;
@@ -1117,6 +1112,9 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
     for (int j = 0; j < m && total < o.max_it; ++j) {
       if ((rc = ensure_vec(w->V, w->dV, j + 1, N)) != STFD_OK) return rc;
       if ((rc = ensure_vec(w->Z, w->dZ, j, N)) != STFD_OK) return rc;
+      // v_j = w_j / ||w_j||: the normalisation deferred from the previous
+      // iteration (dnrm still holds ||w_j||^2), skipped when the cycle stops there
+      if (j > 0) STFD_CU(launch_scale_by_inverse(w->V[j], w->V[j], dnrm, N, 1, st));
       // z_j = P^{-1} v_j ;  w = A z_j  (built in V[j+1]); P^{-T}, A^T when transposed
       if ((rc = fd_apply_one(P, w->V[j], w->Z[j], P->work, tr, st)) != STFD_OK) return rc;
       if ((rc = matvec_one(A, w->Z[j], w->V[j + 1], tr, st)) != STFD_OK) return rc;
@@ -1126,9 +1124,9 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
       STFD_CU(launch_multi_axpy(w->V[j + 1], w->dV, dh, j + 1, N, -1.0, st));
       STFD_CU(launch_dot_multi(w->dV, j + 1, w->V[j + 1], N, w->partial, nb, st));
       STFD_CU(launch_reduce_partial(w->partial, j + 1, nb, dh2, 0, st));
-      STFD_CU(launch_multi_axpy(w->V[j + 1], w->dV, dh2, j + 1, N, -1.0, st));
-      if ((rc = device_dot(w, w->dV + (j + 1), w->V[j + 1], N, dnrm, st)) != STFD_OK) return rc;
-      STFD_CU(launch_scale_by_inverse(w->V[j + 1], w->V[j + 1], dnrm, N, 1, st));
+      // second update fused with ||w||^2 (the normalisation of w happens next iteration)
+      STFD_CU(launch_axpy_norm(w->V[j + 1], w->dV, dh2, j + 1, N, -1.0, 0, w->partial, nb, st));
+      STFD_CU(launch_reduce_partial(w->partial, 1, nb, dnrm, 0, st));
       STFD_CU(cudaMemcpyAsync(hb, dh, (size_t)(2 * m + 3) * sizeof(double), cudaMemcpyDeviceToHost, st));
       STFD_CU(cudaStreamSynchronize(st));
       double* c = &H[(size_t)(m + 1) * j];
@@ -1171,10 +1169,12 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
     }
     std::copy(y.begin(), y.begin() + j_done, hb);
     STFD_CU(cudaMemcpyAsync(dh, hb, (size_t)j_done * sizeof(double), cudaMemcpyHostToDevice, st));
-    STFD_CU(launch_multi_axpy(u, w->dZ, dh, j_done, N, 1.0, st));
+    STFD_CU(launch_axpy_norm(u, w->dZ, dh, j_done, N, 1.0, first_cycle ? 1 : 0, nullptr, nb, st));
+    first_cycle = false;
     if (converged || lucky || total >= o.max_it) break;
     // restart from the true residual
-    if ((rc = residual(false, &nrm2)) != STFD_OK) return rc;
+    if ((rc = residual(false, true, &nrm2)) != STFD_OK) return rc;
+    v0_src = w->V[0];
     beta = std::sqrt(nrm2);
     if (!std::isfinite(beta)) return STFD_ERR_NAN;
     if (beta <= o.tol * fnorm) {
@@ -1183,8 +1183,8 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
       break;
     }
   }
-  // true residual ||f - A u|| / ||f||
-  if ((rc = residual(false, &nrm2)) != STFD_OK) return rc;
+  // true residual ||f - A u|| / ||f|| (explicit matvec, no vector stored)
+  if ((rc = residual(false, false, &nrm2)) != STFD_OK) return rc;
   const double true_res = std::sqrt(nrm2) / fnorm;
   if (info) {
     info->iters = total;

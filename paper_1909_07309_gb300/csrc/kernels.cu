@@ -211,6 +211,57 @@ k_multi_axpy(double* __restrict__ w, const double* const* __restrict__ V, const 
   }
 }
 
+// w[k] = (set ? 0 : w[k]) + sign * sum_i h[i] V_i[k], and partial[block] = the
+// block's share of sum_k w[k]^2 of the result (the norm fused into the update).
+__global__ void __launch_bounds__(kDotThreads)
+k_axpy_norm(double* __restrict__ w, const double* const* __restrict__ V, const double* __restrict__ h, int m,
+            long long N, double sign, int set, double* __restrict__ partial) {
+  __shared__ double red[kDotThreads / 32];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  double sq = 0.0;
+  for (long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; k0 < N; k0 += 4 * stride) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < m; ++i) {
+      const double* vi = V[i];
+      const double hi = h[i];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long k = k0 + u * stride;
+        if (k < N) acc[u] = fma(hi, __ldg(vi + k), acc[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long k = k0 + u * stride;
+      if (k < N) {
+        const double v = set ? sign * acc[u] : fma(sign, acc[u], w[k]);
+        w[k] = v;
+        sq = fma(v, v, sq);
+      }
+    }
+  }
+  if (partial) {
+    const double t = block_sum(sq, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+  }
+}
+
+// r = f - y (y may be NULL: r = f); out[k] = r if out is not NULL; partial[block]
+// = the block's share of sum_k r^2.
+__global__ void __launch_bounds__(kDotThreads)
+k_sub_norm(double* __restrict__ out, const double* __restrict__ f, const double* __restrict__ y, long long N,
+           double* __restrict__ partial) {
+  __shared__ double red[kDotThreads / 32];
+  double sq = 0.0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (long long)gridDim.x * blockDim.x) {
+    const double r = y ? f[k] - y[k] : f[k];
+    if (out) out[k] = r;
+    sq = fma(r, r, sq);
+  }
+  const double t = block_sum(sq, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
 // y = x / den (or x / sqrt(den)); leaves x unscaled when the divisor is not positive.
 __global__ void k_scale_by_inverse(double* __restrict__ y, const double* __restrict__ x,
                                    const double* __restrict__ den, long long N, int sqrt_den) {
@@ -325,6 +376,20 @@ cudaError_t launch_scale_by_inverse(double* y, const double* x, const double* de
                                     int sqrt_den, cudaStream_t st) {
   ProfScope ps("gmres_scale", (double)N, 16.0 * N, st);
   k_scale_by_inverse<<<grid_for(N, 256), 256, 0, st>>>(y, x, den, N, sqrt_den);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_norm(double* w, const double* const* V, const double* h, int m, long long N, double sign,
+                             int set, double* partial, int nblocks, cudaStream_t st) {
+  ProfScope ps("gmres_multi_axpy", 2.0 * N * m + 2.0 * N, 8.0 * N * (m + (set ? 1 : 2)), st);
+  k_axpy_norm<<<nblocks, kDotThreads, 0, st>>>(w, V, h, m, N, sign, set, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub_norm(double* out, const double* f, const double* y, long long N, double* partial,
+                            int nblocks, cudaStream_t st) {
+  ProfScope ps("gmres_sub_norm", 3.0 * N, 8.0 * N * ((y ? 2 : 1) + (out ? 1 : 0)), st);
+  k_sub_norm<<<nblocks, kDotThreads, 0, st>>>(out, f, y, N, partial);
   return cudaGetLastError();
 }
 

@@ -66,6 +66,13 @@ cudaError_t launch_scale_by_inverse(double* y, const double* x, const double* de
                                     int sqrt_den, cudaStream_t st);
 // y[k] = a[k] - b[k]
 cudaError_t launch_sub(double* y, const double* a, const double* b, long long N, cudaStream_t st);
+// w = (set ? 0 : w) + sign sum_i h[i] V_i; partial[b] (nblocks entries, if not NULL)
+// receives block b's share of ||w||^2 of the result.
+cudaError_t launch_axpy_norm(double* w, const double* const* V, const double* h, int m, long long N, double sign,
+                             int set, double* partial, int nblocks, cudaStream_t st);
+// r = f - y (y NULL: r = f), written to out if out is not NULL; partial[b] = block b's share of ||r||^2.
+cudaError_t launch_sub_norm(double* out, const double* f, const double* y, long long N, double* partial,
+                            int nblocks, cudaStream_t st);
 
 // Double-float banded passes of the matvec (band_df.cu); factors row-major (hi, lo):
 //   first direction:  (Uo, Vo) = (x x M, x x K), x FP64
