@@ -141,7 +141,7 @@ __device__ double block_sum(double v, double* red) {
 }
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 2048 / THREADS / 2)
 k_batch(const BProb* __restrict__ probs, const BItem* __restrict__ items, int n_items, const float2* __restrict__ pool,
         const double* __restrict__ f, double* __restrict__ u, double* __restrict__ relres,
         unsigned long long* __restrict__ times, int* __restrict__ counter, float2* __restrict__ scratch,
