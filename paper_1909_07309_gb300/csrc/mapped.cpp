@@ -8,9 +8,9 @@
 //     G = |det J| J^{-1} J^{-T},
 // are integrated by sum factorisation over the tensor Gauss points (one
 // direction contracted at a time), then scattered into the tensor-product
-// stencil layout described in stfd.h. Elements are processed in colours of
-// the last spatial direction (index mod p+1) so that threads never write the
-// same row.
+// stencil layout described in stfd.h. Lines of elements along direction 1 are
+// processed in colours of the outer directions (indices mod p+1) so that
+// threads never write the same row.
 #include <algorithm>
 #include <cmath>
 #include <thread>
@@ -354,14 +354,20 @@ extern "C" int stfd_spatial_quadrature_points(int d, int p, int n_el, int geom, 
   Problem P;
   if (!problem_init(P, d, p, n_el, geom, nq) || !x) return STFD_ERR_ARG;
   const long long Q = P.n_elem * P.Qe;
-  std::vector<double> xe, detw, Gw;
-  int ei[3];
-  for (long long e = 0; e < P.n_elem; ++e) {
-    elem_index(P, e, ei);
-    element_geometry(P, ei, xe, detw, Gw);
-    for (int q = 0; q < P.Qe; ++q)
-      for (int a = 0; a < d; ++a) x[(size_t)a * Q + e * P.Qe + q] = xe[(size_t)q * d + a];
-  }
+  const int nt = (int)std::min<long long>(n_threads(), P.n_elem);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t]() {
+      std::vector<double> xe, detw, Gw;
+      int ei[3];
+      for (long long e = t; e < P.n_elem; e += nt) {
+        elem_index(P, e, ei);
+        element_geometry(P, ei, xe, detw, Gw);
+        for (int q = 0; q < P.Qe; ++q)
+          for (int a = 0; a < d; ++a) x[(size_t)a * Q + e * P.Qe + q] = xe[(size_t)q * d + a];
+      }
+    });
+  for (auto& t : th) t.join();
   return STFD_OK;
 }
 
@@ -423,10 +429,25 @@ extern "C" int stfd_spatial_assemble(int d, int p, int n_el, int geom, int nq, c
       }
     }
   };
-  long long inner_elems = P.n_elem / n_el;   // elements per value of the last index
-  for (int colour = 0; colour <= p; ++colour) {
-    std::vector<int> items;
-    for (int k = colour; k < n_el; k += p + 1) items.push_back(k);
+  // Colours: elements whose outer indices (directions 2 and 3, or direction 1
+  // when d = 1) agree modulo p+1 share no row across different work items.
+  // A work item is one line of elements along direction 1 (one element when
+  // d = 1); lines of one colour run on separate threads.
+  const int nouter = d == 1 ? 1 : d - 1;                 // directions that are coloured
+  const long long line = d == 1 ? 1 : n_el;              // elements per work item
+  int ncol = 1;
+  for (int k = 0; k < nouter; ++k) ncol *= p + 1;
+  for (int colour = 0; colour < ncol; ++colour) {
+    int cc[2] = {colour % (p + 1), colour / (p + 1)};
+    std::vector<long long> items;                        // first element of each line
+    if (d == 1) {
+      for (int k = cc[0]; k < n_el; k += p + 1) items.push_back(k);
+    } else if (d == 2) {
+      for (int k = cc[0]; k < n_el; k += p + 1) items.push_back((long long)k * n_el);
+    } else {
+      for (int k3 = cc[1]; k3 < n_el; k3 += p + 1)
+        for (int k2 = cc[0]; k2 < n_el; k2 += p + 1) items.push_back(((long long)k3 * n_el + k2) * n_el);
+    }
     const int nt = std::min<int>(n_threads(), (int)items.size());
     std::vector<std::thread> th;
     for (int t = 0; t < nt; ++t)
@@ -435,8 +456,8 @@ extern "C" int stfd_spatial_assemble(int d, int p, int n_el, int geom, int nq, c
         std::vector<double> x, detw, Gw, W, Mloc((size_t)Ld * Ld), Kloc((size_t)Ld * Ld);
         int ei[3];
         for (size_t it = t; it < items.size(); it += nt) {
-          for (long long r = 0; r < inner_elems; ++r) {
-            const long long e = r + inner_elems * items[it];
+          for (long long r = 0; r < line; ++r) {
+            const long long e = items[it] + r;
             elem_index(P, e, ei);
             const double* cq = c_q ? c_q + e * P.Qe : nullptr;
             const double* kq = kappa_q ? kappa_q + e * P.Qe : nullptr;
