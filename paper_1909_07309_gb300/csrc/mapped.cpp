@@ -270,35 +270,37 @@ struct SumFact {
             t[a1 * L1 + b1] = s;
           }
       }
-    // stage 2: T2[q3][a2][b2][a1 b1]
-    const int LL1 = L1 * L1;
-    T2.assign((size_t)n3 * L2 * L2 * LL1, 0.0);
+    // stage 2: T2[q3][(a2, a1)][(b2, b1)] -- rows and columns in the order of a
+    // block of Loc, so that stage 3 is a run of contiguous updates
+    const int LL1 = L1 * L1, LB = L1 * L2;       // LB: local functions per (a3) slab
+    T2.assign((size_t)n3 * LB * LB, 0.0);
     for (int q3 = 0; q3 < n3; ++q3)
       for (int a2 = 0; a2 < L2; ++a2)
-        for (int b2 = 0; b2 < L2; ++b2) {
-          double* t2 = &T2[(((size_t)q3 * L2 + a2) * L2 + b2) * LL1];
+        for (int b2 = 0; b2 < L2; ++b2)
           for (int q2 = 0; q2 < n2; ++q2) {
             const double f = R2[a2 * nq + q2] * C2[b2 * nq + q2];
+            if (f == 0.0) continue;
             const double* t1 = &T1[((size_t)q3 * n2 + q2) * LL1];
-            for (int k = 0; k < LL1; ++k) t2[k] += f * t1[k];
+            for (int a1 = 0; a1 < L1; ++a1) {
+              double* __restrict__ t2 = &T2[((size_t)q3 * LB + a2 * L1 + a1) * LB + (size_t)b2 * L1];
+              const double* __restrict__ t1r = t1 + a1 * L1;
+              for (int b1 = 0; b1 < L1; ++b1) t2[b1] += f * t1r[b1];
+            }
           }
-        }
-    // stage 3: Loc[a][b], a = a1 + L a2 + L^2 a3
+    // stage 3: block (a3, b3) of Loc (rows a = r + LB a3, columns c + LB b3) gains
+    // sum_q3 R3[a3][q3] C3[b3][q3] T2[q3][r][c]
     const int Ld = P.Ld;
     for (int a3 = 0; a3 < L3; ++a3)
       for (int b3 = 0; b3 < L3; ++b3)
         for (int q3 = 0; q3 < n3; ++q3) {
           const double f3 = R3[a3 * nq + q3] * C3[b3 * nq + q3];
           if (f3 == 0.0) continue;
-          for (int a2 = 0; a2 < L2; ++a2)
-            for (int b2 = 0; b2 < L2; ++b2) {
-              const double* t2 = &T2[(((size_t)q3 * L2 + a2) * L2 + b2) * LL1];
-              for (int a1 = 0; a1 < L1; ++a1) {
-                const int a = a1 + L * (a2 + L * a3);
-                double* row = Loc + (size_t)a * Ld;
-                for (int b1 = 0; b1 < L1; ++b1) row[b1 + L * (b2 + L * b3)] += f3 * t2[a1 * L1 + b1];
-              }
-            }
+          const double* t2 = &T2[(size_t)q3 * LB * LB];
+          for (int r = 0; r < LB; ++r) {
+            double* __restrict__ dst = Loc + (size_t)(r + LB * a3) * Ld + (size_t)LB * b3;
+            const double* __restrict__ src = t2 + (size_t)r * LB;
+            for (int c = 0; c < LB; ++c) dst[c] += f3 * src[c];
+          }
         }
   }
 };
@@ -399,34 +401,43 @@ extern "C" int stfd_spatial_assemble(int d, int p, int n_el, int geom, int nq, c
   if (Ms) std::fill(Ms, Ms + (size_t)S * P.Ns, 0.0);
   if (Ks) std::fill(Ks, Ks + (size_t)S * P.Ns, 0.0);
   const int L = P.L, Ld = P.Ld;
-  // local function a -> (reduced offset per direction); scatter per element
-  auto scatter = [&](const int* ei, const double* Loc, double* out) {
-    int ia[3], ib[3];
+  // the stencil offset of local pair (a, b) depends on a and b only:
+  // o(a, b) = sum_l (b_l - a_l + p) (2p+1)^(l-1)
+  std::vector<int> off_ab((size_t)Ld * Ld);
+  for (int a = 0; a < Ld; ++a)
+    for (int b = 0; b < Ld; ++b) {
+      int ra = a, rb = b, o = 0, so = 1;
+      for (int l = 0; l < d; ++l) {
+        o += (rb % L - ra % L + p) * so;
+        ra /= L;
+        rb /= L;
+        so *= 2 * p + 1;
+      }
+      off_ab[(size_t)a * Ld + b] = o;
+    }
+  // reduced global row of each local function of element ei (-1: removed by the reduction)
+  auto local_rows = [&](const int* ei, long long* rows) {
     for (int a = 0; a < Ld; ++a) {
       int ra = a;
       long long row = 0, stride = 1;
       bool ok = true;
       for (int l = 0; l < d; ++l) {
-        ia[l] = ei[l] + ra % L - 1;   // reduced index: full index e + a minus the dropped first function
+        const int il = ei[l] + ra % L - 1;   // full index e + a minus the dropped first function
         ra /= L;
-        if (ia[l] < 0 || ia[l] >= P.n_s) ok = false;
-        row += (long long)ia[l] * stride;
+        if (il < 0 || il >= P.n_s) ok = false;
+        row += (long long)il * stride;
         stride *= P.n_s;
       }
-      if (!ok) continue;
-      for (int b = 0; b < Ld; ++b) {
-        int rb = b, o = 0, so = 1;
-        bool okb = true;
-        for (int l = 0; l < d; ++l) {
-          ib[l] = ei[l] + rb % L - 1;
-          rb /= L;
-          if (ib[l] < 0 || ib[l] >= P.n_s) okb = false;
-          o += (ib[l] - ia[l] + p) * so;
-          so *= 2 * p + 1;
-        }
-        if (!okb) continue;
-        out[(size_t)o * P.Ns + row] += Loc[(size_t)a * Ld + b];
-      }
+      rows[a] = ok ? row : -1;
+    }
+  };
+  auto scatter = [&](const long long* rows, const double* Loc, double* out) {
+    for (int a = 0; a < Ld; ++a) {
+      if (rows[a] < 0) continue;
+      const int* oa = &off_ab[(size_t)a * Ld];
+      const double* la = Loc + (size_t)a * Ld;
+      for (int b = 0; b < Ld; ++b)
+        if (rows[b] >= 0) out[(size_t)oa[b] * P.Ns + rows[a]] += la[b];
     }
   };
   // Colours: elements whose outer indices (directions 2 and 3, or direction 1
@@ -454,6 +465,7 @@ extern "C" int stfd_spatial_assemble(int d, int p, int n_el, int geom, int nq, c
       th.emplace_back([&, t]() {
         SumFact sf;
         std::vector<double> x, detw, Gw, W, Mloc((size_t)Ld * Ld), Kloc((size_t)Ld * Ld);
+        std::vector<long long> rows(Ld);
         int ei[3];
         for (size_t it = t; it < items.size(); it += nt) {
           for (long long r = 0; r < line; ++r) {
@@ -463,8 +475,9 @@ extern "C" int stfd_spatial_assemble(int d, int p, int n_el, int geom, int nq, c
             const double* kq = kappa_q ? kappa_q + e * P.Qe : nullptr;
             element_matrices(P, ei, cq, kq, Ms ? Mloc.data() : nullptr, Ks ? Kloc.data() : nullptr, sf, x, detw, Gw,
                              W);
-            if (Ms) scatter(ei, Mloc.data(), Ms);
-            if (Ks) scatter(ei, Kloc.data(), Ks);
+            local_rows(ei, rows.data());
+            if (Ms) scatter(rows.data(), Mloc.data(), Ms);
+            if (Ks) scatter(rows.data(), Kloc.data(), Ks);
           }
         }
       });
