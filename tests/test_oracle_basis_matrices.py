@@ -129,3 +129,21 @@ def test_table3_kappa_time():
         k = np.linalg.cond(tf["Ut"])
         assert format(k, ".1e") == val, (n_el, p, k, val)
         assert abs(k - np.sqrt(np.linalg.cond(Mt))) < 1e-8 * k
+
+
+def test_table_cond_number_direct_time_eigendecomposition():
+    """Table cond_number (Sec. 4.2.1): the condition number of the M_t-normalised
+    complex eigenvectors of (W_t, M_t) from the oracle's time matrices, to the
+    printed two significant figures."""
+    import os
+    import scipy.linalg as sl
+    path = os.path.join(os.path.dirname(__file__), "golden", "table2_kappa_U_direct.txt")
+    for line in open(path):
+        if not line.strip() or line.startswith("#"):
+            continue
+        n_el, p, val = line.split()
+        Wt, Mt = matrices.time_matrices(int(p), int(n_el), 1.0)
+        _, U = sl.eig(Wt, Mt)
+        for j in range(U.shape[1]):
+            U[:, j] /= np.sqrt(np.real(np.conj(U[:, j]) @ Mt @ U[:, j]))
+        assert format(np.linalg.cond(U), ".1e") == val, (n_el, p)
