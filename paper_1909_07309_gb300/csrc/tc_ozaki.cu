@@ -15,10 +15,12 @@
 // (< 2^-47 relative). The six T_c are combined in double-float arithmetic.
 //
 // One persistent CTA per SM (the six accumulators take 480 of the 512 TMEM
-// columns). Per 128-column tile: stage X in shared memory, convert each row to
-// 48-bit fixed point, then for k = 0..5 write digit plane dx_k (double
-// buffered) and issue the MMAs of pairs (k, l <= 5 - k) against the resident
-// planes of J.
+// columns). Per 128-column tile: every thread holds its 20 entries of one row
+// in registers (loaded while the previous tile's MMAs ran), the row exponent is
+// reduced across the row's four threads, each entry is converted to 48-bit
+// fixed point and its six digits are written to the six digit planes at once;
+// then one thread issues all 21 digit-pair MMAs against the resident planes of
+// J and commits them to one mbarrier.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -128,9 +130,32 @@ struct StoreOut<float2> {
 };
 
 // 512 threads: thread t owns tile row r = t % 128 (its TMEM lane) together with
-// three other threads (parts p = t / 128) that split the row's columns.
+// three other threads (parts p = t / 128); part p owns a contiguous block of
+// kCols (even) columns of the row, held in registers from global memory.
 constexpr int kParts = 4;
 constexpr int kThreads = kTile * kParts;
+constexpr int kCols = 20;                      // columns per part: 4 x 20 covers n <= 80
+
+// Byte distance between 8-row groups of an A digit plane: the dense value plus
+// 16 bytes, so that the 4 row groups a warp writes fall in different banks.
+__host__ __device__ inline uint32_t a_sbo(int kcores) { return (uint32_t)kcores * 128u + 16u; }
+
+// Raw 8-byte words of tile `tile`, row r, columns a0 .. a0 + kCols - 1 (0 outside).
+__device__ __forceinline__ void load_raw(const long long* __restrict__ Xw, long long tile, int r, int a0, int a1,
+                                         int n, long long inner, long long Q, long long* raw) {
+  const long long q = tile * kTile + r;
+  const bool valid = q < Q;
+  long long base = 0;
+  if (valid) {
+    const long long o = q / inner;
+    base = o * (long long)n * inner + (q - o * inner);
+  }
+#pragma unroll
+  for (int c = 0; c < kCols; ++c) {
+    const int a = a0 + c;
+    raw[c] = (valid && a < a1) ? __ldg(Xw + base + (long long)a * inner) : 0ll;
+  }
+}
 
 template <typename TIn, typename TOut>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
@@ -138,36 +163,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int n = args.n, npad = args.npad;
   const int kcores = npad / 8;                  // 16-byte core matrices along K (8 BF16 each)
-  const uint32_t sbo = (uint32_t)kcores * 128u;
-  const size_t plane = (size_t)npad * npad * 2;
-  const size_t abytes = (size_t)kTile * npad * 2;
-  const int ld = n + 1;                         // staging row stride (8-byte words)
+  const uint32_t sbo_b = (uint32_t)kcores * 128u, sbo_a = a_sbo(kcores);
+  const size_t plane_b = (size_t)npad * npad * 2;
+  const size_t plane_a = (size_t)(kTile / 8) * sbo_a;
+  const int ld = n + 1;                         // output staging row stride (8-byte words)
   const long long inner = args.inner, Q = args.Q;
-  unsigned char* sB = smem;                                            // kDig planes
-  long long* sF = reinterpret_cast<long long*>(sB + kDig * plane);     // kTile x ld
-  unsigned char* sA = reinterpret_cast<unsigned char*>(sF + (size_t)kTile * ld);   // 2 buffers
-  int* sv = reinterpret_cast<int*>(sA + 2 * abytes);                  // npad
+  unsigned char* sB = smem;                                            // kDig planes of J
+  unsigned char* sA = sB + kDig * plane_b;                             // kDig planes of the tile
+  int* sv = reinterpret_cast<int*>(sA + kDig * plane_a);              // npad
   int* sE = sv + ((npad + 3) & ~3);                                    // kParts x kTile
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sE + kParts * kTile);   // 2 barriers
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sE + kParts * kTile);   // 1 barrier
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   int* sflag = reinterpret_cast<int*>(tslot + 1);
   const int t = threadIdx.x, warp = t >> 5, r = t & (kTile - 1), part = t >> 7;
-  const int nchunk = (n + 7) / 8;               // 8-column chunks holding data
   const int nchunk_pad = npad / 8;
+  const int a0 = part * kCols, a1 = min(n, a0 + kCols);   // this thread's columns
 
   {
     const uint4* src = reinterpret_cast<const uint4*>(args.B);
     uint4* dst = reinterpret_cast<uint4*>(sB);
-    const int nv = (int)(kDig * plane / 16);
+    const int nv = (int)(kDig * plane_b / 16);
     for (int e = t; e < nv; e += kThreads) dst[e] = src[e];
-    uint4* za = reinterpret_cast<uint4*>(sA);
-    const int na = (int)(2 * abytes / 16);
-    for (int e = t; e < na; e += kThreads) za[e] = make_uint4(0, 0, 0, 0);
     for (int i = t; i < npad; i += kThreads) sv[i] = i < n ? args.v[i] : 0;
   }
   if (t == 0) {
     tc::mbar_init(tc::smem_u32(&mbar[0]), 1);
-    tc::mbar_init(tc::smem_u32(&mbar[1]), 1);
     *sflag = 0;
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 512);
@@ -179,16 +199,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   const uint32_t idesc = tc::instr_desc(1u, kTile, npad);
   const uint32_t a_addr = tc::smem_u32(sA), b_addr = tc::smem_u32(sB);
   const int ksteps = npad / 16;
-  // descriptor of the start of each operand; a byte offset o adds o >> 4 to the address field
-  const uint64_t da0 = tc::smem_desc(a_addr, 128u, sbo), db0 = tc::smem_desc(b_addr, 128u, sbo);
-  uint32_t ph[2] = {0u, 0u};
-  const int nitems = kTile * nchunk;            // (row, 8-column chunk) digit items per plane
-  bool staged = false;                          // next tile already in flight (strided modes)
-
-  auto wait_buf = [&](int b) {
-    if (!tc::mbar_wait(tc::smem_u32(&mbar[b]), ph[b], kWaitIters)) *sflag = 1;
-    ph[b] ^= 1u;
-  };
+  const uint64_t da0 = tc::smem_desc(a_addr, 128u, sbo_a), db0 = tc::smem_desc(b_addr, 128u, sbo_b);
+  uint32_t ph = 0u;
+  const long long* Xw = static_cast<const long long*>(args.X);
+  long long raw[kCols];
+  if ((long long)blockIdx.x < args.ntiles) load_raw(Xw, blockIdx.x, r, a0, a1, n, inner, Q, raw);
 
   for (long long tile = blockIdx.x; tile < args.ntiles; tile += gridDim.x) {
     const long long q0 = tile * kTile;
@@ -199,103 +214,73 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
       const long long o = q / inner;
       base = o * (long long)n * inner + (q - o * inner);
     }
-    // ---- stage the tile's raw 8-byte words (row r = tile column q), all copies in flight;
-    // in the strided modes the copies were issued during the previous tile's epilogue
-    const long long* Xw = static_cast<const long long*>(args.X);
-    if (!staged) {
-      if (inner == 1) {
-        const long long* src = Xw + q0 * n;
-        const int cnt = rows * n;
-        for (int e = t; e < cnt; e += kThreads) {
-          const int rr = e / n;
-          tc::cp_async8(&sF[rr * ld + (e - rr * n)], src + e);
-        }
-      } else if (q < Q) {
-        for (int a = part; a < n; a += kParts) tc::cp_async8(&sF[r * ld + a], Xw + base + (long long)a * inner);
+    // ---- row exponent: max over this thread's columns, then over the four parts
+    {
+      int E0 = 0, E1 = 0;
+#pragma unroll
+      for (int c = 0; c < kCols; c += 2) {
+        const unsigned long long w0 = (unsigned long long)raw[c], w1 = (unsigned long long)raw[c + 1];
+        E0 = max(E0, DBL ? (int)((w0 >> 52) & 0x7FF) : (int)((w0 >> 23) & 0xFF));
+        E1 = max(E1, DBL ? (int)((w1 >> 52) & 0x7FF) : (int)((w1 >> 23) & 0xFF));
       }
+      sE[part * kTile + r] = max(E0, E1);
     }
-    staged = false;
-    tc::cp_async_wait_all();
-    __syncthreads();
-    // ---- row exponent (max over the four parts) and fixed-point conversion
-    long long* Frow = sF + r * ld;
-    sE[part * kTile + r] = (r < rows) ? row_max_exp<DBL>(Frow, n, part, kParts) : 0;
     __syncthreads();
     int E = 0;
 #pragma unroll
     for (int pp = 0; pp < kParts; ++pp) E = max(E, sE[pp * kTile + r]);
     const int urow = DBL ? E - 1070 : E - 174;
-    // packed digit source: word0 = sign << 31 | bits 24..47 of |F|, word1 = bits 0..23
-#pragma unroll 4
-    for (int a = part; a < n; a += kParts) {
-      const long long f = (r < rows) ? to_fixed<DBL>(Frow[a], E) : 0;
-      const unsigned long long m = (unsigned long long)(f < 0 ? -f : f);
-      const unsigned int w0 = (unsigned int)(m >> 24) | (f < 0 ? 0x80000000u : 0u);
-      const unsigned int w1 = (unsigned int)(m & 0xFFFFFFull);
-      Frow[a] = (long long)(((unsigned long long)w1 << 32) | w0);
-    }
-    __syncthreads();
-    // ---- digit planes k = 0..5 (double buffered) and their MMAs
+    // ---- 48-bit fixed point and its six digit planes, two columns per 32-bit store
+    {
+      const size_t rbase = (size_t)(r >> 3) * sbo_a + (size_t)(r & 7) * 16;
 #pragma unroll
-    for (int k = 0; k < kDig; ++k) {
-      const int b = k & 1;
-      if (k >= 2) wait_buf(b);
-      unsigned char* A = sA + b * abytes;
-      const int sh = 16 - 8 * (k % 3);
-      // warp 0 issues the MMAs; the other 15 warps write the plane
-      for (int it = t - 32; it >= 0 && it < nitems; it += kThreads - 32) {
-        const int rr = it & (kTile - 1), c8 = it >> 7;
-        const long long* Fr = sF + rr * ld;
-        const int a0 = 8 * c8;
-        uint32_t w[4];
+      for (int c = 0; c < kCols; c += 2) {
+        const int a = a0 + c;   // columns n .. npad-1 are written as zero digits
+        if (a >= npad) break;
+        uint32_t h[2][kDig];
 #pragma unroll
-        for (int tt = 0; tt < 4; ++tt) {
-          uint32_t bits2[2];
+        for (int e = 0; e < 2; ++e) {
+          const long long f = to_fixed<DBL>(raw[c + e], E);
+          const unsigned long long m = (unsigned long long)(f < 0 ? -f : f);
+          const uint32_t sgn = f < 0 ? 0x8000u : 0u;
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int a = a0 + 2 * tt + h;
-            const unsigned long long pw = a < n ? (unsigned long long)Fr[a] : 0ull;
-            const uint32_t w0 = (uint32_t)pw, w1 = (uint32_t)(pw >> 32);
-            const uint32_t dg = ((k < 3 ? w0 : w1) >> sh) & 0xFFu;
-            // exact float of the digit (0x4B000000 | d is 2^23 + d), signed; its top 16 bits are its BF16
+          for (int k = 0; k < kDig; ++k) {
+            const uint32_t dg = (uint32_t)(m >> (40 - 8 * k)) & 0xFFu;
+            // exact float of the digit (0x4B000000 | d is 2^23 + d); its top 16 bits are its BF16
             const float fv = __int_as_float(0x4B000000u | dg) - 8388608.0f;
-            bits2[h] = (uint32_t)__float_as_int(fv) | (w0 & 0x80000000u);
+            h[e][k] = ((uint32_t)__float_as_int(fv) >> 16) | sgn;
           }
-          w[tt] = __byte_perm(bits2[0], bits2[1], 0x7632);
         }
-        *reinterpret_cast<uint4*>(A + canon_off16(rr, a0, kcores)) = make_uint4(w[0], w[1], w[2], w[3]);
+        const size_t off = rbase + (size_t)(a >> 3) * 128 + (size_t)(a & 7) * 2;
+#pragma unroll
+        for (int k = 0; k < kDig; ++k)
+          *reinterpret_cast<uint32_t*>(sA + k * plane_a + off) = h[0][k] | (h[1][k] << 16);
       }
-      tc::fence_async_smem();
-      tc::fence_before_sync();
-      __syncthreads();
-      tc::fence_after_sync();
-      if (t == 0) {
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // ---- all 21 digit-pair MMAs of the tile, one commit
+    if (t == 0) {
+      for (int k = 0; k < kDig; ++k)
         for (int l = 0; l + k < kDig; ++l) {
           const uint32_t dcol = tmem + (uint32_t)((k + l) * npad);
           for (int s = 0; s < ksteps; ++s) {
-            const uint64_t da = da0 + (uint64_t)((b * abytes + s * 256) >> 4);
-            const uint64_t db = db0 + (uint64_t)((l * plane + s * 256) >> 4);
+            const uint64_t da = da0 + (uint64_t)((k * plane_a + s * 256) >> 4);
+            const uint64_t db = db0 + (uint64_t)((l * plane_b + s * 256) >> 4);
             tc::mma<0>(dcol, da, db, idesc, (k > 0 || s > 0) ? 1u : 0u);
           }
         }
-        tc::mma_commit(tc::smem_u32(&mbar[b]));
-      }
+      tc::mma_commit(tc::smem_u32(&mbar[0]));
     }
-    // ---- strided modes: the staging buffer is free now, start the next tile's copies
+    // ---- the next tile's words travel while the tensor cores work
     {
       const long long nt = tile + gridDim.x;
-      if (inner != 1 && nt < args.ntiles) {
-        const long long nq = nt * kTile + r;
-        if (nq < Q) {
-          const long long o = nq / inner;
-          const long long nbase = o * (long long)n * inner + (nq - o * inner);
-          for (int a = part; a < n; a += kParts) tc::cp_async8(&sF[r * ld + a], Xw + nbase + (long long)a * inner);
-        }
-        staged = true;
-      }
+      if (nt < args.ntiles) load_raw(Xw, nt, r, a0, a1, n, inner, Q, raw);
     }
-    wait_buf(0);   // commit of k = 4
-    wait_buf(1);   // commit of k = 5 (covers every MMA of the tile)
+    if (!tc::mbar_wait(tc::smem_u32(&mbar[0]), ph, kWaitIters)) *sflag = 1;
+    ph ^= 1u;
     __syncthreads();
     if (*sflag) {
       if (t == 0) atomicExch(&g_tc_status, 1);
@@ -304,38 +289,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
     tc::fence_after_sync();
     // ---- epilogue: part p combines the six diagonals of row r on chunks p, p+4, ...
     const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    float2* stage = reinterpret_cast<float2*>(sA);   // free once the MMAs are done
     for (int c8 = part; c8 < nchunk_pad; c8 += kParts) {
       uint32_t Tr[kDig][8];
 #pragma unroll
       for (int c = 0; c < kDig; ++c) tc::tmem_ld8_async(lane_base + (uint32_t)(c * npad + 8 * c8), Tr[c]);
       tc::tmem_wait_ld8x6(Tr);
-      float T[kDig][8];
-#pragma unroll
-      for (int c = 0; c < kDig; ++c)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) T[c][j] = __uint_as_float(Tr[c][j]);
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int i = 8 * c8 + j;
         if (i >= n || r >= rows) continue;
+        float T[kDig];
+#pragma unroll
+        for (int c = 0; c < kDig; ++c) T[c] = __uint_as_float(Tr[c][j]);
         // exact two-sums for the three leading diagonals; the trailing three sit
         // below 2^-22 of the total and are summed in plain FP32 (error < 2^-46 of it)
-        float hi = T[0][j], lo = 0.f;
+        float hi = T[0], lo = 0.f;
 #pragma unroll
         for (int c = 1; c < 3; ++c) {
-          const float v = T[c][j] * pow2f(-8 * c);
+          const float v = T[c] * pow2f(-8 * c);
           const float sm = hi + v, bp = sm - hi;
           lo += (hi - (sm - bp)) + (v - bp);
           hi = sm;
         }
-        lo += fmaf(T[5][j], pow2f(-40), fmaf(T[4][j], pow2f(-32), T[3][j] * pow2f(-24)));
-        const dfa::df s = dfa::norm(dfa::df{hi, lo});
+        lo += fmaf(T[5], pow2f(-40), fmaf(T[4], pow2f(-32), T[3] * pow2f(-24)));
+        const dfa::df sres = dfa::norm(dfa::df{hi, lo});
         int sc = urow + sv[i] + 80;
         sc = max(-250, min(250, sc));
         const float f1 = pow2f(sc / 2), f2 = pow2f(sc - sc / 2);
-        const dfa::df y{s.h * f1 * f2, s.l * f1 * f2};
+        const dfa::df y{sres.h * f1 * f2, sres.l * f1 * f2};
         if (inner == 1) {
-          reinterpret_cast<float2*>(sF)[r * ld + i] = make_float2(y.h, y.l);
+          stage[r * ld + i] = make_float2(y.h, y.l);
         } else {
           StoreOut<TOut>::put(static_cast<TOut*>(args.Y), base + (long long)i * inner, y);
         }
@@ -343,19 +327,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
     }
     if (inner == 1) {
       __syncthreads();
-      const float2* st = reinterpret_cast<const float2*>(sF);
       TOut* dst = static_cast<TOut*>(args.Y) + q0 * n;
       const int cnt = rows * n;
       for (int e = t; e < cnt; e += kThreads) {
         const int rr = e / n;
-        const float2 v = st[rr * ld + (e - rr * n)];
+        const float2 v = stage[rr * ld + (e - rr * n)];
         StoreOut<TOut>::put(dst, e, dfa::df{v.x, v.y});
       }
     }
     tc::fence_before_sync();
-    __syncthreads();
+    __syncthreads();   // the staging area and sE are rewritten by the next tile
   }
-  tc::cp_async_wait_all();   // no copy may still target this CTA's shared memory at exit
   tc::fence_after_sync();
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
@@ -372,7 +354,8 @@ int sm_count_oz() {
 
 size_t oz_smem_bytes(int n) {
   const int npad = (n + 15) / 16 * 16;
-  return (size_t)kDig * npad * npad * 2 + (size_t)kTile * (n + 1) * 8 + 2 * (size_t)kTile * npad * 2 +
+  const int kcores = npad / 8;
+  return (size_t)kDig * npad * npad * 2 + (size_t)kDig * (kTile / 8) * a_sbo(kcores) +
          (size_t)((npad + 3) & ~3) * 4 + (size_t)kParts * kTile * 4 + 32;
 }
 
