@@ -203,7 +203,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   uint32_t ph = 0u;
   const long long* Xw = static_cast<const long long*>(args.X);
   long long raw[kCols];
-  if ((long long)blockIdx.x < args.ntiles) load_raw(Xw, blockIdx.x, r, a0, a1, n, inner, Q, raw);
+  // strided modes: each warp's loads are coalesced (consecutive rows are
+  // consecutive addresses), so entries go straight to registers and the next
+  // tile's are fetched while the MMAs run. Mode 1 (inner == 1): a row is
+  // contiguous, so the tile is a contiguous block, copied through shared memory.
+  if (inner != 1 && (long long)blockIdx.x < args.ntiles) load_raw(Xw, blockIdx.x, r, a0, a1, n, inner, Q, raw);
 
   for (long long tile = blockIdx.x; tile < args.ntiles; tile += gridDim.x) {
     const long long q0 = tile * kTile;
@@ -213,6 +217,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
     if (q < Q) {
       const long long o = q / inner;
       base = o * (long long)n * inner + (q - o * inner);
+    }
+    if (inner == 1) {   // coalesced copy of the tile's rows into the (free) plane area
+      long long* blk = reinterpret_cast<long long*>(sA);
+      const long long* src = Xw + q0 * n;
+      const int cnt = rows * n;
+      for (int e = t; e < cnt; e += kThreads) {
+        const int rr = e / n;
+        blk[rr * ld + (e - rr * n)] = __ldg(src + e);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < kCols; ++c) {
+        const int a = a0 + c;
+        raw[c] = (r < rows && a < a1) ? blk[r * ld + a] : 0ll;
+      }
+      __syncthreads();   // the planes overwrite the block below
     }
     // ---- row exponent: max over this thread's columns, then over the four parts
     {
@@ -275,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
       tc::mma_commit(tc::smem_u32(&mbar[0]));
     }
     // ---- the next tile's words travel while the tensor cores work
-    {
+    if (inner != 1) {
       const long long nt = tile + gridDim.x;
       if (nt < args.ntiles) load_raw(Xw, nt, r, a0, a1, n, inner, Q, raw);
     }
