@@ -36,7 +36,7 @@ L2_BYTES = 129 * 2 ** 20
 # DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/,
 # mean over the 8 launches of one fd_apply at the workload); None once the
 # kernel changes until it is captured again.
-NCU_TRAFFIC = {"kernel": "fd_mode_ozaki", "bytes_per_launch": None}
+NCU_TRAFFIC = {"kernel": "fd_mode_ozaki", "bytes_per_launch": 237410336}
 
 
 def measured_peaks():
