@@ -49,6 +49,15 @@ int stfd_probe_fp64_peak(double* flops_per_s, void* stream);
  * clears it. 1 <= max_iters <= 1e6. Synchronous. */
 int stfd_probe_bounded_wait(int max_iters, void* stream);
 
+/* Self-test of the FP64 <-> double-float conversions that the double-float
+ * and tensor-core kernels use at their FP64 inputs and outputs (built from
+ * the IEEE 754 bit fields, off the FP64 pipe). For i < n, all device
+ * pointers: pairs[2i], pairs[2i+1] = the double-float (h, l) of x[i];
+ * back[i] = that pair converted back to FP64; f[i] = x[i] rounded to FP32;
+ * fback[i] = f[i] converted back to FP64. n >= 0. Stream-ordered. */
+int stfd_probe_convert(const double* x, long long n, float* pairs, double* back, float* f, double* fback,
+                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,16 +13,108 @@ struct df {
   float h, l;
 };
 
-__device__ __forceinline__ df from_double(double x) {
-  const float h = __double2float_rn(x);
-  return df{h, __double2float_rn(x - (double)h)};
-}
-__device__ __forceinline__ df from_float2(float2 v) { return df{v.x, v.y}; }
-__device__ __forceinline__ double to_double(df a) { return (double)a.h + (double)a.l; }
-
 __device__ __forceinline__ df norm(df a) {
   const float s = a.h + a.l;
   return df{s, a.l - (s - a.h)};
+}
+
+// 2^e as a float, exact for e in [-126, 127].
+__device__ __forceinline__ float pow2(int e) { return __int_as_float((e + 127) << 23); }
+
+// Conversions between FP64 and double-float. A conversion instruction that
+// touches FP64 issues on the FP64 pipe, which on GB300 runs at ~1/64 of the
+// FP32 rate, so the values are assembled from the IEEE 754 bit fields with
+// integer and FP32 instructions. Only FP64 inputs of magnitude outside
+// [2^-70, 2^127) (FP32 subnormals or overflow) take FP64 instructions, in a
+// function that is not inlined so that the common path never executes them.
+
+__device__ __noinline__ static df from_double_fp64(double x) {
+  const float h = __double2float_rn(x);
+  return df{h, __double2float_rn(x - (double)h)};
+}
+
+// FP64 -> double-float: the 53-bit significand is cut into its top 24 bits
+// (exact in a float) and the remaining 29 bits (rounded to 24), then
+// renormalised; h + l carries at least 48 significant bits of x.
+__device__ __forceinline__ df from_double(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0) return df{0.f, 0.f};   // zero, or below 2^-1022: beyond the FP32 range
+  const int e = E - 1023;
+  if (e < -70 || e > 126) return from_double_fp64(x);
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  float h = __uint2float_rn((unsigned int)(m >> 29)) * pow2(e - 23);
+  float l = __uint2float_rn((unsigned int)(m & 0x1FFFFFFFull)) * pow2(e - 52);
+  if (b >> 63) {
+    h = -h;
+    l = -l;
+  }
+  return norm(df{h, l});
+}
+__device__ __forceinline__ df from_float2(float2 v) { return df{v.x, v.y}; }
+
+// FP64 -> FP32, rounded (the leading float of from_double).
+__device__ __forceinline__ float d2f(double x) { return from_double(x).h; }
+
+// FP32 -> FP64, exact (subnormals normalised, infinities and NaNs kept).
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned long long sgn = (unsigned long long)(b >> 31) << 63;
+  unsigned int e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  unsigned long long field;
+  if (e == 0xFFu) {
+    field = 0x7FFull;
+  } else if (e != 0u) {
+    field = e + 896u;
+  } else {
+    if (m == 0u) return __longlong_as_double((long long)sgn);
+    const int sh = __clz((int)m) - 8;   // moves the leading bit to position 23
+    m = (m << sh) & 0x7FFFFFu;
+    field = (unsigned long long)(897 - sh);
+  }
+  return __longlong_as_double((long long)(sgn | (field << 52) | ((unsigned long long)m << 29)));
+}
+
+// One float of a pair as a signed integer in units of 2^{eb - 181} (the
+// larger float's binade, 2^-54 of it); bits below the unit are rounded off.
+__device__ __forceinline__ long long df_term(unsigned int bits, int eb) {
+  int e = (int)((bits >> 23) & 0xFFu);
+  unsigned long long m = bits & 0x7FFFFFu;
+  if (e != 0) m |= 0x800000u;
+  else e = 1;   // subnormal
+  const int sh = e - eb + 31;
+  unsigned long long t = 0;
+  if (sh >= 0) t = m << sh;
+  else if (sh > -32) t = (m + (1ull << (-sh - 1))) >> -sh;
+  return (bits >> 31) ? -(long long)t : (long long)t;
+}
+
+// double-float -> FP64: h + l summed exactly as one integer (whenever h + l is
+// itself a double, as for every normalised pair from from_double), then
+// normalised to a 53-bit significand (round half up).
+__device__ __forceinline__ double to_double(df a) {
+  const unsigned int bh = __float_as_uint(a.h), bl = __float_as_uint(a.l);
+  const int eh = (int)((bh >> 23) & 0xFFu), el = (int)((bl >> 23) & 0xFFu);
+  if (eh == 0xFF || el == 0xFF) {   // infinity or NaN: that float's value
+    const unsigned int w = eh == 0xFF ? bh : bl;
+    return __longlong_as_double((long long)(((unsigned long long)(w >> 31) << 63) | (0x7FFull << 52) |
+                                            ((unsigned long long)(w & 0x7FFFFFu) << 29)));
+  }
+  const int eb = max(max(eh, el), 1);
+  const long long S = df_term(bh, eb) + df_term(bl, eb);
+  if (S == 0) return 0.0;
+  const unsigned long long sgn = S < 0 ? (1ull << 63) : 0ull;
+  unsigned long long mag = (unsigned long long)(S < 0 ? -S : S);
+  const int lz = __clzll((long long)mag);
+  if (lz < 11) {
+    const int r = 11 - lz;
+    mag = (mag + (1ull << (r - 1))) >> r;
+  } else {
+    mag <<= (lz - 11);
+  }
+  // the significand's leading bit adds one to the exponent field (also after a rounding carry)
+  const unsigned long long field = (unsigned long long)(eb + 905 - lz - 1);
+  return __longlong_as_double((long long)(sgn | ((field << 52) + mag)));
 }
 
 // acc += b * x (the b.l * x.l term, ~2^-48 relative, is dropped)

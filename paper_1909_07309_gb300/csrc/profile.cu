@@ -2,12 +2,14 @@
 // declared in stfd_profile.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
 
+#include "df.cuh"
 #include "kernels.h"
 #include "profile.h"
 #include "stfd.h"
@@ -191,4 +193,29 @@ extern "C" int stfd_probe_fp64_peak(double* flops_per_s, void* stream) {
   if (e1) cudaEventDestroy(e1);
   cudaFree(out);
   return rc;
+}
+
+namespace stfd {
+__global__ void k_probe_convert(const double* __restrict__ x, long long n, float* __restrict__ pairs,
+                                double* __restrict__ back, float* __restrict__ f, double* __restrict__ fback) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const stfd::dfa::df v = stfd::dfa::from_double(x[i]);
+    pairs[2 * i] = v.h;
+    pairs[2 * i + 1] = v.l;
+    back[i] = stfd::dfa::to_double(v);
+    const float r = stfd::dfa::d2f(x[i]);
+    f[i] = r;
+    fback[i] = stfd::dfa::f2d(r);
+  }
+}
+}  // namespace stfd
+
+extern "C" int stfd_probe_convert(const double* x, long long n, float* pairs, double* back, float* f, double* fback,
+                                  void* stream) {
+  if (n < 0 || (n > 0 && (!x || !pairs || !back || !f || !fback))) return STFD_ERR_ARG;
+  if (n == 0) return STFD_OK;
+  const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+  stfd::k_probe_convert<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(x, n, pairs, back, f, fback);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? STFD_OK : STFD_ERR_CUDA;
 }

@@ -136,6 +136,23 @@ __device__ __forceinline__ void tmem_wait_ld8x6(uint32_t (&r)[6][8]) {
                  : "memory");
 }
 
+// 32 lanes x 32 bits, 4 consecutive columns per thread, without the wait:
+// the registers are valid only after tmem_wait_ld4x6 below.
+__device__ __forceinline__ void tmem_ld4_async(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr)
+               : "memory");
+}
+
+// The wait for six 4-column loads, fencing their registers as tmem_wait_ld8x6 does.
+__device__ __forceinline__ void tmem_wait_ld4x6(uint32_t (&r)[6][4]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+    asm volatile("" : "+r"(r[c][0]), "+r"(r[c][1]), "+r"(r[c][2]), "+r"(r[c][3]) : : "memory");
+}
+
 // Asynchronous 8-byte global -> shared copy (no register staging), and the wait
 // for every copy this thread has issued.
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {

@@ -2,29 +2,35 @@
 // exact digit slicing (the error-free splitting of Ozaki, Ogita, Oishi and
 // Rump): Y[q][i] = sum_a X[q][a] J[i][a] with
 //
-//   X[q][a] = 2^{u_q} F[q][a],  F = sum_{k<6} dx_k 2^{40-8k},  |dx_k| <= 255,
-//   J[i][a] = 2^{v_i} G[i][a],  G = sum_{l<6} dj_l 2^{40-8l},  |dj_l| <= 255,
+//   X[q][a] = 2^{u_q} sum_{k<6} dx_k[q][a],   J[i][a] = 2^{v_i} sum_{l<6} dj_l[i][a],
 //
-// one power of two per row (the row's largest exponent), so that every digit
-// is an integer that BF16 holds exactly and every digit product is exact.
-// Then Y[q][i] = 2^{u_q + v_i + 80} sum_{c<6} 2^{-8c} T_c[q][i] with
-// T_c = sum_{k+l=c} sum_a dx_k[q][a] dj_l[i][a]. Each T_c is accumulated in its
-// own FP32 TMEM accumulator by BF16 tcgen05 MMAs: for c <= 2 every partial sum
-// is an integer below 2^24 (n <= 80), hence exact; for c >= 3 the FP32 rounding
-// sits below 2^-44 of the result scale. Pairs with k + l >= 6 are dropped
-// (< 2^-47 relative). The six T_c are combined in double-float arithmetic.
+// one power of two per row (from the row's largest exponent) so that the row
+// lies below 2^7, and signed round-to-nearest digits dx_k, dj_l that are
+// integers times 2^{-8k} (2^{-8l}) with |integer| <= 128 (192 for dx_3, which
+// also absorbs the low float of a double-float entry): BF16 holds every digit
+// exactly and every digit product is exact. Then
+// Y[q][i] = 2^{u_q + v_i} sum_{c<6} T_c[q][i], T_c = sum_{k+l=c} sum_a dx_k dj_l,
+// each T_c accumulated in its own FP32 TMEM accumulator by BF16 tcgen05 MMAs.
+// For n <= 80 every partial sum of T_c is an integer multiple of 2^{-8c}
+// below 2^{24 - 8c}, so all six accumulators are exact; the pairs with
+// k + l >= 6 and the digits beyond dx_5 are dropped (below 2^-47 of the row
+// scale). The six T_c are combined in double-float arithmetic.
+//
+// The digits of an entry come from FP32 additions: adding 1.5 * 2^{23-8k}
+// rounds a value below 2^{22-8k} to a multiple of 2^{-8k}, subtracting it again
+// gives the digit exactly, and subtracting the digit leaves the exact remainder.
 //
 // One persistent CTA per SM (the six accumulators take 480 of the 512 TMEM
-// columns). Per 128-column tile: every thread holds its 20 entries of one row
-// in registers (loaded while the previous tile's MMAs ran), the row exponent is
-// reduced across the row's four threads, each entry is converted to 48-bit
-// fixed point and its six digits are written to the six digit planes at once;
-// then one thread issues all 21 digit-pair MMAs against the resident planes of
-// J and commits them to one mbarrier.
+// columns). Per 128-column tile: every thread holds KC entries of one row in
+// registers (strided modes: loaded while the previous tile's MMAs ran), the
+// row exponent is reduced across the row's four threads, the digits of each
+// entry go to the six digit planes at once; then one thread issues the digit
+// pair MMAs against the resident planes of J and commits them to one mbarrier.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -56,55 +62,6 @@ struct OzArgs {
   long long inner, Q, ntiles;
 };
 
-// Largest biased exponent over the entries a = a0, a0 + step, ... < n of a
-// staged row (FP64 words or double-float words).
-template <bool DBL>
-__device__ __forceinline__ int row_max_exp(const long long* F, int n, int a0, int step) {
-  int E0 = 0, E1 = 0;   // two independent maxima for instruction-level parallelism
-  int a = a0;
-  for (; a + step < n; a += 2 * step) {
-    const unsigned long long w0 = (unsigned long long)F[a], w1 = (unsigned long long)F[a + step];
-    E0 = max(E0, DBL ? (int)((w0 >> 52) & 0x7FF) : (int)((w0 >> 23) & 0xFF));
-    E1 = max(E1, DBL ? (int)((w1 >> 52) & 0x7FF) : (int)((w1 >> 23) & 0xFF));
-  }
-  if (a < n) {
-    const unsigned long long w = (unsigned long long)F[a];
-    E0 = max(E0, DBL ? (int)((w >> 52) & 0x7FF) : (int)((w >> 23) & 0xFF));
-  }
-  return max(E0, E1);
-}
-
-// Staged entry -> signed 48-bit fixed point under the row exponent E:
-// FP64:         x = F 2^{E-1070};   double-float: x = F 2^{E-174}.
-template <bool DBL>
-__device__ __forceinline__ long long to_fixed(long long word, int E) {
-  if (DBL) {
-    const int ex = (int)(((unsigned long long)word >> 52) & 0x7FF);
-    if (ex == 0) return 0;
-    const unsigned long long m = ((unsigned long long)word & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = E - ex + 5;
-    const long long f = sh < 64 ? (long long)(m >> sh) : 0;
-    return word < 0 ? -f : f;
-  }
-  const unsigned long long w = (unsigned long long)word;
-  const unsigned int hb = (unsigned int)(w & 0xFFFFFFFFull), lb = (unsigned int)(w >> 32);
-  long long fh = 0, fl = 0;
-  const int eh = (hb >> 23) & 0xFF, el = (lb >> 23) & 0xFF;
-  if (eh != 0) {
-    const long long mh = (long long)((hb & 0x7FFFFF) | 0x800000);
-    const int sh = 24 + eh - E;          // |h| = mh 2^{eh-150}
-    fh = sh >= 0 ? (mh << sh) : (sh > -64 ? (mh >> -sh) : 0);
-    if (hb >> 31) fh = -fh;
-  }
-  if (el != 0) {
-    const long long ml = (long long)((lb & 0x7FFFFF) | 0x800000);
-    const int sh = 24 + el - E;
-    fl = sh >= 0 ? (ml << sh) : (sh > -64 ? (ml >> -sh) : 0);
-    if (lb >> 31) fl = -fl;
-  }
-  return fh + fl;
-}
-
 __device__ __forceinline__ float pow2f(int e) {   // 2^e for e in [-126, 127]
   return __int_as_float((e + 127) << 23);
 }
@@ -130,17 +87,25 @@ struct StoreOut<float2> {
 };
 
 // 512 threads: thread t owns tile row r = t % 128 (its TMEM lane) together with
-// three other threads (parts p = t / 128); part p owns a contiguous block of
-// kCols (even) columns of the row, held in registers from global memory.
+// three other threads (parts p = t / 128); part p owns the contiguous block of
+// KC (even) columns p KC .. p KC + KC - 1 of the row, held in registers.
 constexpr int kParts = 4;
 constexpr int kThreads = kTile * kParts;
-constexpr int kCols = 20;                      // columns per part: 4 x 20 covers n <= 80
+
+// Columns per part for a factor of order n (4 KC >= n; KC = 18 leaves the
+// padding columns 72 .. 79 to a separate zero fill).
+inline int oz_cols(int n) { return n <= 32 ? 8 : n <= 48 ? 12 : n <= 64 ? 16 : n <= 72 ? 18 : 20; }
+
+// Rounding constants: x + kRound[k] - kRound[k] is x rounded to a multiple of
+// 2^{-8k} (for |x| < 2^{22-8k}).
+__device__ __forceinline__ float round_const(int k) { return 12582912.0f * pow2f(-8 * k); }
 
 // Byte distance between 8-row groups of an A digit plane: the dense value plus
 // 16 bytes, so that the 4 row groups a warp writes fall in different banks.
 __host__ __device__ inline uint32_t a_sbo(int kcores) { return (uint32_t)kcores * 128u + 16u; }
 
-// Raw 8-byte words of tile `tile`, row r, columns a0 .. a0 + kCols - 1 (0 outside).
+// Raw 8-byte words of tile `tile`, row r, columns a0 .. a0 + KC - 1 (0 outside).
+template <int KC>
 __device__ __forceinline__ void load_raw(const long long* __restrict__ Xw, long long tile, int r, int a0, int a1,
                                          int n, long long inner, long long Q, long long* raw) {
   const long long q = tile * kTile + r;
@@ -151,13 +116,41 @@ __device__ __forceinline__ void load_raw(const long long* __restrict__ Xw, long 
     base = o * (long long)n * inner + (q - o * inner);
   }
 #pragma unroll
-  for (int c = 0; c < kCols; ++c) {
+  for (int c = 0; c < KC; ++c) {
     const int a = a0 + c;
     raw[c] = (valid && a < a1) ? __ldg(Xw + base + (long long)a * inner) : 0ll;
   }
 }
 
-template <typename TIn, typename TOut>
+// An entry as a double-float (h, l): FP64 words are split with integer and
+// FP32 instructions, double-float words are the two floats.
+template <bool DBL>
+__device__ __forceinline__ dfa::df entry(long long w) {
+  if (DBL) return dfa::from_double(__longlong_as_double(w));
+  return dfa::df{__int_as_float((int)(unsigned int)((unsigned long long)w & 0xFFFFFFFFull)),
+                 __int_as_float((int)(unsigned int)((unsigned long long)w >> 32))};
+}
+
+// The six digits of one entry, already scaled below 2^7: d_0 .. d_2 from the
+// high float, then the low float joins the remainder (one rounding, below the
+// resolution 2^-40 of d_5) and d_3 .. d_5 follow.
+__device__ __forceinline__ void digits6(float yh, float yl, float* d) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float C = round_const(k);
+    d[k] = (yh + C) - C;
+    yh -= d[k];
+  }
+  float y = yh + yl;
+#pragma unroll
+  for (int k = 3; k < kDig; ++k) {
+    const float C = round_const(k);
+    d[k] = (y + C) - C;
+    y -= d[k];
+  }
+}
+
+template <typename TIn, typename TOut, int KC>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   constexpr bool DBL = IsDouble<TIn>::value;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -176,8 +169,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   int* sflag = reinterpret_cast<int*>(tslot + 1);
   const int t = threadIdx.x, warp = t >> 5, r = t & (kTile - 1), part = t >> 7;
-  const int nchunk_pad = npad / 8;
-  const int a0 = part * kCols, a1 = min(n, a0 + kCols);   // this thread's columns
+  const int nchunk4 = (n + 3) / 4;
+  const int a0 = part * KC, a1 = min(n, a0 + KC);   // this thread's columns
 
   {
     const uint4* src = reinterpret_cast<const uint4*>(args.B);
@@ -196,18 +189,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = tc::instr_desc(1u, kTile, npad);
+  const int mgroup = 256 / npad;                // B planes per MMA (N = mgroup npad <= 256)
   const uint32_t a_addr = tc::smem_u32(sA), b_addr = tc::smem_u32(sB);
   const int ksteps = npad / 16;
   const uint64_t da0 = tc::smem_desc(a_addr, 128u, sbo_a), db0 = tc::smem_desc(b_addr, 128u, sbo_b);
   uint32_t ph = 0u;
   const long long* Xw = static_cast<const long long*>(args.X);
-  long long raw[kCols];
+  long long raw[KC];
   // strided modes: each warp's loads are coalesced (consecutive rows are
   // consecutive addresses), so entries go straight to registers and the next
   // tile's are fetched while the MMAs run. Mode 1 (inner == 1): a row is
   // contiguous, so the tile is a contiguous block, copied through shared memory.
-  if (inner != 1 && (long long)blockIdx.x < args.ntiles) load_raw(Xw, blockIdx.x, r, a0, a1, n, inner, Q, raw);
+  if (inner != 1 && (long long)blockIdx.x < args.ntiles) load_raw<KC>(Xw, blockIdx.x, r, a0, a1, n, inner, Q, raw);
+  // padding columns 4 KC .. npad - 1 (KC = 18): zero digits, written once here
+  // and again per tile where the staging area overwrites them (mode 1)
+  const auto zero_tail = [&]() {
+    const size_t rb = (size_t)(r >> 3) * sbo_a + (size_t)(r & 7) * 16;
+    for (int a = 4 * KC + 2 * part; a < npad; a += 2 * kParts)
+#pragma unroll
+      for (int k = 0; k < kDig; ++k)
+        *reinterpret_cast<uint32_t*>(sA + k * plane_a + rb + (size_t)(a >> 3) * 128 + (size_t)(a & 7) * 2) = 0u;
+  };
+  zero_tail();
 
   for (long long tile = blockIdx.x; tile < args.ntiles; tile += gridDim.x) {
     const long long q0 = tile * kTile;
@@ -228,68 +231,73 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
       }
       __syncthreads();
 #pragma unroll
-      for (int c = 0; c < kCols; ++c) {
+      for (int c = 0; c < KC; ++c) {
         const int a = a0 + c;
         raw[c] = (r < rows && a < a1) ? blk[r * ld + a] : 0ll;
       }
       __syncthreads();   // the planes overwrite the block below
+      zero_tail();
     }
-    // ---- row exponent: max over this thread's columns, then over the four parts
+    // ---- entries as double-floats; row exponent: max over this thread's
+    // columns, then over the four parts
+    float xh[KC], xl[KC];
     {
       int E0 = 0, E1 = 0;
 #pragma unroll
-      for (int c = 0; c < kCols; c += 2) {
-        const unsigned long long w0 = (unsigned long long)raw[c], w1 = (unsigned long long)raw[c + 1];
-        E0 = max(E0, DBL ? (int)((w0 >> 52) & 0x7FF) : (int)((w0 >> 23) & 0xFF));
-        E1 = max(E1, DBL ? (int)((w1 >> 52) & 0x7FF) : (int)((w1 >> 23) & 0xFF));
+      for (int c = 0; c < KC; c += 2) {
+        const dfa::df v0 = entry<DBL>(raw[c]), v1 = entry<DBL>(raw[c + 1]);
+        xh[c] = v0.h;
+        xl[c] = v0.l;
+        xh[c + 1] = v1.h;
+        xl[c + 1] = v1.l;
+        E0 = max(E0, (int)((__float_as_uint(v0.h) >> 23) & 0xFFu));
+        E1 = max(E1, (int)((__float_as_uint(v1.h) >> 23) & 0xFFu));
       }
       sE[part * kTile + r] = max(E0, E1);
     }
     __syncthreads();
-    int E = 0;
+    int E = 7;   // rows below 2^-120 keep fewer than 48 bits
 #pragma unroll
     for (int pp = 0; pp < kParts; ++pp) E = max(E, sE[pp * kTile + r]);
-    const int urow = DBL ? E - 1070 : E - 174;
-    // ---- 48-bit fixed point and its six digit planes, two columns per 32-bit store
+    const int urow = E - 133;         // X[q][a] = 2^urow y_a with |y_a| < 2^7
+    const float S = pow2f(-urow);
+    // ---- six digit planes, two columns per 32-bit store
     {
       const size_t rbase = (size_t)(r >> 3) * sbo_a + (size_t)(r & 7) * 16;
 #pragma unroll
-      for (int c = 0; c < kCols; c += 2) {
-        const int a = a0 + c;   // columns n .. npad-1 are written as zero digits
+      for (int c = 0; c < KC; c += 2) {
+        const int a = a0 + c;   // columns n .. 4 KC - 1 hold zero entries
         if (a >= npad) break;
-        uint32_t h[2][kDig];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const long long f = to_fixed<DBL>(raw[c + e], E);
-          const unsigned long long m = (unsigned long long)(f < 0 ? -f : f);
-          const uint32_t sgn = f < 0 ? 0x8000u : 0u;
-#pragma unroll
-          for (int k = 0; k < kDig; ++k) {
-            const uint32_t dg = (uint32_t)(m >> (40 - 8 * k)) & 0xFFu;
-            // exact float of the digit (0x4B000000 | d is 2^23 + d); its top 16 bits are its BF16
-            const float fv = __int_as_float(0x4B000000u | dg) - 8388608.0f;
-            h[e][k] = ((uint32_t)__float_as_int(fv) >> 16) | sgn;
-          }
-        }
+        float d0[kDig], d1[kDig];
+        digits6(xh[c] * S, xl[c] * S, d0);
+        digits6(xh[c + 1] * S, xl[c + 1] * S, d1);
         const size_t off = rbase + (size_t)(a >> 3) * 128 + (size_t)(a & 7) * 2;
 #pragma unroll
-        for (int k = 0; k < kDig; ++k)
-          *reinterpret_cast<uint32_t*>(sA + k * plane_a + off) = h[0][k] | (h[1][k] << 16);
+        for (int k = 0; k < kDig; ++k) {
+          const __nv_bfloat162 b = __floats2bfloat162_rn(d0[k], d1[k]);   // exact: digits are BF16 numbers
+          *reinterpret_cast<__nv_bfloat162*>(sA + k * plane_a + off) = b;
+        }
       }
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    // ---- all 21 digit-pair MMAs of the tile, one commit
+    // ---- all 21 digit pairs of the tile, one commit. The B planes are stacked
+    // (plane l + 1 follows plane l as the next npad rows) and the accumulators
+    // are adjacent (diagonal c at columns c npad), so one MMA of N = m npad
+    // multiplies A plane k by B planes l .. l + m - 1 into diagonals
+    // k + l .. k + l + m - 1: with N <= 256, 9 MMAs per K step instead of 21.
     if (t == 0) {
       for (int k = 0; k < kDig; ++k)
-        for (int l = 0; l + k < kDig; ++l) {
+        for (int l = 0; l + k < kDig; l += mgroup) {
+          const int m = min(mgroup, kDig - k - l);
           const uint32_t dcol = tmem + (uint32_t)((k + l) * npad);
+          const uint32_t idesc_m = tc::instr_desc(1u, kTile, m * npad);
           for (int s = 0; s < ksteps; ++s) {
             const uint64_t da = da0 + (uint64_t)((k * plane_a + s * 256) >> 4);
             const uint64_t db = db0 + (uint64_t)((l * plane_b + s * 256) >> 4);
-            tc::mma<0>(dcol, da, db, idesc, (k > 0 || s > 0) ? 1u : 0u);
+            tc::mma<0>(dcol, da, db, idesc_m, (k > 0 || s > 0) ? 1u : 0u);
           }
         }
       tc::mma_commit(tc::smem_u32(&mbar[0]));
@@ -297,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
     // ---- the next tile's words travel while the tensor cores work
     if (inner != 1) {
       const long long nt = tile + gridDim.x;
-      if (nt < args.ntiles) load_raw(Xw, nt, r, a0, a1, n, inner, Q, raw);
+      if (nt < args.ntiles) load_raw<KC>(Xw, nt, r, a0, a1, n, inner, Q, raw);
     }
     if (!tc::mbar_wait(tc::smem_u32(&mbar[0]), ph, kWaitIters)) *sflag = 1;
     ph ^= 1u;
@@ -307,36 +315,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
       break;
     }
     tc::fence_after_sync();
-    // ---- epilogue: part p combines the six diagonals of row r on chunks p, p+4, ...
+    // ---- epilogue: part p combines the six diagonals of row r on the 4-column
+    // chunks p, p+4, ... that hold output columns (i < n)
     const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     float2* stage = reinterpret_cast<float2*>(sA);   // free once the MMAs are done
-    for (int c8 = part; c8 < nchunk_pad; c8 += kParts) {
-      uint32_t Tr[kDig][8];
+    for (int c4 = part; c4 < nchunk4; c4 += kParts) {
+      uint32_t Tr[kDig][4];
 #pragma unroll
-      for (int c = 0; c < kDig; ++c) tc::tmem_ld8_async(lane_base + (uint32_t)(c * npad + 8 * c8), Tr[c]);
-      tc::tmem_wait_ld8x6(Tr);
+      for (int c = 0; c < kDig; ++c) tc::tmem_ld4_async(lane_base + (uint32_t)(c * npad + 4 * c4), Tr[c]);
+      tc::tmem_wait_ld4x6(Tr);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int i = 8 * c8 + j;
+      for (int j = 0; j < 4; ++j) {
+        const int i = 4 * c4 + j;
         if (i >= n || r >= rows) continue;
         float T[kDig];
 #pragma unroll
         for (int c = 0; c < kDig; ++c) T[c] = __uint_as_float(Tr[c][j]);
-        // exact two-sums for the three leading diagonals; the trailing three sit
-        // below 2^-22 of the total and are summed in plain FP32 (error < 2^-46 of it)
+        // every T_c is exact; two-sums fold in the two leading diagonals below
+        // T_0, the trailing three (below 2^-23 of the total) are summed in FP32
         float hi = T[0], lo = 0.f;
 #pragma unroll
         for (int c = 1; c < 3; ++c) {
-          const float v = T[c] * pow2f(-8 * c);
-          const float sm = hi + v, bp = sm - hi;
-          lo += (hi - (sm - bp)) + (v - bp);
+          const float sm = hi + T[c], bp = sm - hi;
+          lo += (hi - (sm - bp)) + (T[c] - bp);
           hi = sm;
         }
-        lo += fmaf(T[5], pow2f(-40), fmaf(T[4], pow2f(-32), T[3] * pow2f(-24)));
+        lo += (T[3] + T[4]) + T[5];
         const dfa::df sres = dfa::norm(dfa::df{hi, lo});
-        int sc = urow + sv[i] + 80;
+        int sc = urow + sv[i];
         sc = max(-250, min(250, sc));
-        const float f1 = pow2f(sc / 2), f2 = pow2f(sc - sc / 2);
+        const float f1 = pow2f(sc >> 1), f2 = pow2f(sc - (sc >> 1));
         const dfa::df y{sres.h * f1 * f2, sres.l * f1 * f2};
         if (inner == 1) {
           stage[r * ld + i] = make_float2(y.h, y.l);
@@ -379,7 +387,7 @@ size_t oz_smem_bytes(int n) {
          (size_t)((npad + 3) & ~3) * 4 + (size_t)kParts * kTile * 4 + 32;
 }
 
-template <typename TIn, typename TOut>
+template <typename TIn, typename TOut, int KC>
 cudaError_t launch_oz(const TIn* X, TOut* Y, const unsigned char* B, const int* v, int n, long long inner,
                       long long outer, cudaStream_t st) {
   const long long Q = inner * outer;
@@ -388,8 +396,8 @@ cudaError_t launch_oz(const TIn* X, TOut* Y, const unsigned char* B, const int* 
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   static bool attr_done = false;
   if (!attr_done) {
-    const cudaError_t e = cudaFuncSetAttribute(k_tc_ozaki<TIn, TOut>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               227 * 1024);
+    const cudaError_t e = cudaFuncSetAttribute(k_tc_ozaki<TIn, TOut, KC>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
@@ -398,8 +406,20 @@ cudaError_t launch_oz(const TIn* X, TOut* Y, const unsigned char* B, const int* 
   OzArgs a{X, Y, B, v, n, (n + 15) / 16 * 16, inner, Q, ntiles};
   ProfScope ps("fd_mode_ozaki", 2.0 * (double)Q * n * n, 8.0 * (double)Q * n * 2, st);
   // 227 KB requested so that exactly one CTA (which owns all 512 TMEM columns) fits per SM
-  k_tc_ozaki<TIn, TOut><<<(unsigned)grid, kThreads, 227 * 1024, st>>>(a);
+  k_tc_ozaki<TIn, TOut, KC><<<(unsigned)grid, kThreads, 227 * 1024, st>>>(a);
   return cudaGetLastError();
+}
+
+template <typename TIn, typename TOut>
+cudaError_t launch_oz_cols(const TIn* X, TOut* Y, const unsigned char* B, const int* v, int n, long long inner,
+                           long long outer, cudaStream_t st) {
+  switch (oz_cols(n)) {
+    case 8: return launch_oz<TIn, TOut, 8>(X, Y, B, v, n, inner, outer, st);
+    case 12: return launch_oz<TIn, TOut, 12>(X, Y, B, v, n, inner, outer, st);
+    case 16: return launch_oz<TIn, TOut, 16>(X, Y, B, v, n, inner, outer, st);
+    case 18: return launch_oz<TIn, TOut, 18>(X, Y, B, v, n, inner, outer, st);
+    default: return launch_oz<TIn, TOut, 20>(X, Y, B, v, n, inner, outer, st);
+  }
 }
 
 }  // namespace
@@ -407,7 +427,10 @@ cudaError_t launch_oz(const TIn* X, TOut* Y, const unsigned char* B, const int* 
 int ozaki_max_n() { return 80; }
 
 // Host: digit planes of a row-major n x n factor J (J[i*n + a]) and the
-// per-row scale exponents v_i (J[i][a] ~= 2^{v_i} sum_l dj_l 2^{40-8l}).
+// per-row scale exponents v_i: J[i][a] = 2^{v_i} (sum_l dj_l + remainder), with
+// w = 2^{-v_i} J[i][a] below 2^7 and dj_l = round(w_l 2^{8l}) 2^{-8l} taken from
+// the running remainder w_l (exact in FP64: scalings by powers of two, integer
+// rounding, and the subtraction of a value within half a digit unit).
 std::vector<unsigned char> ozaki_planes(const double* J, int n, std::vector<int>& v) {
   const int npad = (n + 15) / 16 * 16;
   const int kcores = npad / 8;
@@ -421,21 +444,15 @@ std::vector<unsigned char> ozaki_planes(const double* J, int n, std::vector<int>
       std::memcpy(&bits, &J[(size_t)i * n + a], 8);
       E = std::max(E, (int)((bits >> 52) & 0x7FF));
     }
-    v[i] = E - 1070;
+    E = std::max(E, 1);
+    v[i] = E - 1029;   // |J[i][a]| < 2^{E - 1022} = 2^{v_i + 7}
     for (int a = 0; a < n; ++a) {
-      unsigned long long bits;
-      std::memcpy(&bits, &J[(size_t)i * n + a], 8);
-      const int ex = (int)((bits >> 52) & 0x7FF);
-      unsigned long long f = 0;
-      if (ex != 0) {
-        const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const int sh = E - ex + 5;
-        f = sh < 64 ? (m >> sh) : 0;
-      }
-      const bool neg = (bits >> 63) != 0;
+      double w = std::ldexp(J[(size_t)i * n + a], -v[i]);
       for (int l = 0; l < kDig; ++l) {
-        const int dg = (int)((f >> (40 - 8 * l)) & 0xFF);
-        const __nv_bfloat16 h = __float2bfloat16_rn((float)(neg ? -dg : dg));
+        const double dl = std::nearbyint(std::ldexp(w, 8 * l));
+        const double d = std::ldexp(dl, -8 * l);
+        w -= d;
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)d);
         std::memcpy(&img[l * plane + canon_off16(i, a, kcores)], &h, 2);
       }
     }
@@ -445,9 +462,9 @@ std::vector<unsigned char> ozaki_planes(const double* J, int n, std::vector<int>
 
 cudaError_t launch_fd_mode_ozaki(const void* X, int x_is_double, const unsigned char* B, const int* v, void* Y,
                                  int y_is_double, int n, long long inner, long long outer, cudaStream_t st) {
-  if (x_is_double) return launch_oz<double, float2>((const double*)X, (float2*)Y, B, v, n, inner, outer, st);
-  if (y_is_double) return launch_oz<float2, double>((const float2*)X, (double*)Y, B, v, n, inner, outer, st);
-  return launch_oz<float2, float2>((const float2*)X, (float2*)Y, B, v, n, inner, outer, st);
+  if (x_is_double) return launch_oz_cols<double, float2>((const double*)X, (float2*)Y, B, v, n, inner, outer, st);
+  if (y_is_double) return launch_oz_cols<float2, double>((const float2*)X, (double*)Y, B, v, n, inner, outer, st);
+  return launch_oz_cols<float2, float2>((const float2*)X, (float2*)Y, B, v, n, inner, outer, st);
 }
 
 }  // namespace stfd

@@ -116,6 +116,8 @@ SIGNATURES = {
     "stfd_launch_count": (ctypes.c_longlong, []),
     "stfd_probe_fp64_peak": (ctypes.c_int, [_c_dbl_p, ctypes.c_void_p]),
     "stfd_probe_bounded_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p]),
+    "stfd_probe_convert": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
