@@ -434,25 +434,32 @@ int fd_apply_one_df(const stfd_fd* h, const double* r, double* s, double* work, 
   const int d = h->d;
   const int P = 2 * (d + 1);
   auto buf = [&](int k) { return ((P - k) % 2 == 0) ? static_cast<void*>(s) : static_cast<void*>(work); };
+  // The mode products of Steps 2 and 4 commute. The FP64 input is read by the
+  // time mode and the FP64 output written by it (a strided mode: its entries
+  // travel straight to and from registers), so that mode 1, whose rows are
+  // contiguous and go through a shared-memory stage, carries float2 only.
+  // Forward order t, 1, .., d; backward order 1, .., d, t.
+  long long inner_of[kMaxDim + 1];
+  inner_of[0] = 1;
+  for (int l = 1; l <= d; ++l) inner_of[l] = inner_of[l - 1] * h->n[l - 1];
   const void* src = r;
   int pass = 0;
-  long long inner = 1;
-  for (int l = 0; l <= d; ++l) {
-    const long long outer = h->N / (inner * h->n[l]);
+  for (int k = 0; k <= d; ++k) {
+    const int l = k == 0 ? d : k - 1;
+    const long long outer = h->N / (inner_of[l] * h->n[l]);
     void* dst = buf(++pass);
-    STFD_CU(mode(src, pass == 1 ? 1 : 0, l, true, dst, 0, inner, outer));
+    STFD_CU(mode(src, pass == 1 ? 1 : 0, l, true, dst, 0, inner_of[l], outer));
     src = dst;
-    inner *= h->n[l];
   }
   const float2* lam[3] = {h->lam2[0], h->lam2[1], h->lam2[2]};
   STFD_CU(launch_arrowhead_df(static_cast<float2*>(const_cast<void*>(src)), d, h->n[0], d >= 2 ? h->n[1] : 1,
                               h->n[d], h->n_pairs, h->has_zero, h->Ns, lam, h->B2, h->BB2, h->G2, h->Sinv2, h->nu,
                               trans ? -1 : 1, st));
-  for (int l = d; l >= 0; --l) {
-    inner /= h->n[l];
-    const long long outer = h->N / (inner * h->n[l]);
+  for (int k = 0; k <= d; ++k) {
+    const int l = k;
+    const long long outer = h->N / (inner_of[l] * h->n[l]);
     void* dst = buf(++pass);
-    STFD_CU(mode(src, 0, l, false, dst, pass == P ? 1 : 0, inner, outer));
+    STFD_CU(mode(src, 0, l, false, dst, pass == P ? 1 : 0, inner_of[l], outer));
     src = dst;
   }
   return STFD_OK;

@@ -38,17 +38,15 @@ __device__ __noinline__ static df from_double_fp64(double x) {
 // renormalised; h + l carries at least 48 significant bits of x.
 __device__ __forceinline__ df from_double(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int E = (int)((b >> 52) & 0x7FF);
+  const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
+  const int E = (int)((hi >> 20) & 0x7FFu);
   if (E == 0) return df{0.f, 0.f};   // zero, or below 2^-1022: beyond the FP32 range
   const int e = E - 1023;
   if (e < -70 || e > 126) return from_double_fp64(x);
-  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  float h = __uint2float_rn((unsigned int)(m >> 29)) * pow2(e - 23);
-  float l = __uint2float_rn((unsigned int)(m & 0x1FFFFFFFull)) * pow2(e - 52);
-  if (b >> 63) {
-    h = -h;
-    l = -l;
-  }
+  // the sign, the exponent and the top 23 fraction bits form the float h exactly
+  const unsigned int sgn = hi & 0x80000000u;
+  const float h = __uint_as_float(sgn | ((unsigned int)(e + 127) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+  const float l = __uint_as_float(__float_as_uint(__uint2float_rn(lo & 0x1FFFFFFFu) * pow2(e - 52)) | sgn);
   return norm(df{h, l});
 }
 __device__ __forceinline__ df from_float2(float2 v) { return df{v.x, v.y}; }
@@ -89,10 +87,10 @@ __device__ __forceinline__ long long df_term(unsigned int bits, int eb) {
   return (bits >> 31) ? -(long long)t : (long long)t;
 }
 
-// double-float -> FP64: h + l summed exactly as one integer (whenever h + l is
-// itself a double, as for every normalised pair from from_double), then
-// normalised to a 53-bit significand (round half up).
-__device__ __forceinline__ double to_double(df a) {
+// double-float -> FP64 for any pair: h + l summed exactly as one integer
+// (whenever h + l is itself a double, as for every normalised pair from
+// from_double), then normalised to a 53-bit significand (round half up).
+__device__ __noinline__ static double to_double_general(df a) {
   const unsigned int bh = __float_as_uint(a.h), bl = __float_as_uint(a.l);
   const int eh = (int)((bh >> 23) & 0xFFu), el = (int)((bl >> 23) & 0xFFu);
   if (eh == 0xFF || el == 0xFF) {   // infinity or NaN: that float's value
@@ -115,6 +113,26 @@ __device__ __forceinline__ double to_double(df a) {
   // the significand's leading bit adds one to the exponent field (also after a rounding carry)
   const unsigned long long field = (unsigned long long)(eb + 905 - lz - 1);
   return __longlong_as_double((long long)(sgn | ((field << 52) + mag)));
+}
+
+// double-float -> FP64, rounded to nearest: h is exact as a double; l,
+// measured in units of the double ulp of h's binade (a power-of-two scaling,
+// exact), is rounded to an integer k and added to the bit pattern of h, which
+// adds k ulps (a normalised pair, |l| <= ulp_float(h) / 2, never carries out of
+// the binade; when h is a power of two and the sum falls below it, the units
+// are those of the binade below). Pairs that are not normalised or have
+// |h| < 2^-75 take to_double_general.
+__device__ __forceinline__ double to_double(df a) {
+  const unsigned int bh = __float_as_uint(a.h);
+  if ((bh << 1) == 0u && (__float_as_uint(a.l) << 1) == 0u) return 0.0;
+  const int eh = (int)((bh >> 23) & 0xFFu);
+  float v = a.l * pow2(179 - max(eh, 52));
+  if (bh >> 31) v = -v;
+  if ((bh & 0x7FFFFFu) == 0u && v < 0.f) v *= 2.f;
+  if (eh < 52 || eh == 0xFF || !(fabsf(v) < 1073741824.f)) return to_double_general(a);
+  const unsigned long long B = ((unsigned long long)(bh >> 31) << 63) | ((unsigned long long)(eh + 896) << 52) |
+                               ((unsigned long long)(bh & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)(B + (unsigned long long)(long long)__float2int_rn(v)));
 }
 
 // acc += b * x (the b.l * x.l term, ~2^-48 relative, is dropped)

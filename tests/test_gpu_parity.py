@@ -81,7 +81,8 @@ def test_fd_apply_matches_direct_solve(d, p, n_el):
 
 
 MV_CASES = [(1, 3, 30, 1.0, 1.0, 1.0, 1), (2, 2, 16, 1.0, 1.0, 1.0, 2), (2, 4, 11, 0.5, 0.4, 2.5, 1),
-            (3, 3, 13, 1.0, 1.0, 1.0, 1), (3, 1, 17, 2.0, 1.1, 0.9, 1)]
+            (3, 3, 13, 1.0, 1.0, 1.0, 1), (3, 1, 17, 2.0, 1.1, 0.9, 1),
+            (1, 2, 120, 1.0, 1.0, 1.0, 1)]   # n_t = 121: the time pass takes the unpaired kernel
 
 
 @pytest.mark.parametrize("arith", [stfd.STFD_OP_FP64, stfd.STFD_OP_DF32])
