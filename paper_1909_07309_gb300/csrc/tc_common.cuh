@@ -153,6 +153,29 @@ __device__ __forceinline__ void tmem_wait_ld4x6(uint32_t (&r)[6][4]) {
     asm volatile("" : "+r"(r[c][0]), "+r"(r[c][1]), "+r"(r[c][2]), "+r"(r[c][3]) : : "memory");
 }
 
+// Bulk (TMA, untiled) copies. Both addresses 16-byte aligned, size a multiple of 16.
+// global -> shared, completing `bytes` of the mbarrier's transaction count
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar_addr, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_addr), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar_addr) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar_addr) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst_smem, const void* src, uint32_t bytes, uint32_t mbar_addr) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   dst_smem),
+               "l"(src), "r"(bytes), "r"(mbar_addr)
+               : "memory");
+}
+// shared -> global in the issuing thread's bulk group, and the waits on that group
+__device__ __forceinline__ void bulk_s2g(void* dst, uint32_t src_smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src_smem), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // Asynchronous 8-byte global -> shared copy (no register staging), and the wait
 // for every copy this thread has issued.
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {

@@ -159,14 +159,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   const uint32_t sbo_b = (uint32_t)kcores * 128u, sbo_a = a_sbo(kcores);
   const size_t plane_b = (size_t)npad * npad * 2;
   const size_t plane_a = (size_t)(kTile / 8) * sbo_a;
-  const int ld = n + 1;                         // output staging row stride (8-byte words)
   const long long inner = args.inner, Q = args.Q;
   unsigned char* sB = smem;                                            // kDig planes of J
   unsigned char* sA = sB + kDig * plane_b;                             // kDig planes of the tile
   int* sv = reinterpret_cast<int*>(sA + kDig * plane_a);              // npad
   int* sE = sv + ((npad + 3) & ~3);                                    // kParts x kTile
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sE + kParts * kTile);   // 1 barrier
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sE + kParts * kTile);   // MMA, bulk copy
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   int* sflag = reinterpret_cast<int*>(tslot + 1);
   const int t = threadIdx.x, warp = t >> 5, r = t & (kTile - 1), part = t >> 7;
   const int nchunk4 = (n + 3) / 4;
@@ -181,6 +180,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   }
   if (t == 0) {
     tc::mbar_init(tc::smem_u32(&mbar[0]), 1);
+    tc::mbar_init(tc::smem_u32(&mbar[1]), 1);
     *sflag = 0;
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 512);
@@ -193,8 +193,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   const uint32_t a_addr = tc::smem_u32(sA), b_addr = tc::smem_u32(sB);
   const int ksteps = npad / 16;
   const uint64_t da0 = tc::smem_desc(a_addr, 128u, sbo_a), db0 = tc::smem_desc(b_addr, 128u, sbo_b);
-  uint32_t ph = 0u;
+  uint32_t ph = 0u, ph_in = 0u;
   const long long* Xw = static_cast<const long long*>(args.X);
+  // mode 1: the tile is one contiguous block of rows x n words in and out, moved
+  // by bulk copies when the tensors are 16-byte aligned (the block offsets
+  // q0 n 8 bytes are multiples of 1024)
+  const bool bulk_in = (reinterpret_cast<uintptr_t>(args.X) & 15u) == 0u;
+  const bool bulk_out = (reinterpret_cast<uintptr_t>(args.Y) & 15u) == 0u;
   long long raw[KC];
   // strided modes: each warp's loads are coalesced (consecutive rows are
   // consecutive addresses), so entries go straight to registers and the next
@@ -221,19 +226,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
       const long long o = q / inner;
       base = o * (long long)n * inner + (q - o * inner);
     }
-    if (inner == 1) {   // coalesced copy of the tile's rows into the (free) plane area
+    if (inner == 1) {   // the tile's rows into the (free) plane area, row stride n
       long long* blk = reinterpret_cast<long long*>(sA);
       const long long* src = Xw + q0 * n;
       const int cnt = rows * n;
-      for (int e = t; e < cnt; e += kThreads) {
-        const int rr = e / n;
-        blk[rr * ld + (e - rr * n)] = __ldg(src + e);
+      if (bulk_in) {
+        const int cnt2 = cnt & ~1;   // whole 16-byte units; an odd last word by thread 1
+        if (t == 0) {
+          if (bulk_out) tc::bulk_wait_read_all();   // the previous tile's output block has been read out
+          tc::fence_async_smem();
+          if (cnt2 > 0) {
+            tc::mbar_arrive_expect_tx(tc::smem_u32(&mbar[1]), (uint32_t)cnt2 * 8u);
+            tc::bulk_g2s(tc::smem_u32(blk), src, (uint32_t)cnt2 * 8u, tc::smem_u32(&mbar[1]));
+          } else {
+            tc::mbar_arrive(tc::smem_u32(&mbar[1]));
+          }
+        }
+        if (t == 1 && (cnt & 1)) blk[cnt - 1] = __ldg(src + cnt - 1);
+        if (!tc::mbar_wait(tc::smem_u32(&mbar[1]), ph_in, kWaitIters)) *sflag = 1;
+        ph_in ^= 1u;
+      } else {
+        if (bulk_out) {
+          if (t == 0) tc::bulk_wait_read_all();
+          __syncthreads();
+        }
+        for (int e = t; e < cnt; e += kThreads) blk[e] = __ldg(src + e);
       }
       __syncthreads();
+      if (*sflag) {
+        if (t == 0) atomicExch(&g_tc_status, 1);
+        break;
+      }
 #pragma unroll
       for (int c = 0; c < KC; ++c) {
         const int a = a0 + c;
-        raw[c] = (r < rows && a < a1) ? blk[r * ld + a] : 0ll;
+        raw[c] = (r < rows && a < a1) ? blk[r * n + a] : 0ll;
       }
       __syncthreads();   // the planes overwrite the block below
       zero_tail();
@@ -347,26 +374,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
         const float f1 = pow2f(sc >> 1), f2 = pow2f(sc - (sc >> 1));
         const dfa::df y{sres.h * f1 * f2, sres.l * f1 * f2};
         if (inner == 1) {
-          stage[r * ld + i] = make_float2(y.h, y.l);
+          StoreOut<TOut>::put(reinterpret_cast<TOut*>(stage), (long long)r * n + i, y);
         } else {
           StoreOut<TOut>::put(static_cast<TOut*>(args.Y), base + (long long)i * inner, y);
         }
       }
     }
-    if (inner == 1) {
-      __syncthreads();
+    if (inner == 1) {   // the stage (row stride n) is the output block
       TOut* dst = static_cast<TOut*>(args.Y) + q0 * n;
+      const TOut* sst = reinterpret_cast<const TOut*>(stage);
       const int cnt = rows * n;
-      for (int e = t; e < cnt; e += kThreads) {
-        const int rr = e / n;
-        const float2 v = stage[rr * ld + (e - rr * n)];
-        StoreOut<TOut>::put(dst, e, dfa::df{v.x, v.y});
+      if (bulk_out) {
+        tc::fence_async_smem();   // the stage writes, visible to the bulk copy
+        __syncthreads();
+        const int cnt2 = cnt & ~1;
+        if (t == 0 && cnt2 > 0) tc::bulk_s2g(dst, tc::smem_u32(stage), (uint32_t)cnt2 * 8u);
+        if (t == 1 && (cnt & 1)) dst[cnt - 1] = sst[cnt - 1];
+      } else {
+        __syncthreads();
+        for (int e = t; e < cnt; e += kThreads) dst[e] = sst[e];
       }
     }
     tc::fence_before_sync();
     __syncthreads();   // the staging area and sE are rewritten by the next tile
   }
   tc::fence_after_sync();
+  if (t == 0) tc::bulk_wait_all();   // the last output block has left shared memory
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 

@@ -231,3 +231,22 @@ def test_argument_checks_on_device():
     assert lib.stfd_fd_apply(P.handle, None, None, 0, None) == 0   # nrhs = 0 is a no-op
     with pytest.raises(stfd.StfdError):
         stfd.FD(K, M, Wt, Mt, gamma=-1.0)
+
+
+@pytest.mark.parametrize("prec", [stfd.STFD_FP64TC, stfd.STFD_DF32])
+@pytest.mark.parametrize("d,p,n_el", [(2, 3, 21), (3, 3, 13)])
+def test_fd_apply_unaligned_buffers_match(d, p, n_el, prec):
+    """Input and output vectors that start 8 bytes past a 16-byte boundary take
+    the element-wise copies of mode 1 instead of the bulk copies; the result is
+    the same arithmetic, hence bit-identical."""
+    K, M, Wt, Mt = stfd.heat_problem(d, p, n_el)
+    P = stfd.FD(K, M, Wt, Mt, precision=prec)
+    r = dev(inputs.standard_normal(P.N, 4))
+    s_ref = P.apply(r)
+    big_r = torch.zeros(P.N + 1, dtype=torch.float64, device="cuda")
+    big_s = torch.zeros(P.N + 1, dtype=torch.float64, device="cuda")
+    r1, s1 = big_r[1:], big_s[1:]
+    assert r1.data_ptr() % 16 == 8 and s1.data_ptr() % 16 == 8
+    r1.copy_(r)
+    P.apply(r1, s1)
+    assert torch.equal(s1, s_ref)
