@@ -101,13 +101,19 @@ inline int oz_cols(int n) { return n <= 32 ? 8 : n <= 48 ? 12 : n <= 64 ? 16 : n
 __device__ __forceinline__ float round_const(int k) { return 12582912.0f * pow2f(-8 * k); }
 
 // Byte distance between 8-row groups of an A digit plane: the dense value plus
-// 16 bytes, so that the 4 row groups a warp writes fall in different banks.
+// 16 bytes (the tensor cores read the planes faster with the padding).
 __host__ __device__ inline uint32_t a_sbo(int kcores) { return (uint32_t)kcores * 128u + 16u; }
 
-// Raw 8-byte words of tile `tile`, row r, columns a0 .. a0 + KC - 1 (0 outside).
+// Column of the c-th entry held by digit-phase part p: part p owns the column
+// pairs j = 4m + p (columns 8m + 2p and 8m + 2p + 1), so that when the 8 rows x 4
+// parts of a warp store the same m, each thread's 32-bit word lands in its own
+// bank (bank 4 (row mod 8) + p of the 16-byte row chunk, plus the row group's offset).
+__device__ __forceinline__ int part_col(int p, int c) { return 8 * (c >> 1) + 2 * p + (c & 1); }
+
+// Raw 8-byte words of tile `tile`, row r, the KC columns of part p (0 outside).
 template <int KC>
-__device__ __forceinline__ void load_raw(const long long* __restrict__ Xw, long long tile, int r, int a0, int a1,
-                                         int n, long long inner, long long Q, long long* raw) {
+__device__ __forceinline__ void load_raw(const long long* __restrict__ Xw, long long tile, int r, int p, int n,
+                                         long long inner, long long Q, long long* raw) {
   const long long q = tile * kTile + r;
   const bool valid = q < Q;
   long long base = 0;
@@ -117,8 +123,8 @@ __device__ __forceinline__ void load_raw(const long long* __restrict__ Xw, long 
   }
 #pragma unroll
   for (int c = 0; c < KC; ++c) {
-    const int a = a0 + c;
-    raw[c] = (valid && a < a1) ? __ldg(Xw + base + (long long)a * inner) : 0ll;
+    const int a = part_col(p, c);
+    raw[c] = (valid && a < n) ? __ldg(Xw + base + (long long)a * inner) : 0ll;
   }
 }
 
@@ -163,13 +169,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   unsigned char* sB = smem;                                            // kDig planes of J
   unsigned char* sA = sB + kDig * plane_b;                             // kDig planes of the tile
   int* sv = reinterpret_cast<int*>(sA + kDig * plane_a);              // npad
-  int* sE = sv + ((npad + 3) & ~3);                                    // kParts x kTile
+  int* sE = sv + ((npad + 3) & ~3);                                    // kTile row exponents
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sE + kParts * kTile);   // MMA, bulk copy
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   int* sflag = reinterpret_cast<int*>(tslot + 1);
   const int t = threadIdx.x, warp = t >> 5, r = t & (kTile - 1), part = t >> 7;
   const int nchunk4 = (n + 3) / 4;
-  const int a0 = part * KC, a1 = min(n, a0 + KC);   // this thread's columns
+  // digit phase: warp w holds rows 32 (w mod 4) + 8 (w / 4) .. + 7 (inside its TMEM
+  // lane quarter) and, per row, the four parts dp = lane / 8 of the columns
+  const int dk = t & 7, dp = (t >> 3) & 3;
+  const int drow = 32 * (warp & 3) + 8 * (warp >> 2) + dk;
 
   {
     const uint4* src = reinterpret_cast<const uint4*>(args.B);
@@ -205,15 +214,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   // consecutive addresses), so entries go straight to registers and the next
   // tile's are fetched while the MMAs run. Mode 1 (inner == 1): a row is
   // contiguous, so the tile is a contiguous block, copied through shared memory.
-  if (inner != 1 && (long long)blockIdx.x < args.ntiles) load_raw<KC>(Xw, blockIdx.x, r, a0, a1, n, inner, Q, raw);
-  // padding columns 4 KC .. npad - 1 (KC = 18): zero digits, written once here
-  // and again per tile where the staging area overwrites them (mode 1)
+  if (inner != 1 && (long long)blockIdx.x < args.ntiles) load_raw<KC>(Xw, blockIdx.x, drow, dp, n, inner, Q, raw);
+  // padding column pairs 2 KC .. npad / 2 - 1 (KC = 18): zero digits, written once
+  // here and again per tile where the staging area overwrites them (mode 1)
+  const size_t drbase = (size_t)(drow >> 3) * sbo_a + (size_t)(drow & 7) * 16;
   const auto zero_tail = [&]() {
-    const size_t rb = (size_t)(r >> 3) * sbo_a + (size_t)(r & 7) * 16;
-    for (int a = 4 * KC + 2 * part; a < npad; a += 2 * kParts)
+    for (int j = 2 * KC + dp; j < npad / 2; j += kParts)
 #pragma unroll
       for (int k = 0; k < kDig; ++k)
-        *reinterpret_cast<uint32_t*>(sA + k * plane_a + rb + (size_t)(a >> 3) * 128 + (size_t)(a & 7) * 2) = 0u;
+        *reinterpret_cast<uint32_t*>(sA + k * plane_a + drbase + (size_t)(j >> 2) * 128 + (size_t)(j & 3) * 4) = 0u;
   };
   zero_tail();
 
@@ -259,8 +268,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
       }
 #pragma unroll
       for (int c = 0; c < KC; ++c) {
-        const int a = a0 + c;
-        raw[c] = (r < rows && a < a1) ? blk[r * n + a] : 0ll;
+        const int a = part_col(dp, c);
+        raw[c] = (drow < rows && a < n) ? blk[drow * n + a] : 0ll;
       }
       __syncthreads();   // the planes overwrite the block below
       zero_tail();
@@ -268,6 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
     // ---- entries as double-floats; row exponent: max over this thread's
     // columns, then over the four parts
     float xh[KC], xl[KC];
+    int Erow;
     {
       int E0 = 0, E1 = 0;
 #pragma unroll
@@ -280,25 +290,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
         E0 = max(E0, (int)((__float_as_uint(v0.h) >> 23) & 0xFFu));
         E1 = max(E1, (int)((__float_as_uint(v1.h) >> 23) & 0xFFu));
       }
-      sE[part * kTile + r] = max(E0, E1);
+      E0 = max(E0, E1);
+      E0 = max(E0, __shfl_xor_sync(0xFFFFFFFFu, E0, 8));    // over the row's four parts
+      E0 = max(E0, __shfl_xor_sync(0xFFFFFFFFu, E0, 16));
+      Erow = max(E0, 7);   // rows below 2^-120 keep fewer than 48 bits
+      if (dp == 0) sE[drow] = Erow;   // for the epilogue, whose threads own other rows
     }
-    __syncthreads();
-    int E = 7;   // rows below 2^-120 keep fewer than 48 bits
-#pragma unroll
-    for (int pp = 0; pp < kParts; ++pp) E = max(E, sE[pp * kTile + r]);
-    const int urow = E - 133;         // X[q][a] = 2^urow y_a with |y_a| < 2^7
-    const float S = pow2f(-urow);
+    // X[q][a] = 2^{Erow - 133} y_a with |y_a| < 2^7
+    const float S = pow2f(133 - Erow);
     // ---- six digit planes, two columns per 32-bit store
     {
-      const size_t rbase = (size_t)(r >> 3) * sbo_a + (size_t)(r & 7) * 16;
 #pragma unroll
       for (int c = 0; c < KC; c += 2) {
-        const int a = a0 + c;   // columns n .. 4 KC - 1 hold zero entries
-        if (a >= npad) break;
+        const int a = part_col(dp, c);   // columns n .. 4 KC - 1 hold zero entries
+        if (a >= npad) continue;
         float d0[kDig], d1[kDig];
         digits6(xh[c] * S, xl[c] * S, d0);
         digits6(xh[c + 1] * S, xl[c + 1] * S, d1);
-        const size_t off = rbase + (size_t)(a >> 3) * 128 + (size_t)(a & 7) * 2;
+        const size_t off = drbase + (size_t)(a >> 3) * 128 + (size_t)(a & 7) * 2;
 #pragma unroll
         for (int k = 0; k < kDig; ++k) {
           const __nv_bfloat162 b = __floats2bfloat162_rn(d0[k], d1[k]);   // exact: digits are BF16 numbers
@@ -332,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
     // ---- the next tile's words travel while the tensor cores work
     if (inner != 1) {
       const long long nt = tile + gridDim.x;
-      if (nt < args.ntiles) load_raw<KC>(Xw, nt, r, a0, a1, n, inner, Q, raw);
+      if (nt < args.ntiles) load_raw<KC>(Xw, nt, drow, dp, n, inner, Q, raw);
     }
     if (!tc::mbar_wait(tc::smem_u32(&mbar[0]), ph, kWaitIters)) *sflag = 1;
     ph ^= 1u;
@@ -345,6 +354,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
     // ---- epilogue: part p combines the six diagonals of row r on the 4-column
     // chunks p, p+4, ... that hold output columns (i < n)
     const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const int urow_e = sE[r] - 133;   // the exponent of epilogue row r, from the digit phase
     float2* stage = reinterpret_cast<float2*>(sA);   // free once the MMAs are done
     for (int c4 = part; c4 < nchunk4; c4 += kParts) {
       uint32_t Tr[kDig][4];
@@ -369,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
         }
         lo += (T[3] + T[4]) + T[5];
         const dfa::df sres = dfa::norm(dfa::df{hi, lo});
-        int sc = urow + sv[i];
+        int sc = urow_e + sv[i];
         sc = max(-250, min(250, sc));
         const float f1 = pow2f(sc >> 1), f2 = pow2f(sc - (sc >> 1));
         const dfa::df y{sres.h * f1 * f2, sres.l * f1 * f2};
