@@ -147,6 +147,12 @@ struct stfd_op {
   float2* Wb = nullptr;
   float2* WbT = nullptr;
   float2* Mtb = nullptr;
+  // the same bands as coefficient pairs (hi_1, hi_2, lo_1, lo_2) for the paired kernels:
+  // (M_l, K_l), (M_l, M_l), (W_t, M_t), (W_t^T, M_t)
+  float4* MK4[kMaxDim] = {nullptr, nullptr, nullptr};
+  float4* MM4[kMaxDim] = {nullptr, nullptr, nullptr};
+  float4* WMt4 = nullptr;
+  float4* WTMt4 = nullptr;
   // general spatial matrices (stfd_op_create_stencil)
   int kind = 0;                                   // 0: Kronecker factors, 1: stencil
   StencilOpDev sop;
@@ -639,6 +645,12 @@ extern "C" void stfd_op_destroy(stfd_op* A) {
   dev_free(A->Wb);
   dev_free(A->WbT);
   dev_free(A->Mtb);
+  for (int l = 0; l < kMaxDim; ++l) {
+    dev_free(A->MK4[l]);
+    dev_free(A->MM4[l]);
+  }
+  dev_free(A->WMt4);
+  dev_free(A->WTMt4);
   for (int k = 0; k < 4; ++k) dev_free(A->tmp[k]);
   for (int k = 0; k < 7; ++k) dev_free(A->sbuf[k]);
   dev_free(A->MtbU);
@@ -707,6 +719,7 @@ extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const dou
   }
   // double-float copies (hi, lo) of the row-major factors: keep = [M_0, K_0, M_1, K_1, ..., W_t, M_t]
   std::vector<std::vector<float2>> keep2;
+  std::vector<std::vector<float4>> keep4;
   if (rc == STFD_OK && arith == STFD_OP_DF32) {
     auto split = [&](const std::vector<double>& J, float2** dst) {
       keep2.emplace_back(J.size());
@@ -739,14 +752,33 @@ extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const dou
         }
       return split(band, dst);
     };
+    // two band matrices as coefficient pairs (hi_1, hi_2, lo_1, lo_2) per tap
+    auto compress_pair = [&](const std::vector<double>& J1, const std::vector<double>& J2, int nl, int p,
+                             float4** dst) {
+      const int W = 2 * p + 1;
+      keep4.emplace_back((size_t)nl * W, make_float4(0.f, 0.f, 0.f, 0.f));
+      for (int i = 0; i < nl; ++i)
+        for (int t = 0; t < W; ++t) {
+          const int a = i - p + t;
+          if (a < 0 || a >= nl) continue;
+          const double v1 = J1[(size_t)i * nl + a], v2 = J2[(size_t)i * nl + a];
+          const float h1 = (float)v1, h2 = (float)v2;
+          keep4.back()[(size_t)i * W + t] = make_float4(h1, h2, (float)(v1 - (double)h1), (float)(v2 - (double)h2));
+        }
+      return dev_upload(dst, keep4.back().data(), keep4.back().size(), st);
+    };
     if (A->banded) {
       for (int l = 0; l < d && rc == STFD_OK; ++l) {
         rc = compress(keep[2 * l], n[l], A->pb[l], &A->Mb[l]);
         if (rc == STFD_OK) rc = compress(keep[2 * l + 1], n[l], A->pb[l], &A->Kb[l]);
+        if (rc == STFD_OK) rc = compress_pair(keep[2 * l], keep[2 * l + 1], n[l], A->pb[l], &A->MK4[l]);
+        if (rc == STFD_OK) rc = compress_pair(keep[2 * l], keep[2 * l], n[l], A->pb[l], &A->MM4[l]);
       }
       if (rc == STFD_OK) rc = compress(keep[2 * d], n[d], A->pb[d], &A->Wb);
       if (rc == STFD_OK) rc = compress(keep[2 * d + 2], n[d], A->pb[d], &A->WbT);
       if (rc == STFD_OK) rc = compress(keep[2 * d + 1], n[d], A->pb[d], &A->Mtb);
+      if (rc == STFD_OK) rc = compress_pair(keep[2 * d], keep[2 * d + 1], n[d], A->pb[d], &A->WMt4);
+      if (rc == STFD_OK) rc = compress_pair(keep[2 * d + 2], keep[2 * d + 1], n[d], A->pb[d], &A->WTMt4);
     }
   }
   if (rc == STFD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = STFD_ERR_CUDA;
@@ -894,9 +926,9 @@ int matvec_one_df(const stfd_op* A, const double* x, double* y, int trans, cudaS
     const int bw = std::max(A->bwM[l], A->bwK[l]);
     if (A->banded) {
       if (l == 0) {
-        STFD_CU(launch_band_first_dfc(x, A->Mb[l], A->Kb[l], uo, vo, nl, inner, outer, A->pb[l], st));
+        STFD_CU(launch_band_first_pk(x, A->MK4[l], uo, vo, nl, inner, outer, A->pb[l], st));
       } else {
-        STFD_CU(launch_band_mid_dfc(u, v, A->Mb[l], A->Kb[l], uo, vo, nl, inner, outer, A->pb[l], st));
+        STFD_CU(launch_band_mid_pk(u, v, A->MM4[l], A->Kb[l], uo, vo, nl, inner, outer, A->pb[l], st));
       }
     } else if (l == 0) {
       STFD_CU(launch_band_first_df(x, A->JM2[l], A->JK2[l], uo, vo, nl, inner, outer, bw, st));
@@ -909,8 +941,7 @@ int matvec_one_df(const stfd_op* A, const double* x, double* y, int trans, cudaS
   }
   const int nt = A->n[d];
   if (A->banded) {
-    STFD_CU(launch_band_last_dfc(u, v, trans ? A->WbT : A->Wb, A->gamma, A->Mtb, A->nu, y, nt, inner, 1, A->pb[d],
-                                 st));
+    STFD_CU(launch_band_last_pk(u, v, trans ? A->WTMt4 : A->WMt4, A->gamma, A->nu, y, nt, inner, 1, A->pb[d], st));
   } else {
     STFD_CU(launch_band_last_df(u, v, trans ? A->JWT2 : A->JW2, A->gamma, A->JMt2, A->nu, y, nt, inner, 1, std::max(A->bwW, A->bwMt), st));
   }

@@ -197,6 +197,132 @@ k_band_pair_df_p(const TIn* __restrict__ U, const float2* __restrict__ V, const 
   }
 }
 
+// ---- Paired-chain variant of k_band_pair_df_p: two accumulation chains of a
+// pass that share their operand layout are issued together with the sm_100
+// float2 instructions (fma.rn.f32x2 and friends; per component the scalar
+// steps of df_fma in the same order, so the results are those of the scalar
+// kernel): KIND 0 (first direction) pairs M x and K x, the tile holding
+// (x.h, x.h, x.l, x.l); KIND 1 (middle directions) pairs M u and M v, the tile
+// holding (u.h, v.h, u.l, v.l), with K u as a scalar chain; KIND 2 (time) pairs
+// W u and M_t v on the same tile layout. The coefficient tables hold the
+// matching pairs (hi_1, hi_2, lo_1, lo_2) per tap.
+struct df2 {
+  float2 h, l;
+};
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b (b times -1 is exact, one rounding)
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
+// acc += b * x for two independent triples; the steps of df_fma
+__device__ __forceinline__ void df_fma2(df2& acc, float2 bh, float2 bl, float2 xh, float2 xl) {
+  const float2 p = __fmul2_rn(bh, xh);
+  const float2 e = __ffma2_rn(bh, xh, __fmul2_rn(p, make_float2(-1.f, -1.f)));
+  const float2 lo = __ffma2_rn(bh, xl, __ffma2_rn(bl, xh, e));
+  const float2 s = __fadd2_rn(acc.h, p);
+  const float2 bp = sub2(s, acc.h);
+  const float2 err = __fadd2_rn(sub2(acc.h, sub2(s, bp)), sub2(p, bp));
+  acc.h = s;
+  acc.l = __fadd2_rn(acc.l, __fadd2_rn(err, lo));
+}
+
+template <typename TIn, typename TOut, int KIND, int P>
+__global__ void __launch_bounds__(kThreads)
+k_band_pk(const TIn* __restrict__ U, const float2* __restrict__ V, const float4* __restrict__ T4,
+          const float2* __restrict__ T2, float2 s2, float2 s3, float2* __restrict__ Uo, TOut* __restrict__ Vo, int n,
+          long long inner, long long Q, int scale) {
+  constexpr int W = 2 * P + 1;
+  extern __shared__ float4 sm4[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long q = (long long)blockIdx.x * kTC + lane;
+  const bool valid = q < Q;
+  long long base = 0;
+  if (valid) {
+    const long long o = q / inner;
+    base = o * (long long)n * inner + (q - o * inner);
+  }
+  for (int a = warp; a < n; a += kWarps) {
+    const df u = valid ? load_df<TIn>(U, base + (long long)a * inner) : df{0.f, 0.f};
+    if (KIND == 0) {
+      sm4[a * kTC + lane] = make_float4(u.h, u.h, u.l, u.l);
+    } else {
+      const float2 v = valid ? V[base + (long long)a * inner] : make_float2(0.f, 0.f);
+      sm4[a * kTC + lane] = make_float4(u.h, v.x, u.l, v.y);
+    }
+  }
+  __syncthreads();
+  for (int i = warp; i < n; i += kWarps) {
+    const float4* r4 = T4 + (size_t)i * W;
+    const float2* r2 = T2 + (size_t)i * W;
+    df2 c{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    df ck{0.f, 0.f};
+    if (i >= P && i < n - P) {
+      const float4* xr = sm4 + (i - P) * kTC + lane;
+#pragma unroll
+      for (int t = 0; t < W; ++t) {
+        const float4 e = xr[t * kTC];
+        const float4 cf = __ldg(r4 + t);
+        df_fma2(c, make_float2(cf.x, cf.y), make_float2(cf.z, cf.w), make_float2(e.x, e.y), make_float2(e.z, e.w));
+        if (KIND == 1) df_fma(ck, __ldg(r2 + t), df{e.x, e.z});
+      }
+    } else {
+      const int a0 = max(0, i - P), a1 = min(n - 1, i + P);
+      for (int a = a0; a <= a1; ++a) {
+        const int t = a - i + P;
+        const float4 e = sm4[a * kTC + lane];
+        const float4 cf = __ldg(r4 + t);
+        df_fma2(c, make_float2(cf.x, cf.y), make_float2(cf.z, cf.w), make_float2(e.x, e.y), make_float2(e.z, e.w));
+        if (KIND == 1) df_fma(ck, __ldg(r2 + t), df{e.x, e.z});
+      }
+    }
+    if (!valid) continue;
+    const long long off = base + (long long)i * inner;
+    const df c1 = df_norm(df{c.h.x, c.l.x}), c2 = df_norm(df{c.h.y, c.l.y});
+    if (KIND == 0) {          // (M x, K x)
+      store_df(Uo, off, c1);
+      store_df(Vo, off, c2);
+    } else if (KIND == 1) {   // (M u, K u + M v)
+      store_df(Uo, off, c1);
+      store_df(Vo, off, df_add(df_norm(ck), c2));
+    } else {                  // gamma W u + nu M_t v
+      df a2 = c1, a3 = c2;
+      if (scale) {
+        a2 = df_scale(a2, s2);
+        a3 = df_scale(a3, s3);
+      }
+      store_df(Vo, off, df_add(a2, a3));
+    }
+  }
+}
+
+template <typename TIn, typename TOut, int KIND, int P>
+cudaError_t launch_pk(const TIn* U, const float2* V, const float4* T4, const float2* T2, double s2, double s3,
+                      float2* Uo, TOut* Vo, int n, long long inner, long long outer, cudaStream_t st) {
+  const long long Q = inner * outer;
+  if (Q <= 0) return cudaSuccess;
+  static bool attr_done = false;
+  if (!attr_done) {
+    const cudaError_t e = cudaFuncSetAttribute(k_band_pk<TIn, TOut, KIND, P>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               256 * kTC * (int)sizeof(float4));
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const size_t smem = (size_t)n * kTC * sizeof(float4);
+  if (smem > (size_t)256 * kTC * sizeof(float4)) return cudaErrorInvalidValue;
+  double entries = 0.0;
+  for (int i = 0; i < n; ++i) entries += (double)(std::min(n - 1, i + P) - std::max(0, i - P) + 1);
+  const int nprod = KIND == 1 ? 3 : 2;
+  const int nio = KIND == 0 ? 3 : KIND == 1 ? 4 : 3;
+  ProfScope ps("band_pair_df", 2.0 * entries * (double)Q * nprod, 8.0 * (double)Q * n * nio, st);
+  const float h2 = (float)s2, h3 = (float)s3;
+  const float2 c2 = make_float2(h2, (float)(s2 - (double)h2)), c3 = make_float2(h3, (float)(s3 - (double)h3));
+  const int scale = (s2 != 1.0 || s3 != 1.0) ? 1 : 0;
+  k_band_pk<TIn, TOut, KIND, P><<<(unsigned)((Q + kTC - 1) / kTC), kThreads, smem, st>>>(
+      U, V, T4, T2, c2, c3, Uo, Vo, n, inner, Q, scale);
+  return cudaGetLastError();
+}
+
 template <typename TIn, typename TOut, bool HAS_V, bool TWO_OUT, int P>
 cudaError_t launch_pair_p(const TIn* U, const float2* V, const float2* B1, const float2* B2, const float2* B3,
                           double s2, double s3, float2* Uo, TOut* Vo, int n, long long inner, long long outer,
@@ -282,6 +408,27 @@ cudaError_t launch_band_last_dfc(const float2* u, const float2* v, const float2*
                                  double nu, double* y, int n, long long inner, long long outer, int p,
                                  cudaStream_t st) {
 #define CALL(PP) launch_pair_p<float2, double, true, false, PP>(u, v, Mtb, Wb, Mtb, gamma, nu, nullptr, y, n, inner, outer, 0, st)
+  STFD_BAND_DISPATCH(p, CALL)
+#undef CALL
+}
+
+cudaError_t launch_band_first_pk(const double* x, const float4* MK, float2* Uo, float2* Vo, int n, long long inner,
+                                 long long outer, int p, cudaStream_t st) {
+#define CALL(PP) launch_pk<double, float2, 0, PP>(x, nullptr, MK, nullptr, 1.0, 1.0, Uo, Vo, n, inner, outer, st)
+  STFD_BAND_DISPATCH(p, CALL)
+#undef CALL
+}
+
+cudaError_t launch_band_mid_pk(const float2* u, const float2* v, const float4* MM, const float2* Kb, float2* Uo,
+                               float2* Vo, int n, long long inner, long long outer, int p, cudaStream_t st) {
+#define CALL(PP) launch_pk<float2, float2, 1, PP>(u, v, MM, Kb, 1.0, 1.0, Uo, Vo, n, inner, outer, st)
+  STFD_BAND_DISPATCH(p, CALL)
+#undef CALL
+}
+
+cudaError_t launch_band_last_pk(const float2* u, const float2* v, const float4* WMt, double gamma, double nu,
+                                double* y, int n, long long inner, long long outer, int p, cudaStream_t st) {
+#define CALL(PP) launch_pk<float2, double, 2, PP>(u, v, WMt, nullptr, gamma, nu, nullptr, y, n, inner, outer, st)
   STFD_BAND_DISPATCH(p, CALL)
 #undef CALL
 }
