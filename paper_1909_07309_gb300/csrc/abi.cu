@@ -1159,8 +1159,12 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
       // classical Gram-Schmidt twice: h = V^T w, w -= V h, h2 = V^T w, w -= V h2
       STFD_CU(launch_dot_multi(w->dV, j + 1, w->V[j + 1], N, w->partial, nb, st));
       STFD_CU(launch_reduce_partial(w->partial, j + 1, nb, dh, 0, st));
-      STFD_CU(launch_multi_axpy(w->V[j + 1], w->dV, dh, j + 1, N, -1.0, st));
-      STFD_CU(launch_dot_multi(w->dV, j + 1, w->V[j + 1], N, w->partial, nb, st));
+      if (j + 1 <= 4) {   // the first update fused with the second dot products
+        STFD_CU(launch_axpy_dot(w->V[j + 1], w->dV, dh, j + 1, N, w->partial, nb, st));
+      } else {
+        STFD_CU(launch_multi_axpy(w->V[j + 1], w->dV, dh, j + 1, N, -1.0, st));
+        STFD_CU(launch_dot_multi(w->dV, j + 1, w->V[j + 1], N, w->partial, nb, st));
+      }
       STFD_CU(launch_reduce_partial(w->partial, j + 1, nb, dh2, 0, st));
       // second update fused with ||w||^2 (the normalisation of w happens next iteration)
       STFD_CU(launch_axpy_norm(w->V[j + 1], w->dV, dh2, j + 1, N, -1.0, 0, w->partial, nb, st));

@@ -187,16 +187,23 @@ __global__ void k_reduce_partial(const double* __restrict__ partial, int m, int 
 }
 
 // w[k] += sign * sum_i h[i] V_i[k]: each thread owns 4 strided elements and
-// walks the vectors with the pointer and coefficient hoisted per vector.
+// walks the vectors with the pointer and signed coefficient hoisted per vector;
+// the update starts from w[k], one FP64 FMA per vector and element (the FP64
+// pipe, ~1/64 of the FP32 rate on GB300, is as close a bound as the memory).
 __global__ void __launch_bounds__(256)
 k_multi_axpy(double* __restrict__ w, const double* const* __restrict__ V, const double* __restrict__ h, int m,
              long long N, double sign) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; k0 < N; k0 += 4 * stride) {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long k = k0 + u * stride;
+      acc[u] = k < N ? w[k] : 0.0;
+    }
     for (int i = 0; i < m; ++i) {
       const double* vi = V[i];
-      const double hi = h[i];
+      const double hi = sign * h[i];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const long long k = k0 + u * stride;
@@ -206,8 +213,61 @@ k_multi_axpy(double* __restrict__ w, const double* const* __restrict__ V, const 
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const long long k = k0 + u * stride;
-      if (k < N) w[k] = fma(sign, acc[u], w[k]);
+      if (k < N) w[k] = acc[u];
     }
+  }
+}
+
+// w[k] -= sum_{i<C} h[i] V_i[k], and partial[block*C + i] = the block's share of
+// V_i . w (of the updated w): the first update of classical Gram-Schmidt fused
+// with the dot products of the second (one pass instead of two).
+template <int C>
+__global__ void __launch_bounds__(kDotThreads)
+k_axpy_dot(double* __restrict__ w, const double* const* __restrict__ V, const double* __restrict__ h, long long N,
+           double* __restrict__ partial) {
+  __shared__ double red[kDotThreads / 32];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const double* v[C];
+  double nh[C], d[C];
+#pragma unroll
+  for (int b = 0; b < C; ++b) {
+    v[b] = V[b];
+    nh[b] = -h[b];
+    d[b] = 0.0;
+  }
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; k + stride < N; k += 2 * stride) {
+    double wk[2], x[2][C];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      wk[u] = w[k + u * stride];
+#pragma unroll
+      for (int b = 0; b < C; ++b) x[u][b] = __ldg(v[b] + k + u * stride);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+#pragma unroll
+      for (int b = 0; b < C; ++b) wk[u] = fma(nh[b], x[u][b], wk[u]);
+      w[k + u * stride] = wk[u];
+#pragma unroll
+      for (int b = 0; b < C; ++b) d[b] = fma(x[u][b], wk[u], d[b]);
+    }
+  }
+  for (; k < N; k += stride) {
+    double wk = w[k], x[C];
+#pragma unroll
+    for (int b = 0; b < C; ++b) {
+      x[b] = __ldg(v[b] + k);
+      wk = fma(nh[b], x[b], wk);
+    }
+    w[k] = wk;
+#pragma unroll
+    for (int b = 0; b < C; ++b) d[b] = fma(x[b], wk, d[b]);
+  }
+#pragma unroll
+  for (int b = 0; b < C; ++b) {
+    const double t = block_sum(d[b], red);
+    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * C + b] = t;
   }
 }
 
@@ -220,10 +280,15 @@ k_axpy_norm(double* __restrict__ w, const double* const* __restrict__ V, const d
   const long long stride = (long long)gridDim.x * blockDim.x;
   double sq = 0.0;
   for (long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; k0 < N; k0 += 4 * stride) {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long k = k0 + u * stride;
+      acc[u] = (set || k >= N) ? 0.0 : w[k];
+    }
     for (int i = 0; i < m; ++i) {
       const double* vi = V[i];
-      const double hi = h[i];
+      const double hi = sign * h[i];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const long long k = k0 + u * stride;
@@ -234,9 +299,8 @@ k_axpy_norm(double* __restrict__ w, const double* const* __restrict__ V, const d
     for (int u = 0; u < 4; ++u) {
       const long long k = k0 + u * stride;
       if (k < N) {
-        const double v = set ? sign * acc[u] : fma(sign, acc[u], w[k]);
-        w[k] = v;
-        sq = fma(v, v, sq);
+        w[k] = acc[u];
+        if (partial) sq = fma(acc[u], acc[u], sq);
       }
     }
   }
@@ -369,6 +433,19 @@ cudaError_t launch_multi_axpy(double* w, const double* const* V, const double* h
                               long long N, double sign, cudaStream_t st) {
   ProfScope ps("gmres_multi_axpy", 2.0 * N * m, 8.0 * N * (m + 2), st);
   k_multi_axpy<<<grid_for((N + 3) / 4, 256), 256, 0, st>>>(w, V, h, m, N, sign);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_dot(double* w, const double* const* V, const double* h, int m, long long N,
+                            double* partial, int nblocks, cudaStream_t st) {
+  if (m < 1 || m > 4) return cudaErrorInvalidValue;
+  ProfScope ps("gmres_axpy_dot", 4.0 * N * m, 8.0 * N * (m + 2), st);
+  switch (m) {
+    case 1: k_axpy_dot<1><<<nblocks, kDotThreads, 0, st>>>(w, V, h, N, partial); break;
+    case 2: k_axpy_dot<2><<<nblocks, kDotThreads, 0, st>>>(w, V, h, N, partial); break;
+    case 3: k_axpy_dot<3><<<nblocks, kDotThreads, 0, st>>>(w, V, h, N, partial); break;
+    default: k_axpy_dot<4><<<nblocks, kDotThreads, 0, st>>>(w, V, h, N, partial); break;
+  }
   return cudaGetLastError();
 }
 

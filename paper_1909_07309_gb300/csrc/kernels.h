@@ -60,6 +60,10 @@ cudaError_t launch_reduce_partial(const double* partial, int m, int nblocks, dou
 // w[k] += sign * sum_i h[i] V_i[k]
 cudaError_t launch_multi_axpy(double* w, const double* const* V, const double* h, int m,
                               long long N, double sign, cudaStream_t st);
+// w -= sum_{i<m} h[i] V_i and partial[b*m + i] = block b's share of V_i . w (the
+// updated w), for 1 <= m <= 4 (cudaErrorInvalidValue otherwise).
+cudaError_t launch_axpy_dot(double* w, const double* const* V, const double* h, int m, long long N,
+                            double* partial, int nblocks, cudaStream_t st);
 // y[k] = x[k] / *den, or x[k] / sqrt(*den) if sqrt_den (den on the device;
 // a non-positive divisor leaves x unscaled)
 cudaError_t launch_scale_by_inverse(double* y, const double* x, const double* den, long long N,
