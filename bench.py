@@ -33,10 +33,10 @@ METRIC = "fd_apply dofs/s and GMRES time-to-1e-8 residual, FP64 vs TF32/BF16-pre
 UNIT = "dofs/s"
 L2_BYTES = 129 * 2 ** 20
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/,
-# mean over the 8 launches of one fd_apply at the workload); None once the
-# kernel changes until it is captured again.
-NCU_TRAFFIC = {"kernel": "fd_mode_ozaki", "bytes_per_launch": 237410336}
+# DRAM bytes per launch from one ncu capture at the workload (profiles/): the
+# mean over the 8 mode products of one fd_apply, and over the 4 band passes of
+# one st_matvec; None once a kernel changes until it is captured again.
+NCU_TRAFFIC = {"fd_mode_ozaki": 237515552, "band_pair_df": None}
 
 
 def measured_peaks():
@@ -537,7 +537,7 @@ def main():
     mhz = clocks.get("sm_mhz") or 2070.0
     per_launch_s = top["ms"] * 1e-3 / top["launches"]
     achieved = top["flops"] / top["launches"] / per_launch_s
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["kernel"] == top["name"] else None
+    traffic = NCU_TRAFFIC.get(top["name"])
     peaks, peak_src = measured_peaks()
     if top["name"] == "fd_mode_ozaki":
         # 21 exact BF16 digit-pair GEMMs need ~26 us of tensor time per launch at the

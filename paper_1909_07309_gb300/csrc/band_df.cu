@@ -232,6 +232,7 @@ k_band_pk(const TIn* __restrict__ U, const float2* __restrict__ V, const float4*
           const float2* __restrict__ T2, float2 s2, float2 s3, float2* __restrict__ Uo, TOut* __restrict__ Vo, int n,
           long long inner, long long Q, int scale) {
   constexpr int W = 2 * P + 1;
+  constexpr int kLd = kTC + 1;   // tile row stride in float4 (the padding keeps the transposed stores conflict-free)
   extern __shared__ float4 sm4[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long q = (long long)blockIdx.x * kTC + lane;
@@ -241,13 +242,26 @@ k_band_pk(const TIn* __restrict__ U, const float2* __restrict__ V, const float4*
     const long long o = q / inner;
     base = o * (long long)n * inner + (q - o * inner);
   }
-  for (int a = warp; a < n; a += kWarps) {
-    const df u = valid ? load_df<TIn>(U, base + (long long)a * inner) : df{0.f, 0.f};
-    if (KIND == 0) {
-      sm4[a * kTC + lane] = make_float4(u.h, u.h, u.l, u.l);
-    } else {
-      const float2 v = valid ? V[base + (long long)a * inner] : make_float2(0.f, 0.f);
-      sm4[a * kTC + lane] = make_float4(u.h, v.x, u.l, v.y);
+  if (KIND == 0 && inner == 1) {
+    // the CTA's fibres are consecutive rows of length n: one contiguous block,
+    // read with consecutive threads on consecutive words and transposed into the tile
+    const long long q0 = (long long)blockIdx.x * kTC;
+    const int nf = (int)min((long long)kTC, Q - q0);
+    const TIn* src = U + q0 * n;
+    for (int e = threadIdx.x; e < kTC * n; e += kThreads) {
+      const int f = e / n, a = e - f * n;
+      const df u = f < nf ? load_df<TIn>(src, e) : df{0.f, 0.f};
+      sm4[a * kLd + f] = make_float4(u.h, u.h, u.l, u.l);
+    }
+  } else {
+    for (int a = warp; a < n; a += kWarps) {
+      const df u = valid ? load_df<TIn>(U, base + (long long)a * inner) : df{0.f, 0.f};
+      if (KIND == 0) {
+        sm4[a * kLd + lane] = make_float4(u.h, u.h, u.l, u.l);
+      } else {
+        const float2 v = valid ? V[base + (long long)a * inner] : make_float2(0.f, 0.f);
+        sm4[a * kLd + lane] = make_float4(u.h, v.x, u.l, v.y);
+      }
     }
   }
   __syncthreads();
@@ -257,10 +271,10 @@ k_band_pk(const TIn* __restrict__ U, const float2* __restrict__ V, const float4*
     df2 c{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     df ck{0.f, 0.f};
     if (i >= P && i < n - P) {
-      const float4* xr = sm4 + (i - P) * kTC + lane;
+      const float4* xr = sm4 + (i - P) * kLd + lane;
 #pragma unroll
       for (int t = 0; t < W; ++t) {
-        const float4 e = xr[t * kTC];
+        const float4 e = xr[t * kLd];
         const float4 cf = __ldg(r4 + t);
         df_fma2(c, make_float2(cf.x, cf.y), make_float2(cf.z, cf.w), make_float2(e.x, e.y), make_float2(e.z, e.w));
         if (KIND == 1) df_fma(ck, __ldg(r2 + t), df{e.x, e.z});
@@ -269,7 +283,7 @@ k_band_pk(const TIn* __restrict__ U, const float2* __restrict__ V, const float4*
       const int a0 = max(0, i - P), a1 = min(n - 1, i + P);
       for (int a = a0; a <= a1; ++a) {
         const int t = a - i + P;
-        const float4 e = sm4[a * kTC + lane];
+        const float4 e = sm4[a * kLd + lane];
         const float4 cf = __ldg(r4 + t);
         df_fma2(c, make_float2(cf.x, cf.y), make_float2(cf.z, cf.w), make_float2(e.x, e.y), make_float2(e.z, e.w));
         if (KIND == 1) df_fma(ck, __ldg(r2 + t), df{e.x, e.z});
@@ -304,12 +318,12 @@ cudaError_t launch_pk(const TIn* U, const float2* V, const float4* T4, const flo
   if (!attr_done) {
     const cudaError_t e = cudaFuncSetAttribute(k_band_pk<TIn, TOut, KIND, P>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               256 * kTC * (int)sizeof(float4));
+                                               256 * (kTC + 1) * (int)sizeof(float4));
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  const size_t smem = (size_t)n * kTC * sizeof(float4);
-  if (smem > (size_t)256 * kTC * sizeof(float4)) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)n * (kTC + 1) * sizeof(float4);
+  if (smem > (size_t)256 * (kTC + 1) * sizeof(float4)) return cudaErrorInvalidValue;
   double entries = 0.0;
   for (int i = 0; i < n; ++i) entries += (double)(std::min(n - 1, i + P) - std::max(0, i - P) + 1);
   const int nprod = KIND == 1 ? 3 : 2;
