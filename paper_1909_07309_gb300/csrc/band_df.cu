@@ -12,6 +12,7 @@
 
 #include <algorithm>
 
+#include "df.cuh"
 #include "kernels.h"
 #include "profile.h"
 
@@ -210,6 +211,14 @@ struct df2 {
   float2 h, l;
 };
 
+// FP64 loads of the paired kernel convert with integer and FP32 instructions
+// (df.cuh) rather than on the FP64 pipe.
+__device__ __forceinline__ df ld_pk(const double* p, long long i) {
+  const dfa::df v = dfa::from_double(p[i]);
+  return df{v.h, v.l};
+}
+__device__ __forceinline__ df ld_pk(const float2* p, long long i) { return to_df(p[i]); }
+
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b (b times -1 is exact, one rounding)
   return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
 }
@@ -250,12 +259,12 @@ k_band_pk(const TIn* __restrict__ U, const float2* __restrict__ V, const float4*
     const TIn* src = U + q0 * n;
     for (int e = threadIdx.x; e < kTC * n; e += kThreads) {
       const int f = e / n, a = e - f * n;
-      const df u = f < nf ? load_df<TIn>(src, e) : df{0.f, 0.f};
+      const df u = f < nf ? ld_pk(src, e) : df{0.f, 0.f};
       sm4[a * kLd + f] = make_float4(u.h, u.h, u.l, u.l);
     }
   } else {
     for (int a = warp; a < n; a += kWarps) {
-      const df u = valid ? load_df<TIn>(U, base + (long long)a * inner) : df{0.f, 0.f};
+      const df u = valid ? ld_pk(U, base + (long long)a * inner) : df{0.f, 0.f};
       if (KIND == 0) {
         sm4[a * kLd + lane] = make_float4(u.h, u.h, u.l, u.l);
       } else {
