@@ -925,10 +925,11 @@ int matvec_one_df(const stfd_op* A, const double* x, double* y, int trans, cudaS
     float2* vo = (l % 2 == 0) ? T[1] : T[3];
     const int bw = std::max(A->bwM[l], A->bwK[l]);
     if (A->banded) {
+      // rotated layouts: every pass reads its fibres contiguous and writes transposed
       if (l == 0) {
-        STFD_CU(launch_band_first_pk(x, A->MK4[l], uo, vo, nl, inner, outer, A->pb[l], st));
+        STFD_CU(launch_band_first_pk(x, A->MK4[l], uo, vo, nl, 1, A->N / nl, A->pb[l], 1, st));
       } else {
-        STFD_CU(launch_band_mid_pk(u, v, A->MM4[l], A->Kb[l], uo, vo, nl, inner, outer, A->pb[l], st));
+        STFD_CU(launch_band_mid_pk(u, v, A->MM4[l], A->Kb[l], uo, vo, nl, 1, A->N / nl, A->pb[l], 1, st));
       }
     } else if (l == 0) {
       STFD_CU(launch_band_first_df(x, A->JM2[l], A->JK2[l], uo, vo, nl, inner, outer, bw, st));
@@ -941,7 +942,8 @@ int matvec_one_df(const stfd_op* A, const double* x, double* y, int trans, cudaS
   }
   const int nt = A->n[d];
   if (A->banded) {
-    STFD_CU(launch_band_last_pk(u, v, trans ? A->WTMt4 : A->WMt4, A->gamma, A->nu, y, nt, inner, 1, A->pb[d], st));
+    STFD_CU(launch_band_last_pk(u, v, trans ? A->WTMt4 : A->WMt4, A->gamma, A->nu, y, nt, 1, A->N / nt, A->pb[d], 1,
+                                st));
   } else {
     STFD_CU(launch_band_last_df(u, v, trans ? A->JWT2 : A->JW2, A->gamma, A->JMt2, A->nu, y, nt, inner, 1, std::max(A->bwW, A->bwMt), st));
   }

@@ -239,7 +239,7 @@ template <typename TIn, typename TOut, int KIND, int P>
 __global__ void __launch_bounds__(kThreads)
 k_band_pk(const TIn* __restrict__ U, const float2* __restrict__ V, const float4* __restrict__ T4,
           const float2* __restrict__ T2, float2 s2, float2 s3, float2* __restrict__ Uo, TOut* __restrict__ Vo, int n,
-          long long inner, long long Q, int scale) {
+          long long inner, long long Q, int scale, int rot) {
   constexpr int W = 2 * P + 1;
   constexpr int kLd = kTC + 1;   // tile row stride in float4 (the padding keeps the transposed stores conflict-free)
   extern __shared__ float4 sm4[];
@@ -251,16 +251,22 @@ k_band_pk(const TIn* __restrict__ U, const float2* __restrict__ V, const float4*
     const long long o = q / inner;
     base = o * (long long)n * inner + (q - o * inner);
   }
-  if (KIND == 0 && inner == 1) {
+  if (rot || inner == 1) {
     // the CTA's fibres are consecutive rows of length n: one contiguous block,
     // read with consecutive threads on consecutive words and transposed into the tile
     const long long q0 = (long long)blockIdx.x * kTC;
     const int nf = (int)min((long long)kTC, Q - q0);
     const TIn* src = U + q0 * n;
+    const float2* srcv = KIND == 0 ? nullptr : V + q0 * n;
     for (int e = threadIdx.x; e < kTC * n; e += kThreads) {
       const int f = e / n, a = e - f * n;
       const df u = f < nf ? ld_pk(src, e) : df{0.f, 0.f};
-      sm4[a * kLd + f] = make_float4(u.h, u.h, u.l, u.l);
+      if (KIND == 0) {
+        sm4[a * kLd + f] = make_float4(u.h, u.h, u.l, u.l);
+      } else {
+        const float2 v = f < nf ? srcv[e] : make_float2(0.f, 0.f);
+        sm4[a * kLd + f] = make_float4(u.h, v.x, u.l, v.y);
+      }
     }
   } else {
     for (int a = warp; a < n; a += kWarps) {
@@ -299,7 +305,9 @@ k_band_pk(const TIn* __restrict__ U, const float2* __restrict__ V, const float4*
       }
     }
     if (!valid) continue;
-    const long long off = base + (long long)i * inner;
+    // rotated layout: entry i of fibre q goes to i Q + q, so that the direction
+    // just applied becomes the slowest index and the next one the fastest
+    const long long off = rot ? q + (long long)i * Q : base + (long long)i * inner;
     const df c1 = df_norm(df{c.h.x, c.l.x}), c2 = df_norm(df{c.h.y, c.l.y});
     if (KIND == 0) {          // (M x, K x)
       store_df(Uo, off, c1);
@@ -320,7 +328,7 @@ k_band_pk(const TIn* __restrict__ U, const float2* __restrict__ V, const float4*
 
 template <typename TIn, typename TOut, int KIND, int P>
 cudaError_t launch_pk(const TIn* U, const float2* V, const float4* T4, const float2* T2, double s2, double s3,
-                      float2* Uo, TOut* Vo, int n, long long inner, long long outer, cudaStream_t st) {
+                      float2* Uo, TOut* Vo, int n, long long inner, long long outer, int rot, cudaStream_t st) {
   const long long Q = inner * outer;
   if (Q <= 0) return cudaSuccess;
   static bool attr_done = false;
@@ -342,7 +350,7 @@ cudaError_t launch_pk(const TIn* U, const float2* V, const float4* T4, const flo
   const float2 c2 = make_float2(h2, (float)(s2 - (double)h2)), c3 = make_float2(h3, (float)(s3 - (double)h3));
   const int scale = (s2 != 1.0 || s3 != 1.0) ? 1 : 0;
   k_band_pk<TIn, TOut, KIND, P><<<(unsigned)((Q + kTC - 1) / kTC), kThreads, smem, st>>>(
-      U, V, T4, T2, c2, c3, Uo, Vo, n, inner, Q, scale);
+      U, V, T4, T2, c2, c3, Uo, Vo, n, inner, Q, scale, rot);
   return cudaGetLastError();
 }
 
@@ -436,22 +444,22 @@ cudaError_t launch_band_last_dfc(const float2* u, const float2* v, const float2*
 }
 
 cudaError_t launch_band_first_pk(const double* x, const float4* MK, float2* Uo, float2* Vo, int n, long long inner,
-                                 long long outer, int p, cudaStream_t st) {
-#define CALL(PP) launch_pk<double, float2, 0, PP>(x, nullptr, MK, nullptr, 1.0, 1.0, Uo, Vo, n, inner, outer, st)
+                                 long long outer, int p, int rot, cudaStream_t st) {
+#define CALL(PP) launch_pk<double, float2, 0, PP>(x, nullptr, MK, nullptr, 1.0, 1.0, Uo, Vo, n, inner, outer, rot, st)
   STFD_BAND_DISPATCH(p, CALL)
 #undef CALL
 }
 
 cudaError_t launch_band_mid_pk(const float2* u, const float2* v, const float4* MM, const float2* Kb, float2* Uo,
-                               float2* Vo, int n, long long inner, long long outer, int p, cudaStream_t st) {
-#define CALL(PP) launch_pk<float2, float2, 1, PP>(u, v, MM, Kb, 1.0, 1.0, Uo, Vo, n, inner, outer, st)
+                               float2* Vo, int n, long long inner, long long outer, int p, int rot, cudaStream_t st) {
+#define CALL(PP) launch_pk<float2, float2, 1, PP>(u, v, MM, Kb, 1.0, 1.0, Uo, Vo, n, inner, outer, rot, st)
   STFD_BAND_DISPATCH(p, CALL)
 #undef CALL
 }
 
 cudaError_t launch_band_last_pk(const float2* u, const float2* v, const float4* WMt, double gamma, double nu,
-                                double* y, int n, long long inner, long long outer, int p, cudaStream_t st) {
-#define CALL(PP) launch_pk<float2, double, 2, PP>(u, v, WMt, nullptr, gamma, nu, nullptr, y, n, inner, outer, st)
+                                double* y, int n, long long inner, long long outer, int p, int rot, cudaStream_t st) {
+#define CALL(PP) launch_pk<float2, double, 2, PP>(u, v, WMt, nullptr, gamma, nu, nullptr, y, n, inner, outer, rot, st)
   STFD_BAND_DISPATCH(p, CALL)
 #undef CALL
 }

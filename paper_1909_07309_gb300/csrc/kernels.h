@@ -102,13 +102,17 @@ cudaError_t launch_band_last_dfc(const float2* u, const float2* v, const float2*
 // The same three passes with two accumulation chains issued together on the
 // paired FP32 instructions; tables of (hi_1, hi_2, lo_1, lo_2) per band tap:
 // first direction (M, K), middle directions (M, M) with K from the band table Kb,
-// time (W_t or W_t^T, M_t). Results equal those of the _dfc launchers.
+// time (W_t or W_t^T, M_t). Results equal those of the _dfc launchers. With
+// rot = 1 the inputs hold the direction fastest (fibres contiguous, inner = 1)
+// and entry i of fibre q is written to i Q + q (Q = inner * outer fibres): each
+// pass leaves the next direction fastest, and after the time pass the layout
+// is the original one again.
 cudaError_t launch_band_first_pk(const double* x, const float4* MK, float2* Uo, float2* Vo, int n, long long inner,
-                                 long long outer, int p, cudaStream_t st);
+                                 long long outer, int p, int rot, cudaStream_t st);
 cudaError_t launch_band_mid_pk(const float2* u, const float2* v, const float4* MM, const float2* Kb, float2* Uo,
-                               float2* Vo, int n, long long inner, long long outer, int p, cudaStream_t st);
+                               float2* Vo, int n, long long inner, long long outer, int p, int rot, cudaStream_t st);
 cudaError_t launch_band_last_pk(const float2* u, const float2* v, const float4* WMt, double gamma, double nu,
-                                double* y, int n, long long inner, long long outer, int p, cudaStream_t st);
+                                double* y, int n, long long inner, long long outer, int p, int rot, cudaStream_t st);
 
 // Double-float Algorithm 1 (fd_df.cu): dense mode product with (hi, lo) row-major
 // factor J, X FP64 or float2, Y float2 or FP64 (not both FP64); Step 3 in place on
