@@ -258,14 +258,22 @@ k_band_pk(const TIn* __restrict__ U, const float2* __restrict__ V, const float4*
     const int nf = (int)min((long long)kTC, Q - q0);
     const TIn* src = U + q0 * n;
     const float2* srcv = KIND == 0 ? nullptr : V + q0 * n;
+    // (f, a) of element e = f n + a, advanced by kThreads without a division per element
+    const int df_step = kThreads / n, da_step = kThreads - df_step * n;
+    int f = threadIdx.x / n, a = threadIdx.x - f * n;
     for (int e = threadIdx.x; e < kTC * n; e += kThreads) {
-      const int f = e / n, a = e - f * n;
       const df u = f < nf ? ld_pk(src, e) : df{0.f, 0.f};
       if (KIND == 0) {
         sm4[a * kLd + f] = make_float4(u.h, u.h, u.l, u.l);
       } else {
         const float2 v = f < nf ? srcv[e] : make_float2(0.f, 0.f);
         sm4[a * kLd + f] = make_float4(u.h, v.x, u.l, v.y);
+      }
+      f += df_step;
+      a += da_step;
+      if (a >= n) {
+        a -= n;
+        ++f;
       }
     }
   } else {
