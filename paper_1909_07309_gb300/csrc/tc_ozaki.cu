@@ -62,6 +62,10 @@ struct OzArgs {
   long long inner, Q, ntiles;
 };
 
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b (b times -1 is exact, one rounding)
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
 __device__ __forceinline__ float pow2f(int e) {   // 2^e for e in [-126, 127]
   return __int_as_float((e + 127) << 23);
 }
@@ -361,32 +365,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
 #pragma unroll
       for (int c = 0; c < kDig; ++c) tc::tmem_ld4_async(lane_base + (uint32_t)(c * npad + 4 * c4), Tr[c]);
       tc::tmem_wait_ld4x6(Tr);
+      // two output columns at a time on the paired FP32 instructions (per
+      // column the scalar steps: the results do not depend on the pairing)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int i = 4 * c4 + j;
+      for (int j = 0; j < 4; j += 2) {
+        const int i = 4 * c4 + j;   // i + 1 < npad: sv is padded
         if (i >= n || r >= rows) continue;
-        float T[kDig];
+        float2 T[kDig];
 #pragma unroll
-        for (int c = 0; c < kDig; ++c) T[c] = __uint_as_float(Tr[c][j]);
+        for (int c = 0; c < kDig; ++c) T[c] = make_float2(__uint_as_float(Tr[c][j]), __uint_as_float(Tr[c][j + 1]));
         // every T_c is exact; two-sums fold in the two leading diagonals below
         // T_0, the trailing three (below 2^-23 of the total) are summed in FP32
-        float hi = T[0], lo = 0.f;
+        float2 hi = T[0], lo = make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 1; c < 3; ++c) {
-          const float sm = hi + T[c], bp = sm - hi;
-          lo += (hi - (sm - bp)) + (T[c] - bp);
+          const float2 sm = __fadd2_rn(hi, T[c]), bp = sub2(sm, hi);
+          lo = __fadd2_rn(lo, __fadd2_rn(sub2(hi, sub2(sm, bp)), sub2(T[c], bp)));
           hi = sm;
         }
-        lo += (T[3] + T[4]) + T[5];
-        const dfa::df sres = dfa::norm(dfa::df{hi, lo});
-        int sc = urow_e + sv[i];
-        sc = max(-250, min(250, sc));
-        const float f1 = pow2f(sc >> 1), f2 = pow2f(sc - (sc >> 1));
-        const dfa::df y{sres.h * f1 * f2, sres.l * f1 * f2};
-        if (inner == 1) {
-          StoreOut<TOut>::put(reinterpret_cast<TOut*>(stage), (long long)r * n + i, y);
-        } else {
-          StoreOut<TOut>::put(static_cast<TOut*>(args.Y), base + (long long)i * inner, y);
+        lo = __fadd2_rn(lo, __fadd2_rn(__fadd2_rn(T[3], T[4]), T[5]));
+        const float2 nh = __fadd2_rn(hi, lo), nl = sub2(lo, sub2(nh, hi));   // normalised pair
+        int sc0 = urow_e + sv[i], sc1 = urow_e + sv[i + 1];
+        sc0 = max(-250, min(250, sc0));
+        sc1 = max(-250, min(250, sc1));
+        const float2 f1 = make_float2(pow2f(sc0 >> 1), pow2f(sc1 >> 1));
+        const float2 f2 = make_float2(pow2f(sc0 - (sc0 >> 1)), pow2f(sc1 - (sc1 >> 1)));
+        const float2 yh = __fmul2_rn(__fmul2_rn(nh, f1), f2), yl = __fmul2_rn(__fmul2_rn(nl, f1), f2);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          if (i + e >= n) break;
+          const dfa::df y{e == 0 ? yh.x : yh.y, e == 0 ? yl.x : yl.y};
+          if (inner == 1) {
+            StoreOut<TOut>::put(reinterpret_cast<TOut*>(stage), (long long)r * n + i + e, y);
+          } else {
+            StoreOut<TOut>::put(static_cast<TOut*>(args.Y), base + (long long)(i + e) * inner, y);
+          }
         }
       }
     }
