@@ -15,6 +15,7 @@
 #include "df.cuh"
 #include "kernels.h"
 #include "profile.h"
+#include "tc_common.cuh"
 
 namespace stfd {
 namespace {
@@ -251,6 +252,7 @@ k_band_pk(const TIn* __restrict__ U, const float2* __restrict__ V, const float4*
     const long long o = q / inner;
     base = o * (long long)n * inner + (q - o * inner);
   }
+  tc::grid_dependency_wait();   // programmatic dependent launch: inputs from here on
   if (rot || inner == 1) {
     // the CTA's fibres are consecutive rows of length n: one contiguous block,
     // read with consecutive threads on consecutive words and transposed into the tile
@@ -288,6 +290,7 @@ k_band_pk(const TIn* __restrict__ U, const float2* __restrict__ V, const float4*
     }
   }
   __syncthreads();
+  tc::grid_launch_dependents();
   for (int i = warp; i < n; i += kWarps) {
     const float4* r4 = T4 + (size_t)i * W;
     const float2* r2 = T2 + (size_t)i * W;
@@ -357,9 +360,19 @@ cudaError_t launch_pk(const TIn* U, const float2* V, const float4* T4, const flo
   const float h2 = (float)s2, h3 = (float)s3;
   const float2 c2 = make_float2(h2, (float)(s2 - (double)h2)), c3 = make_float2(h3, (float)(s3 - (double)h3));
   const int scale = (s2 != 1.0 || s3 != 1.0) ? 1 : 0;
-  k_band_pk<TIn, TOut, KIND, P><<<(unsigned)((Q + kTC - 1) / kTC), kThreads, smem, st>>>(
-      U, V, T4, T2, c2, c3, Uo, Vo, n, inner, Q, scale, rot);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((Q + kTC - 1) / kTC));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_band_pk<TIn, TOut, KIND, P>, U, V, T4, T2, c2, c3, Uo, Vo, n,
+                                           inner, Q, scale, rot);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename TIn, typename TOut, bool HAS_V, bool TWO_OUT, int P>

@@ -153,6 +153,14 @@ __device__ __forceinline__ void tmem_wait_ld4x6(uint32_t (&r)[6][4]) {
     asm volatile("" : "+r"(r[c][0]), "+r"(r[c][1]), "+r"(r[c][2]), "+r"(r[c][3]) : : "memory");
 }
 
+// Programmatic dependent launch: wait for the preceding kernel in the stream
+// (its completion and memory) before the first access of data it may write or
+// read, and let the following kernel start launching.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Bulk (TMA, untiled) copies. Both addresses 16-byte aligned, size a multiple of 16.
 // global -> shared, completing `bytes` of the mbarrier's transaction count
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar_addr, uint32_t bytes) {

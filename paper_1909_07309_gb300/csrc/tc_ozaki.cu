@@ -218,6 +218,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   // consecutive addresses), so entries go straight to registers and the next
   // tile's are fetched while the MMAs run. Mode 1 (inner == 1): a row is
   // contiguous, so the tile is a contiguous block, copied through shared memory.
+  // everything above (factor planes, TMEM, barriers) overlaps the end of the
+  // preceding kernel; its output is read, and this kernel's written, only from here
+  tc::grid_dependency_wait();
   if (inner != 1 && (long long)blockIdx.x < args.ntiles) load_raw<KC>(Xw, blockIdx.x, drow, dp, n, inner, Q, raw);
   // padding column pairs 2 KC .. npad / 2 - 1 (KC = 18): zero digits, written once
   // here and again per tile where the staging area overwrites them (mode 1)
@@ -231,6 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   zero_tail();
 
   for (long long tile = blockIdx.x; tile < args.ntiles; tile += gridDim.x) {
+    if (tile + gridDim.x >= args.ntiles) tc::grid_launch_dependents();   // this CTA's last tile
     const long long q0 = tile * kTile;
     const int rows = (int)min((long long)kTile, Q - q0);
     const long long q = q0 + r;
@@ -462,8 +466,19 @@ cudaError_t launch_oz(const TIn* X, TOut* Y, const unsigned char* B, const int* 
   OzArgs a{X, Y, B, v, n, (n + 15) / 16 * 16, inner, Q, ntiles};
   ProfScope ps("fd_mode_ozaki", 2.0 * (double)Q * n * n, 8.0 * (double)Q * n * 2, st);
   // 227 KB requested so that exactly one CTA (which owns all 512 TMEM columns) fits per SM
-  k_tc_ozaki<TIn, TOut, KC><<<(unsigned)grid, kThreads, 227 * 1024, st>>>(a);
-  return cudaGetLastError();
+  // programmatic dependent launch: the next kernel's prologue may overlap this one's tail
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 227 * 1024;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_ozaki<TIn, TOut, KC>, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename TIn, typename TOut>
