@@ -11,6 +11,7 @@
 #include "df.cuh"
 #include "kernels.h"
 #include "profile.h"
+#include "tc_common.cuh"
 
 namespace stfd {
 namespace {
@@ -76,6 +77,8 @@ k_mode_df(const TIn* __restrict__ X, const float2* __restrict__ J, TOut* __restr
 
 // Step 3 per spatial index k (see k_arrowhead in kernels.cu for the algebra).
 __global__ void k_arrowhead_df(float2* __restrict__ X, ArrowDF p) {
+  tc::grid_dependency_wait();   // programmatic dependent launch
+  tc::grid_launch_dependents();
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < p.Ns;
        k += (long long)gridDim.x * blockDim.x)
     arrowhead_df_point(X, p, k);
@@ -143,8 +146,7 @@ cudaError_t launch_arrowhead_df(float2* X, int d, int n1, int n2, int nt, int n_
   ProfScope ps("arrowhead_df", (double)Ns * (10.0 * n_pairs + 4.0), 16.0 * (double)Ns * nt, st);
   const long long want = (Ns + 255) / 256;
   const int grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)sms() * 8));
-  k_arrowhead_df<<<grid, 256, 0, st>>>(X, p);
-  return cudaGetLastError();
+  return tc::launch_pdl(k_arrowhead_df, dim3(grid), dim3(256), 0, st, X, p);
 }
 
 }  // namespace stfd

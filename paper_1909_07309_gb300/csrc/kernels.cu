@@ -327,7 +327,7 @@ k_sub_norm(double* __restrict__ out, const double* __restrict__ f, const double*
 }
 
 // y = x / den (or x / sqrt(den)); leaves x unscaled when the divisor is not positive.
-__global__ void k_scale_by_inverse(double* __restrict__ y, const double* __restrict__ x,
+__global__ void k_scale_by_inverse(double* y, const double* x,   // may be the same vector
                                    const double* __restrict__ den, long long N, int sqrt_den) {
   const double dv = sqrt_den ? sqrt(den[0]) : den[0];
   const double inv = dv > 0.0 ? 1.0 / dv : 1.0;

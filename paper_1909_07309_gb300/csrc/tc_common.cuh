@@ -4,7 +4,10 @@
 // a "memory" clobber so the compiler cannot move shared-memory stores across
 // the proxy fences.
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstdint>
+#include <utility>
 
 namespace stfd {
 namespace tc {
@@ -159,6 +162,26 @@ __device__ __forceinline__ void tmem_wait_ld4x6(uint32_t (&r)[6][4]) {
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Host: launch with the programmatic-stream-serialisation attribute, so that
+// the kernel (which calls grid_dependency_wait before touching global data)
+// may be scheduled while the preceding kernel in the stream finishes.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // Bulk (TMA, untiled) copies. Both addresses 16-byte aligned, size a multiple of 16.
