@@ -419,14 +419,15 @@ def main():
     value = job_throughput(N, args.steps, world, ms)
 
     # ---- end to end through the public API: every step copies its right-hand side
-    # from pinned host memory, solves, and copies the solution back. The copies run
-    # on a second stream: the upload of step k+1 and the download of step k-1
-    # overlap the solve of step k (double-buffered device vectors).
+    # from pinned host memory, solves, and copies the solution back. Uploads and
+    # downloads run on two more streams (one per direction, so that they use the
+    # link both ways at once): the upload of step k+1 and the download of step
+    # k-1 overlap the solve of step k (double-buffered device vectors).
     f_host = [torch.from_numpy(f_np).pin_memory() for _ in range(2)]
     u_host = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(2)]
     f_dev = [torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(2)]
     u_dev = [torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(2)]
-    copy_s = torch.cuda.Stream()
+    up_s, down_s = torch.cuda.Stream(), torch.cuda.Stream()
     comp_s = torch.cuda.current_stream()
     h2d = [torch.cuda.Event() for _ in range(2)]
     solved = [torch.cuda.Event() for _ in range(2)]
@@ -434,30 +435,31 @@ def main():
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    with torch.cuda.stream(copy_s):
+    with torch.cuda.stream(up_s):
         f_dev[0].copy_(f_host[0], non_blocking=True)
-    h2d[0].record(copy_s)
+    h2d[0].record(up_s)
     for k in range(args.steps):
         b = k % 2
         comp_s.wait_event(h2d[b])
         if k + 1 < args.steps:
             nb = (k + 1) % 2           # read by solve k-1, which has returned
-            with torch.cuda.stream(copy_s):
+            with torch.cuda.stream(up_s):
                 f_dev[nb].copy_(f_host[nb], non_blocking=True)
-            h2d[nb].record(copy_s)
+            h2d[nb].record(up_s)
         if k >= 2:
             comp_s.wait_event(d2h[b])  # u_dev[b] still being downloaded for step k-2
         A.gmres(P, f_dev[b], u_dev[b], tol=1e-8, restart=args.restart, stream=comp_s.cuda_stream)
         solved[b].record(comp_s)
-        copy_s.wait_event(solved[b])
-        with torch.cuda.stream(copy_s):
+        down_s.wait_event(solved[b])
+        with torch.cuda.stream(down_s):
             u_host[b].copy_(u_dev[b], non_blocking=True)
-        d2h[b].record(copy_s)
+        d2h[b].record(down_s)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     u_ref = u.cpu()
     e2e_dev = float(torch.linalg.norm(u_host[(args.steps - 1) % 2] - u_ref) / torch.linalg.norm(u_ref))
-    e2e = {"value": N * args.steps * world / e2e_s, "unit": UNIT, "overlap": "copies on a second stream",
+    e2e = {"value": N * args.steps * world / e2e_s, "unit": UNIT,
+           "overlap": "uploads and downloads on two more streams, overlapping the solves",
            "rel_diff_vs_device_run": e2e_dev,
            "h2d_bytes_per_step": int(f_np.nbytes), "d2h_bytes_per_step": int(f_np.nbytes)}
 

@@ -114,7 +114,8 @@ struct GmresWork {
   double* partial = nullptr;     // dot_blocks() * (restart + 1)
   int partial_cap = 0;
   double* h = nullptr;           // 2 restart + 6: h, h2, ||w||^2
-  double* hostbuf = nullptr;     // pinned mirror of h
+  double* hostbuf = nullptr;     // pinned, device-mapped mirror of h
+  double* hostbuf_dev = nullptr; // its device address
   int hcap = 0;
 };
 
@@ -1063,8 +1064,11 @@ int ensure_work(GmresWork* w, int restart) {
     w->h = nullptr;
     if (w->hostbuf) cudaFreeHost(w->hostbuf);
     w->hostbuf = nullptr;
+    w->hostbuf_dev = nullptr;
     if (cudaMalloc((void**)&w->h, (size_t)(2 * restart + 6) * sizeof(double)) != cudaSuccess) return STFD_ERR_ALLOC;
-    if (cudaMallocHost((void**)&w->hostbuf, (size_t)(2 * restart + 6) * sizeof(double)) != cudaSuccess)
+    if (cudaHostAlloc((void**)&w->hostbuf, (size_t)(2 * restart + 6) * sizeof(double), cudaHostAllocMapped) !=
+            cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&w->hostbuf_dev, w->hostbuf, 0) != cudaSuccess)
       return STFD_ERR_ALLOC;
     w->hcap = restart + 3;
   }
@@ -1119,7 +1123,7 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
     }
     STFD_CU(launch_sub_norm(write_v0 ? w->V[0] : nullptr, f, Au, N, w->partial, nb, st));
     STFD_CU(launch_reduce_partial(w->partial, 1, nb, dnrm, 0, st));
-    STFD_CU(cudaMemcpyAsync(hb + 2 * m + 2, dnrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+    STFD_CU(launch_copy_doubles(w->hostbuf_dev + 2 * m + 2, dnrm, 1, st));
     STFD_CU(cudaStreamSynchronize(st));
     *nrm2 = hb[2 * m + 2];
     return STFD_OK;
@@ -1171,7 +1175,7 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
       // second update fused with ||w||^2 (the normalisation of w happens next iteration)
       STFD_CU(launch_axpy_norm(w->V[j + 1], w->dV, dh2, j + 1, N, -1.0, 0, w->partial, nb, st));
       STFD_CU(launch_reduce_partial(w->partial, 1, nb, dnrm, 0, st));
-      STFD_CU(cudaMemcpyAsync(hb, dh, (size_t)(2 * m + 3) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      STFD_CU(launch_copy_doubles(w->hostbuf_dev, dh, 2 * m + 3, st));
       STFD_CU(cudaStreamSynchronize(st));
       double* c = &H[(size_t)(m + 1) * j];
       for (int i = 0; i <= j; ++i) c[i] = hb[i] + hb[m + 1 + i];
@@ -1212,7 +1216,7 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
       y[i] = t / H[i + (size_t)(m + 1) * i];
     }
     std::copy(y.begin(), y.begin() + j_done, hb);
-    STFD_CU(cudaMemcpyAsync(dh, hb, (size_t)j_done * sizeof(double), cudaMemcpyHostToDevice, st));
+    STFD_CU(launch_copy_doubles(dh, w->hostbuf_dev, j_done, st));
     STFD_CU(launch_axpy_norm(u, w->dZ, dh, j_done, N, 1.0, first_cycle ? 1 : 0, nullptr, nb, st));
     first_cycle = false;
     if (converged || lucky || total >= o.max_it) break;

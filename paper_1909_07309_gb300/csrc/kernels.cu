@@ -470,6 +470,19 @@ cudaError_t launch_sub_norm(double* out, const double* f, const double* y, long 
   return cudaGetLastError();
 }
 
+// A few doubles between device memory and host-mapped pinned memory, copied by
+// a kernel: the solver's scalars do not queue on a copy engine behind bulk
+// transfers that other streams may have in flight.
+__global__ void k_copy_doubles(double* __restrict__ dst, const double* __restrict__ src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+cudaError_t launch_copy_doubles(double* dst, const double* src, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_copy_doubles<<<1, 128, 0, st>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sub(double* y, const double* a, const double* b, long long N, cudaStream_t st) {
   ProfScope ps("gmres_sub", (double)N, 24.0 * N, st);
   k_sub<<<grid_for(N, 256), 256, 0, st>>>(y, a, b, N);

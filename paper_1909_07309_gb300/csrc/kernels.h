@@ -70,6 +70,8 @@ cudaError_t launch_scale_by_inverse(double* y, const double* x, const double* de
                                     int sqrt_den, cudaStream_t st);
 // y[k] = a[k] - b[k]
 cudaError_t launch_sub(double* y, const double* a, const double* b, long long N, cudaStream_t st);
+// dst[i] = src[i], i < n, by a one-block kernel (either side may be host-mapped memory).
+cudaError_t launch_copy_doubles(double* dst, const double* src, int n, cudaStream_t st);
 // w = (set ? 0 : w) + sign sum_i h[i] V_i; partial[b] (nblocks entries, if not NULL)
 // receives block b's share of ||w||^2 of the result.
 cudaError_t launch_axpy_norm(double* w, const double* const* V, const double* h, int m, long long N, double sign,
