@@ -227,7 +227,7 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b (b times
 // acc += b * x for two independent triples; the steps of df_fma
 __device__ __forceinline__ void df_fma2(df2& acc, float2 bh, float2 bl, float2 xh, float2 xl) {
   const float2 p = __fmul2_rn(bh, xh);
-  const float2 e = __ffma2_rn(bh, xh, __fmul2_rn(p, make_float2(-1.f, -1.f)));
+  const float2 e = __ffma2_rn(bh, xh, make_float2(-p.x, -p.y));
   const float2 lo = __ffma2_rn(bh, xl, __ffma2_rn(bl, xh, e));
   const float2 s = __fadd2_rn(acc.h, p);
   const float2 bp = sub2(s, acc.h);
