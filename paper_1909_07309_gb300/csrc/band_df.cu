@@ -220,8 +220,8 @@ __device__ __forceinline__ df ld_pk(const double* p, long long i) {
 }
 __device__ __forceinline__ df ld_pk(const float2* p, long long i) { return to_df(p[i]); }
 
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b (b times -1 is exact, one rounding)
-  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
 }
 
 // acc += b * x for two independent triples; the steps of df_fma

@@ -62,8 +62,8 @@ struct OzArgs {
   long long inner, Q, ntiles;
 };
 
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b (b times -1 is exact, one rounding)
-  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
 }
 
 __device__ __forceinline__ float pow2f(int e) {   // 2^e for e in [-126, 127]
