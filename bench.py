@@ -585,7 +585,8 @@ def main():
                    "restart": args.restart, "gmres_iters": infos[-1]["iters"],
                    "rel_res_true": infos[-1]["rel_res_true"],
                    "precond": "Algorithm 1, FP64-accurate: mode products on tcgen05 via exact BF16 digit slices "
-                              "(6 x 8-bit, FP32 accumulate, double-float recombination), Step 3 double-float",
+                              "(6 signed round-to-nearest digits per entry, exact FP32 accumulation of the 21 digit pairs, "
+                              "double-float recombination), Step 3 double-float",
                    "matvec": "double-float (2 x FP32, ~48-bit), FP64 in/out", "gmres": "FP64",
                    "setup_ms": setup_ms,
                    "l2": "inputs larger than L2 (working set %.2f GB > 129 MB)" % (10 * N * 8 / 1e9),
