@@ -117,6 +117,104 @@ k_stencil(const T* __restrict__ Ms, const T* __restrict__ Ks, const T* __restric
   }
 }
 
+// Pass 2 in double-float with two time slices per paired FP32 instruction
+// (fma.rn.f32x2 and friends; per slice the scalar steps of dfa::fma_acc in the
+// same order, so the results equal those of k_stencil<float2>). The staged
+// slices are stored as high and low planes of slice pairs, [kTC/2][span] of
+// float2 (slice 2u, slice 2u + 1), so that one 8-byte load gives an operand.
+struct df2 {
+  float2 h, l;
+};
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+// acc += b * x on two slices (b the same coefficient for both); the steps of fma_acc
+__device__ __forceinline__ void fma_acc2(df2& acc, float2 bh, float2 bl, float2 xh, float2 xl) {
+  const float2 p = __fmul2_rn(bh, xh);
+  const float2 e = __ffma2_rn(bh, xh, make_float2(-p.x, -p.y));
+  const float2 lo = __ffma2_rn(bh, xl, __ffma2_rn(bl, xh, e));
+  const float2 s = __fadd2_rn(acc.h, p);
+  const float2 bp = sub2(s, acc.h);
+  const float2 err = __fadd2_rn(sub2(acc.h, sub2(s, bp)), sub2(p, bp));
+  acc.h = s;
+  acc.l = __fadd2_rn(acc.l, __fadd2_rn(err, lo));
+}
+
+template <int kTC, int PP>
+__global__ void __launch_bounds__(kRows)
+k_stencil_pk(const float2* __restrict__ Ms, const float2* __restrict__ Ks, const float2* __restrict__ Z1,
+             const float2* __restrict__ Z2, double* __restrict__ y, StencilDims g) {
+  constexpr int kTP = kTC / 2;
+  extern __shared__ unsigned char smem_raw[];
+  const int p = PP > 0 ? PP : g.p;
+  const int W = 2 * p + 1, span = kRows + 2 * p;
+  float2* z1h = reinterpret_cast<float2*>(smem_raw);   // [kTP][span] each
+  float2* z1l = z1h + kTP * span;
+  float2* z2h = z1l + kTP * span;
+  float2* z2l = z2h + kTP * span;
+  const int n_chunks = (g.nt + kTC - 1) / kTC;
+  const long long i0 = (long long)(blockIdx.x / n_chunks) * kRows;
+  const int t0 = (int)(blockIdx.x % n_chunks) * kTC;
+  const long long i = i0 + threadIdx.x;
+  const bool valid = i < g.Ns;
+  const int ntc = min(kTC, g.nt - t0);
+  const int S23 = g.d >= 3 ? W * W : (g.d == 2 ? W : 1);
+  const float2* mrow = Ms + (valid ? i : 0);
+  const float2* krow = Ks + (valid ? i : 0);
+  df2 acc[kTP];
+#pragma unroll
+  for (int u = 0; u < kTP; ++u) acc[u] = df2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  for (int o23 = 0; o23 < S23; ++o23) {
+    const int o2 = g.d >= 2 ? o23 % W : p, o3 = g.d >= 3 ? o23 / W : p;
+    const long long base = i0 - p + (long long)(o2 - p) * g.n1 + (long long)(o3 - p) * g.n1 * g.n2;
+    __syncthreads();
+    for (int c = threadIdx.x; c < span; c += kRows) {
+      long long j = base + c;
+      j = j < 0 ? 0 : (j >= g.Ns ? g.Ns - 1 : j);   // the coefficient is 0 for columns outside the box
+#pragma unroll
+      for (int u = 0; u < kTP; ++u) {
+        float2 a1{0.f, 0.f}, b1{0.f, 0.f}, a2{0.f, 0.f}, b2{0.f, 0.f};   // slices 2u, 2u + 1
+        if (2 * u < ntc) {
+          a1 = Z1[(long long)(t0 + 2 * u) * g.Ns + j];
+          a2 = Z2[(long long)(t0 + 2 * u) * g.Ns + j];
+        }
+        if (2 * u + 1 < ntc) {
+          b1 = Z1[(long long)(t0 + 2 * u + 1) * g.Ns + j];
+          b2 = Z2[(long long)(t0 + 2 * u + 1) * g.Ns + j];
+        }
+        z1h[u * span + c] = make_float2(a1.x, b1.x);
+        z1l[u * span + c] = make_float2(a1.y, b1.y);
+        z2h[u * span + c] = make_float2(a2.x, b2.x);
+        z2l[u * span + c] = make_float2(a2.y, b2.y);
+      }
+    }
+    __syncthreads();
+    const long long ob = (long long)W * o23 * g.Ns;
+#pragma unroll
+    for (int o1 = 0; o1 < (PP > 0 ? 2 * PP + 1 : W); ++o1) {
+      if (PP == 0 && o1 >= W) break;
+      const float2 m = mrow[ob + (long long)o1 * g.Ns], kk = krow[ob + (long long)o1 * g.Ns];
+      const float2 mh = make_float2(m.x, m.x), ml = make_float2(m.y, m.y);
+      const float2 kh = make_float2(kk.x, kk.x), kl = make_float2(kk.y, kk.y);
+      const int c = threadIdx.x + o1;
+#pragma unroll
+      for (int u = 0; u < kTP; ++u) {
+        fma_acc2(acc[u], mh, ml, z1h[u * span + c], z1l[u * span + c]);
+        fma_acc2(acc[u], kh, kl, z2h[u * span + c], z2l[u * span + c]);
+      }
+    }
+  }
+  if (valid) {
+#pragma unroll
+    for (int u = 0; u < kTP; ++u) {   // static indices keep acc[] in registers
+      if (2 * u < ntc)
+        y[(long long)(t0 + 2 * u) * g.Ns + i] = dfa::to_double(dfa::norm(df{acc[u].h.x, acc[u].l.x}));
+      if (2 * u + 1 < ntc)
+        y[(long long)(t0 + 2 * u + 1) * g.Ns + i] = dfa::to_double(dfa::norm(df{acc[u].h.y, acc[u].l.y}));
+    }
+  }
+}
+
 // Pass 1: Z1[t] = gamma sum_tau W[t, tau] x[tau], Z2[t] = nu sum_tau Mt[t, tau] x[tau]
 // with band-compressed rows Wb[t][k] = W[t][t - pt + k] (already scaled).
 template <typename T>
@@ -172,6 +270,18 @@ cudaError_t run_stencil(const StencilOpDev& op, T* Z1, T* Z2, double* y, const S
     attr = true;
   }
   const long long blocks = ((g.Ns + kRows - 1) / kRows) * ((g.nt + kTC - 1) / kTC);
+  if constexpr (std::is_same<T, float2>::value) {   // double-float: slices paired on the FP32 pipes
+    static bool attr_pk = false;
+    if (!attr_pk) {
+      const cudaError_t e = cudaFuncSetAttribute(k_stencil_pk<kTC, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 96 * 1024);
+      if (e != cudaSuccess) return e;
+      attr_pk = true;
+    }
+    k_stencil_pk<kTC, PP><<<(unsigned)blocks, kRows, smem, st>>>(static_cast<const float2*>(op.Ms),
+                                                                  static_cast<const float2*>(op.Ks), Z1, Z2, y, g);
+    return cudaGetLastError();
+  }
   k_stencil<T, kTC, PP><<<(unsigned)blocks, kRows, smem, st>>>(static_cast<const T*>(op.Ms),
                                                                 static_cast<const T*>(op.Ks), Z1, Z2, y, g);
   return cudaGetLastError();
