@@ -36,7 +36,7 @@ L2_BYTES = 129 * 2 ** 20
 # DRAM bytes per launch from one ncu capture at the workload (profiles/): the
 # mean over the 8 mode products of one fd_apply, and over the 4 band passes of
 # one st_matvec; None once a kernel changes until it is captured again.
-NCU_TRAFFIC = {"fd_mode_ozaki": 237515552, "band_pair_df": 457856384}
+NCU_TRAFFIC = {"fd_mode_ozaki": 237753728, "band_pair_df": 457856384}
 
 
 def measured_peaks():
