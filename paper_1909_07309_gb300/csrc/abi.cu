@@ -140,14 +140,11 @@ struct stfd_op {
   float2* JW2 = nullptr;
   float2* JWT2 = nullptr;
   float2* JMt2 = nullptr;
-  // band-compressed double-float factors Ab[i][t] = A[i][i-p+t] (when every p <= 4)
+  // band-compressed double-float factors Ab[i][t] = A[i][i-p+t] (when every p <= 4):
+  // K_l as (hi, lo) for the scalar chain of the middle directions
   int pb[kMaxDim + 1] = {0, 0, 0, 0};
   bool banded = false;
-  float2* Mb[kMaxDim] = {nullptr, nullptr, nullptr};
   float2* Kb[kMaxDim] = {nullptr, nullptr, nullptr};
-  float2* Wb = nullptr;
-  float2* WbT = nullptr;
-  float2* Mtb = nullptr;
   // the same bands as coefficient pairs (hi_1, hi_2, lo_1, lo_2) for the paired kernels:
   // (M_l, K_l), (M_l, M_l), (W_t, M_t), (W_t^T, M_t)
   float4* MK4[kMaxDim] = {nullptr, nullptr, nullptr};
@@ -640,12 +637,8 @@ extern "C" void stfd_op_destroy(stfd_op* A) {
   dev_free(A->JWT2);
   dev_free(A->JMt2);
   for (int l = 0; l < kMaxDim; ++l) {
-    dev_free(A->Mb[l]);
     dev_free(A->Kb[l]);
   }
-  dev_free(A->Wb);
-  dev_free(A->WbT);
-  dev_free(A->Mtb);
   for (int l = 0; l < kMaxDim; ++l) {
     dev_free(A->MK4[l]);
     dev_free(A->MM4[l]);
@@ -770,14 +763,10 @@ extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const dou
     };
     if (A->banded) {
       for (int l = 0; l < d && rc == STFD_OK; ++l) {
-        rc = compress(keep[2 * l], n[l], A->pb[l], &A->Mb[l]);
-        if (rc == STFD_OK) rc = compress(keep[2 * l + 1], n[l], A->pb[l], &A->Kb[l]);
+        rc = compress(keep[2 * l + 1], n[l], A->pb[l], &A->Kb[l]);
         if (rc == STFD_OK) rc = compress_pair(keep[2 * l], keep[2 * l + 1], n[l], A->pb[l], &A->MK4[l]);
         if (rc == STFD_OK) rc = compress_pair(keep[2 * l], keep[2 * l], n[l], A->pb[l], &A->MM4[l]);
       }
-      if (rc == STFD_OK) rc = compress(keep[2 * d], n[d], A->pb[d], &A->Wb);
-      if (rc == STFD_OK) rc = compress(keep[2 * d + 2], n[d], A->pb[d], &A->WbT);
-      if (rc == STFD_OK) rc = compress(keep[2 * d + 1], n[d], A->pb[d], &A->Mtb);
       if (rc == STFD_OK) rc = compress_pair(keep[2 * d], keep[2 * d + 1], n[d], A->pb[d], &A->WMt4);
       if (rc == STFD_OK) rc = compress_pair(keep[2 * d + 2], keep[2 * d + 1], n[d], A->pb[d], &A->WTMt4);
     }

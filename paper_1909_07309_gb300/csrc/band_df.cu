@@ -131,79 +131,11 @@ k_band_pair_df(const TIn* __restrict__ U, const float2* __restrict__ V, const fl
   }
 }
 
-// Same pass with a compile-time half-bandwidth P: interior rows (P <= i < n-P)
-// run fully unrolled taps over band-compressed coefficient rows Ab[i][t] =
-// A[i][i-P+t] (t < 2P+1); the first and last P rows take the bounded loop.
-// When A3 == A1 (the mass factor of the middle directions) its taps are loaded once.
-template <typename TIn, typename TOut, bool HAS_V, bool TWO_OUT, int P>
-__global__ void __launch_bounds__(kThreads)
-k_band_pair_df_p(const TIn* __restrict__ U, const float2* __restrict__ V, const float2* __restrict__ B1,
-                 const float2* __restrict__ B2, const float2* __restrict__ B3, float2 s2, float2 s3,
-                 float2* __restrict__ Uo, TOut* __restrict__ Vo, int n, long long inner, long long Q, int scale,
-                 int same13) {
-  constexpr int W = 2 * P + 1;
-  extern __shared__ float2 sm2[];
-  float2* xu = sm2;
-  float2* xv = sm2 + (size_t)n * kTC;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long q = (long long)blockIdx.x * kTC + lane;
-  const bool valid = q < Q;
-  long long base = 0;
-  if (valid) {
-    const long long o = q / inner;
-    base = o * (long long)n * inner + (q - o * inner);
-  }
-  for (int a = warp; a < n; a += kWarps) {
-    const df v = valid ? load_df<TIn>(U, base + (long long)a * inner) : df{0.f, 0.f};
-    xu[a * kTC + lane] = make_float2(v.h, v.l);
-    if (HAS_V) xv[a * kTC + lane] = valid ? V[base + (long long)a * inner] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  for (int i = warp; i < n; i += kWarps) {
-    const float2* r1 = B1 + (size_t)i * W;
-    const float2* r2 = B2 + (size_t)i * W;
-    const float2* r3 = B3 + (size_t)i * W;
-    df c1{0.f, 0.f}, c2{0.f, 0.f}, c3{0.f, 0.f};
-    if (i >= P && i < n - P) {
-      const float2* xr = xu + (i - P) * kTC + lane;
-      const float2* vr = xv + (i - P) * kTC + lane;
-#pragma unroll
-      for (int t = 0; t < W; ++t) {
-        const df xa = to_df(xr[t * kTC]);
-        const float2 m1 = (TWO_OUT || (HAS_V && same13)) ? __ldg(r1 + t) : make_float2(0.f, 0.f);
-        if (TWO_OUT) df_fma(c1, m1, xa);
-        df_fma(c2, __ldg(r2 + t), xa);
-        if (HAS_V) df_fma(c3, same13 ? m1 : __ldg(r3 + t), to_df(vr[t * kTC]));
-      }
-    } else {
-      const int a0 = max(0, i - P), a1 = min(n - 1, i + P);
-      for (int a = a0; a <= a1; ++a) {
-        const int t = a - i + P;
-        const df xa = to_df(xu[a * kTC + lane]);
-        if (TWO_OUT) df_fma(c1, __ldg(r1 + t), xa);
-        df_fma(c2, __ldg(r2 + t), xa);
-        if (HAS_V) df_fma(c3, __ldg(r3 + t), to_df(xv[a * kTC + lane]));
-      }
-    }
-    df vo = df_norm(c2);
-    if (scale) vo = df_scale(vo, s2);
-    if (HAS_V) {
-      df tt = df_norm(c3);
-      if (scale) tt = df_scale(tt, s3);
-      vo = df_add(vo, tt);
-    }
-    if (valid) {
-      if (TWO_OUT) store_df(Uo, base + (long long)i * inner, df_norm(c1));
-      store_df(Vo, base + (long long)i * inner, vo);
-    }
-  }
-}
-
-// ---- Paired-chain variant of k_band_pair_df_p: two accumulation chains of a
+// ---- Band passes with compile-time half-bandwidth P: two accumulation chains of a
 // pass that share their operand layout are issued together with the sm_100
 // float2 instructions (fma.rn.f32x2 and friends; per component the scalar
-// steps of df_fma in the same order, so the results are those of the scalar
-// kernel): KIND 0 (first direction) pairs M x and K x, the tile holding
+// steps of df_fma in the same order, so the results equal those of scalar
+// double-float code): KIND 0 (first direction) pairs M x and K x, the tile holding
 // (x.h, x.h, x.l, x.l); KIND 1 (middle directions) pairs M u and M v, the tile
 // holding (u.h, v.h, u.l, v.l), with K u as a scalar chain; KIND 2 (time) pairs
 // W u and M_t v on the same tile layout. The coefficient tables hold the
@@ -375,34 +307,6 @@ cudaError_t launch_pk(const TIn* U, const float2* V, const float4* T4, const flo
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-template <typename TIn, typename TOut, bool HAS_V, bool TWO_OUT, int P>
-cudaError_t launch_pair_p(const TIn* U, const float2* V, const float2* B1, const float2* B2, const float2* B3,
-                          double s2, double s3, float2* Uo, TOut* Vo, int n, long long inner, long long outer,
-                          int same13, cudaStream_t st) {
-  const long long Q = inner * outer;
-  if (Q <= 0) return cudaSuccess;
-  static bool attr_done = false;
-  if (!attr_done) {
-    const cudaError_t e = cudaFuncSetAttribute(k_band_pair_df_p<TIn, TOut, HAS_V, TWO_OUT, P>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               2 * 256 * kTC * (int)sizeof(float2));
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
-  const size_t smem = (size_t)(HAS_V ? 2 : 1) * n * kTC * sizeof(float2);
-  double entries = 0.0;
-  for (int i = 0; i < n; ++i) entries += (double)(std::min(n - 1, i + P) - std::max(0, i - P) + 1);
-  const int nprod = (TWO_OUT ? 1 : 0) + 1 + (HAS_V ? 1 : 0);
-  const int nio = (HAS_V ? 2 : 1) + (TWO_OUT ? 2 : 1);
-  ProfScope ps("band_pair_df", 2.0 * entries * (double)Q * nprod, 8.0 * (double)Q * n * nio, st);
-  const float h2 = (float)s2, h3 = (float)s3;
-  const float2 c2 = make_float2(h2, (float)(s2 - (double)h2)), c3 = make_float2(h3, (float)(s3 - (double)h3));
-  const int scale = (s2 != 1.0 || s3 != 1.0) ? 1 : 0;
-  k_band_pair_df_p<TIn, TOut, HAS_V, TWO_OUT, P><<<(unsigned)((Q + kTC - 1) / kTC), kThreads, smem, st>>>(
-      U, V, B1, B2, B3, c2, c3, Uo, Vo, n, inner, Q, scale, same13);
-  return cudaGetLastError();
-}
-
 template <typename TIn, typename TOut, bool HAS_V, bool TWO_OUT>
 cudaError_t launch_pair(const TIn* U, const float2* V, const float2* A1, const float2* A2, const float2* A3,
                         double s2, double s3, float2* Uo, TOut* Vo, int n, long long inner, long long outer, int bw,
@@ -441,28 +345,6 @@ cudaError_t launch_pair(const TIn* U, const float2* V, const float2* A1, const f
     case 4: return CALL(4);                \
     default: return cudaErrorInvalidValue; \
   }
-
-cudaError_t launch_band_first_dfc(const double* x, const float2* Mb, const float2* Kb, float2* Uo, float2* Vo, int n,
-                                  long long inner, long long outer, int p, cudaStream_t st) {
-#define CALL(PP) launch_pair_p<double, float2, false, true, PP>(x, nullptr, Mb, Kb, nullptr, 1.0, 1.0, Uo, Vo, n, inner, outer, 0, st)
-  STFD_BAND_DISPATCH(p, CALL)
-#undef CALL
-}
-
-cudaError_t launch_band_mid_dfc(const float2* u, const float2* v, const float2* Mb, const float2* Kb, float2* Uo,
-                                float2* Vo, int n, long long inner, long long outer, int p, cudaStream_t st) {
-#define CALL(PP) launch_pair_p<float2, float2, true, true, PP>(u, v, Mb, Kb, Mb, 1.0, 1.0, Uo, Vo, n, inner, outer, 1, st)
-  STFD_BAND_DISPATCH(p, CALL)
-#undef CALL
-}
-
-cudaError_t launch_band_last_dfc(const float2* u, const float2* v, const float2* Wb, double gamma, const float2* Mtb,
-                                 double nu, double* y, int n, long long inner, long long outer, int p,
-                                 cudaStream_t st) {
-#define CALL(PP) launch_pair_p<float2, double, true, false, PP>(u, v, Mtb, Wb, Mtb, gamma, nu, nullptr, y, n, inner, outer, 0, st)
-  STFD_BAND_DISPATCH(p, CALL)
-#undef CALL
-}
 
 cudaError_t launch_band_first_pk(const double* x, const float4* MK, float2* Uo, float2* Vo, int n, long long inner,
                                  long long outer, int p, int rot, cudaStream_t st) {

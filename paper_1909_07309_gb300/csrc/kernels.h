@@ -91,20 +91,12 @@ cudaError_t launch_band_mid_df(const float2* u, const float2* v, const float2* M
 cudaError_t launch_band_last_df(const float2* u, const float2* v, const float2* W, double gamma, const float2* Mt,
                                 double nu, double* y, int n, long long inner, long long outer, int bw,
                                 cudaStream_t st);
-// Same passes with band-compressed factors Ab[i][t] = A[i][i-p+t], t < 2p+1, and a
-// compile-time half-bandwidth p in 1..4 (cudaErrorInvalidValue otherwise).
-cudaError_t launch_band_first_dfc(const double* x, const float2* Mb, const float2* Kb, float2* Uo, float2* Vo, int n,
-                                  long long inner, long long outer, int p, cudaStream_t st);
-cudaError_t launch_band_mid_dfc(const float2* u, const float2* v, const float2* Mb, const float2* Kb, float2* Uo,
-                                float2* Vo, int n, long long inner, long long outer, int p, cudaStream_t st);
-cudaError_t launch_band_last_dfc(const float2* u, const float2* v, const float2* Wb, double gamma, const float2* Mtb,
-                                 double nu, double* y, int n, long long inner, long long outer, int p,
-                                 cudaStream_t st);
-
-// The same three passes with two accumulation chains issued together on the
-// paired FP32 instructions; tables of (hi_1, hi_2, lo_1, lo_2) per band tap:
-// first direction (M, K), middle directions (M, M) with K from the band table Kb,
-// time (W_t or W_t^T, M_t). Results equal those of the _dfc launchers. With
+// The same three passes with a compile-time half-bandwidth p in 1..4
+// (cudaErrorInvalidValue otherwise) over band-compressed factors
+// Ab[i][t] = A[i][i-p+t], t < 2p+1, two accumulation chains issued together on
+// the paired FP32 instructions; tables of (hi_1, hi_2, lo_1, lo_2) per band tap:
+// first direction (M, K), middle directions (M, M) with K from the (hi, lo) band
+// table Kb, time (W_t or W_t^T, M_t). With
 // rot = 1 the inputs hold the direction fastest (fibres contiguous, inner = 1)
 // and entry i of fibre q is written to i Q + q (Q = inner * outer fibres): each
 // pass leaves the next direction fastest, and after the time pass the layout
