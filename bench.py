@@ -14,6 +14,7 @@ replicas (no data-path collective; "scaling": "weak"). `--impl reference`
 times the CPU FP64 oracle (the only reference this paper has) on the host.
 """
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -48,55 +49,111 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every `interval_ms` during
+    the timed region. All GPUs are queried (nvidia-smi does not follow
+    CUDA_VISIBLE_DEVICES) and the lines of this process's GPU are picked by UUID;
+    only samples whose timestamps fall inside the marked region are kept."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
+    def __init__(self, gpu_index, uuid=None, interval_ms=50):
+        self.gpu = str(gpu_index)
+        self.uuid = (uuid or "").lower()
+        self.interval_ms = interval_ms
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
 
-    def start(self):
+    def start(self, first_sample_timeout_s=5.0):
+        """Start nvidia-smi and wait (bounded) for its first sample."""
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
-        except (OSError, FileNotFoundError):
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", str(self.interval_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
             self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        deadline = time.time() + first_sample_timeout_s
+        while not self.lines and time.time() < deadline and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_stop(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _stamp(text, fallback):
+        try:
+            return datetime.datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return fallback
+
+    def _mine(self, rows):
+        """Rows of this process's GPU: by UUID, else the only GPU, else by index."""
+        if self.uuid:
+            own = [r for r in rows if r["uuid"].lower().endswith(self.uuid)]
+            if own:
+                return own
+        if len({r["index"] for r in rows}) == 1:
+            return rows
+        return [r for r in rows if r["index"] == self.gpu]
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        if self.t1 is None:
+            self.mark_stop()
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+            self.proc.wait(timeout=5)
+        self.thread.join(timeout=5)
+        rows = []
+        for arrived, line in list(self.lines):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < len(self.FIELDS.split(",")):
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                sm, smax = float(parts[3]), float(parts[4])
             except ValueError:
                 continue
-            for nm, flag in zip(names, parts[5:9]):
-                if flag.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+            rows.append({"t": self._stamp(parts[0], arrived), "index": parts[1], "uuid": parts[2], "sm": sm,
+                         "smax": smax, "flags": parts[7:11]})
+        rows = self._mine(rows)
+        t0 = self.t0 if self.t0 is not None else float("-inf")
+        window = "timed region"
+        sel = [r for r in rows if t0 <= r["t"] <= self.t1]
+        if not sel:   # region shorter than the sampling interval: the nearest samples
+            window = "timed region +- 0.5 s"
+            sel = [r for r in rows if t0 - 0.5 <= r["t"] <= self.t1 + 0.5]
+        reasons = sorted({nm for r in sel for nm, flag in zip(self.REASONS, r["flags"])
+                          if flag.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r["sm"] for r in sel) if sel else None,
+                "sm_max_mhz": max(r["smax"] for r in sel) if sel else None,
+                "reasons": reasons, "samples": len(sel), "interval_ms": self.interval_ms, "window": window}
+
+
+def device_uuid(index):
+    """UUID of CUDA device `index` as 8-4-4-4-12 hex (nvidia-smi prints it after "GPU-"), or None."""
+    import torch
+    try:
+        text = str(torch.cuda.get_device_properties(index).uuid)
+    except (AttributeError, RuntimeError):
+        return None
+    return text[4:] if text.upper().startswith("GPU-") else text
 
 
 def max_over_ranks(x, world, device):
@@ -399,12 +456,13 @@ def main():
     torch.cuda.synchronize()
 
     # ---- timed region: K full solves, inputs resident in HBM (working set > L2)
-    sampler = ClockSampler(local_rank)
+    sampler = ClockSampler(local_rank, uuid=device_uuid(local_rank))
     sampler.start()
     barrier()
     torch.cuda.synchronize()
     launches0 = stfd.stfd_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark_start()
     e0.record(stream)
     infos = []
     for _ in range(args.steps):
@@ -412,6 +470,7 @@ def main():
         infos.append(info)
     e1.record(stream)
     torch.cuda.synchronize()
+    sampler.mark_stop()
     barrier()
     clocks = sampler.stop()
     launches = stfd.stfd_launch_count() - launches0

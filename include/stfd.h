@@ -26,8 +26,10 @@
  *  - Every int-returning call returns STFD_OK (0) or a negative STFD_ERR_*
  *    code (STFD_NOT_CONVERGED = 1 is a warning); nothing is thrown across
  *    the ABI. stfd_strerror() names a code.
- *  - Handles are immutable after creation, except the Krylov workspace that
- *    stfd_gmres_solve caches inside an stfd_op (one solve per op at a time).
+ *  - Handles are immutable after creation, except their device scratch (the
+ *    intermediate tensors of an apply or matvec, and the Krylov workspace that
+ *    stfd_gmres_solve caches inside an stfd_op): calls on one handle must not
+ *    overlap in time, whether from several streams or several host threads.
  */
 #ifndef STFD_H
 #define STFD_H
