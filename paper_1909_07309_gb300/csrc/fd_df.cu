@@ -84,92 +84,6 @@ __global__ void k_arrowhead_df(float2* __restrict__ X, ArrowDF p) {
     arrowhead_df_point(X, p, k);
 }
 
-// Step 3 for a tile of kArTK consecutive spatial indices, staged in shared
-// memory: the whole [nt x kArTK] block is read once with coalesced loads (all
-// in flight together) and each result is written once. Two threads share a
-// spatial index: thread half h solves the 2 x 2 blocks j = h, h + 2, ...; the
-// two partial sums of the Schur right-hand side meet in shared memory. Per
-// block the arithmetic is that of arrowhead_df_point.
-constexpr int kArTK = 128;
-constexpr int kArThreads = 2 * kArTK;
-constexpr size_t kArSmemMax = 200 * 1024;   // larger time dimensions take k_arrowhead_df
-
-__global__ void __launch_bounds__(kArThreads, 3) k_arrowhead_df_tile(float2* __restrict__ X, ArrowDF p) {
-  using dfa::df;
-  extern __shared__ float2 xs[];   // [nt][kArTK] tile, then [kArTK] partial sums / q_n
-  float2* part = xs + (size_t)p.nt * kArTK;
-  const int c = threadIdx.x % kArTK, half = threadIdx.x / kArTK;
-  const long long k0 = (long long)blockIdx.x * kArTK, k = k0 + c;
-  const long long Ns = p.Ns;
-  const bool valid = k < Ns;
-  tc::grid_dependency_wait();   // programmatic dependent launch
-  tc::grid_launch_dependents();
-  const int total = p.nt * kArTK;
-#pragma unroll 8
-  for (int i = threadIdx.x; i < total; i += kArThreads) {
-    const long long kk = k0 + i % kArTK;
-    xs[i] = kk < Ns ? X[(long long)(i / kArTK) * Ns + kk] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  df a{0.f, 0.f}, a2{0.f, 0.f}, y{0.f, 0.f};
-  const int z = 2 * p.n_pairs;
-  if (valid) {
-    long long rest = k;
-    const int i1 = (int)(rest % p.n1);
-    rest /= p.n1;
-    df mu = dfa::from_float2(p.lam[0][i1]);
-    if (p.d >= 2) {
-      const int i2 = (int)(rest % p.n2);
-      rest /= p.n2;
-      mu = dfa::add(mu, dfa::from_float2(p.lam[1][i2]));
-    }
-    if (p.d >= 3) mu = dfa::add(mu, dfa::from_float2(p.lam[2][rest]));
-    a = dfa::mul(dfa::from_float2(p.nu), mu);
-    a2 = dfa::mul(a, a);
-    if (half == 0) y = dfa::from_float2(xs[(p.nt - 1) * kArTK + c]);
-    for (int j = half; j < p.n_pairs; j += 2) {
-      const df x1 = dfa::from_float2(xs[(2 * j) * kArTK + c]);
-      const df x2 = dfa::from_float2(xs[(2 * j + 1) * kArTK + c]);
-      const df b = sgnd(p.B[j], p.sgn);
-      const df inv = dfa::recip(dfa::add(a2, dfa::from_float2(p.BB[j])));
-      const df h1 = dfa::mul(dfa::sub(dfa::mul(a, x1), dfa::mul(b, x2)), inv);
-      const df h2 = dfa::mul(dfa::add(dfa::mul(b, x1), dfa::mul(a, x2)), inv);
-      y = dfa::add(y, dfa::add(dfa::mul(sgnd(p.G[2 * j], p.sgn), h1), dfa::mul(sgnd(p.G[2 * j + 1], p.sgn), h2)));
-    }
-    if (half == 1) part[c] = make_float2(y.h, y.l);
-  }
-  __syncthreads();
-  df x0{0.f, 0.f}, inva{0.f, 0.f};
-  if (valid && half == 0) {
-    y = dfa::add(y, dfa::from_float2(part[c]));
-    if (p.has_zero) {
-      x0 = dfa::from_float2(xs[z * kArTK + c]);
-      inva = dfa::recip(a);
-      y = dfa::add(y, dfa::mul(sgnd(p.G[z], p.sgn), dfa::mul(x0, inva)));
-    }
-    const df qn = dfa::mul(y, dfa::from_float2(p.Sinv[k]));
-    part[c] = make_float2(qn.h, qn.l);
-    X[(long long)(p.nt - 1) * Ns + k] = make_float2(qn.h, qn.l);
-  }
-  __syncthreads();
-  if (!valid) return;
-  const df qn = dfa::from_float2(part[c]);
-  for (int j = half; j < p.n_pairs; j += 2) {
-    const df b = sgnd(p.B[j], p.sgn);
-    const df inv = dfa::recip(dfa::add(a2, dfa::from_float2(p.BB[j])));
-    const df r1 = dfa::sub(dfa::from_float2(xs[(2 * j) * kArTK + c]), dfa::mul(sgnd(p.G[2 * j], p.sgn), qn));
-    const df r2 = dfa::sub(dfa::from_float2(xs[(2 * j + 1) * kArTK + c]), dfa::mul(sgnd(p.G[2 * j + 1], p.sgn), qn));
-    const df q1 = dfa::mul(dfa::sub(dfa::mul(a, r1), dfa::mul(b, r2)), inv);
-    const df q2 = dfa::mul(dfa::add(dfa::mul(b, r1), dfa::mul(a, r2)), inv);
-    X[(long long)(2 * j) * Ns + k] = make_float2(q1.h, q1.l);
-    X[(long long)(2 * j + 1) * Ns + k] = make_float2(q2.h, q2.l);
-  }
-  if (half == 0 && p.has_zero) {
-    const df q0 = dfa::mul(dfa::sub(x0, dfa::mul(sgnd(p.G[z], p.sgn), qn)), inva);
-    X[(long long)z * Ns + k] = make_float2(q0.h, q0.l);
-  }
-}
-
 int sms() {
   static int s = 0;
   if (s == 0) {
@@ -230,18 +144,6 @@ cudaError_t launch_arrowhead_df(float2* X, int d, int n1, int n2, int nt, int n_
   const float nh = (float)nu;
   p.nu = make_float2(nh, (float)(nu - (double)nh));
   ProfScope ps("arrowhead_df", (double)Ns * (10.0 * n_pairs + 4.0), 16.0 * (double)Ns * nt, st);
-  const size_t smem = (size_t)(nt + 1) * kArTK * sizeof(float2);
-  if (smem <= kArSmemMax) {
-    static bool attr_done = false;
-    if (!attr_done) {
-      const cudaError_t e =
-          cudaFuncSetAttribute(k_arrowhead_df_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kArSmemMax);
-      if (e != cudaSuccess) return e;
-      attr_done = true;
-    }
-    return tc::launch_pdl(k_arrowhead_df_tile, dim3((unsigned)((Ns + kArTK - 1) / kArTK)), dim3(kArThreads), smem,
-                          st, X, p);
-  }
   const long long want = (Ns + 255) / 256;
   const int grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)sms() * 8));
   return tc::launch_pdl(k_arrowhead_df, dim3(grid), dim3(256), 0, st, X, p);
