@@ -479,6 +479,7 @@ __global__ void k_copy_doubles(double* __restrict__ dst, const double* __restric
 
 cudaError_t launch_copy_doubles(double* dst, const double* src, int n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  count_launch();
   k_copy_doubles<<<1, 128, 0, st>>>(dst, src, n);
   return cudaGetLastError();
 }
