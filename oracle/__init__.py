@@ -16,6 +16,8 @@ Sangalli, Tani) and cites the section / equation it restates:
 * ``assemble`` -- the space-time system matrix A and preconditioner P
   assembled directly by (d+1)-dimensional quadrature of the bilinear form
   (Sec. 3.1-3.3), never by Kronecker products.
+* ``direct``   -- banded Gaussian elimination with partial pivoting, an
+  independent check of the sparse direct solves (Sec. 3.3, eq. sys_solve).
 * ``kron``     -- m-mode products and the Kronecker form of A (eqs.
   kron_vec_multi, syst_mat).
 * ``fd``       -- Algorithm 1 (extended Fast Diagonalization) in complex

@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
 
-from oracle import assemble, fd, kron, matrices
+from oracle import assemble, direct, fd, kron, matrices
 from paper_1909_07309_gb300 import inputs
 
 rng = np.random.default_rng(99)
@@ -50,6 +50,25 @@ def test_mixed_degrees_assembly():
     K, M, Wt, Mt = _factors(d, p, n_el, [1.0, 1.0], 1.0, p_t, n_el_t)
     Ak = kron.st_matrix_kron(K, M, Wt, Mt)
     assert abs(A - Ak).max() <= 1e-14 * abs(A).max()
+
+
+@pytest.mark.parametrize("d,p,n_el,T,gamma,nu", [(1, 2, 5, 1.0, 1.0, 1.0), (1, 3, 6, 2.0, 0.7, 1.3),
+                                                   (2, 2, 3, 1.0, 1.0, 1.0), (2, 1, 4, 0.5, 2.0, 0.5),
+                                                   (2, 3, 3, 1.0, 1.0, 1.0), (3, 1, 3, 1.0, 1.0, 1.0)])
+def test_banded_lu_agrees_with_superlu(d, p, n_el, T, gamma, nu):
+    """The oracle's own banded Gaussian elimination with partial pivoting and
+    the library routine (SuperLU) solve the directly assembled A (and A^T)
+    alike; in vec order A's bandwidth is p (1 + n_s + ... + n_s^d) on both
+    sides of the diagonal (supports of p + 1 spans in every direction)."""
+    A = assemble.assemble_space_time(d, p, n_el, p, n_el, gamma, nu, T=T)
+    n_s = n_el + p - 2
+    assert direct.bandwidths(A) == (p * sum(n_s ** l for l in range(d + 1)),) * 2
+    for M_ in (A, A.T.tocsr()):
+        r = rng.standard_normal(M_.shape[0])
+        x = direct.banded_solve(direct.banded_lu(M_), r)
+        x_ref = spla.spsolve(M_.tocsc(), r)
+        assert np.linalg.norm(x - x_ref) <= 1e-12 * np.linalg.norm(x_ref)
+        assert np.linalg.norm(M_ @ x - r) <= 1e-13 * np.linalg.norm(r)
 
 
 @pytest.mark.parametrize("d,p,n_el,lengths,T,gamma,nu", CASES)
