@@ -136,3 +136,8 @@ def test_setup_identities(p, n_el):
     np.testing.assert_allclose(im, -im[::-1], atol=1e-12 * np.abs(im).max())
     if (n - 1) % 2 == 1:
         assert np.min(np.abs(im)) < 1e-10 * np.abs(im).max()
+    # a square M-orthonormal U has U U^T = M^{-1}: its singular values are the
+    # inverse square roots of M's eigenvalues, so kappa_2(U) = sqrt(kappa_2(M))
+    # (the quantity Tables 1 and 3 report for the spatial and time factors)
+    np.testing.assert_allclose(np.linalg.cond(U), np.sqrt(np.linalg.cond(M)), rtol=1e-9)
+    np.testing.assert_allclose(np.linalg.cond(Ut), np.sqrt(np.linalg.cond(Mt)), rtol=1e-9)
