@@ -14,8 +14,6 @@ the batched solver on the first COUNT problems of the batched workload
 """
 import sys
 
-import numpy as np
-
 
 def main(argv):
     import torch
