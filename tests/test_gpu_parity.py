@@ -201,6 +201,30 @@ def test_fd_apply_full_size_residual_samples(prec):
     assert worst <= 1e-10 * np.max(np.abs(r)), worst
 
 
+@pytest.mark.parametrize("arith", [stfd.STFD_OP_DF32, stfd.STFD_OP_FP64])
+def test_st_matvec_full_size_samples(arith):
+    """Workload at scale (d = 3, p = 3, 64 elements, N = 18,125,250), the
+    matvec the bench times: 400 sampled entries of A x against the rows the
+    oracle's univariate matrices give one by one (eq. syst_mat), 1e-13
+    relative to the largest entry as at the small sizes."""
+    cfg = inputs.SCALE
+    d, p, n_el = cfg["d"], cfg["p"], cfg["n_el"]
+    K, M, Wt, Mt = stfd.heat_problem(d, p, n_el)
+    A = stfd.KronOp(K, M, Wt, Mt, arith=arith)
+    x = inputs.standard_normal(A.N, cfg["rhs_seed"])
+    y = host(A.matvec(dev(x)))
+    oK, oM, oWt, oMt = oracle_factors(d, p, n_el)
+    shape = [k.shape[0] for k in oK] + [oWt.shape[0]]
+    X = x.reshape(shape, order="F")
+    Y = y.reshape(shape, order="F")
+    g = np.random.default_rng(2025)
+    worst = 0.0
+    for _ in range(400):
+        idx = [int(g.integers(0, n)) for n in shape]
+        worst = max(worst, abs(_row_of_A(X, idx, oK, oM, oWt, oMt, 1.0, 1.0, p) - Y[tuple(idx)]))
+    assert worst <= 1e-13 * np.max(np.abs(y)), worst
+
+
 def test_gmres_rejects_nan_and_reports_not_converged():
     K, M, Wt, Mt = stfd.heat_problem(2, 2, 6)
     A = stfd.KronOp(K, M, Wt, Mt, 1.0, 3.0)
