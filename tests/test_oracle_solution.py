@@ -120,3 +120,45 @@ def test_gmres_mismatched_preconditioner():
     assert np.linalg.norm(f - A @ x) / np.linalg.norm(f) <= 1e-8
     xd = spla.spsolve(A.tocsc(), f)
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-6
+
+
+def test_gmres_minimises_the_residual_over_the_krylov_space():
+    """GMRES's defining property: after j steps x_j = P^{-1} V_j y minimises
+    ||f - A x|| over x in P^{-1} K_j(A P^{-1}, f). Checked against a least-squares
+    solve on the explicit (power) Krylov basis, for j = 1..4 and restarted runs:
+    a restart cycle minimises from the current residual instead."""
+    g = np.random.default_rng(17)
+    n = 60
+    A = np.eye(n) * 3.0 + g.standard_normal((n, n)) / np.sqrt(n)
+    Pm = np.eye(n) * 3.0 + np.triu(g.standard_normal((n, n)) / np.sqrt(n))
+    f = g.standard_normal(n)
+    AP = A @ np.linalg.inv(Pm)
+    for j in range(1, 5):
+        x, info = gmres.gmres(lambda v: A @ v, lambda v: np.linalg.solve(Pm, v), f, tol=1e-30, max_it=j)
+        assert info["iters"] == j and not info["converged"]
+        Kb = np.stack([np.linalg.matrix_power(AP, i) @ f for i in range(j)], axis=1)
+        c = np.linalg.lstsq(AP @ Kb, f, rcond=None)[0]
+        best = np.linalg.norm(f - AP @ Kb @ c)
+        np.testing.assert_allclose(np.linalg.norm(f - A @ x), best, rtol=1e-10)
+        np.testing.assert_allclose(info["history"][-1] * np.linalg.norm(f), best, rtol=1e-10)
+    # GMRES(2) for 4 steps: two cycles, the second from r_2 = f - A x_2
+    x2, _ = gmres.gmres(lambda v: A @ v, lambda v: np.linalg.solve(Pm, v), f, tol=1e-30, restart=2, max_it=2)
+    x4, info = gmres.gmres(lambda v: A @ v, lambda v: np.linalg.solve(Pm, v), f, tol=1e-30, restart=2, max_it=4)
+    r2 = f - A @ x2
+    Kb = np.stack([r2, AP @ r2], axis=1)
+    c = np.linalg.lstsq(AP @ Kb, r2, rcond=None)[0]
+    np.testing.assert_allclose(np.linalg.norm(f - A @ x4), np.linalg.norm(r2 - AP @ Kb @ c), rtol=1e-10)
+    assert np.all(np.diff(info["history"]) <= 1e-15)
+
+
+def test_gmres_finite_termination_on_a_low_rank_perturbation():
+    """Textbook termination: for A = I + U W^T of rank r (and P = I) the Krylov
+    space has dimension at most r + 1, so GMRES reaches the solution in at
+    most r + 1 steps."""
+    g = np.random.default_rng(23)
+    n, r = 80, 3
+    A = np.eye(n) + g.standard_normal((n, r)) @ g.standard_normal((r, n)) / n
+    f = g.standard_normal(n)
+    x, info = gmres.gmres(lambda v: A @ v, lambda v: v, f, tol=1e-12)
+    assert info["converged"] and info["iters"] <= r + 1
+    np.testing.assert_allclose(x, np.linalg.solve(A, f), rtol=1e-10, atol=1e-12)
