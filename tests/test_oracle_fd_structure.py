@@ -71,6 +71,28 @@ def test_banded_lu_agrees_with_superlu(d, p, n_el, T, gamma, nu):
         assert np.linalg.norm(M_ @ x - r) <= 1e-13 * np.linalg.norm(r)
 
 
+@pytest.mark.parametrize("n,kl,ku", [(50, 3, 5), (60, 10, 10), (200, 4, 4), (40, 0, 6), (40, 6, 0)])
+def test_banded_lu_pivots_on_random_band_matrices(n, kl, ku):
+    """The space-time matrices happen not to need row interchanges, so the
+    pivoting path is pinned on random band matrices with a small diagonal
+    (interchanges at most steps): same solution as LAPACK's dense solve."""
+    import scipy.sparse as sp
+    g = np.random.default_rng(n + 7 * kl + 13 * ku)
+    D = np.zeros((n, n))
+    for i in range(n):
+        for j in range(max(0, i - kl), min(n, i + ku + 1)):
+            D[i, j] = g.standard_normal()
+    D[np.arange(n), np.arange(n)] = 0.05 * D[np.arange(n), np.arange(n)] + (kl == 0 or ku == 0)
+    b = g.standard_normal(n)
+    fac = direct.banded_lu(sp.csr_matrix(D))
+    assert direct.bandwidths(sp.csr_matrix(D)) == (kl, ku)
+    if kl > 0:
+        assert np.count_nonzero(fac[1] != np.arange(n)) > n // 4
+    x = direct.banded_solve(fac, b)
+    ref = np.linalg.solve(D, b)
+    assert np.linalg.norm(x - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
 @pytest.mark.parametrize("d,p,n_el,lengths,T,gamma,nu", CASES)
 def test_fd_equals_direct_solve(d, p, n_el, lengths, T, gamma, nu):
     """Algorithm 1 reproduces P^{-1} r: compared with a sparse direct solve
