@@ -115,6 +115,35 @@ def test_geometry_preconditioner_box_is_exact_and_diagonal_matches():
         assert np.linalg.norm(s - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
+def test_transposed_geometry_preconditioner_and_misfit_definition():
+    """(A^G)^{-T} is the adjoint of (A^G)^{-1} on the quarter annulus
+    (<P^{-T} a, b> = <a, P^{-1} b>), and on the box with constant coefficients
+    both invert A exactly (A^G = A). The misfit of the adjoint workload is half
+    the squared space-time L2 norm of u_h - u_obs,h (c = 1), which a separate
+    quadrature of the discrete functions reproduces exactly on the box."""
+    d, p, n_el = 2, 2, 4
+    Wt, Mt = omat.time_matrices(p, n_el, 1.0)
+    g = np.random.default_rng(31)
+    kap = g.uniform(0.5, 2.0, n_el ** d)
+    Ms, Ks = mapped.spatial_matrices(d, p, n_el, "quarter_annulus", kappa_elem=kap)
+    A = mapped.space_time(Ms, Ks, Wt, Mt)
+    P = mapped.geometry_preconditioner(A, d, p, n_el, Wt, Mt, "quarter_annulus", kappa_elem=kap)
+    PT = mapped.geometry_preconditioner(A, d, p, n_el, Wt, Mt, "quarter_annulus", kappa_elem=kap, transpose=True)
+    a, b = g.standard_normal(A.shape[0]), g.standard_normal(A.shape[0])
+    assert abs(PT(a) @ b - a @ P(b)) <= 1e-12 * np.linalg.norm(PT(a)) * np.linalg.norm(b)
+    Ms, Ks = mapped.spatial_matrices(d, p, n_el, "box")
+    A = mapped.space_time(Ms, Ks, Wt, Mt)
+    x = g.standard_normal(A.shape[0])
+    for tr, Ax in ((False, A @ x), (True, A.T @ x)):
+        Pb = mapped.geometry_preconditioner(A, d, p, n_el, Wt, Mt, "box", transpose=tr)
+        assert np.linalg.norm(Pb(Ax) - x) <= 1e-11 * np.linalg.norm(x)
+    f = g.standard_normal(A.shape[0])
+    u_obs = 0.1 * g.standard_normal(A.shape[0])
+    L, u, _, _ = mapped.loss_and_grads(np.ones(n_el ** d), f, u_obs, d, p, n_el, p, n_el, geom="box")
+    e = mapped.l2_error(u - u_obs, d, p, n_el, p, n_el, lambda X, t: 0.0 * X[..., 0] * t, geom="box")
+    assert abs(L - 0.5 * e ** 2) <= 1e-12 * abs(L)
+
+
 def test_adjoint_gradient_matches_central_differences():
     """dL/dkappa_e and dL/df of the direct-solve loss against central
     differences (h = 1e-6) on random directions."""
