@@ -86,6 +86,20 @@ def test_separation_reproduces_separable_data():
             assert abs(pm / ph[l, e[l]] * Ph[l, e[l]] - C[l, k]) <= 1e-13 * C[l, k]
 
 
+def test_coefficient_diagonal_at_element_midpoints():
+    """The reading of the separation step: diag(C) is taken at each element's
+    midpoint. On the box |det J| = 1 and J^{-1} J^{-T} = I, so the rows are
+    kappa and c at the midpoints ((e_l + 1/2) / n_el), elements colexicographic."""
+    d, n_el = 2, 4
+    kappa = lambda X: 1.0 + X[..., 0] + 2.0 * X[..., 1] ** 2
+    c = lambda X: 2.0 + np.sin(X[..., 0] * X[..., 1])
+    C = mapped.coefficient_diagonal(d, n_el, "box", c=c, kappa=kappa)
+    for k, e in enumerate(mapped.element_ids(d, n_el)):
+        mid = (np.array(e, dtype=np.float64) + 0.5) / n_el
+        assert e == (k % n_el, k // n_el)
+        np.testing.assert_allclose(C[:, k], [kappa(mid), kappa(mid), c(mid)], rtol=1e-15)
+
+
 def test_geometry_preconditioner_box_is_exact_and_diagonal_matches():
     """Box, constant coefficients: A~ = A and D = I. Quarter annulus: diag of
     D^{1/2} A~ D^{1/2} equals diag(A) (eq. prec_geo) and the oracle's FD
