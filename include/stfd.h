@@ -79,11 +79,29 @@ enum {
 const char* stfd_strerror(int code);
 int stfd_version(void);
 
-/* Reads and clears the device flag that the tensor-core kernels set when a
- * bounded wait on the tensor-core pipeline gives up (they then skip their
- * remaining work, release tensor memory and return). Synchronises the device.
- * Returns STFD_OK, STFD_ERR_TIMEOUT if the flag was set, or STFD_ERR_CUDA. */
+/* Device-side failure detection. The tensor-core kernels wait on their own
+ * asynchronous tensor-core operations and bulk copies with bounded mbarrier
+ * waits. A wait that runs out raises a status word (pinned host memory that
+ * every device writes through its mapping); the kernel then lets its own
+ * operations in flight finish (bounded), skips its remaining tiles, releases
+ * tensor memory and returns, so the CUDA context stays usable but the result
+ * of that launch is not valid. The word is read and cleared by:
+ *  - stfd_device_status(): synchronises the device first, returns
+ *    STFD_ERR_TIMEOUT if the word was raised, else STFD_OK (STFD_ERR_CUDA if
+ *    the synchronisation fails);
+ *  - stfd_gmres_solve(): after each of its per-iteration synchronisations, so
+ *    a solve whose preconditioner timed out returns STFD_ERR_TIMEOUT;
+ *  - stfd_fd_apply() and stfd_fd_apply_transpose() on entry (they are
+ *    asynchronous, so they report a timeout of an earlier launch that has
+ *    completed by then). */
 int stfd_device_status(void);
+
+/* Iteration limit of every bounded device wait (default 1 << 22, about a
+ * second of polling). Process-wide, read at each launch. 0 makes every wait
+ * give up at once (used to test the reporting path). Returns STFD_ERR_ARG
+ * outside [0, 2^40]. */
+int stfd_set_wait_limit(long long iters);
+long long stfd_get_wait_limit(void);
 
 /* ------------------------------------------------------------------------
  * Univariate spline matrices (host, CPU only).

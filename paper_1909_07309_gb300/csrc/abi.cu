@@ -10,6 +10,7 @@
 #include <new>
 #include <vector>
 
+#include "device_state.h"
 #include "kernels.h"
 #include "stfd.h"
 #include "stfd_internal.h"
@@ -179,9 +180,7 @@ extern "C" int stfd_version(void) { return 1; }
 
 extern "C" int stfd_device_status(void) {
   if (cudaDeviceSynchronize() != cudaSuccess) return STFD_ERR_CUDA;
-  int flag = 0;
-  if (tc_status_read_and_clear(&flag) != 0) return STFD_ERR_CUDA;
-  return flag ? STFD_ERR_TIMEOUT : STFD_OK;
+  return (status_read_and_clear() & kStatusTimeout) ? STFD_ERR_TIMEOUT : STFD_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -587,6 +586,8 @@ namespace {
 int fd_apply_batch(const stfd_fd* h, const double* r, double* s, int nrhs, int trans, void* stream) {
   if (!h || nrhs < 0 || (nrhs > 0 && (!r || !s))) return STFD_ERR_ARG;
   if (nrhs > 0 && r == s) return STFD_ERR_ARG;
+  // a bounded device wait of an earlier, completed launch ran out
+  if (status_read_and_clear() & kStatusTimeout) return STFD_ERR_TIMEOUT;
   cudaStream_t st = (cudaStream_t)stream;
   for (int k = 0; k < nrhs; ++k) {
     const int rc = fd_apply_one(h, r + (size_t)k * h->N, s + (size_t)k * h->N, h->work, trans, st);
@@ -1076,6 +1077,7 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
   if (opts) o = *opts;
   if (o.restart < 1 || o.restart > 1000 || o.max_it < 1 || !(o.tol > 0.0)) return STFD_ERR_ARG;
   if (o.transpose != 0 && o.transpose != 1) return STFD_ERR_ARG;
+  if (status_read_and_clear() & kStatusTimeout) return STFD_ERR_TIMEOUT;
   const int tr = o.transpose;
   stfd_op* A = const_cast<stfd_op*>(Ac);   // the Krylov workspace is cached in the op
   cudaStream_t st = (cudaStream_t)stream;
@@ -1114,6 +1116,7 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
     STFD_CU(launch_reduce_partial(w->partial, 1, nb, dnrm, 0, st));
     STFD_CU(launch_copy_doubles(w->hostbuf_dev + 2 * m + 2, dnrm, 1, st));
     STFD_CU(cudaStreamSynchronize(st));
+    if (status_read_and_clear() & kStatusTimeout) return STFD_ERR_TIMEOUT;
     *nrm2 = hb[2 * m + 2];
     return STFD_OK;
   };
@@ -1166,6 +1169,9 @@ extern "C" int stfd_gmres_solve(const stfd_op* Ac, const stfd_fd* P, const doubl
       STFD_CU(launch_reduce_partial(w->partial, 1, nb, dnrm, 0, st));
       STFD_CU(launch_copy_doubles(w->hostbuf_dev, dh, 2 * m + 3, st));
       STFD_CU(cudaStreamSynchronize(st));
+      // the preconditioner's tensor-core kernels raise the status word when a
+      // bounded wait runs out (they then skip work): the iterate is not valid
+      if (status_read_and_clear() & kStatusTimeout) return STFD_ERR_TIMEOUT;
       double* c = &H[(size_t)(m + 1) * j];
       for (int i = 0; i <= j; ++i) c[i] = hb[i] + hb[m + 1 + i];
       const double hn = std::sqrt(hb[2 * m + 2]);

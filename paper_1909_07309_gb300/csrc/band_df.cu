@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "df.cuh"
+#include "device_state.h"
 #include "kernels.h"
 #include "profile.h"
 #include "tc_common.cuh"
@@ -274,13 +275,9 @@ cudaError_t launch_pk(const TIn* U, const float2* V, const float4* T4, const flo
                       float2* Uo, TOut* Vo, int n, long long inner, long long outer, int rot, cudaStream_t st) {
   const long long Q = inner * outer;
   if (Q <= 0) return cudaSuccess;
-  static bool attr_done = false;
-  if (!attr_done) {
-    const cudaError_t e = cudaFuncSetAttribute(k_band_pk<TIn, TOut, KIND, P>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               256 * (kTC + 1) * (int)sizeof(float4));
+  {
+    const cudaError_t e = ensure_smem_attr(k_band_pk<TIn, TOut, KIND, P>, 256 * (kTC + 1) * (int)sizeof(float4));
     if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   const size_t smem = (size_t)n * (kTC + 1) * sizeof(float4);
   if (smem > (size_t)256 * (kTC + 1) * sizeof(float4)) return cudaErrorInvalidValue;
@@ -313,13 +310,9 @@ cudaError_t launch_pair(const TIn* U, const float2* V, const float2* A1, const f
                         cudaStream_t st) {
   const long long Q = inner * outer;
   if (Q <= 0) return cudaSuccess;
-  static bool attr_done = false;
-  if (!attr_done) {
-    const cudaError_t e = cudaFuncSetAttribute(k_band_pair_df<TIn, TOut, HAS_V, TWO_OUT>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               2 * 256 * kTC * (int)sizeof(float2));
+  {
+    const cudaError_t e = ensure_smem_attr(k_band_pair_df<TIn, TOut, HAS_V, TWO_OUT>, 2 * 256 * kTC * (int)sizeof(float2));
     if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   const size_t smem = (size_t)(HAS_V ? 2 : 1) * n * kTC * sizeof(float2);
   double entries = 0.0;

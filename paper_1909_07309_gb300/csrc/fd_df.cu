@@ -9,6 +9,7 @@
 
 #include "arrow_df.cuh"
 #include "df.cuh"
+#include "device_state.h"
 #include "kernels.h"
 #include "profile.h"
 #include "tc_common.cuh"
@@ -84,27 +85,16 @@ __global__ void k_arrowhead_df(float2* __restrict__ X, ArrowDF p) {
     arrowhead_df_point(X, p, k);
 }
 
-int sms() {
-  static int s = 0;
-  if (s == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s <= 0) s = 148;
-  }
-  return s;
-}
+int sms() { return sm_count_current(); }
 
 template <typename TIn, typename TOut>
 cudaError_t launch_mode(const TIn* X, const float2* J, TOut* Y, int n, long long inner, long long outer,
                         cudaStream_t st) {
   const long long Q = inner * outer;
   if (Q <= 0) return cudaSuccess;
-  static bool attr_done = false;
-  if (!attr_done) {
-    const cudaError_t e = cudaFuncSetAttribute(k_mode_df<TIn, TOut>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               256 * kTC * (int)sizeof(float2));
+  {
+    const cudaError_t e = ensure_smem_attr(k_mode_df<TIn, TOut>, 256 * kTC * (int)sizeof(float2));
     if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   ProfScope ps("fd_mode_df", 2.0 * (double)Q * n * n, 8.0 * (double)Q * n * 2, st);
   k_mode_df<TIn, TOut><<<(unsigned)((Q + kTC - 1) / kTC), kThreads, (size_t)n * kTC * sizeof(float2), st>>>(

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 
+#include "device_state.h"
 #include "kernels.h"
 #include "profile.h"
 
@@ -343,15 +344,7 @@ __global__ void k_sub(double* __restrict__ y, const double* __restrict__ a, cons
     y[k] = a[k] - b[k];
 }
 
-int sm_count() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
-  }
-  return sms;
-}
+int sm_count() { return sm_count_current(); }
 
 int grid_for(long long n, int threads) {
   const long long want = (n + threads - 1) / threads;
@@ -370,12 +363,9 @@ static cudaError_t launch_mode_impl(const char* name, const double* X1, const do
   const long long Q = inner * outer;
   if (Q <= 0) return cudaSuccess;
   const size_t smem = (size_t)(X2 ? 2 : 1) * n * kTC * sizeof(double);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_mode_fp64<BAND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         2 * 256 * kTC * (int)sizeof(double));
+  {
+    const cudaError_t e = ensure_smem_attr(k_mode_fp64<BAND>, 2 * 256 * kTC * (int)sizeof(double));
     if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   // algorithmic work: 2 flops per stored band entry per column and input
   double entries = 0.0;

@@ -48,8 +48,6 @@ cudaError_t launch_tc_mode(int kind, const void* X, int x_is_double, void* Y, in
 std::vector<unsigned char> tc_operand_image(const double* J, int n, int kind);
 // Self-test of the bounded mbarrier wait (never satisfied): sets the status flag.
 cudaError_t launch_probe_bounded_wait(int max_iters, cudaStream_t st);
-// Host: read and clear the device flag set when a bounded tensor-core wait gives up.
-int tc_status_read_and_clear(int* status);
 
 // GMRES BLAS: partial[b*m + i] = sum over block b's range of V_i[k] * w[k].
 cudaError_t launch_dot_multi(const double* const* V, int m, const double* w, long long N,

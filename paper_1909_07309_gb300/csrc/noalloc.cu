@@ -5,8 +5,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <mutex>
 
+#include "device_state.h"
 #include "profile.h"
 #include "stfd.h"
 #include "stfd_internal.h"
@@ -24,16 +26,23 @@ static __device__ __align__(256) double g_scratch[4 * kNoAllocMaxN];
 std::mutex g_mu;
 double* g_scratch_addr[kMaxDevices] = {nullptr};
 
-// Device address of g_scratch on the current device (looked up once per device).
-int scratch_address(double** out) {
+// Device address of g_scratch on the current device. It is looked up (with
+// that device current) on every call made outside stream capture, so that a
+// device reset, which reloads the module, is picked up; a call made while `st`
+// is being captured uses the address cached by an earlier call on the device.
+int scratch_address(cudaStream_t st, double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return STFD_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return STFD_ERR_ARG;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return STFD_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return STFD_ERR_CUDA;
     g_scratch_addr[dev] = static_cast<double*>(p);
+  } else if (!g_scratch_addr[dev]) {
+    return STFD_ERR_ARG;   // first call on this device inside a capture
   }
   *out = g_scratch_addr[dev];
   return STFD_OK;
@@ -77,12 +86,9 @@ k_band_mode_colmajor(const double* __restrict__ X1, const double* __restrict__ J
 
 cudaError_t launch(const double* X1, const double* J1, double s1, const double* X2, const double* J2,
                    double s2, double* Y, int n, long long inner, long long outer, int bw, cudaStream_t st) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    const cudaError_t e = cudaFuncSetAttribute(k_band_mode_colmajor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               2 * kMaxN * kTC * (int)sizeof(double));
+  {
+    const cudaError_t e = ensure_smem_attr(k_band_mode_colmajor, 2 * kMaxN * kTC * (int)sizeof(double));
     if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   const long long Q = inner * outer;
   const size_t smem = (size_t)(X2 ? 2 : 1) * n * kTC * sizeof(double);
@@ -102,7 +108,6 @@ extern "C" int stfd_st_matvec_noalloc(int d, const int* n, const double* const* 
                                       const int* bw, double gamma, double nu, const double* x_dev,
                                       double* y_dev, void* stream) {
   if (d < 1 || d > kMaxDim || !n || !K_dev || !M_dev || !Wt_dev || !Mt_dev || !x_dev || !y_dev) return STFD_ERR_ARG;
-  if (x_dev == y_dev) return STFD_ERR_ARG;
   long long N = 1;
   for (int l = 0; l <= d; ++l) {
     if (n[l] < 1 || n[l] > kMaxN) return STFD_ERR_ARG;
@@ -110,11 +115,15 @@ extern "C" int stfd_st_matvec_noalloc(int d, const int* n, const double* const* 
     N *= n[l];
   }
   if (n[d] < 2 || N > kNoAllocMaxN) return STFD_ERR_ARG;
+  // x and y may not overlap at all (a partial overlap would be read after written)
+  const uintptr_t xb = reinterpret_cast<uintptr_t>(x_dev), yb = reinterpret_cast<uintptr_t>(y_dev);
+  const uintptr_t bytes = static_cast<uintptr_t>(N) * sizeof(double);
+  if (xb < yb + bytes && yb < xb + bytes) return STFD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
   double* scratch = nullptr;
-  const int rc = scratch_address(&scratch);
+  const int rc = scratch_address(st, &scratch);
   if (rc != STFD_OK) return rc;
   double* T[4] = {scratch, scratch + kNoAllocMaxN, scratch + 2 * kNoAllocMaxN, scratch + 3 * kNoAllocMaxN};
-  cudaStream_t st = (cudaStream_t)stream;
   auto band = [&](int l) { return (bw && bw[l] >= 0) ? std::min(bw[l], n[l] - 1) : n[l] - 1; };
   // Same sum-factorisation as stfd_st_matvec: (u, v) = (x x_1 M_1, x x_1 K_1), then
   // (u, v) <- (u x_l M_l, u x_l K_l + v x_l M_l), and y = gamma u x W_t + nu v x M_t.

@@ -19,6 +19,7 @@
 #include <type_traits>
 
 #include "df.cuh"
+#include "device_state.h"
 #include "kernels.h"
 #include "profile.h"
 
@@ -249,34 +250,20 @@ __global__ void k_time_pair(const double* __restrict__ x, const T* __restrict__ 
   }
 }
 
-int sm_count() {
-  static int s = 0;
-  if (s == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s <= 0) s = 148;
-  }
-  return s;
-}
+int sm_count() { return sm_count_current(); }
 
 template <typename T, int kTC, int PP>
 cudaError_t run_stencil(const StencilOpDev& op, T* Z1, T* Z2, double* y, const StencilDims& g, cudaStream_t st) {
   const size_t smem = (size_t)2 * kTC * (kRows + 2 * op.p) * sizeof(T);
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_stencil<T, kTC, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               96 * 1024);
+  {
+    const cudaError_t e = ensure_smem_attr(k_stencil<T, kTC, PP>, 96 * 1024);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   const long long blocks = ((g.Ns + kRows - 1) / kRows) * ((g.nt + kTC - 1) / kTC);
   if constexpr (std::is_same<T, float2>::value) {   // double-float: slices paired on the FP32 pipes
-    static bool attr_pk = false;
-    if (!attr_pk) {
-      const cudaError_t e = cudaFuncSetAttribute(k_stencil_pk<kTC, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 96 * 1024);
+    {
+      const cudaError_t e = ensure_smem_attr(k_stencil_pk<kTC, PP>, 96 * 1024);
       if (e != cudaSuccess) return e;
-      attr_pk = true;
     }
     k_stencil_pk<kTC, PP><<<(unsigned)blocks, kRows, smem, st>>>(static_cast<const float2*>(op.Ms),
                                                                   static_cast<const float2*>(op.Ks), Z1, Z2, y, g);

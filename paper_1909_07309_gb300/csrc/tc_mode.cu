@@ -16,18 +16,15 @@
 #include <cstring>
 #include <vector>
 
+#include "device_state.h"
 #include "kernels.h"
 #include "profile.h"
 #include "tc_common.cuh"
 
 namespace stfd {
-
-__device__ int g_tc_status = 0;   // set to 1 when a bounded tensor-core wait gives up
-
 namespace {
 
 constexpr int kTile = 128;                 // UMMA M
-constexpr long kWaitIters = 1L << 22;      // bounded mbarrier wait
 
 __host__ __device__ inline int esz_of(int kind) { return kind == 0 ? 2 : 4; }
 
@@ -56,6 +53,8 @@ struct TcArgs {
   const unsigned char* B;   // factor image, npad x npad in the operand format
   int n, npad, ncols;
   long long inner, Q, ntiles;
+  int* status;              // host-mapped status word (kStatusTimeout), may be null
+  long long wait;           // bounded-wait iteration limit
 };
 
 template <int KIND, typename TIn, typename TOut>
@@ -101,6 +100,7 @@ __global__ void __launch_bounds__(kTile) k_tc_mode(TcArgs args) {
   const uint32_t idesc = tc::instr_desc(KIND == 0 ? 1u : 2u, kTile, npad);
   const uint32_t a_addr = tc::smem_u32(sA), b_addr = tc::smem_u32(sB);
   uint32_t phase = 0;
+  int pend = -1;   // thread 0: phase of an MMA commit not yet seen complete
 
   for (long long tile = blockIdx.x; tile < args.ntiles; tile += gridDim.x) {
     const long long q0 = tile * kTile;
@@ -136,14 +136,12 @@ __global__ void __launch_bounds__(kTile) k_tc_mode(TcArgs args) {
       }
       tc::mma_commit(tc::smem_u32(mbar));
     }
-    const bool ok = tc::mbar_wait(tc::smem_u32(mbar), phase, kWaitIters);
-    phase ^= 1u;
+    const bool ok = tc::mbar_wait(tc::smem_u32(mbar), phase, args.wait);
     if (!ok) *sflag = 1;
+    if (tid == 0) pend = ok ? -1 : (int)phase;
+    phase ^= 1u;
     __syncthreads();
-    if (*sflag) {
-      if (tid == 0) atomicExch(&g_tc_status, 1);
-      break;
-    }
+    if (*sflag) break;
     tc::fence_after_sync();
     // ---- epilogue: TMEM row tid -> Y
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
@@ -172,17 +170,15 @@ __global__ void __launch_bounds__(kTile) k_tc_mode(TcArgs args) {
     __syncthreads();
   }
   tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tmem, (uint32_t)args.ncols);
-}
-
-int sm_count_cached() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+  if (tid == 0 && *sflag) {
+    // a wait ran out: report it and let the MMAs in flight finish (bounded)
+    // before tensor memory is released
+    if (args.status) atomicOr(args.status, kStatusTimeout);
+    if (pend >= 0) tc::mbar_wait(tc::smem_u32(mbar), (uint32_t)pend, kDrainIters);
+    tc::fence_after_sync();
   }
-  return sms;
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, (uint32_t)args.ncols);
 }
 
 template <int KIND, typename TIn, typename TOut>
@@ -196,12 +192,9 @@ cudaError_t launch_impl(const TIn* X, TOut* Y, const unsigned char* B, int n, lo
   while (ncols < npad) ncols <<= 1;
   const size_t stage = (inner == 1) ? (((size_t)kTile * (n + 1) * sizeof(float) + 15) & ~(size_t)15) : 0;
   const size_t smem = (size_t)npad * npad * esz + (size_t)kTile * npad * esz + stage + 32;
-  static bool attr_done = false;
-  if (!attr_done) {
-    const cudaError_t e = cudaFuncSetAttribute(k_tc_mode<KIND, TIn, TOut>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  {
+    const cudaError_t e = ensure_smem_attr(k_tc_mode<KIND, TIn, TOut>, 227 * 1024);
     if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   const int by_smem = (int)std::max<size_t>(1, (228 * 1024) / (smem + 1024));
@@ -211,8 +204,8 @@ cudaError_t launch_impl(const TIn* X, TOut* Y, const unsigned char* B, int n, lo
   // memory has columns for (a surplus CTA would block in tcgen05.alloc).
   const size_t smem_req = std::max(smem, (size_t)(228 * 1024) / per_sm - 1024 + 1);
   const long long ntiles = (Q + kTile - 1) / kTile;
-  const long long grid = std::min<long long>(ntiles, (long long)sm_count_cached() * per_sm);
-  TcArgs a{X, Y, B, n, npad, ncols, inner, Q, ntiles};
+  const long long grid = std::min<long long>(ntiles, (long long)sm_count_current() * per_sm);
+  TcArgs a{X, Y, B, n, npad, ncols, inner, Q, ntiles, status_word(), wait_limit()};
   const double flops = 2.0 * (double)Q * n * n;
   const double bytes = (double)Q * n * (sizeof(TIn) + sizeof(TOut));
   ProfScope ps(KIND == 0 ? "tc_mode_bf16" : "tc_mode_tf32", flops, bytes, st);
@@ -260,24 +253,17 @@ cudaError_t launch_tc_mode(int kind, const void* X, int x_is_double, void* Y, in
 namespace {
 // An mbarrier that expects one arrival which never comes: the bounded wait must
 // give up and raise the status flag.
-__global__ void k_probe_bounded_wait(int max_iters) {
+__global__ void k_probe_bounded_wait(int max_iters, int* status) {
   __shared__ uint64_t bar;
   if (threadIdx.x != 0) return;
   tc::mbar_init(tc::smem_u32(&bar), 1);
-  if (!tc::mbar_wait(tc::smem_u32(&bar), 0, max_iters)) atomicExch(&g_tc_status, 1);
+  if (!tc::mbar_wait(tc::smem_u32(&bar), 0, max_iters) && status) atomicOr(status, kStatusTimeout);
 }
 }  // namespace
 
 cudaError_t launch_probe_bounded_wait(int max_iters, cudaStream_t st) {
-  k_probe_bounded_wait<<<1, 32, 0, st>>>(max_iters);
+  k_probe_bounded_wait<<<1, 32, 0, st>>>(max_iters, status_word());
   return cudaGetLastError();
-}
-
-int tc_status_read_and_clear(int* status) {
-  int zero = 0;
-  if (cudaMemcpyFromSymbol(status, g_tc_status, sizeof(int)) != cudaSuccess) return -1;
-  if (cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int)) != cudaSuccess) return -1;
-  return 0;
 }
 
 }  // namespace stfd

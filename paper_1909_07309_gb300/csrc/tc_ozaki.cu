@@ -34,6 +34,7 @@
 #include <cstring>
 #include <vector>
 
+#include "device_state.h"
 #include "df.cuh"
 #include "kernels.h"
 #include "profile.h"
@@ -41,13 +42,10 @@
 
 namespace stfd {
 
-extern __device__ int g_tc_status;
-
 namespace {
 
 constexpr int kTile = 128;
 constexpr int kDig = 6;
-constexpr long kWaitIters = 1L << 22;
 
 __host__ __device__ inline size_t canon_off16(int r, int k, int kcores) {
   return (size_t)(r >> 3) * (kcores * 128) + (size_t)(k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
@@ -60,6 +58,8 @@ struct OzArgs {
   const int* v;             // per output row i: 2^{v_i} scale of J
   int n, npad;
   long long inner, Q, ntiles;
+  int* status;              // host-mapped status word (kStatusTimeout), may be null
+  long long wait;           // bounded-wait iteration limit
 };
 
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b
@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
   const int ksteps = npad / 16;
   const uint64_t da0 = tc::smem_desc(a_addr, 128u, sbo_a), db0 = tc::smem_desc(b_addr, 128u, sbo_b);
   uint32_t ph = 0u, ph_in = 0u;
+  int pend_mma = -1, pend_in = -1;   // thread 0: phases of an MMA commit / bulk load not yet seen complete
   const long long* Xw = static_cast<const long long*>(args.X);
   // mode 1: the tile is one contiguous block of rows x n words in and out, moved
   // by bulk copies when the tensors are 16-byte aligned (the block offsets
@@ -260,7 +261,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
           }
         }
         if (t == 1 && (cnt & 1)) blk[cnt - 1] = __ldg(src + cnt - 1);
-        if (!tc::mbar_wait(tc::smem_u32(&mbar[1]), ph_in, kWaitIters)) *sflag = 1;
+        if (tc::mbar_wait(tc::smem_u32(&mbar[1]), ph_in, args.wait)) {
+          if (t == 0) pend_in = -1;
+        } else {
+          *sflag = 1;
+          if (t == 0) pend_in = (int)ph_in;   // the copy may still be landing: drained below
+        }
         ph_in ^= 1u;
       } else {
         if (bulk_out) {
@@ -270,10 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
         for (int e = t; e < cnt; e += kThreads) blk[e] = __ldg(src + e);
       }
       __syncthreads();
-      if (*sflag) {
-        if (t == 0) atomicExch(&g_tc_status, 1);
-        break;
-      }
+      if (*sflag) break;
 #pragma unroll
       for (int c = 0; c < KC; ++c) {
         const int a = part_col(dp, c);
@@ -345,19 +348,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
           }
         }
       tc::mma_commit(tc::smem_u32(&mbar[0]));
+      pend_mma = (int)ph;
     }
     // ---- the next tile's words travel while the tensor cores work
     if (inner != 1) {
       const long long nt = tile + gridDim.x;
       if (nt < args.ntiles) load_raw<KC>(Xw, nt, drow, dp, n, inner, Q, raw);
     }
-    if (!tc::mbar_wait(tc::smem_u32(&mbar[0]), ph, kWaitIters)) *sflag = 1;
+    if (tc::mbar_wait(tc::smem_u32(&mbar[0]), ph, args.wait)) {
+      if (t == 0) pend_mma = -1;
+    } else {
+      *sflag = 1;
+    }
     ph ^= 1u;
     __syncthreads();
-    if (*sflag) {
-      if (t == 0) atomicExch(&g_tc_status, 1);
-      break;
-    }
+    if (*sflag) break;
     tc::fence_after_sync();
     // ---- epilogue: part p combines the six diagonals of row r on the 4-column
     // chunks p, p+4, ... that hold output columns (i < n)
@@ -426,18 +431,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_ozaki(OzArgs args) {
     __syncthreads();   // the staging area and sE are rewritten by the next tile
   }
   tc::fence_after_sync();
-  if (t == 0) tc::bulk_wait_all();   // the last output block has left shared memory
-  if (warp == 0) tc::tmem_dealloc(tmem, 512);
-}
-
-int sm_count_oz() {
-  static int s = 0;
-  if (s == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s <= 0) s = 148;
+  if (t == 0) {
+    tc::bulk_wait_all();   // the last output block has left shared memory
+    if (*sflag) {
+      // a wait ran out: report it, and let this CTA's own MMAs and bulk loads
+      // still in flight finish (bounded) before tensor memory is released
+      if (args.status) atomicOr(args.status, kStatusTimeout);
+      if (pend_mma >= 0) tc::mbar_wait(tc::smem_u32(&mbar[0]), (uint32_t)pend_mma, kDrainIters);
+      if (pend_in >= 0) tc::mbar_wait(tc::smem_u32(&mbar[1]), (uint32_t)pend_in, kDrainIters);
+      tc::fence_after_sync();
+    }
   }
-  return s;
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
 size_t oz_smem_bytes(int n) {
@@ -454,16 +460,13 @@ cudaError_t launch_oz(const TIn* X, TOut* Y, const unsigned char* B, const int* 
   if (Q <= 0) return cudaSuccess;
   const size_t smem = oz_smem_bytes(n);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  static bool attr_done = false;
-  if (!attr_done) {
-    const cudaError_t e = cudaFuncSetAttribute(k_tc_ozaki<TIn, TOut, KC>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  {
+    const cudaError_t e = ensure_smem_attr(k_tc_ozaki<TIn, TOut, KC>, 227 * 1024);
     if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   const long long ntiles = (Q + kTile - 1) / kTile;
-  const long long grid = std::min<long long>(ntiles, sm_count_oz());
-  OzArgs a{X, Y, B, v, n, (n + 15) / 16 * 16, inner, Q, ntiles};
+  const long long grid = std::min<long long>(ntiles, sm_count_current());
+  OzArgs a{X, Y, B, v, n, (n + 15) / 16 * 16, inner, Q, ntiles, status_word(), wait_limit()};
   ProfScope ps("fd_mode_ozaki", 2.0 * (double)Q * n * n, 8.0 * (double)Q * n * 2, st);
   // 227 KB requested so that exactly one CTA (which owns all 512 TMEM columns) fits per SM
   // programmatic dependent launch: the next kernel's prologue may overlap this one's tail

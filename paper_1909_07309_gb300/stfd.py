@@ -49,6 +49,8 @@ SIGNATURES = {
     "stfd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "stfd_version": (ctypes.c_int, []),
     "stfd_device_status": (ctypes.c_int, []),
+    "stfd_set_wait_limit": (ctypes.c_int, [ctypes.c_longlong]),
+    "stfd_get_wait_limit": (ctypes.c_longlong, []),
     "stfd_spline_matrices": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_int_p]),
     "stfd_spline_load_trig": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,

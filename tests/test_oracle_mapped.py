@@ -271,3 +271,120 @@ def test_spatial_rows_equal_assembled_rows():
         assert np.array_equal(cols, Ms[r].indices[np.argsort(Ms[r].indices)])
         assert np.max(np.abs(mv - Ms[r].toarray()[0, cols])) <= 1e-15
         assert np.max(np.abs(kv - Ks[r].toarray()[0, cols])) <= 1e-14
+
+
+# ---------------------------------------------------------------------------
+# weighted_matrices (eq. over_A) with non-unit, element-dependent weights
+# ---------------------------------------------------------------------------
+
+def _cardinal_element_matrices(p):
+    """Exact element mass and stiffness matrices of the p + 1 uniform (cardinal)
+    B-splines active on one interior element of unit length, from the truncated
+    power form B(x) = (1/p!) sum_k (-1)^k C(p+1, k) (x - k)_+^p (no Cox-de Boor,
+    no quadrature): rational arithmetic, polynomials as coefficient lists."""
+    from fractions import Fraction as Fr
+    from math import comb, factorial
+
+    def pmul(a, b):
+        out = [Fr(0)] * (len(a) + len(b) - 1)
+        for i, x in enumerate(a):
+            for j, y in enumerate(b):
+                out[i + j] += x * y
+        return out
+
+    def ppow_shift(c, e):   # (t + c)^e as coefficients in t
+        return [Fr(comb(e, k)) * Fr(c) ** (e - k) for k in range(e + 1)]
+
+    def piece(j):           # B on [j, j + 1] as a polynomial in t = x - j
+        out = [Fr(0)] * (p + 1)
+        for k in range(j + 1):
+            for i, v in enumerate(ppow_shift(j - k, p)):
+                out[i] += Fr((-1) ** k * comb(p + 1, k), factorial(p)) * v
+        return out
+
+    def deriv(a):
+        return [i * a[i] for i in range(1, len(a))] or [Fr(0)]
+
+    def integ01(a):
+        return sum(c / (i + 1) for i, c in enumerate(a))
+
+    # local function a (0..p) on the element [0, 1] is the translate starting at a - p,
+    # whose piece there is j = p - a
+    P = [piece(p - a) for a in range(p + 1)]
+    D = [deriv(q) for q in P]
+    M = np.array([[float(integ01(pmul(P[a], P[b]))) for b in range(p + 1)] for a in range(p + 1)])
+    K = np.array([[float(integ01(pmul(D[a], D[b]))) for b in range(p + 1)] for a in range(p + 1)])
+    return M, K
+
+
+def test_cardinal_element_matrices_sanity():
+    """p = 1: h/6 [[2, 1], [1, 2]] and 1/h [[1, -1], [-1, 1]] at h = 1; every
+    degree: the element mass matrix sums to 1 (partition of unity), the
+    stiffness rows sum to 0."""
+    M1, K1 = _cardinal_element_matrices(1)
+    np.testing.assert_allclose(M1, np.array([[2, 1], [1, 2]]) / 6.0, rtol=1e-15)
+    np.testing.assert_allclose(K1, np.array([[1, -1], [-1, 1]]), rtol=1e-15)
+    for p in (2, 3, 4):
+        M, K = _cardinal_element_matrices(p)
+        assert abs(M.sum() - 1.0) <= 1e-15 and np.max(np.abs(K.sum(axis=1))) <= 1e-15
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_weighted_matrices_single_element_weight(p):
+    """Weight on one element only (different for mass and stiffness, so that a
+    swap of phi and Phi shows): the reduced M~, K~ are that element's mass and
+    stiffness matrices (cardinal, interior element) times the weight, at the
+    rows and columns of its active functions shifted by the Dirichlet
+    reduction, and zero elsewhere. Every interior element is checked, so a
+    weight read from a neighbouring element fails."""
+    n_el = 2 * p + 6
+    h = 1.0 / n_el
+    Mref, Kref = _cardinal_element_matrices(p)
+    for e in range(p, n_el - p):          # elements whose p + 1 functions are all cardinal
+        wm = np.zeros(n_el)
+        ws = np.zeros(n_el)
+        wm[e], ws[e] = 3.0, 5.0
+        K, M = mapped.weighted_matrices(p, n_el, wm, ws)
+        EM = np.zeros_like(M)
+        EK = np.zeros_like(K)
+        idx = np.arange(e, e + p + 1) - 1   # full-basis functions e .. e + p, minus the dropped b_0
+        EM[np.ix_(idx, idx)] = 3.0 * h * Mref
+        EK[np.ix_(idx, idx)] = 5.0 / h * Kref
+        assert np.max(np.abs(M - EM)) <= 1e-15 * 3.0 * h * 10
+        assert np.max(np.abs(K - EK)) <= 1e-15 * 5.0 / h * 10
+
+
+def test_weighted_matrices_p1_every_element():
+    """p = 1 (hat functions, uniform up to the boundary): every element's weight
+    lands on its own 2 x 2 block of the reduced matrices."""
+    n_el = 7
+    h = 1.0 / n_el
+    w_m = 1.0 + np.arange(n_el)          # distinct weights per element
+    w_s = 10.0 + 3.0 * np.arange(n_el)
+    K, M = mapped.weighted_matrices(1, n_el, w_m, w_s)
+    EM = np.zeros((n_el + 1, n_el + 1))
+    EK = np.zeros((n_el + 1, n_el + 1))
+    for e in range(n_el):
+        EM[e:e + 2, e:e + 2] += w_m[e] * h / 6.0 * np.array([[2, 1], [1, 2]])
+        EK[e:e + 2, e:e + 2] += w_s[e] / h * np.array([[1, -1], [-1, 1]])
+    np.testing.assert_allclose(M, EM[1:-1, 1:-1], rtol=1e-14, atol=1e-16)
+    np.testing.assert_allclose(K, EK[1:-1, 1:-1], rtol=1e-14, atol=1e-16)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_weighted_matrices_row_sums_random_weights(p):
+    """Random weights: for a row i whose support avoids the two dropped boundary
+    functions' columns, sum_j M~_ij = int w b_i = sum_e w_e h int_e b_i (the
+    cardinal pieces integrate to the column sums of the element mass matrix)
+    and sum_j K~_ij = 0."""
+    n_el = 12
+    h = 1.0 / n_el
+    g = np.random.default_rng(7)
+    wm, ws = g.uniform(0.5, 2.0, n_el), g.uniform(0.5, 2.0, n_el)
+    K, M = mapped.weighted_matrices(p, n_el, wm, ws)
+    Mref, _ = _cardinal_element_matrices(p)
+    local_int = Mref.sum(axis=1)          # int_0^1 of local function a (partition of unity)
+    for i_full in range(2 * p, n_el - p):     # rows away from both ends (all elements cardinal)
+        want = sum(wm[e] * h * local_int[i_full - e] for e in range(i_full - p, i_full + 1))
+        assert abs(M[i_full - 1].sum() - want) <= 1e-14
+        assert abs(K[i_full - 1].sum()) <= 1e-12

@@ -4,8 +4,9 @@ stfd_st_matvec_noalloc is for callers that must not allocate device memory
 (a host application that owns all device memory through its own allocator,
 or a latency-critical loop where cudaMalloc would synchronise the device).
 It keeps its scratch in a static device array shared by every call; these
-tests check it against stfd_st_matvec on two calls in a row (the second call
-starts from the first call's leftover scratch) and that oversize problems are
+tests check it against stfd_st_matvec and against the oracle's sum-factorised
+matvec on two calls in a row (the second call starts from the first call's
+leftover scratch) and that oversize problems and overlapping vectors are
 refused. This file is collected last so that a failure here cannot hide one
 elsewhere.
 """
@@ -14,6 +15,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from oracle import kron as okron, matrices as omat
 from paper_1909_07309_gb300 import inputs, stfd
 
 pytestmark = pytest.mark.gpu
@@ -43,8 +45,11 @@ def test_noalloc_matvec_matches_st_matvec_twice(d, p, n_el, gamma, nu):
     Kd, Md = [_dev_colmajor(k) for k in K], [_dev_colmajor(m) for m in M]
     Wd, Mtd = _dev_colmajor(Wt), _dev_colmajor(Mt)
     bw = [p] * (d + 1)
+    sm = [omat.space_matrices(p, n_el) for _ in range(d)]
+    oWt, oMt = omat.time_matrices(p, n_el)
     for seed in (31, 32):                       # two calls in a row
-        x = torch.as_tensor(inputs.standard_normal(A.N, seed), device="cuda")
+        x_np = inputs.standard_normal(A.N, seed)
+        x = torch.as_tensor(x_np, device="cuda")
         y = torch.full_like(x, float("nan"))
         rc = _noalloc(lib, A.n, Kd, Md, Wd, Mtd, bw, gamma, nu, x, y)
         assert rc == 0, stfd._strerror(rc)
@@ -52,6 +57,10 @@ def test_noalloc_matvec_matches_st_matvec_twice(d, p, n_el, gamma, nu):
         torch.cuda.synchronize()
         err = float(torch.max(torch.abs(y - ref)) / torch.max(torch.abs(ref)))
         assert err <= 1e-13, err
+        # and the oracle (plain CPU FP64), element by element
+        ref_o = okron.st_matvec(x_np, [k for k, _ in sm], [m for _, m in sm], oWt, oMt, gamma, nu)
+        y_np = y.cpu().numpy()
+        assert np.max(np.abs(y_np - ref_o)) <= 1e-13 * np.max(np.abs(ref_o))
 
 
 def test_noalloc_dense_band_and_size_limit():
@@ -69,3 +78,25 @@ def test_noalloc_dense_band_and_size_limit():
     big = [256, 256, 9]                          # N = 589,824 > STFD_NOALLOC_MAX_N
     assert _noalloc(lib, big, [Kd[0], Kd[0]], [Md[0], Md[0]], Wd, Mtd, [2, 2, 2], 1.0, 1.0, x, y) == -1
     assert _noalloc(lib, A.n, Kd, Md, Wd, Mtd, [2, 2, 2], 1.0, 1.0, x, x) == -1  # aliasing
+    both = torch.zeros(2 * A.N, dtype=torch.float64, device="cuda")
+    assert _noalloc(lib, A.n, Kd, Md, Wd, Mtd, [2, 2, 2], 1.0, 1.0, both[:A.N], both[A.N // 2:A.N // 2 + A.N]) == -1
+    assert _noalloc(lib, A.n, Kd, Md, Wd, Mtd, [2, 2, 2], 1.0, 1.0, both[A.N:], both[:A.N]) == 0  # adjacent: fine
+
+
+@pytest.mark.skipif(not torch.cuda.is_available() or torch.cuda.device_count() < 2,
+                    reason="needs two visible GPUs")
+def test_noalloc_second_device():
+    """The shared-memory attribute and the scratch address are per device: a
+    dense-band call (the largest shared-memory request) works on device 1 after
+    device 0 has been used."""
+    lib = stfd.load()
+    K, M, Wt, Mt = stfd.heat_problem(1, 2, 150)
+    for devno in (0, 1):
+        with torch.cuda.device(devno):
+            Kd, Md = [_dev_colmajor(k).to(devno) for k in K], [_dev_colmajor(m).to(devno) for m in M]
+            Wd, Mtd = _dev_colmajor(Wt).to(devno), _dev_colmajor(Mt).to(devno)
+            n = [K[0].shape[0], Wt.shape[0]]
+            x = torch.as_tensor(inputs.standard_normal(n[0] * n[1], 3), device="cuda:%d" % devno)
+            y = torch.empty_like(x)
+            assert _noalloc(lib, n, Kd, Md, Wd, Mtd, [-1, -1], 1.0, 1.0, x, y) == 0
+            torch.cuda.synchronize()
