@@ -37,7 +37,13 @@ L2_BYTES = 129 * 2 ** 20
 # DRAM bytes per launch from one ncu capture at the workload (profiles/): the
 # mean over the 8 mode products of one fd_apply, and over the 4 band passes of
 # one st_matvec; None once a kernel changes until it is captured again.
-NCU_TRAFFIC = {"fd_mode_ozaki": 237753728, "band_pair_df": 457856384}
+NCU_TRAFFIC = {}
+
+# Arithmetic of the headline solve: IEEE FP64 throughout (Algorithm 1 with FP64
+# mode products and an FP64 Step 3, the FP64 banded matvec, FP64 GMRES).
+HEADLINE = dict(precond="STFD_FP64", matvec="STFD_OP_FP64", dtype="f64",
+                precond_text="Algorithm 1 in IEEE FP64: mode products and Step 3 on the FP64 pipe",
+                matvec_text="IEEE FP64 sum-factorised banded products (FP64 pipe)")
 
 
 def measured_peaks():
@@ -460,10 +466,9 @@ def main():
     cfg = inputs.SCALE
     K, M, Wt, Mt, f_np = build_workload(cfg)
     t_setup = time.perf_counter()
-    # FP64-accurate solve: Algorithm 1 with tensor-core digit-sliced mode products
-    # (STFD_FP64TC) and the double-float matvec on the FP32 pipes
-    A = stfd.KronOp(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], arith=stfd.STFD_OP_DF32)
-    P = stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=stfd.STFD_FP64TC)
+    A = stfd.KronOp(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], arith=getattr(stfd, HEADLINE["matvec"]))
+    P = stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=getattr(stfd, HEADLINE["precond"]))
+    head_prec = getattr(stfd, HEADLINE["precond"])
     setup_ms = (time.perf_counter() - t_setup) * 1e3
     N = P.N
     f = torch.from_numpy(f_np).cuda()
@@ -572,10 +577,16 @@ def main():
 
     # ---- preconditioner variants inside the same FP64 flexible GMRES
     variants = {}
-    A64 = stfd.KronOp(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], arith=stfd.STFD_OP_FP64)
-    for name, prec, op in (("fp64tc", stfd.STFD_FP64TC, A), ("df32", stfd.STFD_DF32, A),
-                           ("fp64_ieee", stfd.STFD_FP64, A64), ("tf32", stfd.STFD_TF32, A), ("bf16", stfd.STFD_BF16, A)):
-        Pv = P if prec == stfd.STFD_FP64TC else stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=prec)
+    A64 = A if HEADLINE["matvec"] == "STFD_OP_FP64" else \
+        stfd.KronOp(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], arith=stfd.STFD_OP_FP64)
+    Adf = stfd.KronOp(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], arith=stfd.STFD_OP_DF32)
+    vlist = [("fp64_ieee", stfd.STFD_FP64, A64)]
+    if hasattr(stfd, "STFD_FP64TC7"):
+        vlist.append(("fp64tc7", stfd.STFD_FP64TC7, A64))
+    vlist += [("fp64tc48_df32mv", stfd.STFD_FP64TC, Adf), ("df32_df32mv", stfd.STFD_DF32, Adf),
+              ("tf32", stfd.STFD_TF32, A64), ("bf16", stfd.STFD_BF16, A64)]
+    for name, prec, op in vlist:
+        Pv = P if prec == head_prec else stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=prec)
         for _ in range(3):
             Pv.apply(r, s)
         torch.cuda.synchronize()
@@ -595,12 +606,14 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         v_gm = e0.elapsed_time(e1) / args.steps
-        variants[name] = {"precond": name, "matvec": "fp64_ieee" if op is A64 else "df32",
+        variants[name] = {"precond": name, "matvec": "fp64_ieee" if op is A64 else "df32 (2 x FP32, ~48-bit)",
                           "fd_apply_ms": v_fd, "fd_apply_dofs_per_s": N / (v_fd * 1e-3), "gmres_ms": v_gm,
                           "gmres_iters": vinfo["iters"], "rel_res_true": vinfo["rel_res_true"], "_s": s_v}
         if Pv is not P:
             Pv.close()
-    A64.close()
+    if A64 is not A:
+        A64.close()
+    Adf.close()
     ref_s = variants["fp64_ieee"]["_s"]
     for name in variants:
         sv = variants[name].pop("_s")
@@ -665,14 +678,12 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "df32", "data": "synthetic",
+        "vs_baseline": None, "dtype": HEADLINE["dtype"], "data": "synthetic",
         "config": {"workload": cfg["name"], "N": N, "solve": "FD-preconditioned flexible GMRES to 1e-8, x0 = 0",
                    "restart": args.restart, "gmres_iters": infos[-1]["iters"],
                    "rel_res_true": infos[-1]["rel_res_true"],
-                   "precond": "Algorithm 1, FP64-accurate: mode products on tcgen05 via exact BF16 digit slices "
-                              "(6 signed round-to-nearest digits per entry, exact FP32 accumulation of the 21 digit pairs, "
-                              "double-float recombination), Step 3 double-float",
-                   "matvec": "double-float (2 x FP32, ~48-bit), FP64 in/out", "gmres": "FP64",
+                   "precond": HEADLINE["precond_text"], "matvec": HEADLINE["matvec_text"],
+                   "gmres": "FP64 (CGS2, residuals, norms)",
                    "setup_ms": setup_ms,
                    "l2": "inputs larger than L2 (working set %.2f GB > 129 MB)" % (10 * N * 8 / 1e9),
                    "parallelism": "replicas x%d" % world},

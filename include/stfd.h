@@ -57,13 +57,21 @@ enum {
  * FP32 intermediates and an FP32 Step 3; input and output vectors stay FP64.
  * The low-precision preconditioner is meant for flexible GMRES, which keeps
  * the outer iteration, the system matvec and the residual in FP64. */
-enum { STFD_FP64 = 0, STFD_TF32 = 1, STFD_BF16 = 2, STFD_DF32 = 3, STFD_FP64TC = 4 };
-/* STFD_FP64TC: FP64-accurate Algorithm 1 with the mode products on the tcgen05
- * tensor cores: each row of the tensor and of the factor is split exactly into
- * six signed 8-bit digits under its own power of two, digit products run as
- * BF16 MMAs with FP32 accumulation (exact for the leading diagonals), and the
- * partial sums are recombined in double-float arithmetic; Step 3 in double-float.
- * Requires every n[l] <= 80. Agrees with STFD_FP64 to about 1e-13. */
+enum { STFD_FP64 = 0, STFD_TF32 = 1, STFD_BF16 = 2, STFD_DF32 = 3, STFD_FP64TC = 4, STFD_FP64TC7 = 5 };
+/* STFD_FP64TC7: FP64 Algorithm 1 with the mode products on the tcgen05 tensor
+ * cores, no narrower than IEEE FP64. Each row of the tensor and of the factor
+ * is written under its own power of two as a 55-bit integer (exact for entries
+ * within a factor 4 of the row maximum, rounded at 2^-55 of the row scale for
+ * the others) and cut exactly into seven signed 8-bit digits; the 28 digit
+ * pairs that reach 2^-48 of the row scales run as BF16 MMAs whose FP32
+ * accumulators are exact, the partial sums are combined in 64-bit integers and
+ * rounded once to FP64. Intermediates between the mode products are FP64, and
+ * Step 3 is IEEE FP64. The dropped digit pairs are below 2^-44 of
+ * n max|row of X| max|row of U|, under the worst-case rounding error of an FP64
+ * dot product of length n. Requires every n[l] <= 80.
+ * STFD_FP64TC: the same on six digits (21 pairs, about 48 significant bits),
+ * partial sums recombined in double-float, double-float intermediates and
+ * Step 3. Requires every n[l] <= 80. Agrees with STFD_FP64 to about 1e-13. */
 /* STFD_DF32: FP64-accurate Algorithm 1 in double-float arithmetic on the FP32
  * pipes (every value an unevaluated pair hi + lo of floats, about 48
  * significant bits; products split exactly by FMA, sums by error-free
@@ -149,7 +157,8 @@ int stfd_fd_factors(int d, const int* n, const double* const* K, const double* c
 /* ------------------------------------------------------------------------
  * Preconditioner handle (Algorithm 1). d in {1, 2, 3}, 1 <= n[l] <= 256,
  * 2 <= n_t <= 256, gamma > 0, nu > 0, precision one of STFD_FP64 / STFD_TF32 /
- * STFD_BF16 (low precision: n[l] <= 128). The factorisation runs on the host;
+ * STFD_BF16 / STFD_DF32 / STFD_FP64TC / STFD_FP64TC7 (low precision: n[l] <= 128;
+ * digit-sliced: n[l] <= 80). The factorisation runs on the host;
  * factors are uploaded on `stream` and the call synchronises that stream
  * before returning. Device memory held: the factors, one N-vector of
  * scratch and N_s Schur-complement reciprocals.

@@ -79,6 +79,10 @@ struct stfd_fd {
   double* g = nullptr;
   double* Sinv = nullptr;
   double* work = nullptr;
+  // FP64 Step 3 (STFD_FP64, STFD_FP64TC7): complex reciprocals w_jk, about one
+  // N-vector (n_pairs x N_s double2), and G = gamma g
+  double2* wtab = nullptr;
+  double* Gg = nullptr;
   int n_pairs = 0, has_zero = 0;
   double sigma = 0.0;
   // low-precision path (STFD_TF32 / STFD_BF16): operand images of U^T / U and FP32 copies
@@ -97,6 +101,7 @@ struct stfd_fd {
   float2* G2 = nullptr;
   float2* Sinv2 = nullptr;
   // tensor-core FP64-accurate path (STFD_FP64TC): digit planes and row scales of U^T / U
+  // (STFD_FP64TC7: seven-digit planes and row exponents, same fields)
   unsigned char* Zf[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};
   unsigned char* Zb[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};
   int* zvf[kMaxDim + 1] = {nullptr, nullptr, nullptr, nullptr};
@@ -198,6 +203,8 @@ extern "C" void stfd_fd_destroy(stfd_fd* h) {
   dev_free(h->g);
   dev_free(h->Sinv);
   dev_free(h->work);
+  dev_free(h->wtab);
+  dev_free(h->Gg);
   for (int l = 0; l <= kMaxDim; ++l) {
     dev_free(h->Bf[l]);
     dev_free(h->Bb[l]);
@@ -234,11 +241,14 @@ extern "C" int stfd_fd_setup(stfd_fd** out, int d, const int* n, const double* c
   if (!sizes_ok(d, n) || !K || !M || !Wt || !Mt) return STFD_ERR_ARG;
   if (!(gamma > 0.0) || !(nu > 0.0) || !std::isfinite(gamma) || !std::isfinite(nu)) return STFD_ERR_ARG;
   if (precision != STFD_FP64 && precision != STFD_TF32 && precision != STFD_BF16 && precision != STFD_DF32 &&
-      precision != STFD_FP64TC)
+      precision != STFD_FP64TC && precision != STFD_FP64TC7)
     return STFD_ERR_ARG;
   if (precision == STFD_FP64TC)
     for (int l = 0; l <= d; ++l)
       if (n[l] > ozaki_max_n()) return STFD_ERR_ARG;
+  if (precision == STFD_FP64TC7)
+    for (int l = 0; l <= d; ++l)
+      if (n[l] > oz7_max_n()) return STFD_ERR_ARG;
   if (precision == STFD_TF32 || precision == STFD_BF16)
     for (int l = 0; l <= d; ++l)
       if (n[l] > 128) return STFD_ERR_ARG;   // factor + tile + staging must fit in shared memory
@@ -290,6 +300,32 @@ extern "C" int stfd_fd_setup(stfd_fd** out, int d, const int* n, const double* c
   if (rc == STFD_OK && f.n_pairs > 0) rc = dev_upload(&h->lamt, f.lamt.data(), f.lamt.size(), st);
   if (rc == STFD_OK) rc = dev_upload(&h->g, f.g.data(), f.g.size(), st);
   if (rc == STFD_OK) rc = dev_upload<double>(&h->work, nullptr, (size_t)h->N, st);
+  std::vector<double> G(f.g.size());   // alive until the stream is synchronised below
+  if (rc == STFD_OK && (precision == STFD_FP64 || precision == STFD_FP64TC7)) {
+    for (size_t j = 0; j < f.g.size(); ++j) G[j] = gamma * f.g[j];
+    rc = dev_upload(&h->Gg, G.data(), G.size(), st);
+    if (rc == STFD_OK && f.n_pairs > 0) {
+      rc = dev_upload<double2>(&h->wtab, nullptr, (size_t)f.n_pairs * (size_t)h->Ns, st);
+      if (rc == STFD_OK) {
+        ArrowParams ap;
+        ap.d = d;
+        ap.n1 = n[0];
+        ap.n2 = d >= 2 ? n[1] : 1;
+        ap.nt = n[d];
+        ap.n_pairs = f.n_pairs;
+        ap.has_zero = f.has_zero;
+        ap.Ns = h->Ns;
+        for (int l = 0; l < 3; ++l) ap.lam[l] = l < d ? h->lam[l] : nullptr;
+        ap.lamt = h->lamt;
+        ap.g = h->g;
+        ap.Sinv = h->Sinv;
+        ap.gamma = gamma;
+        ap.nu = nu;
+        ap.sgn = 1.0;
+        if (launch_arrow_wtab(h->wtab, ap, st) != cudaSuccess) rc = STFD_ERR_CUDA;
+      }
+    }
+  }
   // low precision: operand images and FP32 copies (kept alive in `keep` until the sync)
   std::vector<std::vector<float>> keepf;
   std::vector<std::vector<unsigned char>> keepb;
@@ -304,11 +340,16 @@ extern "C" int stfd_fd_setup(stfd_fd** out, int d, const int* n, const double* c
   };
   std::vector<std::vector<unsigned char>> keepz;
   std::vector<std::vector<int>> keepv;
-  if (rc == STFD_OK && precision == STFD_FP64TC) {
+  if (rc == STFD_OK && (precision == STFD_FP64TC || precision == STFD_FP64TC7)) {
     for (int l = 0; l <= d && rc == STFD_OK; ++l) {
       for (int dir = 0; dir < 2 && rc == STFD_OK; ++dir) {
         keepv.emplace_back();
-        keepz.push_back(ozaki_planes(keep[2 * l + dir].data(), n[l], keepv.back()));
+        const double* J = keep[2 * l + dir].data();
+        for (size_t k = 0; k < (size_t)n[l] * n[l]; ++k)
+          if (!std::isfinite(J[k])) rc = STFD_ERR_EIG;
+        if (rc != STFD_OK) break;
+        keepz.push_back(precision == STFD_FP64TC ? ozaki_planes(J, n[l], keepv.back())
+                                                 : oz7_planes(J, n[l], keepv.back()));
         rc = dev_upload(dir == 0 ? &h->Zf[l] : &h->Zb[l], keepz.back().data(), keepz.back().size(), st);
         if (rc == STFD_OK) rc = dev_upload(dir == 0 ? &h->zvf[l] : &h->zvb[l], keepv.back().data(), keepv.back().size(), st);
       }
@@ -474,18 +515,27 @@ int fd_apply_one_df(const stfd_fd* h, const double* r, double* s, double* work, 
 // which in the real 2 x 2-block form flips the signs of lambda_j and g.
 int fd_apply_core(const stfd_fd* h, const double* r, double* s, double* work, int trans, cudaStream_t st) {
   if (h->precision == STFD_DF32 || h->precision == STFD_FP64TC) return fd_apply_one_df(h, r, s, work, trans, st);
-  if (h->precision != STFD_FP64) return fd_apply_one_lowp(h, r, s, work, trans, st);
+  if (h->precision != STFD_FP64 && h->precision != STFD_FP64TC7) return fd_apply_one_lowp(h, r, s, work, trans, st);
   const int d = h->d;
   const int P = 2 * (d + 1);
   auto buf = [&](int k) { return ((P - k) % 2 == 0) ? s : work; };   // pass k writes buf(k), buf(P) = s
   const double* src = r;
   int pass = 0;
+  // FP64 mode products: on the FP64 pipe, or on the tensor cores by seven exact
+  // digit slices per entry (STFD_FP64TC7); both FP64 in and out
+  const bool tc7 = h->precision == STFD_FP64TC7;
+  auto mode = [&](const double* X, int l, bool fwd, double* Y, long long inner, long long outer) {
+    if (tc7)
+      return launch_fd_mode_tc7(X, fwd ? h->Zf[l] : h->Zb[l], fwd ? h->zvf[l] : h->zvb[l], Y, h->n[l], inner, outer,
+                                st);
+    return launch_fd_mode_fp64(X, fwd ? h->Jf[l] : h->Jb[l], Y, h->n[l], inner, outer, st);
+  };
   // Step 2: X x_1 U_1^T ... x_d U_d^T x_{d+1} U_t^T
   long long inner = 1;
   for (int l = 0; l <= d; ++l) {
     const long long outer = h->N / (inner * h->n[l]);
     double* dst = buf(++pass);
-    STFD_CU(launch_fd_mode_fp64(src, h->Jf[l], dst, h->n[l], inner, outer, st));
+    STFD_CU(mode(src, l, true, dst, inner, outer));
     src = dst;
     inner *= h->n[l];
   }
@@ -505,13 +555,17 @@ int fd_apply_core(const stfd_fd* h, const double* r, double* s, double* work, in
   ap.gamma = h->gamma;
   ap.nu = h->nu;
   ap.sgn = trans ? -1.0 : 1.0;
-  STFD_CU(launch_arrowhead_fp64(const_cast<double*>(src), ap, st));
+  if (h->Gg && (h->wtab || h->n_pairs == 0)) {
+    STFD_CU(launch_arrowhead_fp64_tab(const_cast<double*>(src), ap, h->wtab, h->Gg, st));
+  } else {
+    STFD_CU(launch_arrowhead_fp64(const_cast<double*>(src), ap, st));
+  }
   // Step 4: x_{d+1} U_t, then x_d U_d ... x_1 U_1
   for (int l = d; l >= 0; --l) {
     inner /= h->n[l];
     const long long outer = h->N / (inner * h->n[l]);
     double* dst = buf(++pass);
-    STFD_CU(launch_fd_mode_fp64(src, h->Jb[l], dst, h->n[l], inner, outer, st));
+    STFD_CU(mode(src, l, false, dst, inner, outer));
     src = dst;
   }
   return STFD_OK;

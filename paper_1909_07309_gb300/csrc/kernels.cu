@@ -108,6 +108,82 @@ __global__ void k_arrowhead(T* __restrict__ X, ArrowParamsT<T> p) {
   }
 }
 
+// Table of Step 3 (FP64, once per handle): for every pair j and spatial index
+// k, w_jk = (a_k + i b_j) / (a_k^2 + b_j^2) with a_k = nu mu_k and b_j = gamma
+// lam_j, so that H_j^{-1} x_j is the complex product w_jk z_j, z_j = x_2j + i
+// x_2j+1 (the 2 x 2 blocks of the Remark in Sec. 4.5). Stored [j][k].
+__global__ void k_arrow_wtab(double2* __restrict__ W, ArrowParamsT<double> p) {
+  const long long total = p.Ns * (long long)p.n_pairs;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / p.Ns);
+    const long long k = idx - (long long)j * p.Ns;
+    long long rest = k;
+    const int i1 = (int)(rest % p.n1);
+    rest /= p.n1;
+    double mu = p.lam[0][i1];
+    if (p.d >= 2) {
+      const int i2 = (int)(rest % p.n2);
+      rest /= p.n2;
+      mu += p.lam[1][i2];
+    }
+    if (p.d >= 3) mu += p.lam[2][rest];
+    const double a = p.nu * mu, b = p.gamma * p.lamt[j];
+    const double inv = 1.0 / fma(a, a, b * b);
+    W[idx] = make_double2(a * inv, b * inv);
+  }
+}
+
+// FP64 Step 3 with the table above: per pair and index 12 FP64 operations
+// (pass 1: h_j = w z_j and y += G_j . h_j; pass 2: q_j = w (z_j - G_j q_n)).
+// The transposed system (sgn = -1) flips b_j and G_j: w's imaginary part and
+// G change sign (sign-bit flips, no arithmetic).
+__global__ void k_arrowhead_f64(double* __restrict__ X, ArrowParamsT<double> p, const double2* __restrict__ W,
+                                const double* __restrict__ G) {
+  const long long Ns = p.Ns;
+  const unsigned long long flip = p.sgn < 0.0 ? 0x8000000000000000ull : 0ull;
+  auto fl = [&](double v) { return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(v) ^ flip)); };
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < Ns;
+       k += (long long)gridDim.x * blockDim.x) {
+    double y = X[(long long)(p.nt - 1) * Ns + k];
+    for (int j = 0; j < p.n_pairs; ++j) {
+      const double x1 = X[(long long)(2 * j) * Ns + k], x2 = X[(long long)(2 * j + 1) * Ns + k];
+      const double2 w = W[(long long)j * Ns + k];
+      const double wi = fl(w.y);
+      const double h1 = fma(w.x, x1, -wi * x2), h2 = fma(wi, x1, w.x * x2);
+      y = fma(fl(G[2 * j]), h1, fma(fl(G[2 * j + 1]), h2, y));
+    }
+    const int z = 2 * p.n_pairs;
+    double x0 = 0.0, a = 1.0;
+    if (p.has_zero) {
+      long long rest = k;
+      const int i1 = (int)(rest % p.n1);
+      rest /= p.n1;
+      double mu = p.lam[0][i1];
+      if (p.d >= 2) {
+        const int i2 = (int)(rest % p.n2);
+        rest /= p.n2;
+        mu += p.lam[1][i2];
+      }
+      if (p.d >= 3) mu += p.lam[2][rest];
+      a = p.nu * mu;
+      x0 = X[(long long)z * Ns + k];
+      y = fma(fl(G[z]), x0 / a, y);
+    }
+    const double qn = y * p.Sinv[k];
+    X[(long long)(p.nt - 1) * Ns + k] = qn;
+    for (int j = 0; j < p.n_pairs; ++j) {
+      const long long o1 = (long long)(2 * j) * Ns + k, o2 = (long long)(2 * j + 1) * Ns + k;
+      const double2 w = W[(long long)j * Ns + k];
+      const double wi = fl(w.y);
+      const double r1 = fma(-fl(G[2 * j]), qn, X[o1]), r2 = fma(-fl(G[2 * j + 1]), qn, X[o2]);
+      X[o1] = fma(w.x, r1, -wi * r2);
+      X[o2] = fma(wi, r1, w.x * r2);
+    }
+    if (p.has_zero) X[(long long)z * Ns + k] = fma(-fl(G[z]), qn, x0) / a;
+  }
+}
+
 constexpr int kDotThreads = 256;
 constexpr int kDotGroup = 4;
 
@@ -395,6 +471,22 @@ cudaError_t launch_arrowhead_fp64(double* X, const ArrowParams& p, cudaStream_t 
   if (p.Ns <= 0) return cudaSuccess;
   ProfScope ps("arrowhead_fp64", (double)p.Ns * (10.0 * p.n_pairs + 4.0), 16.0 * (double)p.Ns * p.nt, st);
   k_arrowhead<double><<<grid_for(p.Ns, 256), 256, 0, st>>>(X, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_arrow_wtab(double2* W, const ArrowParams& p, cudaStream_t st) {
+  if (p.Ns <= 0 || p.n_pairs <= 0) return cudaSuccess;
+  count_launch();
+  k_arrow_wtab<<<grid_for(p.Ns * p.n_pairs, 256), 256, 0, st>>>(W, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_arrowhead_fp64_tab(double* X, const ArrowParams& p, const double2* W, const double* G,
+                                      cudaStream_t st) {
+  if (p.Ns <= 0) return cudaSuccess;
+  ProfScope ps("arrowhead_fp64", (double)p.Ns * (12.0 * p.n_pairs + 4.0),
+               16.0 * (double)p.Ns * p.nt + 16.0 * (double)p.Ns * p.n_pairs, st);
+  k_arrowhead_f64<<<grid_for(p.Ns, 128), 128, 0, st>>>(X, p, W, G);
   return cudaGetLastError();
 }
 

@@ -36,6 +36,11 @@ struct ArrowParamsT {
 };
 using ArrowParams = ArrowParamsT<double>;
 cudaError_t launch_arrowhead_fp64(double* X, const ArrowParams& p, cudaStream_t st);
+// FP64 Step 3 with the per-(pair, index) complex reciprocals W[j][k] of
+// launch_arrow_wtab (n_pairs x Ns double2, set-up) and G = gamma g (nt - 1).
+cudaError_t launch_arrow_wtab(double2* W, const ArrowParams& p, cudaStream_t st);
+cudaError_t launch_arrowhead_fp64_tab(double* X, const ArrowParams& p, const double2* W, const double* G,
+                                      cudaStream_t st);
 // FP32 variant for the mixed-precision preconditioner
 cudaError_t launch_arrowhead_fp32(float* X, const ArrowParamsT<float>& p, cudaStream_t st);
 
@@ -121,6 +126,13 @@ cudaError_t launch_fd_mode_ozaki(const void* X, int x_is_double, const unsigned 
                                  int y_is_double, int n, long long inner, long long outer, cudaStream_t st);
 std::vector<unsigned char> ozaki_planes(const double* J, int n, std::vector<int>& v);
 int ozaki_max_n();
+
+// FP64 mode product on tcgen05 by seven exact BF16 digit slices per entry
+// (tc_oz7.cu): X and Y FP64 (Y must not alias X); B / ej from oz7_planes.
+cudaError_t launch_fd_mode_tc7(const double* X, const unsigned char* B, const int* ej, double* Y, int n,
+                               long long inner, long long outer, cudaStream_t st);
+std::vector<unsigned char> oz7_planes(const double* J, int n, std::vector<int>& ej);
+int oz7_max_n();
 
 int dot_blocks();
 

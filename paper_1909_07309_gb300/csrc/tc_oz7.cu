@@ -1,0 +1,450 @@
+// FP64 mode products of Algorithm 1 (Steps 2 and 4) on the tcgen05 tensor
+// cores, no narrower than IEEE FP64: Y[q][i] = sum_a X[q][a] J[i][a] with FP64
+// input and output, by exact digit slicing (the error-free splitting of Ozaki,
+// Ogita, Oishi and Rump) with seven 8-bit digits per entry.
+//
+// Every row of X (and of J) is written under its own power of two as a 55-bit
+// integer: with E the largest biased exponent of the row, an entry of biased
+// exponent e and 53-bit significand m becomes V = round(m 2^{2 - (E - e)}),
+// exact for the entries within a factor 4 of the row maximum and rounded at
+// 2^-55 of the row scale for the others. V is cut into seven signed digits,
+//     V = sum_{k<7} d_k 256^{6-k},   d_k in [-128, 127] (d_0 in [-128, 129]),
+// read off the bytes of V + 0x80808080808080 (each byte minus 128): integers of
+// at most 8 significant bits, exact in BF16, whose products are exact in FP32.
+// With T_c = sum_{k+l=c} sum_a dx_k[q][a] dj_l[i][a] (c <= 6, 28 digit pairs),
+//     Y[q][i] ~ 2^{Ex_q + Ej_i - 2106} Z,   Z = sum_{c<=6} T_c 256^{6-c},
+// and the pairs dropped (c >= 7) sum to at most 6 n 129^2 256^5 in units where
+// the kept sum is up to n 2^110: below 2^-44 of n max|X| max|J| -- under the
+// error bound n u sum|X||J| of an IEEE FP64 dot product, and about the size
+// of one FP64 rounding of a typical entry. Each T_c is accumulated exactly in
+// its own FP32 tensor-memory accumulator (|T_c| <= 7 n 129^2 < 2^24 for
+// n <= 144); the seven are converted to integers, Z is formed exactly in two
+// 64-bit limbs and rounded once, to nearest even, to the FP64 result.
+//
+// Tile: M = 128 tensor rows q (R = 112 of them valid when n > 64, so that the
+// seven digit planes of the tile and of J fit in shared memory; the MMA's
+// rows 112..127 read the next plane and are ignored), K = N = n rounded up to
+// 16. Tensor memory holds the seven accumulators of 32 output columns at a time
+// (224 columns), double-buffered: the MMAs of output chunk j + 1 run while the
+// epilogue of chunk j reads its accumulators and writes FP64 results, and the
+// MMAs of chunk j + 2 are issued as soon as chunk j's accumulators are read.
+// One persistent 512-thread CTA per SM; the next tile's entries are loaded into
+// registers while the MMAs run.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "device_state.h"
+#include "kernels.h"
+#include "profile.h"
+#include "tc_common.cuh"
+
+namespace stfd {
+namespace {
+
+constexpr int kDig = 7;
+constexpr int kThreads = 512;
+constexpr int kParts = 4;
+constexpr int kChunk = 32;                 // output columns per tensor-memory buffer
+constexpr int kBufCols = kDig * kChunk;    // 224 columns per buffer
+constexpr unsigned long long kByteBias = 0x80808080808080ull;
+
+struct Oz7Args {
+  const double* X;
+  double* Y;
+  const unsigned char* B;   // digit planes of J, chunk-stacked (see oz7_planes)
+  const int* ej;            // per output column i: largest biased exponent of row i of J
+  int n, npad, R, nchunk;
+  long long inner, Q, ntiles;
+  int* status;
+  long long wait;
+};
+
+// Column of the c-th entry held by digit-phase part p (pairs 4m + p: conflict-free
+// 32-bit digit stores, as in the six-digit kernel).
+__device__ __forceinline__ int part_col(int p, int c) { return 8 * (c >> 1) + 2 * p + (c & 1); }
+
+__host__ __device__ inline uint32_t a_sbo(int kcores) { return (uint32_t)kcores * 128u + 16u; }
+
+__host__ __device__ inline size_t canon_off16(int r, int k, int kcores, uint32_t sbo) {
+  return (size_t)(r >> 3) * sbo + (size_t)(k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+// Largest of 1 and the biased exponent of an FP64 bit pattern.
+__device__ __forceinline__ int bexp(long long w) {
+  return max(1, (int)(((unsigned long long)w >> 52) & 0x7FF));
+}
+
+// The seven digits of one entry (bit pattern w) of a row whose largest biased
+// exponent is E, as floats (small integers, exact in BF16). Branch-free:
+// V = round(4 m 2^-s) with s = E - max(e, 1) >= 0 (exact for s <= 2).
+__device__ __forceinline__ void digits7(long long w, int E, float* d) {
+  const unsigned long long u = (unsigned long long)w;
+  const int e = (int)((u >> 52) & 0x7FF);
+  const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(e != 0) << 52);
+  const int s = min(E - max(e, 1), 63);
+  const unsigned long long V = ((m << 2) + ((1ull << s) >> 1)) >> s;
+  const unsigned long long W = V + kByteBias;
+  const float sg = (u >> 63) ? -1.0f : 1.0f;
+  const float off = -(8388608.0f + 128.0f) * sg;
+  const uint32_t lo = (uint32_t)W, hi = (uint32_t)(W >> 32);
+  // bytes of W from the top: d_0 = W >> 48 (up to 9 bits), then bytes 5 .. 0
+  const uint32_t b[kDig] = {hi >> 16, (hi >> 8) & 0xFFu, hi & 0xFFu, lo >> 24, (lo >> 16) & 0xFFu,
+                            (lo >> 8) & 0xFFu, lo & 0xFFu};
+#pragma unroll
+  for (int k = 0; k < kDig; ++k) d[k] = fmaf(__uint_as_float(0x4B000000u | b[k]), sg, off);   // (b - 128) sg
+}
+
+// Rare cases of combine7: |Z| below 2^24, or a result outside the normal range.
+__device__ __noinline__ double combine7_slow(long long zh, long long zl, int SE) {
+  // Z = zh 2^24 + zl exactly, |Z| < 2^75: two exact FP64 terms, one rounding
+  const double hi = (double)zh * 16777216.0, lo = (double)zl;
+  return scalbn(hi + lo, SE);
+}
+
+// Z = sum_c T_c 256^{6-c} (exact) rounded to nearest even, times 2^SE, as FP64.
+// Z is formed exactly as zh 2^24 + zl in two 64-bit words; its magnitude
+// Mt 2^24 + mr (0 <= mr < 2^24) is normalised as a 128-bit value, the leading
+// 53 bits rounded once (round, guard and sticky bits), and the FP64 bit pattern
+// assembled with integer instructions (the FP64 pipe is not used).
+__device__ __forceinline__ double combine7(const float* T, int SE) {
+  int I[kDig];
+#pragma unroll
+  for (int c = 0; c < kDig; ++c) I[c] = __float2int_rn(T[c]);   // exact: integers below 2^24
+  const long long zh = (long long)I[0] * 16777216ll + (long long)I[1] * 65536ll + (long long)I[2] * 256ll + I[3];
+  const long long zl = (long long)I[4] * 65536ll + (long long)I[5] * 256ll + I[6];
+  const long long Zt = zh + (zl >> 24);                     // Z = Zt 2^24 + zr, 0 <= zr < 2^24
+  const unsigned zr = (unsigned)zl & 0xFFFFFFu;
+  const bool neg = Zt < 0;
+  const unsigned long long Mt = neg ? (unsigned long long)(~Zt) + (zr == 0u) : (unsigned long long)Zt;
+  const unsigned mr = neg ? ((0x1000000u - zr) & 0xFFFFFFu) : zr;
+  if (Mt == 0ull) return combine7_slow(zh, zl, SE);
+  const int lz = __clzll((long long)Mt);                   // 13 .. 63
+  const unsigned long long lo64 = (unsigned long long)mr << 40;
+  const unsigned long long hi = (Mt << lz) | (lo64 >> (64 - lz));
+  const unsigned long long lo = lo64 << lz;
+  unsigned long long mant = hi >> 11;
+  const unsigned rb = (unsigned)hi & 0x7FFu;
+  const unsigned up = (rb > 0x400u) | ((rb == 0x400u) & ((lo != 0ull) | (unsigned)(mant & 1ull)));
+  mant += up;
+  const int c = (int)(mant >> 53);
+  mant >>= c;
+  const int be = 87 - lz + c + SE + 1023;
+  if (be < 1 || be > 2046) return combine7_slow(zh, zl, SE);
+  const unsigned long long bits =
+      ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (mant & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
+
+// Raw 8-byte words of tile `tile`, row r, the KC columns of part p (0 outside).
+template <int KC>
+__device__ __forceinline__ void load_raw(const long long* __restrict__ Xw, long long tile, int R, int r, int p, int n,
+                                         long long inner, long long Q, long long* raw) {
+  const long long q = tile * R + r;
+  const bool valid = r < R && q < Q;
+  long long base = 0;
+  if (valid) {
+    const long long o = q / inner;
+    base = o * (long long)n * inner + (q - o * inner);
+  }
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    const int a = part_col(p, c);
+    raw[c] = (valid && a < n) ? __ldg(Xw + base + (long long)a * inner) : 0ll;
+  }
+}
+
+template <int KC>
+__global__ void __launch_bounds__(kThreads, 1) k_tc_oz7(Oz7Args args) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int n = args.n, npad = args.npad, R = args.R, nchunk = args.nchunk;
+  const int kcores = npad / 8;
+  const uint32_t sbo_a = a_sbo(kcores), sbo_b = (uint32_t)kcores * 128u;
+  const size_t plane_a = (size_t)(R / 8) * sbo_a;
+  const long long inner = args.inner, Q = args.Q;
+  unsigned char* sB = smem;                                        // 7 npad x npad BF16
+  unsigned char* sA = sB + (size_t)kDig * npad * npad * 2;         // 7 planes of R rows (+ overrun)
+  const size_t a_bytes = (size_t)(kDig * (R / 8) + (128 - R) / 8) * sbo_a;
+  int* sEj = reinterpret_cast<int*>(sA + a_bytes);                 // npad
+  int* sEx = sEj + npad;                                           // 128 row exponents
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sEx + 128);         // 2 buffers
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  // digit phase: warp w holds rows 32 (w mod 4) + 8 (w / 4) + (lane mod 8), part lane / 8
+  const int dk = lane & 7, dp = (lane >> 3) & 3;
+  const int drow = 32 * (warp & 3) + 8 * (warp >> 2) + dk;
+  // epilogue: TMEM lane quadrant warp mod 4 (row 32 (w mod 4) + lane), column part w / 4
+  const int erow = 32 * (warp & 3) + lane, epart = warp >> 2;
+
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(args.B);
+    uint4* dst = reinterpret_cast<uint4*>(sB);
+    const int nv = kDig * npad * npad * 2 / 16;
+    for (int e = t; e < nv; e += kThreads) dst[e] = src[e];
+    uint4* za = reinterpret_cast<uint4*>(sA);   // zero the digit planes once (padding, overrun)
+    for (size_t e = t; e < a_bytes / 16; e += kThreads) za[e] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = t; i < npad; i += kThreads) sEj[i] = i < n ? args.ej[i] : 1;
+  }
+  if (t == 0) {
+    tc::mbar_init(tc::smem_u32(&mbar[0]), 1);
+    tc::mbar_init(tc::smem_u32(&mbar[1]), 1);
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 512);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t a_addr = tc::smem_u32(sA), b_addr = tc::smem_u32(sB);
+  const int ksteps = npad / 16;
+  uint32_t ph0 = 0u, ph1 = 0u;
+  int pend0 = -1, pend1 = -1;   // thread 0: phases of commits not yet seen complete
+  const long long* Xw = reinterpret_cast<const long long*>(args.X);
+  long long raw[KC];
+  const size_t drbase = (size_t)(drow >> 3) * sbo_a + (size_t)(drow & 7) * 16;
+  bool timed_out = false;   // uniform: agreed through __syncthreads_or
+
+  // MMAs of output chunk j into buffer j & 1 (one thread), one commit.
+  auto issue_chunk = [&](int j) {
+    const int nc = min(kChunk, npad - kChunk * j);
+    const uint32_t dbase = tmem + (uint32_t)((j & 1) * kBufCols);
+    const uint32_t brow0 = (uint32_t)(kDig * kChunk * j);   // stacked rows before chunk j
+    const uint64_t db0 = tc::smem_desc(b_addr + (brow0 / 8) * sbo_b, 128u, sbo_b);
+    for (int k = 0; k < kDig; ++k) {
+      const uint32_t idesc = tc::instr_desc(1u, 128, (kDig - k) * nc);
+      const uint64_t da0 = tc::smem_desc(a_addr + (uint32_t)(k * plane_a), 128u, sbo_a);
+      for (int s = 0; s < ksteps; ++s)
+        tc::mma<0>(dbase + (uint32_t)(k * nc), da0 + (uint64_t)((s * 256) >> 4), db0 + (uint64_t)((s * 256) >> 4),
+                   idesc, (k > 0 || s > 0) ? 1u : 0u);
+    }
+    tc::mma_commit(tc::smem_u32(&mbar[j & 1]));
+    if (j & 1) pend1 = (int)ph1;
+    else pend0 = (int)ph0;
+  };
+
+  tc::grid_dependency_wait();   // the preceding kernel's output is read from here on
+  if ((long long)blockIdx.x < args.ntiles) load_raw<KC>(Xw, blockIdx.x, R, drow, dp, n, inner, Q, raw);
+
+  for (long long tile = blockIdx.x; tile < args.ntiles; tile += gridDim.x) {
+    if (tile + gridDim.x >= args.ntiles) tc::grid_launch_dependents();
+    const long long q0 = tile * R;
+    // ---- row exponent and the seven digit planes (rows >= R belong to the next plane)
+    {
+      int E = 1;
+#pragma unroll
+      for (int c = 0; c < KC; ++c) E = max(E, bexp(raw[c]));
+      E = max(E, __shfl_xor_sync(0xFFFFFFFFu, E, 8));
+      E = max(E, __shfl_xor_sync(0xFFFFFFFFu, E, 16));
+      if (dp == 0) sEx[drow] = E;
+      if (drow < R) {
+#pragma unroll
+        for (int c = 0; c < KC; c += 2) {
+          const int a = part_col(dp, c);
+          if (a >= npad) continue;
+          float d0[kDig], d1[kDig];
+          digits7(raw[c], E, d0);
+          digits7(raw[c + 1], E, d1);
+          const size_t off = drbase + (size_t)(a >> 3) * 128 + (size_t)(a & 7) * 2;
+#pragma unroll
+          for (int k = 0; k < kDig; ++k)
+            *reinterpret_cast<__nv_bfloat162*>(sA + k * plane_a + off) = __floats2bfloat162_rn(d0[k], d1[k]);
+        }
+      }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (t == 0) {
+      issue_chunk(0);
+      if (nchunk > 1) issue_chunk(1);
+    }
+    // ---- the next tile's entries travel while the tensor cores work
+    {
+      const long long nt = tile + gridDim.x;
+      if (nt < args.ntiles) load_raw<KC>(Xw, nt, R, drow, dp, n, inner, Q, raw);
+    }
+    // ---- epilogue, chunk by chunk
+    const long long q = q0 + erow;
+    const bool row_ok = erow < R && q < Q;
+    long long base = 0;
+    if (row_ok) {
+      const long long o = q / inner;
+      base = o * (long long)n * inner + (q - o * inner);
+    }
+    const int ex = sEx[erow];
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    for (int j = 0; j < nchunk && !timed_out; ++j) {
+      const int b = j & 1;
+      const int nc = min(kChunk, npad - kChunk * j);
+      const int per = nc / kParts;   // 8 or 4 columns of this part
+      // warp-uniform, so that the .sync.aligned tensor-memory loads below are too
+      const uint32_t phb = b ? ph1 : ph0;
+      const bool ok = __all_sync(0xFFFFFFFFu, tc::mbar_wait(tc::smem_u32(&mbar[b]), phb, args.wait));
+      if (ok && t == 0) {
+        if (b) pend1 = -1;
+        else pend0 = -1;
+      }
+      if (b) ph1 ^= 1u;
+      else ph0 ^= 1u;
+      tc::fence_after_sync();
+      for (int g = 0; g < per; g += 4) {
+        const int col0 = kChunk * j + epart * per + g;   // first output column of this group
+        uint32_t Tr[kDig][4];
+        if (ok) {
+#pragma unroll
+          for (int c = 0; c < kDig; ++c)
+            tc::tmem_ld4_async(lane_base + (uint32_t)(b * kBufCols + c * nc + epart * per + g), Tr[c]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int c = 0; c < kDig; ++c)
+            asm volatile("" : "+r"(Tr[c][0]), "+r"(Tr[c][1]), "+r"(Tr[c][2]), "+r"(Tr[c][3]) : : "memory");
+        }
+        if (g + 4 >= per) {
+          // every thread has read this buffer: the MMAs of chunk j + 2 may overwrite it.
+          // The barrier also agrees on whether any warp's wait ran out.
+          tc::fence_before_sync();
+          timed_out = __syncthreads_or(ok ? 0 : 1) != 0;
+          if (!timed_out && t == 0 && j + 2 < nchunk) {
+            tc::fence_after_sync();
+            issue_chunk(j + 2);
+          }
+        }
+        if (timed_out) break;
+        if (!ok) continue;   // still reaches this chunk's barrier above
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int i = col0 + e;
+          if (!row_ok || i >= n) continue;
+          float T[kDig];
+#pragma unroll
+          for (int c = 0; c < kDig; ++c) T[c] = __uint_as_float(Tr[c][e]);
+          const int ej = sEj[i];
+          double y;
+          if (ex >= 2047 || ej >= 2047) {
+            y = __longlong_as_double(0x7FF8000000000000ll);   // non-finite input row: NaN
+          } else {
+            y = combine7(T, ex + ej - 2106);
+          }
+          args.Y[base + (long long)i * inner] = y;
+        }
+      }
+    }
+    if (timed_out) break;
+    tc::fence_before_sync();
+    __syncthreads();   // sEx and the digit planes are rewritten by the next tile
+    tc::fence_after_sync();
+  }
+  tc::fence_after_sync();
+  if (t == 0 && timed_out) {
+    // a wait ran out: report it and let this CTA's MMAs in flight finish
+    // (bounded) before tensor memory is released
+    if (args.status) atomicOr(args.status, kStatusTimeout);
+    if (pend0 >= 0) tc::mbar_wait(tc::smem_u32(&mbar[0]), (uint32_t)pend0, kDrainIters);
+    if (pend1 >= 0) tc::mbar_wait(tc::smem_u32(&mbar[1]), (uint32_t)pend1, kDrainIters);
+    tc::fence_after_sync();
+  }
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+inline int oz7_cols(int n) { return n <= 32 ? 8 : n <= 48 ? 12 : n <= 64 ? 16 : n <= 72 ? 18 : 20; }
+inline int oz7_rows(int n) { return n <= 64 ? 128 : 112; }
+
+size_t oz7_smem_bytes(int n) {
+  const int npad = (n + 15) / 16 * 16;
+  const int R = oz7_rows(n);
+  const size_t a_bytes = (size_t)(kDig * (R / 8) + (128 - R) / 8) * a_sbo(npad / 8);
+  return (size_t)kDig * npad * npad * 2 + a_bytes + (size_t)npad * 4 + 128 * 4 + 2 * 8 + 16;
+}
+
+template <int KC>
+cudaError_t launch_oz7(const double* X, double* Y, const unsigned char* B, const int* ej, int n, long long inner,
+                       long long outer, cudaStream_t st) {
+  const long long Q = inner * outer;
+  if (Q <= 0) return cudaSuccess;
+  const size_t smem = oz7_smem_bytes(n);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  {
+    const cudaError_t e = ensure_smem_attr(k_tc_oz7<KC>, 227 * 1024);
+    if (e != cudaSuccess) return e;
+  }
+  const int npad = (n + 15) / 16 * 16;
+  const int R = oz7_rows(n);
+  const long long ntiles = (Q + R - 1) / R;
+  const long long grid = std::min<long long>(ntiles, sm_count_current());
+  Oz7Args a{X, Y, B, ej, n, npad, R, (npad + kChunk - 1) / kChunk, inner, Q, ntiles, status_word(), wait_limit()};
+  ProfScope ps("fd_mode_tc7", 2.0 * (double)Q * n * n, 8.0 * (double)Q * n * 2, st);
+  // 227 KB requested so that exactly one CTA (which owns all 512 TMEM columns) fits per SM
+  return tc::launch_pdl(k_tc_oz7<KC>, dim3((unsigned)grid), dim3(kThreads), (size_t)227 * 1024, st, a);
+}
+
+}  // namespace
+
+int oz7_max_n() { return 80; }
+
+// Host: the seven digit planes of a row-major n x n factor J (J[i*n + a]) in the
+// chunk-stacked B layout of the kernel, and per row i the largest biased
+// exponent ej[i] (rows scaled exactly as the kernel scales rows of X). Row
+// r of the stacked image, for output column i in chunk j (i = 32 j + u) and
+// digit l, is 7 * 32 * j + l * nc_j + u with nc_j the chunk's width.
+std::vector<unsigned char> oz7_planes(const double* J, int n, std::vector<int>& ej) {
+  const int npad = (n + 15) / 16 * 16;
+  const int kcores = npad / 8;
+  const uint32_t sbo = (uint32_t)kcores * 128u;
+  std::vector<unsigned char> img((size_t)kDig * npad * npad * 2, 0);
+  ej.assign(n, 1);
+  for (int i = 0; i < n; ++i) {
+    int E = 1;
+    for (int a = 0; a < n; ++a) {
+      unsigned long long bits;
+      std::memcpy(&bits, &J[(size_t)i * n + a], 8);
+      E = std::max(E, std::max(1, (int)((bits >> 52) & 0x7FF)));
+    }
+    ej[i] = E;
+    const int j = i / kChunk, u = i % kChunk;
+    const int nc = std::min(kChunk, npad - kChunk * j);
+    for (int a = 0; a < n; ++a) {
+      unsigned long long bits;
+      std::memcpy(&bits, &J[(size_t)i * n + a], 8);
+      const int e = (int)((bits >> 52) & 0x7FF);
+      unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+      if (e) m |= 1ull << 52;
+      const int s = E - std::max(e, 1);
+      unsigned long long V;
+      if (s <= 2) {
+        V = m << (2 - s);
+      } else {
+        const int sh = s - 2;
+        V = sh >= 60 ? 0ull : (m + (1ull << (sh - 1))) >> sh;
+      }
+      const unsigned long long W = V + kByteBias;
+      const int sg = (bits >> 63) ? -1 : 1;
+      for (int l = 0; l < kDig; ++l) {
+        const int byte = l == 0 ? (int)(W >> 48) : (int)((W >> (8 * (6 - l))) & 0xFF);
+        const float dl = (float)(sg * (byte - 128));
+        const __nv_bfloat16 h = __float2bfloat16_rn(dl);   // exact: at most 8 significant bits
+        const int row = kDig * kChunk * j + l * nc + u;
+        std::memcpy(&img[canon_off16(row, a, kcores, sbo)], &h, 2);
+      }
+    }
+  }
+  return img;
+}
+
+cudaError_t launch_fd_mode_tc7(const double* X, const unsigned char* B, const int* ej, double* Y, int n,
+                               long long inner, long long outer, cudaStream_t st) {
+  switch (oz7_cols(n)) {
+    case 8: return launch_oz7<8>(X, Y, B, ej, n, inner, outer, st);
+    case 12: return launch_oz7<12>(X, Y, B, ej, n, inner, outer, st);
+    case 16: return launch_oz7<16>(X, Y, B, ej, n, inner, outer, st);
+    case 18: return launch_oz7<18>(X, Y, B, ej, n, inner, outer, st);
+    default: return launch_oz7<20>(X, Y, B, ej, n, inner, outer, st);
+  }
+}
+
+}  // namespace stfd

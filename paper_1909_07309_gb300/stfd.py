@@ -15,7 +15,7 @@ from . import build as _build
 
 STFD_OK = 0
 STFD_NOT_CONVERGED = 1
-STFD_FP64, STFD_TF32, STFD_BF16, STFD_DF32, STFD_FP64TC = 0, 1, 2, 3, 4
+STFD_FP64, STFD_TF32, STFD_BF16, STFD_DF32, STFD_FP64TC, STFD_FP64TC7 = 0, 1, 2, 3, 4, 5
 STFD_BC_NONE, STFD_BC_INITIAL, STFD_BC_DIRICHLET = 0, 1, 2
 STFD_NOALLOC_MAX_N = 524288
 STFD_OP_FP64, STFD_OP_DF32 = 0, 1

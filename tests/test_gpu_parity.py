@@ -46,15 +46,15 @@ FD_CASES = [  # d, p, n_el, T, gamma, nu, nrhs  (n_t - 1 = n_el + p - 2 takes bo
 ]
 
 
-@pytest.mark.parametrize("prec", [stfd.STFD_FP64, stfd.STFD_DF32, stfd.STFD_FP64TC])
+@pytest.mark.parametrize("prec", [stfd.STFD_FP64, stfd.STFD_DF32, stfd.STFD_FP64TC, stfd.STFD_FP64TC7])
 @pytest.mark.parametrize("d,p,n_el,T,gamma,nu,nrhs", FD_CASES)
 def test_fd_apply_matches_oracle(d, p, n_el, T, gamma, nu, nrhs, prec):
-    """FP64, double-float and tensor-core digit-sliced (all FP64-accurate)
+    """FP64, double-float and tensor-core digit-sliced (six and seven digits)
     Algorithm 1 against the oracle, 1e-11."""
     if n_el + p - 2 < 1:
         pytest.skip("no spatial dofs")
-    if prec == stfd.STFD_FP64TC and n_el + p - 1 > 80:
-        pytest.skip("tensor-core FP64 path takes univariate sizes <= 80")
+    if prec in (stfd.STFD_FP64TC, stfd.STFD_FP64TC7) and n_el + p - 1 > 80:
+        pytest.skip("tensor-core digit-sliced paths take univariate sizes <= 80")
     K, M, Wt, Mt = stfd.heat_problem(d, p, n_el, T=T)
     P = stfd.FD(K, M, Wt, Mt, gamma, nu, precision=prec)
     r = inputs.standard_normal(P.N, seed=11 + d + p, batch=nrhs).reshape(nrhs, P.N)
@@ -100,7 +100,8 @@ def test_st_matvec_matches_oracle(d, p, n_el, T, gamma, nu, nrhs, arith):
 
 
 @pytest.mark.parametrize("arith,prec", [(stfd.STFD_OP_FP64, stfd.STFD_FP64), (stfd.STFD_OP_DF32, stfd.STFD_FP64),
-                                        (stfd.STFD_OP_DF32, stfd.STFD_DF32), (stfd.STFD_OP_DF32, stfd.STFD_FP64TC)])
+                                        (stfd.STFD_OP_DF32, stfd.STFD_DF32), (stfd.STFD_OP_DF32, stfd.STFD_FP64TC),
+                                        (stfd.STFD_OP_FP64, stfd.STFD_FP64TC7)])
 def test_gmres_unit_cube_single_iteration(arith, prec):
     """Unit cube, T = 1, constant coefficients: P = A, one iteration (Sec. 4, F = id)."""
     d, p, n_el = 3, 3, 12
@@ -178,7 +179,7 @@ def _row_of_A(S, idx, oK, oM, oWt, oMt, gamma, nu, p):
     return float(val)
 
 
-@pytest.mark.parametrize("prec", [stfd.STFD_FP64, stfd.STFD_DF32, stfd.STFD_FP64TC])
+@pytest.mark.parametrize("prec", [stfd.STFD_FP64, stfd.STFD_DF32, stfd.STFD_FP64TC, stfd.STFD_FP64TC7])
 def test_fd_apply_full_size_residual_samples(prec):
     """Workload at scale (d = 3, p = 3, 64 elements, N = 18,125,250): P = A on
     the unit cube, so A (P^{-1} r) = r holds at every entry; checked on 400
@@ -240,10 +241,11 @@ def test_gmres_rejects_nan_and_reports_not_converged():
     assert info["status"] == 1 and not info["converged"] and info["iters"] == 2
 
 
-def test_fp64tc_rejects_large_factor():
+@pytest.mark.parametrize("prec", [stfd.STFD_FP64TC, stfd.STFD_FP64TC7])
+def test_fp64tc_rejects_large_factor(prec):
     K, M, Wt, Mt = stfd.heat_problem(1, 2, 90)      # n_t = 91 > 80
     with pytest.raises(stfd.StfdError):
-        stfd.FD(K, M, Wt, Mt, precision=stfd.STFD_FP64TC)
+        stfd.FD(K, M, Wt, Mt, precision=prec)
 
 
 def test_argument_checks_on_device():
@@ -258,7 +260,7 @@ def test_argument_checks_on_device():
         stfd.FD(K, M, Wt, Mt, gamma=-1.0)
 
 
-@pytest.mark.parametrize("prec", [stfd.STFD_FP64TC, stfd.STFD_DF32])
+@pytest.mark.parametrize("prec", [stfd.STFD_FP64TC, stfd.STFD_DF32, stfd.STFD_FP64TC7])
 @pytest.mark.parametrize("d,p,n_el", [(2, 3, 21), (3, 3, 13)])
 def test_fd_apply_unaligned_buffers_match(d, p, n_el, prec):
     """Input and output vectors that start 8 bytes past a 16-byte boundary take

@@ -1,0 +1,67 @@
+"""The GPU solution of the workload at scale against its exact solution.
+
+u = sin(pi x) sin(pi y) sin(pi z) sin(t) on the unit cube x (0, 1), d = 3,
+p = 3, gamma = nu = 1, f = u_t - Lap u (Sec. 5.1). The right-hand side is
+built by the library (stfd_spline_load_trig, as bench.py does), the solve is
+the library's FD-preconditioned FGMRES to 1e-8. The space-time L2 error of
+u_h = sum_i c_i B_i is computed from quantities the oracle gives in closed
+form: ||u - u_h||^2 = ||u||^2 - 2 c^T F_u + c^T (M_t (x) M_s) c with
+F_u = int u B_i (a Kronecker product of 1D loads, eq. kron_vec_multi) and
+||u||^2 = (1/2)^3 (1/2 - sin(2)/4). Sec. 5.1 (Fig. 2) reports the optimal
+order h^{p+1} in L2: the error ratio per halving of h approaches 2^{p+1} = 16.
+"""
+import numpy as np
+import pytest
+
+from oracle import kron as okron, loads as oloads, matrices as omat
+from paper_1909_07309_gb300 import stfd
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+D, P_DEG = 3, 3
+
+
+def _rhs(n_el):
+    """The library's load of f = u_t - Lap u (bench.py's construction)."""
+    Fx = stfd.stfd_spline_load_trig(P_DEG, n_el, 1.0, stfd.STFD_BC_DIRICHLET, np.pi, 1.0, 0.0)
+    Ft = stfd.stfd_spline_load_trig(P_DEG, n_el, 1.0, stfd.STFD_BC_INITIAL, 1.0, D * np.pi ** 2, 1.0)
+    f = np.ones(1)
+    for F in [Fx] * D + [Ft]:
+        f = np.outer(F, f).ravel()
+    return f
+
+
+def l2_error(c, n_el):
+    """Space-time L2 norm of u - u_h (oracle quantities, 12-point Gauss loads)."""
+    K, M = omat.space_matrices(P_DEG, n_el)
+    Wt, Mt = omat.time_matrices(P_DEG, n_el)
+    Fx = oloads.load_1d(P_DEG, n_el, 1.0, lambda x: np.sin(np.pi * x), 12)
+    Ft = oloads.load_1d(P_DEG, n_el, 1.0, np.sin, 12, True, False)
+    Fu = oloads.load_separable([Fx] * D, Ft)
+    Mc = okron.st_matvec(c, [M] * D, [M] * D, Mt, Mt, 1.0, 0.0)       # (M_t (x) M_s) c
+    u2 = 0.5 ** D * (0.5 - np.sin(2.0) / 4.0)
+    e2 = u2 - 2.0 * float(c @ Fu) + float(c @ Mc)
+    return np.sqrt(max(e2, 0.0))
+
+
+def solve(n_el, prec, arith):
+    K, M, Wt, Mt = stfd.heat_problem(D, P_DEG, n_el)
+    A = stfd.KronOp(K, M, Wt, Mt, arith=arith)
+    P = stfd.FD(K, M, Wt, Mt, precision=prec)
+    u, info = A.gmres(P, torch.as_tensor(_rhs(n_el), device="cuda"), tol=1e-8)
+    assert info["converged"] and info["rel_res_true"] <= 1e-8
+    c = u.cpu().numpy()
+    A.close()
+    P.close()
+    return c
+
+
+@pytest.mark.parametrize("prec,arith", [(stfd.STFD_FP64, stfd.STFD_OP_FP64),
+                                        (stfd.STFD_FP64TC, stfd.STFD_OP_DF32)])
+def test_l2_error_converges_at_order_p_plus_1(prec, arith):
+    errs = [l2_error(solve(n, prec, arith), n) for n in (8, 16, 32)]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    # the rate approaches p + 1 = 4 from the pre-asymptotic side
+    assert rates[-1] > P_DEG + 0.7 and rates[-1] < P_DEG + 1.5, (errs, rates)
+    assert errs[-1] < 1e-5, errs
