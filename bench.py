@@ -39,10 +39,14 @@ L2_BYTES = 129 * 2 ** 20
 # one st_matvec; None once a kernel changes until it is captured again.
 NCU_TRAFFIC = {}
 
-# Arithmetic of the headline solve: IEEE FP64 throughout (Algorithm 1 with FP64
-# mode products and an FP64 Step 3, the FP64 banded matvec, FP64 GMRES).
-HEADLINE = dict(precond="STFD_FP64", matvec="STFD_OP_FP64", dtype="f64",
-                precond_text="Algorithm 1 in IEEE FP64: mode products and Step 3 on the FP64 pipe",
+# Arithmetic of the headline solve, no narrower than FP64 anywhere: Algorithm 1
+# with the mode products on the tensor cores by seven exact digit slices per
+# entry (kept digit pairs accumulated exactly, one rounding to FP64, FP64
+# intermediates) and an IEEE-FP64 Step 3; the IEEE-FP64 banded matvec; FP64 GMRES.
+HEADLINE = dict(precond="STFD_FP64TC7", matvec="STFD_OP_FP64", dtype="f64",
+                precond_text="Algorithm 1, FP64: mode products on tcgen05 by seven exact BF16 digit slices per entry "
+                             "(28 digit pairs, exact FP32 accumulators, one rounding to FP64; FP64 intermediates), "
+                             "Step 3 in IEEE FP64",
                 matvec_text="IEEE FP64 sum-factorised banded products (FP64 pipe)")
 
 

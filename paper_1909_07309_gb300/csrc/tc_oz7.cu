@@ -47,8 +47,6 @@ namespace stfd {
 namespace {
 
 constexpr int kDig = 7;
-constexpr int kThreads = 512;
-constexpr int kParts = 4;
 constexpr int kChunk = 32;                 // output columns per tensor-memory buffer
 constexpr int kBufCols = kDig * kChunk;    // 224 columns per buffer
 constexpr unsigned long long kByteBias = 0x80808080808080ull;
@@ -77,26 +75,6 @@ __host__ __device__ inline size_t canon_off16(int r, int k, int kcores, uint32_t
 // Largest of 1 and the biased exponent of an FP64 bit pattern.
 __device__ __forceinline__ int bexp(long long w) {
   return max(1, (int)(((unsigned long long)w >> 52) & 0x7FF));
-}
-
-// The seven digits of one entry (bit pattern w) of a row whose largest biased
-// exponent is E, as floats (small integers, exact in BF16). Branch-free:
-// V = round(4 m 2^-s) with s = E - max(e, 1) >= 0 (exact for s <= 2).
-__device__ __forceinline__ void digits7(long long w, int E, float* d) {
-  const unsigned long long u = (unsigned long long)w;
-  const int e = (int)((u >> 52) & 0x7FF);
-  const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(e != 0) << 52);
-  const int s = min(E - max(e, 1), 63);
-  const unsigned long long V = ((m << 2) + ((1ull << s) >> 1)) >> s;
-  const unsigned long long W = V + kByteBias;
-  const float sg = (u >> 63) ? -1.0f : 1.0f;
-  const float off = -(8388608.0f + 128.0f) * sg;
-  const uint32_t lo = (uint32_t)W, hi = (uint32_t)(W >> 32);
-  // bytes of W from the top: d_0 = W >> 48 (up to 9 bits), then bytes 5 .. 0
-  const uint32_t b[kDig] = {hi >> 16, (hi >> 8) & 0xFFu, hi & 0xFFu, lo >> 24, (lo >> 16) & 0xFFu,
-                            (lo >> 8) & 0xFFu, lo & 0xFFu};
-#pragma unroll
-  for (int k = 0; k < kDig; ++k) d[k] = fmaf(__uint_as_float(0x4B000000u | b[k]), sg, off);   // (b - 128) sg
 }
 
 // Rare cases of combine7: |Z| below 2^24, or a result outside the normal range.
@@ -158,8 +136,38 @@ __device__ __forceinline__ void load_raw(const long long* __restrict__ Xw, long 
   }
 }
 
+// The biased 55-bit integer of one entry, W = V + 0x80808080808080 (its bytes
+// minus 128 are the seven digits of |x|, see above), for a row of largest
+// biased exponent E. Branch-free: V = round(4 m 2^-s), s = E - max(e, 1).
+__device__ __forceinline__ unsigned long long wbias(long long w, int E) {
+  const unsigned long long u = (unsigned long long)w;
+  const int e = (int)((u >> 52) & 0x7FF);
+  const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(e != 0) << 52);
+  const int s = min(E - max(e, 1), 63);
+  return (((m << 2) + ((1ull << s) >> 1)) >> s) + kByteBias;
+}
+
+// Digit k of an entry with biased integer (hi, lo) as a float: byte k from the
+// top (the top one up to 9 bits) minus 128 -- the magnitude's digit; the
+// entry's sign is applied to the packed BF16 pair.
+template <int k>
+__device__ __forceinline__ float digit_of(uint32_t hi, uint32_t lo) {
+  const uint32_t b = k == 0 ? (hi >> 16) : k == 1 ? ((hi >> 8) & 0xFFu) : k == 2 ? (hi & 0xFFu)
+                   : k == 3 ? (lo >> 24) : k == 4 ? ((lo >> 16) & 0xFFu) : k == 5 ? ((lo >> 8) & 0xFFu) : (lo & 0xFFu);
+  return __uint_as_float(0x4B000000u | b) - 8388736.0f;   // (2^23 + b) - (2^23 + 128)
+}
+
+// 17 warps: warps 0..15 convert the tile's entries into digit planes, one plane
+// at a time (each plane announced on its own mbarrier), then read the
+// accumulators chunk by chunk and write the FP64 results; warp 16 issues the
+// MMAs of each plane as soon as it is written (so the digit conversion and the
+// tensor cores overlap), and the MMAs of a chunk once its tensor-memory buffer
+// has been read out (empty/full mbarrier pairs per buffer).
+constexpr int kWorkers = 512;
+constexpr int kThreadsTotal = kWorkers + 32;
+
 template <int KC>
-__global__ void __launch_bounds__(kThreads, 1) k_tc_oz7(Oz7Args args) {
+__global__ void __launch_bounds__(kThreadsTotal, 1) k_tc_oz7(Oz7Args args) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int n = args.n, npad = args.npad, R = args.R, nchunk = args.nchunk;
   const int kcores = npad / 8;
@@ -170,28 +178,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_oz7(Oz7Args args) {
   unsigned char* sA = sB + (size_t)kDig * npad * npad * 2;         // 7 planes of R rows (+ overrun)
   const size_t a_bytes = (size_t)(kDig * (R / 8) + (128 - R) / 8) * sbo_a;
   int* sEj = reinterpret_cast<int*>(sA + a_bytes);                 // npad
-  int* sEx = sEj + npad;                                           // 128 row exponents
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sEx + 128);         // 2 buffers
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  int* sEx = sEj + npad;                                           // 2 x 128 row exponents (by tile parity)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sEx + 256);          // pl[7], full[2], empty[2], exq[4]
+  uint64_t* pl = bar;
+  uint64_t* full = bar + kDig;
+  uint64_t* empty = bar + kDig + 2;
+  uint64_t* exq = bar + kDig + 4;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + kDig + 8);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  // digit phase: warp w holds rows 32 (w mod 4) + 8 (w / 4) + (lane mod 8), part lane / 8
-  const int dk = lane & 7, dp = (lane >> 3) & 3;
-  const int drow = 32 * (warp & 3) + 8 * (warp >> 2) + dk;
-  // epilogue: TMEM lane quadrant warp mod 4 (row 32 (w mod 4) + lane), column part w / 4
-  const int erow = 32 * (warp & 3) + lane, epart = warp >> 2;
+  const bool mma_warp = warp == kWorkers / 32;
 
   {
     const uint4* src = reinterpret_cast<const uint4*>(args.B);
     uint4* dst = reinterpret_cast<uint4*>(sB);
     const int nv = kDig * npad * npad * 2 / 16;
-    for (int e = t; e < nv; e += kThreads) dst[e] = src[e];
+    for (int e = t; e < nv; e += kThreadsTotal) dst[e] = src[e];
     uint4* za = reinterpret_cast<uint4*>(sA);   // zero the digit planes once (padding, overrun)
-    for (size_t e = t; e < a_bytes / 16; e += kThreads) za[e] = make_uint4(0u, 0u, 0u, 0u);
-    for (int i = t; i < npad; i += kThreads) sEj[i] = i < n ? args.ej[i] : 1;
+    for (size_t e = t; e < a_bytes / 16; e += kThreadsTotal) za[e] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = t; i < npad; i += kThreadsTotal) sEj[i] = i < n ? args.ej[i] : 1;
   }
   if (t == 0) {
-    tc::mbar_init(tc::smem_u32(&mbar[0]), 1);
-    tc::mbar_init(tc::smem_u32(&mbar[1]), 1);
+    for (int k = 0; k < kDig; ++k) tc::mbar_init(tc::smem_u32(&pl[k]), kWorkers);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(tc::smem_u32(&full[b]), 1);
+      tc::mbar_init(tc::smem_u32(&empty[b]), kWorkers);
+    }
+    for (int qd = 0; qd < 4; ++qd) tc::mbar_init(tc::smem_u32(&exq[qd]), 128);
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 512);
   tc::fence_async_smem();
@@ -199,103 +211,158 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_oz7(Oz7Args args) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
-  const uint32_t a_addr = tc::smem_u32(sA), b_addr = tc::smem_u32(sB);
-  const int ksteps = npad / 16;
-  uint32_t ph0 = 0u, ph1 = 0u;
-  int pend0 = -1, pend1 = -1;   // thread 0: phases of commits not yet seen complete
-  const long long* Xw = reinterpret_cast<const long long*>(args.X);
-  long long raw[KC];
-  const size_t drbase = (size_t)(drow >> 3) * sbo_a + (size_t)(drow & 7) * 16;
-  bool timed_out = false;   // uniform: agreed through __syncthreads_or
+  bool timed_out = false;
+  int pend0 = -1, pend1 = -1;   // MMA thread: phases of commits not yet seen complete
 
-  // MMAs of output chunk j into buffer j & 1 (one thread), one commit.
-  auto issue_chunk = [&](int j) {
-    const int nc = min(kChunk, npad - kChunk * j);
-    const uint32_t dbase = tmem + (uint32_t)((j & 1) * kBufCols);
-    const uint32_t brow0 = (uint32_t)(kDig * kChunk * j);   // stacked rows before chunk j
-    const uint64_t db0 = tc::smem_desc(b_addr + (brow0 / 8) * sbo_b, 128u, sbo_b);
-    for (int k = 0; k < kDig; ++k) {
+  if (mma_warp) {
+    // ================= MMA issue: the whole warp waits, lane 0 issues =================
+    const uint32_t a_addr = tc::smem_u32(sA), b_addr = tc::smem_u32(sB);
+    const int ksteps = npad / 16;
+    uint32_t ph_pl = 0u, ph_e0 = 0u, ph_e1 = 0u;
+    int uses0 = 0, uses1 = 0;     // buffer uses so far (the first needs no drain wait)
+    auto issue_plane = [&](int j, int k) {
+      if (lane != 0) return;
+      const int nc = min(kChunk, npad - kChunk * j);
+      const uint32_t dbase = tmem + (uint32_t)((j & 1) * kBufCols);
+      const uint32_t brow0 = (uint32_t)(kDig * kChunk * j);
+      const uint64_t db0 = tc::smem_desc(b_addr + (brow0 / 8) * sbo_b, 128u, sbo_b);
       const uint32_t idesc = tc::instr_desc(1u, 128, (kDig - k) * nc);
       const uint64_t da0 = tc::smem_desc(a_addr + (uint32_t)(k * plane_a), 128u, sbo_a);
       for (int s = 0; s < ksteps; ++s)
         tc::mma<0>(dbase + (uint32_t)(k * nc), da0 + (uint64_t)((s * 256) >> 4), db0 + (uint64_t)((s * 256) >> 4),
                    idesc, (k > 0 || s > 0) ? 1u : 0u);
+    };
+    auto wait_empty = [&](int b) -> bool {   // buffer b drained by the workers
+      if ((b ? uses1 : uses0) == 0) return true;
+      const bool ok = __all_sync(0xFFFFFFFFu, tc::mbar_wait(tc::smem_u32(&empty[b]), b ? ph_e1 : ph_e0, args.wait));
+      if (b) ph_e1 ^= 1u;
+      else ph_e0 ^= 1u;
+      return ok;
+    };
+    auto commit = [&](int b) {
+      if (lane == 0) tc::mma_commit(tc::smem_u32(&full[b]));
+      if (b) pend1 = uses1++ & 1;
+      else pend0 = uses0++ & 1;
+    };
+    const int first = min(nchunk, 2);
+    for (long long tile = blockIdx.x; tile < args.ntiles && !timed_out; tile += gridDim.x) {
+      if (tile + gridDim.x >= args.ntiles) tc::grid_launch_dependents();
+      for (int j = 0; j < first && !timed_out; ++j) timed_out = !wait_empty(j);
+      for (int k = 0; k < kDig && !timed_out; ++k) {
+        if (!__all_sync(0xFFFFFFFFu, tc::mbar_wait(tc::smem_u32(&pl[k]), ph_pl, args.wait))) {
+          timed_out = true;
+          break;
+        }
+        tc::fence_after_sync();
+        for (int j = 0; j < first; ++j) {
+          issue_plane(j, k);
+          if (k == kDig - 1) commit(j);
+        }
+      }
+      ph_pl ^= 1u;
+      for (int j = 2; j < nchunk && !timed_out; ++j) {
+        if (!wait_empty(j & 1)) {
+          timed_out = true;
+          break;
+        }
+        tc::fence_after_sync();
+        for (int k = 0; k < kDig; ++k) issue_plane(j, k);
+        commit(j & 1);
+      }
     }
-    tc::mma_commit(tc::smem_u32(&mbar[j & 1]));
-    if (j & 1) pend1 = (int)ph1;
-    else pend0 = (int)ph0;
-  };
-
-  tc::grid_dependency_wait();   // the preceding kernel's output is read from here on
-  if ((long long)blockIdx.x < args.ntiles) load_raw<KC>(Xw, blockIdx.x, R, drow, dp, n, inner, Q, raw);
-
-  for (long long tile = blockIdx.x; tile < args.ntiles; tile += gridDim.x) {
-    if (tile + gridDim.x >= args.ntiles) tc::grid_launch_dependents();
-    const long long q0 = tile * R;
-    // ---- row exponent and the seven digit planes (rows >= R belong to the next plane)
-    {
+  } else {
+    // ================= workers: digits, then the epilogue =================
+    const int dk = lane & 7, dp = (lane >> 3) & 3;
+    const int drow = 32 * (warp & 3) + 8 * (warp >> 2) + dk;
+    const int erow = 32 * (warp & 3) + lane, epart = warp >> 2;
+    const size_t drbase = (size_t)(drow >> 3) * sbo_a + (size_t)(drow & 7) * 16;
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const long long* Xw = reinterpret_cast<const long long*>(args.X);
+    long long raw[KC];
+    uint32_t ph_f0 = 0u, ph_f1 = 0u;
+    tc::grid_dependency_wait();   // the preceding kernel's output is read from here on
+    if ((long long)blockIdx.x < args.ntiles) load_raw<KC>(Xw, blockIdx.x, R, drow, dp, n, inner, Q, raw);
+    int par = 0;
+    for (long long tile = blockIdx.x; tile < args.ntiles && !timed_out; tile += gridDim.x, par ^= 1) {
+      if (tile + gridDim.x >= args.ntiles) tc::grid_launch_dependents();
+      const long long q0 = tile * R;
+      // ---- row exponent, the biased integers, then the seven planes one by one
       int E = 1;
 #pragma unroll
       for (int c = 0; c < KC; ++c) E = max(E, bexp(raw[c]));
       E = max(E, __shfl_xor_sync(0xFFFFFFFFu, E, 8));
       E = max(E, __shfl_xor_sync(0xFFFFFFFFu, E, 16));
-      if (dp == 0) sEx[drow] = E;
-      if (drow < R) {
+      if (dp == 0) sEx[par * 128 + drow] = E;
+      uint32_t whi[KC], wlo[KC], neg = 0u;
 #pragma unroll
-        for (int c = 0; c < KC; c += 2) {
-          const int a = part_col(dp, c);
-          if (a >= npad) continue;
-          float d0[kDig], d1[kDig];
-          digits7(raw[c], E, d0);
-          digits7(raw[c + 1], E, d1);
-          const size_t off = drbase + (size_t)(a >> 3) * 128 + (size_t)(a & 7) * 2;
-#pragma unroll
-          for (int k = 0; k < kDig; ++k)
-            *reinterpret_cast<__nv_bfloat162*>(sA + k * plane_a + off) = __floats2bfloat162_rn(d0[k], d1[k]);
+      for (int c = 0; c < KC; ++c) {
+        const unsigned long long W = wbias(raw[c], E);
+        whi[c] = (uint32_t)(W >> 32);
+        wlo[c] = (uint32_t)W;
+        neg |= (uint32_t)((unsigned long long)raw[c] >> 63) << c;
+      }
+      const bool rows_ok = drow < R;   // rows >= R of the MMA read the next plane
+#define STFD_OZ7_PLANE(k)                                                                                  \
+  {                                                                                                      \
+    if (rows_ok) {                                                                                       \
+      _Pragma("unroll") for (int c = 0; c < KC; c += 2) {                                                \
+        const int a = part_col(dp, c);                                                                   \
+        if (a >= npad) continue;                                                                         \
+        const __nv_bfloat162 v = __floats2bfloat162_rn(digit_of<k>(whi[c], wlo[c]),                      \
+                                                       digit_of<k>(whi[c + 1], wlo[c + 1]));             \
+        const uint32_t sgn = (((neg >> c) & 1u) << 15) | (((neg >> (c + 1)) & 1u) << 31);                \
+        *reinterpret_cast<uint32_t*>(sA + (k) * plane_a + drbase + (size_t)(a >> 3) * 128 +              \
+                                     (size_t)(a & 7) * 2) = *reinterpret_cast<const uint32_t*>(&v) ^ sgn; \
+      }                                                                                                  \
+    }                                                                                                    \
+    tc::fence_async_smem();                                                                              \
+    tc::mbar_arrive(tc::smem_u32(&pl[k]));                                                               \
+  }
+      STFD_OZ7_PLANE(0)
+      STFD_OZ7_PLANE(1)
+      STFD_OZ7_PLANE(2)
+      STFD_OZ7_PLANE(3)
+      STFD_OZ7_PLANE(4)
+      STFD_OZ7_PLANE(5)
+      STFD_OZ7_PLANE(6)
+#undef STFD_OZ7_PLANE
+      // the row exponents of this quadrant's rows (written above by the four
+      // warps that also read them in the epilogue) are complete: a bounded wait,
+      // so that a warp that left on a timeout cannot stall the others
+      tc::mbar_arrive(tc::smem_u32(&exq[warp & 3]));
+      if (!__all_sync(0xFFFFFFFFu, tc::mbar_wait(tc::smem_u32(&exq[warp & 3]), (uint32_t)par, args.wait))) {
+        timed_out = true;
+        break;
+      }
+      // ---- the next tile's entries travel while the tensor cores work
+      {
+        const long long nt = tile + gridDim.x;
+        if (nt < args.ntiles) load_raw<KC>(Xw, nt, R, drow, dp, n, inner, Q, raw);
+      }
+      // ---- epilogue, chunk by chunk
+      const long long q = q0 + erow;
+      const bool row_ok = erow < R && q < Q;
+      long long base = 0;
+      if (row_ok) {
+        const long long o = q / inner;
+        base = o * (long long)n * inner + (q - o * inner);
+      }
+      for (int j = 0; j < nchunk; ++j) {
+        const int b = j & 1;
+        const int nc = min(kChunk, npad - kChunk * j);
+        const int per = nc / 4;   // 8 or 4 columns of this part
+        const bool ok = __all_sync(0xFFFFFFFFu, tc::mbar_wait(tc::smem_u32(&full[b]), b ? ph_f1 : ph_f0, args.wait));
+        if (b) ph_f1 ^= 1u;
+        else ph_f0 ^= 1u;
+        if (!ok) {
+          timed_out = true;
+          break;
         }
-      }
-    }
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (t == 0) {
-      issue_chunk(0);
-      if (nchunk > 1) issue_chunk(1);
-    }
-    // ---- the next tile's entries travel while the tensor cores work
-    {
-      const long long nt = tile + gridDim.x;
-      if (nt < args.ntiles) load_raw<KC>(Xw, nt, R, drow, dp, n, inner, Q, raw);
-    }
-    // ---- epilogue, chunk by chunk
-    const long long q = q0 + erow;
-    const bool row_ok = erow < R && q < Q;
-    long long base = 0;
-    if (row_ok) {
-      const long long o = q / inner;
-      base = o * (long long)n * inner + (q - o * inner);
-    }
-    const int ex = sEx[erow];
-    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    for (int j = 0; j < nchunk && !timed_out; ++j) {
-      const int b = j & 1;
-      const int nc = min(kChunk, npad - kChunk * j);
-      const int per = nc / kParts;   // 8 or 4 columns of this part
-      // warp-uniform, so that the .sync.aligned tensor-memory loads below are too
-      const uint32_t phb = b ? ph1 : ph0;
-      const bool ok = __all_sync(0xFFFFFFFFu, tc::mbar_wait(tc::smem_u32(&mbar[b]), phb, args.wait));
-      if (ok && t == 0) {
-        if (b) pend1 = -1;
-        else pend0 = -1;
-      }
-      if (b) ph1 ^= 1u;
-      else ph0 ^= 1u;
-      tc::fence_after_sync();
-      for (int g = 0; g < per; g += 4) {
-        const int col0 = kChunk * j + epart * per + g;   // first output column of this group
-        uint32_t Tr[kDig][4];
-        if (ok) {
+        tc::fence_after_sync();
+        const int ex = sEx[par * 128 + erow];
+        for (int g = 0; g < per; g += 4) {
+          const int col0 = kChunk * j + epart * per + g;
+          uint32_t Tr[kDig][4];
 #pragma unroll
           for (int c = 0; c < kDig; ++c)
             tc::tmem_ld4_async(lane_base + (uint32_t)(b * kBufCols + c * nc + epart * per + g), Tr[c]);
@@ -303,51 +370,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_oz7(Oz7Args args) {
 #pragma unroll
           for (int c = 0; c < kDig; ++c)
             asm volatile("" : "+r"(Tr[c][0]), "+r"(Tr[c][1]), "+r"(Tr[c][2]), "+r"(Tr[c][3]) : : "memory");
-        }
-        if (g + 4 >= per) {
-          // every thread has read this buffer: the MMAs of chunk j + 2 may overwrite it.
-          // The barrier also agrees on whether any warp's wait ran out.
-          tc::fence_before_sync();
-          timed_out = __syncthreads_or(ok ? 0 : 1) != 0;
-          if (!timed_out && t == 0 && j + 2 < nchunk) {
-            tc::fence_after_sync();
-            issue_chunk(j + 2);
+          if (g + 4 >= per) {   // this thread has read its share of the buffer
+            tc::fence_before_sync();
+            tc::mbar_arrive(tc::smem_u32(&empty[b]));
           }
-        }
-        if (timed_out) break;
-        if (!ok) continue;   // still reaches this chunk's barrier above
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int i = col0 + e;
-          if (!row_ok || i >= n) continue;
-          float T[kDig];
+          for (int e = 0; e < 4; ++e) {
+            const int i = col0 + e;
+            if (!row_ok || i >= n) continue;
+            float T[kDig];
 #pragma unroll
-          for (int c = 0; c < kDig; ++c) T[c] = __uint_as_float(Tr[c][e]);
-          const int ej = sEj[i];
-          double y;
-          if (ex >= 2047 || ej >= 2047) {
-            y = __longlong_as_double(0x7FF8000000000000ll);   // non-finite input row: NaN
-          } else {
-            y = combine7(T, ex + ej - 2106);
+            for (int c = 0; c < kDig; ++c) T[c] = __uint_as_float(Tr[c][e]);
+            const int ej = sEj[i];
+            const double y = (ex >= 2047 || ej >= 2047) ? __longlong_as_double(0x7FF8000000000000ll)
+                                                        : combine7(T, ex + ej - 2106);
+            args.Y[base + (long long)i * inner] = y;
           }
-          args.Y[base + (long long)i * inner] = y;
         }
       }
     }
-    if (timed_out) break;
-    tc::fence_before_sync();
-    __syncthreads();   // sEx and the digit planes are rewritten by the next tile
-    tc::fence_after_sync();
+  }
+  // ---- exit: a wait that ran out is reported; the MMA thread lets its own
+  // MMAs in flight finish (bounded) before tensor memory is released
+  const bool any_timeout = __syncthreads_or(timed_out ? 1 : 0) != 0;
+  if (mma_warp && lane == 0 && any_timeout) {   // pend*: the last commit on each buffer
+    if (args.status) atomicOr(args.status, kStatusTimeout);
+    if (pend0 >= 0) tc::mbar_wait(tc::smem_u32(&full[0]), (uint32_t)pend0, kDrainIters);
+    if (pend1 >= 0) tc::mbar_wait(tc::smem_u32(&full[1]), (uint32_t)pend1, kDrainIters);
   }
   tc::fence_after_sync();
-  if (t == 0 && timed_out) {
-    // a wait ran out: report it and let this CTA's MMAs in flight finish
-    // (bounded) before tensor memory is released
-    if (args.status) atomicOr(args.status, kStatusTimeout);
-    if (pend0 >= 0) tc::mbar_wait(tc::smem_u32(&mbar[0]), (uint32_t)pend0, kDrainIters);
-    if (pend1 >= 0) tc::mbar_wait(tc::smem_u32(&mbar[1]), (uint32_t)pend1, kDrainIters);
-    tc::fence_after_sync();
-  }
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
@@ -359,7 +410,7 @@ size_t oz7_smem_bytes(int n) {
   const int npad = (n + 15) / 16 * 16;
   const int R = oz7_rows(n);
   const size_t a_bytes = (size_t)(kDig * (R / 8) + (128 - R) / 8) * a_sbo(npad / 8);
-  return (size_t)kDig * npad * npad * 2 + a_bytes + (size_t)npad * 4 + 128 * 4 + 2 * 8 + 16;
+  return (size_t)kDig * npad * npad * 2 + a_bytes + (size_t)npad * 4 + 256 * 4 + (kDig + 8) * 8 + 16;
 }
 
 template <int KC>
@@ -380,7 +431,7 @@ cudaError_t launch_oz7(const double* X, double* Y, const unsigned char* B, const
   Oz7Args a{X, Y, B, ej, n, npad, R, (npad + kChunk - 1) / kChunk, inner, Q, ntiles, status_word(), wait_limit()};
   ProfScope ps("fd_mode_tc7", 2.0 * (double)Q * n * n, 8.0 * (double)Q * n * 2, st);
   // 227 KB requested so that exactly one CTA (which owns all 512 TMEM columns) fits per SM
-  return tc::launch_pdl(k_tc_oz7<KC>, dim3((unsigned)grid), dim3(kThreads), (size_t)227 * 1024, st, a);
+  return tc::launch_pdl(k_tc_oz7<KC>, dim3((unsigned)grid), dim3(kThreadsTotal), (size_t)227 * 1024, st, a);
 }
 
 }  // namespace

@@ -32,7 +32,7 @@ def test_context_usable_after_timeout():
     assert lib.stfd_device_status() == 0
 
 
-@pytest.mark.parametrize("prec", [stfd.STFD_FP64TC, stfd.STFD_TF32])
+@pytest.mark.parametrize("prec", [stfd.STFD_FP64TC, stfd.STFD_FP64TC7, stfd.STFD_TF32])
 def test_solve_reports_timeout_of_its_preconditioner(prec):
     """With the wait limit at 0 every tensor-core wait gives up at once: the
     kernels let their own work in flight finish, skip the rest and return, and
