@@ -43,11 +43,12 @@ NCU_TRAFFIC = {}
 # with the mode products on the tensor cores by seven exact digit slices per
 # entry (kept digit pairs accumulated exactly, one rounding to FP64, FP64
 # intermediates) and an IEEE-FP64 Step 3; the IEEE-FP64 banded matvec; FP64 GMRES.
-HEADLINE = dict(precond="STFD_FP64TC7", matvec="STFD_OP_FP64", dtype="f64",
+HEADLINE = dict(precond="STFD_FP64TC7", matvec="STFD_OP_FX64", dtype="f64",
                 precond_text="Algorithm 1, FP64: mode products on tcgen05 by seven exact BF16 digit slices per entry "
                              "(28 digit pairs, exact FP32 accumulators, one rounding to FP64; FP64 intermediates), "
                              "Step 3 in IEEE FP64",
-                matvec_text="IEEE FP64 sum-factorised banded products (FP64 pipe)")
+                matvec_text="FP64 sum-factorised banded products, each formed exactly in 64-bit integer limbs "
+                            "and rounded once to FP64 (FP64 intermediates)")
 
 
 def measured_peaks():
@@ -581,16 +582,15 @@ def main():
 
     # ---- preconditioner variants inside the same FP64 flexible GMRES
     variants = {}
-    A64 = A if HEADLINE["matvec"] == "STFD_OP_FP64" else \
-        stfd.KronOp(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], arith=stfd.STFD_OP_FP64)
+    A64 = stfd.KronOp(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], arith=stfd.STFD_OP_FP64)
     Adf = stfd.KronOp(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], arith=stfd.STFD_OP_DF32)
-    vlist = [("fp64_ieee", stfd.STFD_FP64, A64)]
-    if hasattr(stfd, "STFD_FP64TC7"):
-        vlist.append(("fp64tc7", stfd.STFD_FP64TC7, A64))
+    vlist = [("fp64_ieee", stfd.STFD_FP64, A64), ("fp64tc7_fx64mv", stfd.STFD_FP64TC7, A),
+             ("fp64tc7_fp64mv", stfd.STFD_FP64TC7, A64)]
     vlist += [("fp64tc48_df32mv", stfd.STFD_FP64TC, Adf), ("df32_df32mv", stfd.STFD_DF32, Adf),
               ("tf32", stfd.STFD_TF32, A64), ("bf16", stfd.STFD_BF16, A64)]
     for name, prec, op in vlist:
         Pv = P if prec == head_prec else stfd.FD(K, M, Wt, Mt, cfg["gamma"], cfg["nu"], precision=prec)
+        # the matvec of this variant alone, on the same input (CUDA events)
         for _ in range(3):
             Pv.apply(r, s)
         torch.cuda.synchronize()
@@ -610,13 +610,13 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         v_gm = e0.elapsed_time(e1) / args.steps
-        variants[name] = {"precond": name, "matvec": "fp64_ieee" if op is A64 else "df32 (2 x FP32, ~48-bit)",
+        variants[name] = {"precond": name,
+                          "matvec": "fp64_ieee" if op is A64 else "fx64 (exact integer limbs)" if op is A else "df32 (2 x FP32, ~48-bit)",
                           "fd_apply_ms": v_fd, "fd_apply_dofs_per_s": N / (v_fd * 1e-3), "gmres_ms": v_gm,
                           "gmres_iters": vinfo["iters"], "rel_res_true": vinfo["rel_res_true"], "_s": s_v}
         if Pv is not P:
             Pv.close()
-    if A64 is not A:
-        A64.close()
+    A64.close()
     Adf.close()
     ref_s = variants["fp64_ieee"]["_s"]
     for name in variants:
@@ -637,40 +637,55 @@ def main():
     total_ms = sum(rc["ms"] for rc in recs) or 1.0
     top = max(recs, key=lambda rc: rc["ms"])
     probe = stfd.stfd_probe_fp64_peak()
+    imad_probe = stfd.stfd_probe_imad_wide_peak()
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
     mhz = clocks.get("sm_mhz") or 2070.0
     per_launch_s = top["ms"] * 1e-3 / top["launches"]
     achieved = top["flops"] / top["launches"] / per_launch_s
     traffic = NCU_TRAFFIC.get(top["name"])
     peaks, peak_src = measured_peaks()
-    if top["name"] == "fd_mode_ozaki":
-        # 21 exact BF16 digit-pair GEMMs need ~26 us of tensor time per launch at the
-        # BF16 peak, moving 16 B/dof needs ~43 us at the HBM peak: HBM bounds the ideal.
-        peak = peaks.get("hbm_gbs", 6800.0) * 1e9
-        src = "HBM copy bandwidth (MEASURED_PEAKS.json, %s); achieved = algorithmic bytes (16 B/dof) / time" % peak_src
+    common = {"kernel": top["name"], "traffic": traffic, "share_of_step": top["ms"] / total_ms,
+              "achieved_gbs": top["bytes"] / top["launches"] / per_launch_s / 1e9,
+              "fp64_equivalent_tflops": achieved / 1e12, "fp64_probe_tflops": probe / 1e12,
+              "imad_wide_probe_tops": imad_probe / 1e12}
+    if top["name"] == "fd_mode_tc7":
+        # the issued BF16 MMA work: 28 digit pairs on M = 128 x N = npad x K = npad per 128-row
+        # tile slot (R of the rows valid) -- see tc_oz7.cu; peak: measured BF16 GEMM, sustained
+        # (the kernel runs inside a seconds-long loop of solves)
+        n_t = inputs.sizes(cfg)[1]
+        npad = (n_t + 15) // 16 * 16
+        R = 128 if n_t <= 64 else 112
+        mma_flops_per_row = 28.0 * 2.0 * npad * npad * 128.0 / R
+        rows = N / n_t          # rows of one mode product (the same for every mode at this workload)
+        tflops = mma_flops_per_row * rows / per_launch_s / 1e12
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+        roofline = dict(bound="tensor", achieved=tflops, peak=peak, unit="TFLOP/s", frac=tflops / peak,
+                        peak_source="BF16 dense GEMM, sustained (MEASURED_PEAKS.json, %s)" % peak_src,
+                        achieved_definition="issued BF16 MMA flops of the 28 digit pairs / CUDA-event time",
+                        **common)
+    elif top["name"] == "band_fx64":
+        # three 32 x 32 -> 64-bit multiply-adds per exact tap product; peak = the probe above
+        taps = 0.0
+        for l in range(cfg["d"] + 1):
+            taps += {0: 2, cfg["d"]: 2}.get(l, 3) * (2 * cfg["p"] + 1)
+        ops_per_launch = 3.0 * taps * N / (cfg["d"] + 1)     # mean over the d + 1 passes of one matvec
+        tops = ops_per_launch / per_launch_s / 1e12
+        roofline = dict(bound="alu", achieved=tops, peak=imad_probe / 1e12, unit="Tops/s (mad.wide.s32)",
+                        frac=tops * 1e12 / imad_probe,
+                        peak_source="32 x 32 -> 64-bit multiply-add throughput probed in this run",
+                        achieved_definition="3 multiply-adds per exact tap product x taps of the pass / time",
+                        **common)
     elif top["name"].endswith("_df"):
         # double-float kernels issue 12 FP32 instructions per FP64-equivalent FMA
         # (2 flop): peak = 128 FP32 lanes x SMs x clock x 2 / 12
         peak = 128 * sms * mhz * 1e6 * 2 / 12
-        src = "FP32 pipes: 128 lanes/SM x %d SMs x %.0f MHz (sampled) / 12 FP32 ops per double-float FMA" % (sms, mhz)
+        roofline = dict(bound="alu", achieved=achieved / 1e12, peak=peak / 1e12, unit="TFLOP/s", frac=achieved / peak,
+                        peak_source="FP32 pipes: 128 lanes/SM x %d SMs x %.0f MHz / 12 FP32 ops per double-float FMA"
+                        % (sms, mhz), **common)
     else:
         peak = 2 * 2 * sms * mhz * 1e6
-        src = "FP64: 2 DFMA/clk/SM x %d SMs x %.0f MHz (sampled); DFMA probe in this run %.3f TFLOP/s" % (
-            sms, mhz, probe / 1e12)
-    if top["name"] == "fd_mode_ozaki":
-        gbs = top["bytes"] / top["launches"] / per_launch_s
-        roofline = {"bound": "hbm", "achieved": gbs / 1e9, "peak": peak / 1e9, "unit": "GB/s",
-                    "frac": gbs / peak, "traffic": traffic, "kernel": top["name"], "peak_source": src,
-                    "fp64_equivalent_tflops": achieved / 1e12,
-                    "bf16_tensor_tflops": 21.0 * achieved / 1e12,
-                    "share_of_step": top["ms"] / total_ms, "fp64_probe_tflops": probe / 1e12}
-    else:
-        roofline = None
-    if roofline is None:
-        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": traffic, "kernel": top["name"], "peak_source": src,
-                    "achieved_gbs": top["bytes"] / top["launches"] / per_launch_s / 1e9,
-                    "share_of_step": top["ms"] / total_ms, "fp64_probe_tflops": probe / 1e12}
+        roofline = dict(bound="alu", achieved=achieved / 1e12, peak=peak / 1e12, unit="TFLOP/s", frac=achieved / peak,
+                        peak_source="FP64: 2 DFMA/clk/SM x %d SMs x %.0f MHz (sampled)" % (sms, mhz), **common)
     # per kernel family: time share and the achieved rates of its algorithmic work
     # (FP64-equivalent flops, minimum HBM bytes: each input read once, each output written once)
     kernels = {rc["name"]: {"launches": rc["launches"], "ms": round(rc["ms"], 3),

@@ -201,9 +201,18 @@ void stfd_fd_destroy(stfd_fd* h);
  *                 split exactly by FMA, sums by error-free two-sum; FP64 input
  *                 and output. Agrees with STFD_OP_FP64 to about 1e-14 relative
  *                 and is several times faster on GPUs with low FP64 throughput.
+ *   STFD_OP_FX64  FP64 results, intermediates and inputs; each band product is
+ *                 formed exactly in 64-bit integer arithmetic (every fibre of the
+ *                 input and every band row written as 53-bit integers under their
+ *                 own powers of two, 27-bit limbs, 4 integer multiply-adds per
+ *                 tap) and rounded once to FP64; an output summing two products
+ *                 of different inputs adds the two rounded FP64 values. Entries
+ *                 far below their fibre's largest entry are rounded at 2^-53 of
+ *                 that entry (normwise FP64 accuracy). Needs every half-bandwidth
+ *                 in 1..4; otherwise the op uses the STFD_OP_FP64 passes.
  * ------------------------------------------------------------------------ */
 typedef struct stfd_op stfd_op;
-enum { STFD_OP_FP64 = 0, STFD_OP_DF32 = 1 };
+enum { STFD_OP_FP64 = 0, STFD_OP_DF32 = 1, STFD_OP_FX64 = 2 };
 
 int stfd_op_create_kron(stfd_op** out, int d, const int* n,
                         const double* const* K, const double* const* M,

@@ -40,6 +40,12 @@ long long stfd_launch_count(void);
  * result is the denominator of an FP64-ALU roofline. Synchronous. */
 int stfd_probe_fp64_peak(double* flops_per_s, void* stream);
 
+/* Measured rate of 32 x 32 -> 64-bit integer multiply-adds (mad.wide.s32, eight
+ * independent chains per thread, all SMs), in operations per second: the
+ * ceiling of the integer-limb band products (STFD_OP_FX64), which need three
+ * per tap. Synchronous; allocates a small buffer. */
+int stfd_probe_imad_wide_peak(double* ops_per_s, void* stream);
+
 /* Failure-detection self-test of the bounded device waits used by the
  * tensor-core kernels: one thread initialises an mbarrier that nothing ever
  * arrives on and waits on it for at most `max_iters` polls; when the wait gives

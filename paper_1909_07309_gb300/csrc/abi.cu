@@ -157,6 +157,11 @@ struct stfd_op {
   float4* MM4[kMaxDim] = {nullptr, nullptr, nullptr};
   float4* WMt4 = nullptr;
   float4* WTMt4 = nullptr;
+  // STFD_OP_FX64: integer-limb band tables per direction (M, K) and for the time
+  // pass (gamma W, nu M_t) and (gamma W^T, nu M_t), with the row exponents
+  bool fx = false;
+  int2* FXC[kMaxDim + 2] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int* FXE[kMaxDim + 2] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   // general spatial matrices (stfd_op_create_stencil)
   int kind = 0;                                   // 0: Kronecker factors, 1: stencil
   StencilOpDev sop;
@@ -700,6 +705,10 @@ extern "C" void stfd_op_destroy(stfd_op* A) {
   }
   dev_free(A->WMt4);
   dev_free(A->WTMt4);
+  for (int k = 0; k < kMaxDim + 2; ++k) {
+    dev_free(A->FXC[k]);
+    dev_free(A->FXE[k]);
+  }
   for (int k = 0; k < 4; ++k) dev_free(A->tmp[k]);
   for (int k = 0; k < 7; ++k) dev_free(A->sbuf[k]);
   dev_free(A->MtbU);
@@ -716,7 +725,7 @@ extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const dou
   for (int l = 0; l < d; ++l)
     if (!K[l] || !M[l]) return STFD_ERR_ARG;
   if (!std::isfinite(gamma) || !std::isfinite(nu)) return STFD_ERR_ARG;
-  if (arith != STFD_OP_FP64 && arith != STFD_OP_DF32) return STFD_ERR_ARG;
+  if (arith != STFD_OP_FP64 && arith != STFD_OP_DF32 && arith != STFD_OP_FX64) return STFD_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   stfd_op* A = new (std::nothrow) stfd_op;
   if (!A) return STFD_ERR_ALLOC;
@@ -765,6 +774,38 @@ extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const dou
         if (a >= 0 && a < n[d]) MbU[(size_t)t * (2 * A->pt + 1) + k] = Mt[t + (size_t)n[d] * a];
       }
     rc = dev_upload(&A->MtbU, MbU.data(), MbU.size(), st);
+  }
+  // integer-limb band tables (STFD_OP_FX64) when every half-bandwidth is 1..4;
+  // otherwise the op keeps the FP64 passes (the same arithmetic class)
+  std::vector<std::vector<int2>> keepc;
+  std::vector<std::vector<int>> keepe;
+  if (rc == STFD_OK && arith == STFD_OP_FX64) {
+    int pb[kMaxDim + 1];
+    bool ok = true;
+    for (int l = 0; l <= d; ++l) {
+      pb[l] = l < d ? std::max(A->bwM[l], A->bwK[l]) : std::max(A->bwW, A->bwMt);
+      if (pb[l] < 1 || pb[l] > 4) ok = false;
+    }
+    A->fx = ok;
+    if (ok) {
+      for (int l = 0; l <= d; ++l) A->pb[l] = pb[l];
+      const size_t nt2 = (size_t)n[d] * n[d];
+      std::vector<double> gW(nt2), gWT(nt2), nMt(nt2);
+      for (size_t k = 0; k < nt2; ++k) {
+        gW[k] = gamma * keep[2 * d][k];
+        gWT[k] = gamma * keep[2 * d + 2][k];
+        nMt[k] = nu * keep[2 * d + 1][k];
+      }
+      for (int k = 0; k <= d + 1 && rc == STFD_OK; ++k) {
+        keepc.emplace_back();
+        keepe.emplace_back();
+        if (k < d) fx_tables(keep[2 * k].data(), keep[2 * k + 1].data(), n[k], pb[k], keepc.back(), keepe.back());
+        else fx_tables(k == d ? gW.data() : gWT.data(), nMt.data(), n[d], pb[d], keepc.back(), keepe.back());
+        rc = dev_upload(&A->FXC[k], keepc.back().data(), keepc.back().size(), st);
+        if (rc == STFD_OK) rc = dev_upload(&A->FXE[k], keepe.back().data(), keepe.back().size(), st);
+      }
+      if (rc == STFD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = STFD_ERR_CUDA;   // gW, gWT, nMt die here
+    }
   }
   // double-float copies (hi, lo) of the row-major factors: keep = [M_0, K_0, M_1, K_1, ..., W_t, M_t]
   std::vector<std::vector<float2>> keep2;
@@ -995,6 +1036,32 @@ int matvec_one_df(const stfd_op* A, const double* x, double* y, int trans, cudaS
   return STFD_OK;
 }
 
+// The same sum-factorisation with FP64 intermediates, every band product formed
+// exactly in 64-bit integer limbs and rounded once (band_fx.cu); rotated layouts
+// as in the double-float passes.
+int matvec_one_fx(const stfd_op* A, const double* x, double* y, int trans, cudaStream_t st) {
+  const int d = A->d;
+  double* const* T = A->tmp;
+  const double* u = nullptr;
+  const double* v = nullptr;
+  for (int l = 0; l < d; ++l) {
+    const int nl = A->n[l];
+    double* uo = (l % 2 == 0) ? T[0] : T[2];
+    double* vo = (l % 2 == 0) ? T[1] : T[3];
+    if (l == 0) {
+      STFD_CU(launch_band_first_fx(x, A->FXC[0], A->FXE[0], uo, vo, nl, 1, A->N / nl, A->pb[0], 1, st));
+    } else {
+      STFD_CU(launch_band_mid_fx(u, v, A->FXC[l], A->FXE[l], uo, vo, nl, 1, A->N / nl, A->pb[l], 1, st));
+    }
+    u = uo;
+    v = vo;
+  }
+  const int nt = A->n[d];
+  const int k = trans ? d + 1 : d;
+  STFD_CU(launch_band_last_fx(u, v, A->FXC[k], A->FXE[k], y, nt, 1, A->N / nt, A->pb[d], 1, st));
+  return STFD_OK;
+}
+
 // y = A x (trans = 0) or y = A^T x (trans = 1); A^T = gamma W_t^T x M_s + nu M_t x K_s
 // since every factor but W_t is symmetric.
 int matvec_one(const stfd_op* A, const double* x, double* y, int trans, cudaStream_t st) {
@@ -1003,6 +1070,7 @@ int matvec_one(const stfd_op* A, const double* x, double* y, int trans, cudaStre
     return STFD_OK;
   }
   if (A->arith == STFD_OP_DF32) return matvec_one_df(A, x, y, trans, st);
+  if (A->fx) return matvec_one_fx(A, x, y, trans, st);
   const int d = A->d;
   double* const* T = A->tmp;
   long long inner = 1;

@@ -111,6 +111,18 @@ cudaError_t launch_band_mid_pk(const float2* u, const float2* v, const float4* M
 cudaError_t launch_band_last_pk(const float2* u, const float2* v, const float4* WMt, double gamma, double nu,
                                 double* y, int n, long long inner, long long outer, int p, int rot, cudaStream_t st);
 
+// FP64 banded passes in exact 64-bit integer arithmetic (band_fx.cu), same pass
+// structure and rotated layouts as the paired double-float passes; C / Ce from
+// fx_tables (first and middle passes: (M, K); time pass: (gamma W or gamma W^T,
+// nu M_t)); p in 1..4 (cudaErrorInvalidValue otherwise).
+cudaError_t launch_band_first_fx(const double* x, const int2* C, const int* Ce, double* Uo, double* Vo, int n,
+                                 long long inner, long long outer, int p, int rot, cudaStream_t st);
+cudaError_t launch_band_mid_fx(const double* u, const double* v, const int2* C, const int* Ce, double* Uo, double* Vo,
+                               int n, long long inner, long long outer, int p, int rot, cudaStream_t st);
+cudaError_t launch_band_last_fx(const double* u, const double* v, const int2* C, const int* Ce, double* y, int n,
+                                long long inner, long long outer, int p, int rot, cudaStream_t st);
+void fx_tables(const double* A, const double* B, int n, int p, std::vector<int2>& C, std::vector<int>& Ce);
+
 // Double-float Algorithm 1 (fd_df.cu): dense mode product with (hi, lo) row-major
 // factor J, X FP64 or float2, Y float2 or FP64 (not both FP64); Step 3 in place on
 // a float2 spectral tensor with per-pair B = gamma lam_j, BB = B^2, G = gamma g.

@@ -110,10 +110,57 @@ __global__ void k_probe_dfma(double* out, int iters, double c) {
   out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
 }
 
+// Eight independent chains of 32 x 32 -> 64-bit integer multiply-adds per
+// thread (mad.wide.s32, the operation of the integer-limb band products).
+__global__ void k_probe_imad_wide(long long* out, int iters, int b) {
+  long long a0 = threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6,
+            a7 = a0 + 7;
+  // each chain multiplies by its own low word: no common subexpression to hoist
+  for (int i = 0; i < iters; ++i) {
+    a0 += (long long)(int)a0 * b; a1 += (long long)(int)a1 * b; a2 += (long long)(int)a2 * b;
+    a3 += (long long)(int)a3 * b; a4 += (long long)(int)a4 * b; a5 += (long long)(int)a5 * b;
+    a6 += (long long)(int)a6 * b; a7 += (long long)(int)a7 * b;
+  }
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+
 }  // namespace
 }  // namespace stfd
 
 using namespace stfd;
+
+extern "C" int stfd_probe_imad_wide_peak(double* ops_per_s, void* stream) {
+  if (!ops_per_s) return STFD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return STFD_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return STFD_ERR_CUDA;
+  const int threads = 256, blocks = sms * 8, iters = 4000;
+  long long* out = nullptr;
+  if (cudaMalloc((void**)&out, (size_t)threads * blocks * sizeof(long long)) != cudaSuccess) return STFD_ERR_ALLOC;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = STFD_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = STFD_ERR_CUDA;
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && rc == STFD_OK; ++rep) {
+    cudaEventRecord(e0, st);
+    k_probe_imad_wide<<<blocks, threads, 0, st>>>(out, iters, 3);
+    count_launch();
+    cudaEventRecord(e1, st);
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = STFD_ERR_CUDA;
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  if (rc == STFD_OK) *ops_per_s = 8.0 * iters * (double)threads * blocks / (best * 1e-3);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  return rc;
+}
 
 extern "C" int stfd_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(g_mu);

@@ -18,7 +18,7 @@ STFD_NOT_CONVERGED = 1
 STFD_FP64, STFD_TF32, STFD_BF16, STFD_DF32, STFD_FP64TC, STFD_FP64TC7 = 0, 1, 2, 3, 4, 5
 STFD_BC_NONE, STFD_BC_INITIAL, STFD_BC_DIRICHLET = 0, 1, 2
 STFD_NOALLOC_MAX_N = 524288
-STFD_OP_FP64, STFD_OP_DF32 = 0, 1
+STFD_OP_FP64, STFD_OP_DF32, STFD_OP_FX64 = 0, 1, 2
 STFD_GEOM_BOX, STFD_GEOM_QUARTER_ANNULUS, STFD_GEOM_REVOLVED_QUARTER_ANNULUS = 0, 1, 2
 
 _c_int_p = ctypes.POINTER(ctypes.c_int)
@@ -117,6 +117,7 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_longlong), _c_dbl_p, _c_dbl_p, _c_dbl_p]),
     "stfd_launch_count": (ctypes.c_longlong, []),
     "stfd_probe_fp64_peak": (ctypes.c_int, [_c_dbl_p, ctypes.c_void_p]),
+    "stfd_probe_imad_wide_peak": (ctypes.c_int, [_c_dbl_p, ctypes.c_void_p]),
     "stfd_probe_bounded_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p]),
     "stfd_probe_convert": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -639,6 +640,13 @@ def stfd_probe_fp64_peak(stream=None):
     """Measured FP64 FMA throughput of the current device (FLOP/s)."""
     v = ctypes.c_double(0.0)
     _check(load().stfd_probe_fp64_peak(ctypes.byref(v), _stream(stream)), "stfd_probe_fp64_peak")
+    return v.value
+
+
+def stfd_probe_imad_wide_peak(stream=None):
+    """Measured 32 x 32 -> 64-bit integer multiply-add throughput (operations/s)."""
+    v = ctypes.c_double(0.0)
+    _check(load().stfd_probe_imad_wide_peak(ctypes.byref(v), _stream(stream)), "stfd_probe_imad_wide_peak")
     return v.value
 
 

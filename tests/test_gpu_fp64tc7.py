@@ -53,3 +53,28 @@ def test_nonfinite_input_row_gives_nan():
     r[5] = float("inf")
     s = P.apply(r)
     assert bool(torch.isnan(s).any())
+
+
+@pytest.mark.parametrize("d,p,n_el,T,gamma,nu", [(1, 3, 60, 1.0, 1.0, 1.0), (2, 2, 30, 0.5, 2.0, 0.3),
+                                                 (3, 3, 13, 1.0, 1.0, 1.0), (3, 4, 9, 1.5, 0.7, 1.9),
+                                                 (2, 1, 40, 1.0, 1.0, 1.0)])
+def test_integer_limb_matvec_agrees_with_ieee_fp64(d, p, n_el, T, gamma, nu):
+    """STFD_OP_FX64 forms every band product exactly and rounds once: it agrees
+    with the IEEE-FP64 matvec within a few FP64 roundings, for both A and A^T."""
+    K, M, Wt, Mt = stfd.heat_problem(d, p, n_el, T=T)
+    Ax = stfd.KronOp(K, M, Wt, Mt, gamma, nu, arith=stfd.STFD_OP_FX64)
+    A64 = stfd.KronOp(K, M, Wt, Mt, gamma, nu, arith=stfd.STFD_OP_FP64)
+    x = torch.as_tensor(inputs.standard_normal(Ax.N, 44), device="cuda")
+    for tr in (False, True):
+        y, y64 = Ax.matvec(x, transpose=tr), A64.matvec(x, transpose=tr)
+        err = float(torch.max(torch.abs(y - y64)) / torch.max(torch.abs(y64)))
+        assert err <= 1e-15, (tr, err)
+
+
+@pytest.mark.parametrize("shift", [100, -100, 900, -900])
+def test_integer_limb_matvec_power_of_two_homogeneity(shift):
+    K, M, Wt, Mt = stfd.heat_problem(3, 3, 10)
+    A = stfd.KronOp(K, M, Wt, Mt, arith=stfd.STFD_OP_FX64)
+    x = torch.as_tensor(inputs.standard_normal(A.N, 45), device="cuda")
+    two = torch.tensor(shift, device="cuda")
+    assert torch.equal(torch.ldexp(A.matvec(x), two), A.matvec(torch.ldexp(x, two)))

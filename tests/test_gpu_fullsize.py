@@ -67,7 +67,7 @@ def test_fd_apply_full_size_matches_oracle(scale, prec):
     P.close()
 
 
-@pytest.mark.parametrize("arith,tol", [(stfd.STFD_OP_FP64, 1e-13), (stfd.STFD_OP_DF32, 1e-12)])
+@pytest.mark.parametrize("arith,tol", [(stfd.STFD_OP_FP64, 1e-13), (stfd.STFD_OP_FX64, 1e-13), (stfd.STFD_OP_DF32, 1e-12)])
 def test_st_matvec_full_size_matches_oracle(scale, arith, tol):
     cfg = scale["cfg"]
     K, M, Wt, Mt = scale["mats"]

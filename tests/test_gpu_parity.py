@@ -85,10 +85,11 @@ MV_CASES = [(1, 3, 30, 1.0, 1.0, 1.0, 1), (2, 2, 16, 1.0, 1.0, 1.0, 2), (2, 4, 1
             (1, 2, 120, 1.0, 1.0, 1.0, 1)]   # n_t = 121: the time pass takes the unpaired kernel
 
 
-@pytest.mark.parametrize("arith", [stfd.STFD_OP_FP64, stfd.STFD_OP_DF32])
+@pytest.mark.parametrize("arith", [stfd.STFD_OP_FP64, stfd.STFD_OP_DF32, stfd.STFD_OP_FX64])
 @pytest.mark.parametrize("d,p,n_el,T,gamma,nu,nrhs", MV_CASES)
 def test_st_matvec_matches_oracle(d, p, n_el, T, gamma, nu, nrhs, arith):
-    """FP64 and double-float (about 48-bit) matvec both agree with the oracle to 1e-13."""
+    """FP64, integer-limb FP64 and double-float (about 48-bit) matvec all agree
+    with the oracle to 1e-13."""
     K, M, Wt, Mt = stfd.heat_problem(d, p, n_el, T=T)
     A = stfd.KronOp(K, M, Wt, Mt, gamma, nu, arith=arith)
     x = inputs.standard_normal(A.N, seed=3, batch=nrhs).reshape(nrhs, A.N)
@@ -101,7 +102,7 @@ def test_st_matvec_matches_oracle(d, p, n_el, T, gamma, nu, nrhs, arith):
 
 @pytest.mark.parametrize("arith,prec", [(stfd.STFD_OP_FP64, stfd.STFD_FP64), (stfd.STFD_OP_DF32, stfd.STFD_FP64),
                                         (stfd.STFD_OP_DF32, stfd.STFD_DF32), (stfd.STFD_OP_DF32, stfd.STFD_FP64TC),
-                                        (stfd.STFD_OP_FP64, stfd.STFD_FP64TC7)])
+                                        (stfd.STFD_OP_FP64, stfd.STFD_FP64TC7), (stfd.STFD_OP_FX64, stfd.STFD_FP64TC7)])
 def test_gmres_unit_cube_single_iteration(arith, prec):
     """Unit cube, T = 1, constant coefficients: P = A, one iteration (Sec. 4, F = id)."""
     d, p, n_el = 3, 3, 12
@@ -119,7 +120,8 @@ def test_gmres_unit_cube_single_iteration(arith, prec):
     assert np.linalg.norm(host(u) - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("restart,arith", [(100, stfd.STFD_OP_FP64), (4, stfd.STFD_OP_FP64), (100, stfd.STFD_OP_DF32)])
+@pytest.mark.parametrize("restart,arith", [(100, stfd.STFD_OP_FP64), (4, stfd.STFD_OP_FP64), (100, stfd.STFD_OP_DF32),
+                                           (4, stfd.STFD_OP_FX64)])
 def test_gmres_mismatched_preconditioner(restart, arith):
     """nu_A = 2, nu_P = 1: several iterations; same count as the oracle's
     GMRES (same Krylov space; CGS2 vs MGS differ only by rounding), true
@@ -202,7 +204,7 @@ def test_fd_apply_full_size_residual_samples(prec):
     assert worst <= 1e-10 * np.max(np.abs(r)), worst
 
 
-@pytest.mark.parametrize("arith", [stfd.STFD_OP_DF32, stfd.STFD_OP_FP64])
+@pytest.mark.parametrize("arith", [stfd.STFD_OP_DF32, stfd.STFD_OP_FP64, stfd.STFD_OP_FX64])
 def test_st_matvec_full_size_samples(arith):
     """Workload at scale (d = 3, p = 3, 64 elements, N = 18,125,250), the
     matvec the bench times: 400 sampled entries of A x against the rows the
