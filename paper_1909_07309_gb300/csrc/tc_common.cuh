@@ -85,6 +85,17 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t da, uint64_t db, u
         : "memory");
 }
 
+// BF16 MMA with the two descriptors given as 32-bit halves (the start-address
+// field lives in the low half, so consecutive K steps advance only that word).
+__device__ __forceinline__ void mma_bf16_lohi(uint32_t tmem_d, uint32_t da_lo, uint32_t da_hi, uint32_t db_lo,
+                                              uint32_t db_hi, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n .reg .b64 da, db;\n setp.ne.b32 p, %6, 0;\n mov.b64 da, {%1, %2};\n"
+      " mov.b64 db, {%3, %4};\n tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n}\n" ::"r"(tmem_d),
+      "r"(da_lo), "r"(da_hi), "r"(db_lo), "r"(db_hi), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t mbar_addr) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr)
                : "memory");

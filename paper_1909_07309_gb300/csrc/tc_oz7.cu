@@ -136,25 +136,34 @@ __device__ __forceinline__ void load_raw(const long long* __restrict__ Xw, long 
   }
 }
 
-// The biased 55-bit integer of one entry, W = V + 0x80808080808080 (its bytes
-// minus 128 are the seven digits of |x|, see above), for a row of largest
-// biased exponent E. Branch-free: V = round(4 m 2^-s), s = E - max(e, 1).
+// The biased integer W = V + 0x80808080808080 of one entry, V = +-round(4 m
+// 2^-s) the signed 55-bit integer of the entry in a row of largest biased
+// exponent E (s = E - max(e, 1); branch-free). |V| < 2^55 < the bias, so W > 0,
+// and the bytes of W minus 128 are the signed digits of V (d_0 from the top
+// bits: W >> 48 minus 128, in [-128, 129]; the others in [-128, 127]).
 __device__ __forceinline__ unsigned long long wbias(long long w, int E) {
   const unsigned long long u = (unsigned long long)w;
   const int e = (int)((u >> 52) & 0x7FF);
   const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(e != 0) << 52);
   const int s = min(E - max(e, 1), 63);
-  return (((m << 2) + ((1ull << s) >> 1)) >> s) + kByteBias;
+  const long long mag = (long long)(((m << 2) + ((1ull << s) >> 1)) >> s);
+  return (unsigned long long)((u >> 63) ? -mag : mag) + kByteBias;
 }
 
 // Digit k of an entry with biased integer (hi, lo) as a float: byte k from the
-// top (the top one up to 9 bits) minus 128 -- the magnitude's digit; the
-// entry's sign is applied to the packed BF16 pair.
+// top (the top one up to 9 bits) minus 128.
+// For k >= 1 one byte permute moves the byte next to the exponent bits of 2^23.
 template <int k>
 __device__ __forceinline__ float digit_of(uint32_t hi, uint32_t lo) {
-  const uint32_t b = k == 0 ? (hi >> 16) : k == 1 ? ((hi >> 8) & 0xFFu) : k == 2 ? (hi & 0xFFu)
-                   : k == 3 ? (lo >> 24) : k == 4 ? ((lo >> 16) & 0xFFu) : k == 5 ? ((lo >> 8) & 0xFFu) : (lo & 0xFFu);
-  return __uint_as_float(0x4B000000u | b) - 8388736.0f;   // (2^23 + b) - (2^23 + 128)
+  uint32_t f;
+  if (k == 0) {
+    f = 0x4B000000u | (hi >> 16);
+  } else {
+    // selector: result bytes (b0, b1, b2, b3) = (byte of the word, 0, 0, 0x4B) from {word, 0x4B000000}
+    constexpr uint32_t byte_sel = k == 1 ? 1u : k == 2 ? 0u : k == 3 ? 3u : k == 4 ? 2u : k == 5 ? 1u : 0u;
+    f = __byte_perm(k <= 2 ? hi : lo, 0x4B000000u, byte_sel | 0x4440u | 0x7000u);
+  }
+  return __uint_as_float(f) - 8388736.0f;   // (2^23 + b) - (2^23 + 128)
 }
 
 // 17 warps: warps 0..15 convert the tile's entries into digit planes, one plane
@@ -220,17 +229,31 @@ __global__ void __launch_bounds__(kThreadsTotal, 1) k_tc_oz7(Oz7Args args) {
     const int ksteps = npad / 16;
     uint32_t ph_pl = 0u, ph_e0 = 0u, ph_e1 = 0u;
     int uses0 = 0, uses1 = 0;     // buffer uses so far (the first needs no drain wait)
-    auto issue_plane = [&](int j, int k) {
+    // descriptors: the start-address field (low word) advances by 16 (256 bytes) per K step
+    const uint64_t da_base = tc::smem_desc(a_addr, 128u, sbo_a);
+    const uint64_t db_base = tc::smem_desc(b_addr, 128u, sbo_b);
+    const uint32_t a_hi = (uint32_t)(da_base >> 32), b_hi = (uint32_t)(db_base >> 32);
+    const uint32_t a_lo0 = (uint32_t)da_base, b_lo0 = (uint32_t)db_base;
+    // MMAs of plane k for chunks j0 .. j0 + cnt - 1, their K steps interleaved so
+    // that consecutive MMAs accumulate into different tensor-memory buffers
+    auto issue_plane = [&](int j0, int cnt, int k) {
       if (lane != 0) return;
-      const int nc = min(kChunk, npad - kChunk * j);
-      const uint32_t dbase = tmem + (uint32_t)((j & 1) * kBufCols);
-      const uint32_t brow0 = (uint32_t)(kDig * kChunk * j);
-      const uint64_t db0 = tc::smem_desc(b_addr + (brow0 / 8) * sbo_b, 128u, sbo_b);
-      const uint32_t idesc = tc::instr_desc(1u, 128, (kDig - k) * nc);
-      const uint64_t da0 = tc::smem_desc(a_addr + (uint32_t)(k * plane_a), 128u, sbo_a);
-      for (int s = 0; s < ksteps; ++s)
-        tc::mma<0>(dbase + (uint32_t)(k * nc), da0 + (uint64_t)((s * 256) >> 4), db0 + (uint64_t)((s * 256) >> 4),
-                   idesc, (k > 0 || s > 0) ? 1u : 0u);
+      uint32_t dcol[2], db[2], idesc[2];
+      for (int u = 0; u < cnt; ++u) {
+        const int j = j0 + u;
+        const int nc = min(kChunk, npad - kChunk * j);
+        dcol[u] = tmem + (uint32_t)((j & 1) * kBufCols + k * nc);
+        db[u] = b_lo0 + (uint32_t)(kDig * kChunk * j / 8) * (sbo_b >> 4);
+        idesc[u] = tc::instr_desc(1u, 128, (kDig - k) * nc);
+      }
+      uint32_t da = a_lo0 + (uint32_t)(k * (plane_a >> 4));
+      for (int s = 0; s < ksteps; ++s) {
+        for (int u = 0; u < cnt; ++u) {
+          tc::mma_bf16_lohi(dcol[u], da, a_hi, db[u], b_hi, idesc[u], (k > 0 || s > 0) ? 1u : 0u);
+          db[u] += 16u;
+        }
+        da += 16u;
+      }
     };
     auto wait_empty = [&](int b) -> bool {   // buffer b drained by the workers
       if ((b ? uses1 : uses0) == 0) return true;
@@ -254,10 +277,9 @@ __global__ void __launch_bounds__(kThreadsTotal, 1) k_tc_oz7(Oz7Args args) {
           break;
         }
         tc::fence_after_sync();
-        for (int j = 0; j < first; ++j) {
-          issue_plane(j, k);
-          if (k == kDig - 1) commit(j);
-        }
+        issue_plane(0, first, k);
+        if (k == kDig - 1)
+          for (int j = 0; j < first; ++j) commit(j);
       }
       ph_pl ^= 1u;
       for (int j = 2; j < nchunk && !timed_out; ++j) {
@@ -266,7 +288,7 @@ __global__ void __launch_bounds__(kThreadsTotal, 1) k_tc_oz7(Oz7Args args) {
           break;
         }
         tc::fence_after_sync();
-        for (int k = 0; k < kDig; ++k) issue_plane(j, k);
+        for (int k = 0; k < kDig; ++k) issue_plane(j, 1, k);
         commit(j & 1);
       }
     }
@@ -293,13 +315,12 @@ __global__ void __launch_bounds__(kThreadsTotal, 1) k_tc_oz7(Oz7Args args) {
       E = max(E, __shfl_xor_sync(0xFFFFFFFFu, E, 8));
       E = max(E, __shfl_xor_sync(0xFFFFFFFFu, E, 16));
       if (dp == 0) sEx[par * 128 + drow] = E;
-      uint32_t whi[KC], wlo[KC], neg = 0u;
+      uint32_t whi[KC], wlo[KC];
 #pragma unroll
       for (int c = 0; c < KC; ++c) {
         const unsigned long long W = wbias(raw[c], E);
         whi[c] = (uint32_t)(W >> 32);
         wlo[c] = (uint32_t)W;
-        neg |= (uint32_t)((unsigned long long)raw[c] >> 63) << c;
       }
       const bool rows_ok = drow < R;   // rows >= R of the MMA read the next plane
 #define STFD_OZ7_PLANE(k)                                                                                  \
@@ -310,9 +331,8 @@ __global__ void __launch_bounds__(kThreadsTotal, 1) k_tc_oz7(Oz7Args args) {
         if (a >= npad) continue;                                                                         \
         const __nv_bfloat162 v = __floats2bfloat162_rn(digit_of<k>(whi[c], wlo[c]),                      \
                                                        digit_of<k>(whi[c + 1], wlo[c + 1]));             \
-        const uint32_t sgn = (((neg >> c) & 1u) << 15) | (((neg >> (c + 1)) & 1u) << 31);                \
-        *reinterpret_cast<uint32_t*>(sA + (k) * plane_a + drbase + (size_t)(a >> 3) * 128 +              \
-                                     (size_t)(a & 7) * 2) = *reinterpret_cast<const uint32_t*>(&v) ^ sgn; \
+        *reinterpret_cast<__nv_bfloat162*>(sA + (k) * plane_a + drbase + (size_t)(a >> 3) * 128 +        \
+                                           (size_t)(a & 7) * 2) = v;                                     \
       }                                                                                                  \
     }                                                                                                    \
     tc::fence_async_smem();                                                                              \
