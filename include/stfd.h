@@ -383,11 +383,10 @@ int stfd_grad_kappa_elements(const stfd_op* A, int p, int n_el, const double* Ke
  * (0,1)^d x (0,T), constant coefficients gamma, nu, each with its own number
  * of elements n_el[k], degree p[k] (space and time) and number of right-hand
  * sides nrhs[k]. Not a section of the paper: it batches its method. On the
- * unit box the preconditioner of eq. prec_definition equals A, so FD-
- * preconditioned GMRES converges in one iteration (Sec. 4); the batched
- * solve performs exactly that iteration, u = P^{-1} f by Algorithm 1, and the
- * true relative residual ||f - A u|| / ||f|| (eq. syst_mat, sum-factorised)
- * per right-hand side, all in FP64-accurate double-float arithmetic.
+ * unit box the preconditioner of eq. prec_definition equals A (Sec. 4); each
+ * item runs FD-preconditioned iterative refinement (see stfd_batch_create_ex)
+ * with the true relative residual ||f - A u|| / ||f|| (eq. syst_mat,
+ * sum-factorised) checked after every step, in IEEE FP64 or double-float.
  *
  * The work runs as ONE persistent kernel launch: every CTA repeatedly takes
  * the next (problem, right-hand side) item from a list sorted by size
@@ -408,6 +407,23 @@ typedef struct stfd_batch stfd_batch;
 
 int stfd_batch_create(stfd_batch** out, int count, int d, const int* n_el, const int* p, const int* nrhs,
                       double T, double gamma, double nu, int autotune, void* stream);
+
+/* As stfd_batch_create, with the arithmetic and the refinement of each item:
+ * precision STFD_FP64 (IEEE FP64 on the FP64 pipe) or STFD_DF32 (double-float);
+ * every item runs FD-preconditioned iterative refinement, u_0 = 0 and
+ * u_{k+1} = u_k + P^{-1} (f - A u_k) by Algorithm 1, until the true relative
+ * residual ||f - A u|| / ||f|| <= tol or max_it iterations (1 <= max_it <=
+ * 1000, tol >= 0). stfd_batch_create is precision STFD_DF32, tol 0, max_it 1
+ * (one application). Device memory: the factors in the chosen arithmetic, 5 x
+ * max_N 8-byte entries of scratch per CTA slot and one int per item. */
+int stfd_batch_create_ex(stfd_batch** out, int count, int d, const int* n_el, const int* p, const int* nrhs,
+                         double T, double gamma, double nu, int precision, double tol, int max_it, int autotune,
+                         void* stream);
+
+/* After a solve has completed: iterations done per item (n_items ints, item
+ * order as relres: problem-major, then right-hand side). An item whose
+ * relres is still above tol used all max_it iterations. Synchronous. */
+int stfd_batch_iterations(const stfd_batch* b, int* iters);
 
 /* Packed vector layout: problem k's nrhs[k] right-hand sides (each of
  * N_k = n_s^d n_t dofs, vec order) start at offsets[k] (count + 1 entries,

@@ -1,13 +1,15 @@
 // Batched solver for many independent small space-time heat problems on the
 // unit box (constant coefficients): one persistent kernel, captured in a CUDA
 // graph, drains a work list of (problem, right-hand side) items sorted by size
-// (largest first) through an atomic counter. Each CTA solves its item alone:
-// s = P^{-1} f by Algorithm 1 (2(d+1) mode products and the Step 3 arrowhead
-// solve, double-float arithmetic on the FP32 pipes) and then the true residual
-// ||f - A s|| / ||f|| with the sum-factorised Kronecker matvec of eq. syst_mat.
-// On the unit box with constant coefficients the preconditioner of eq.
-// prec_definition equals A, so this is the single iteration that FD-
-// preconditioned GMRES takes there (Sec. 4); the residual is reported per item.
+// (largest first) through an atomic counter. Each CTA solves its item alone by
+// FD-preconditioned iterative refinement: u_0 = 0, r_0 = f, and per iteration
+// u += P^{-1} r by Algorithm 1 (2(d+1) mode products and the Step 3 arrowhead
+// solve), then r = f - A u with the sum-factorised Kronecker matvec of eq.
+// syst_mat, until ||r|| / ||f|| <= tol or max_it iterations; the relative
+// residual and the iteration count are reported per item. Arithmetic: IEEE
+// FP64 (FP64 pipe) or double-float on the FP32 pipes. On the unit box with
+// constant coefficients the preconditioner of eq. prec_definition equals A, so
+// one iteration reaches the rounding level there (Sec. 4).
 // The CTA size and the number of CTAs per SM are chosen by timing the
 // candidates on the batch itself (autotuning at creation).
 #include <cuda_runtime.h>
@@ -18,6 +20,7 @@
 #include <vector>
 
 #include "arrow_df.cuh"
+#include "device_state.h"
 #include "df.cuh"
 #include "kernels.h"
 #include "profile.h"
@@ -129,6 +132,116 @@ __device__ void pair_pass(const double* Ud, const float2* Uf, const float2* Vf, 
   }
 }
 
+// FP64 versions (IEEE FP64 on the FP64 pipe): the same passes on double.
+template <int THREADS>
+__device__ void mode_pass64(const double* X, const double* __restrict__ J, double* Y, int n, int inner, int N,
+                            double* xs, bool accumulate) {
+  constexpr int kW = THREADS / 32;
+  constexpr int kIB = 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int Q = N / n;
+  for (int q0 = 0; q0 < Q; q0 += 32) {
+    const int q = q0 + lane;
+    const bool valid = q < Q;
+    int base = 0;
+    if (valid) {
+      const int o = q / inner;
+      base = o * n * inner + (q - o * inner);
+    }
+    for (int a = warp; a < n; a += kW) xs[a * 32 + lane] = valid ? X[base + a * inner] : 0.0;
+    __syncthreads();
+    for (int i0 = warp; i0 < n; i0 += kW * kIB) {
+      double acc[kIB];
+      const double* row[kIB];
+#pragma unroll
+      for (int b = 0; b < kIB; ++b) {
+        acc[b] = 0.0;
+        row[b] = J + min(i0 + b * kW, n - 1) * n;
+      }
+      for (int a = 0; a < n; ++a) {
+        const double x = xs[a * 32 + lane];
+#pragma unroll
+        for (int b = 0; b < kIB; ++b) acc[b] = fma(__ldg(row[b] + a), x, acc[b]);
+      }
+      if (valid) {
+#pragma unroll
+        for (int b = 0; b < kIB; ++b) {
+          const int i = i0 + b * kW;
+          if (i >= n) continue;
+          const int o = base + i * inner;
+          Y[o] = accumulate ? Y[o] + acc[b] : acc[b];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int THREADS>
+__device__ void pair_pass64(const double* U, const double* V, const double* __restrict__ Mb,
+                            const double* __restrict__ Kb, double* Uo, double* Vo, int n, int p, int inner, int N) {
+  const int W = 2 * p + 1;
+  for (int e = threadIdx.x; e < N; e += THREADS) {
+    const int c = e % inner, r = e / inner;
+    const int i = r % n, o = r / n;
+    const int base = o * n * inner + c;
+    double mu = 0.0, kv = 0.0, mv = 0.0;
+    for (int t = 0; t < W; ++t) {
+      const int a = i - p + t;
+      if (a < 0 || a >= n) continue;
+      const int idx = base + a * inner;
+      const double x = U[idx];
+      mu = fma(Mb[i * W + t], x, mu);
+      kv = fma(Kb[i * W + t], x, kv);
+      if (V) mv = fma(Mb[i * W + t], V[idx], mv);
+    }
+    Uo[e] = mu;
+    Vo[e] = kv + mv;
+  }
+}
+
+// Step 3 (FP64) for one spatial index k; nu is folded into lam, gamma into B, G.
+__device__ __forceinline__ void arrowhead_f64_point(double* __restrict__ X, int d, int n1, int nt, int n_pairs,
+                                                    int has_zero, int Ns, const double* lam, const double* B,
+                                                    const double* BB, const double* G, const double* Sinv, int k) {
+  int rest = k;
+  const int i1 = rest % n1;
+  rest /= n1;
+  double a = lam[i1];
+  if (d >= 2) {
+    const int i2 = rest % n1;
+    rest /= n1;
+    a += lam[i2];
+  }
+  if (d >= 3) a += lam[rest];
+  const double a2 = a * a;
+  double y = X[(nt - 1) * Ns + k];
+  for (int j = 0; j < n_pairs; ++j) {
+    const double x1 = X[(2 * j) * Ns + k], x2 = X[(2 * j + 1) * Ns + k];
+    const double b = B[j];
+    const double inv = 1.0 / (a2 + BB[j]);
+    const double h1 = (a * x1 - b * x2) * inv, h2 = (b * x1 + a * x2) * inv;
+    y = fma(G[2 * j], h1, fma(G[2 * j + 1], h2, y));
+  }
+  const int z = 2 * n_pairs;
+  double x0 = 0.0;
+  if (has_zero) {
+    x0 = X[z * Ns + k];
+    y = fma(G[z], x0 / a, y);
+  }
+  const double qn = y * Sinv[k];
+  X[(nt - 1) * Ns + k] = qn;
+  for (int j = 0; j < n_pairs; ++j) {
+    const int o1 = (2 * j) * Ns + k, o2 = (2 * j + 1) * Ns + k;
+    const double b = B[j];
+    const double inv = 1.0 / (a2 + BB[j]);
+    const double r1 = fma(-G[2 * j], qn, X[o1]), r2 = fma(-G[2 * j + 1], qn, X[o2]);
+    X[o1] = (a * r1 - b * r2) * inv;
+    X[o2] = (b * r1 + a * r2) * inv;
+  }
+  if (has_zero) X[z * Ns + k] = fma(-G[z], qn, x0) / a;
+}
+
 template <int THREADS>
 __device__ double block_sum(double v, double* red) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -140,17 +253,27 @@ __device__ double block_sum(double v, double* red) {
   return t;   // every thread
 }
 
-template <int THREADS>
+// Per item: iterative refinement with Algorithm 1 as the preconditioner (see
+// the top of the file). Scratch per CTA slot: 5 vectors of max_N 8-byte entries
+// (mode-product ping-pong, the matvec's two partial sums per direction, r).
+template <int THREADS, bool F64>
 __global__ void __launch_bounds__(THREADS, 2048 / THREADS / 2)
-k_batch(const BProb* __restrict__ probs, const BItem* __restrict__ items, int n_items, const float2* __restrict__ pool,
-        const double* __restrict__ f, double* __restrict__ u, double* __restrict__ relres,
-        unsigned long long* __restrict__ times, int* __restrict__ counter, float2* __restrict__ scratch,
-        int max_N) {
-  extern __shared__ float2 xs[];   // [max n][32] staging of mode_pass
+k_batch(const BProb* __restrict__ probs, const BItem* __restrict__ items, int n_items, const void* __restrict__ pool_v,
+        const double* __restrict__ f, double* __restrict__ u, double* __restrict__ relres, int* __restrict__ iters,
+        unsigned long long* __restrict__ times, int* __restrict__ counter, void* __restrict__ scratch_v, int max_N,
+        double tol, int max_it) {
+  extern __shared__ float2 xs[];   // [max n][32] staging of the mode products (8-byte entries)
   __shared__ int item_s;
   __shared__ double red[THREADS / 32];
-  float2* buf[4];
-  for (int k = 0; k < 4; ++k) buf[k] = scratch + ((size_t)blockIdx.x * 4 + k) * (size_t)max_N;
+  __shared__ int stop_s;
+  const float2* pool = static_cast<const float2*>(pool_v);
+  const double* pool64 = static_cast<const double*>(pool_v);
+  float2* buf[5];
+  double* buf64[5];
+  for (int k = 0; k < 5; ++k) {
+    buf[k] = static_cast<float2*>(scratch_v) + ((size_t)blockIdx.x * 5 + k) * (size_t)max_N;
+    buf64[k] = reinterpret_cast<double*>(buf[k]);
+  }
   for (;;) {
     if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
     __syncthreads();
@@ -163,85 +286,141 @@ k_batch(const BProb* __restrict__ probs, const BItem* __restrict__ items, int n_
     const double* fx = f + P.vec_off + (long long)item.rhs * P.N;
     double* ux = u + P.vec_off + (long long)item.rhs * P.N;
     const int d = P.d, N = P.N;
-    // Step 2: s~ = (U_t^T x U^T ... x U^T) f
-    int cur = 0, inner = 1;
-    for (int l = 0; l < d; ++l) {
-      mode_pass<THREADS>(l == 0 ? fx : nullptr, l == 0 ? nullptr : buf[cur ^ 1], pool + P.Uf, buf[cur], nullptr,
-                         P.ns, inner, N, xs);
-      __syncthreads();
-      cur ^= 1;
-      inner *= P.ns;
-    }
-    mode_pass<THREADS>(nullptr, buf[cur ^ 1], pool + P.Utf, buf[cur], nullptr, P.nt, inner, N, xs);
-    __syncthreads();
-    // Step 3 in place on buf[cur]
-    {
-      ArrowDF ap;
-      ap.d = d;
-      ap.n1 = P.ns;
-      ap.n2 = P.ns;
-      ap.nt = P.nt;
-      ap.n_pairs = P.n_pairs;
-      ap.has_zero = P.has_zero;
-      ap.Ns = P.Ns;
-      for (int l = 0; l < 3; ++l) ap.lam[l] = pool + P.lam;
-      ap.B = pool + P.B;
-      ap.BB = pool + P.BB;
-      ap.G = pool + P.G;
-      ap.Sinv = pool + P.Sinv;
-      ap.nu = make_float2(1.0f, 0.0f);   // nu is folded into lam at creation
-      ap.sgn = 1.0f;
-      for (int k = threadIdx.x; k < P.Ns; k += THREADS) arrowhead_df_point(buf[cur], ap, k);
-    }
-    __syncthreads();
-    // Step 4: s = (U_t x U ... x U) q~, the last pass writes the FP64 solution
-    mode_pass<THREADS>(nullptr, buf[cur], pool + P.Utb, buf[cur ^ 1], nullptr, P.nt, inner, N, xs);
-    __syncthreads();
-    cur ^= 1;
-    for (int l = d - 1; l >= 0; --l) {
-      inner /= P.ns;
-      mode_pass<THREADS>(nullptr, buf[cur], pool + P.Ub, l == 0 ? nullptr : buf[cur ^ 1], l == 0 ? ux : nullptr,
-                         P.ns, inner, N, xs);
-      __syncthreads();
-      cur ^= 1;
-    }
-    // true residual f - A s: (u, v) chains through the spatial directions, then time
-    inner = 1;
-    int in = -1;   // -1: the solution itself
-    for (int l = 0; l < d; ++l) {
-      const int out = (in == 0) ? 2 : 0;
-      pair_pass<THREADS>(in < 0 ? ux : nullptr, in < 0 ? nullptr : buf[in], in < 0 ? nullptr : buf[in + 1],
-                         pool + P.Mb, pool + P.Kb, buf[out], buf[out + 1], P.ns, P.p, inner, N);
-      __syncthreads();
-      in = out;
-      inner *= P.ns;
-    }
-    double rr = 0.0, ff = 0.0;
-    {
-      const int W = 2 * P.pt + 1;
-      const float2* Wb = pool + P.Wb;
-      const float2* Mtb = pool + P.Mtb;
-      const float2* Us = buf[in];
-      const float2* Vs = buf[in + 1];
-      for (int e = threadIdx.x; e < N; e += THREADS) {
-        const int k = e % P.Ns, t = e / P.Ns;
-        df y{0.f, 0.f};
-        for (int q = 0; q < W; ++q) {
-          const int tau = t - P.pt + q;
-          if (tau < 0 || tau >= P.nt) continue;
-          dfa::fma_acc(y, Wb[t * W + q], dfa::from_float2(Us[tau * P.Ns + k]));
-          dfa::fma_acc(y, Mtb[t * W + q], dfa::from_float2(Vs[tau * P.Ns + k]));
+    double rel = 0.0;
+    int iter = 0;
+    for (iter = 0; iter < max_it; ++iter) {
+      const bool first = iter == 0;
+      // ---- u += P^{-1} r (r = f on the first iteration, else buf 4)
+      int cur = 0, inner = 1;
+      for (int l = 0; l < d; ++l) {
+        if (F64) {
+          mode_pass64<THREADS>(l == 0 ? (first ? fx : buf64[4]) : buf64[cur ^ 1], pool64 + P.Uf, buf64[cur], P.ns,
+                               inner, N, reinterpret_cast<double*>(xs), false);
+        } else {
+          const float2* src = l == 0 ? (first ? nullptr : buf[4]) : buf[cur ^ 1];
+          mode_pass<THREADS>(l == 0 && first ? fx : nullptr, src, pool + P.Uf, buf[cur], nullptr, P.ns, inner, N, xs);
         }
-        const double fe = fx[e];
-        const double r = fe - dfa::to_double(dfa::norm(y));
-        rr = fma(r, r, rr);
-        ff = fma(fe, fe, ff);
+        __syncthreads();
+        cur ^= 1;
+        inner *= P.ns;
+      }
+      if (F64)
+        mode_pass64<THREADS>(buf64[cur ^ 1], pool64 + P.Utf, buf64[cur], P.nt, inner, N, reinterpret_cast<double*>(xs),
+                             false);
+      else
+        mode_pass<THREADS>(nullptr, buf[cur ^ 1], pool + P.Utf, buf[cur], nullptr, P.nt, inner, N, xs);
+      __syncthreads();
+      if (F64) {
+        for (int k = threadIdx.x; k < P.Ns; k += THREADS)
+          arrowhead_f64_point(buf64[cur], d, P.ns, P.nt, P.n_pairs, P.has_zero, P.Ns, pool64 + P.lam, pool64 + P.B,
+                              pool64 + P.BB, pool64 + P.G, pool64 + P.Sinv, k);
+      } else {
+        ArrowDF ap;
+        ap.d = d;
+        ap.n1 = P.ns;
+        ap.n2 = P.ns;
+        ap.nt = P.nt;
+        ap.n_pairs = P.n_pairs;
+        ap.has_zero = P.has_zero;
+        ap.Ns = P.Ns;
+        for (int l = 0; l < 3; ++l) ap.lam[l] = pool + P.lam;
+        ap.B = pool + P.B;
+        ap.BB = pool + P.BB;
+        ap.G = pool + P.G;
+        ap.Sinv = pool + P.Sinv;
+        ap.nu = make_float2(1.0f, 0.0f);   // nu is folded into lam at creation
+        ap.sgn = 1.0f;
+        for (int k = threadIdx.x; k < P.Ns; k += THREADS) arrowhead_df_point(buf[cur], ap, k);
+      }
+      __syncthreads();
+      if (F64)
+        mode_pass64<THREADS>(buf64[cur], pool64 + P.Utb, buf64[cur ^ 1], P.nt, inner, N, reinterpret_cast<double*>(xs),
+                             false);
+      else
+        mode_pass<THREADS>(nullptr, buf[cur], pool + P.Utb, buf[cur ^ 1], nullptr, P.nt, inner, N, xs);
+      __syncthreads();
+      cur ^= 1;
+      for (int l = d - 1; l >= 0; --l) {
+        inner /= P.ns;
+        if (F64) {
+          mode_pass64<THREADS>(buf64[cur], pool64 + P.Ub, l == 0 ? ux : buf64[cur ^ 1], P.ns, inner, N,
+                               reinterpret_cast<double*>(xs), l == 0 && !first);
+        } else if (l == 0 && !first) {   // u += s: the last pass into scratch, then added in FP64
+          mode_pass<THREADS>(nullptr, buf[cur], pool + P.Ub, buf[cur ^ 1], nullptr, P.ns, inner, N, xs);
+          __syncthreads();
+          for (int e = threadIdx.x; e < N; e += THREADS) ux[e] += dfa::to_double(dfa::from_float2(buf[cur ^ 1][e]));
+        } else {
+          mode_pass<THREADS>(nullptr, buf[cur], pool + P.Ub, l == 0 ? nullptr : buf[cur ^ 1], l == 0 ? ux : nullptr,
+                             P.ns, inner, N, xs);
+        }
+        __syncthreads();
+        cur ^= 1;
+      }
+      // ---- r = f - A u: (u, v) chains through the spatial directions, then time
+      inner = 1;
+      int in = -1;   // -1: the solution itself
+      for (int l = 0; l < d; ++l) {
+        const int out = (in == 0) ? 2 : 0;
+        if (F64)
+          pair_pass64<THREADS>(in < 0 ? ux : buf64[in], in < 0 ? nullptr : buf64[in + 1], pool64 + P.Mb, pool64 + P.Kb,
+                               buf64[out], buf64[out + 1], P.ns, P.p, inner, N);
+        else
+          pair_pass<THREADS>(in < 0 ? ux : nullptr, in < 0 ? nullptr : buf[in], in < 0 ? nullptr : buf[in + 1],
+                             pool + P.Mb, pool + P.Kb, buf[out], buf[out + 1], P.ns, P.p, inner, N);
+        __syncthreads();
+        in = out;
+        inner *= P.ns;
+      }
+      double rr = 0.0, ff = 0.0;
+      {
+        const int W = 2 * P.pt + 1;
+        for (int e = threadIdx.x; e < N; e += THREADS) {
+          const int k = e % P.Ns, t = e / P.Ns;
+          double yv;
+          if (F64) {
+            double y = 0.0;
+            for (int q = 0; q < W; ++q) {
+              const int tau = t - P.pt + q;
+              if (tau < 0 || tau >= P.nt) continue;
+              y = fma(pool64[P.Wb + t * W + q], buf64[in][tau * P.Ns + k], y);
+              y = fma(pool64[P.Mtb + t * W + q], buf64[in + 1][tau * P.Ns + k], y);
+            }
+            yv = y;
+          } else {
+            df y{0.f, 0.f};
+            for (int q = 0; q < W; ++q) {
+              const int tau = t - P.pt + q;
+              if (tau < 0 || tau >= P.nt) continue;
+              dfa::fma_acc(y, pool[P.Wb + t * W + q], dfa::from_float2(buf[in][tau * P.Ns + k]));
+              dfa::fma_acc(y, pool[P.Mtb + t * W + q], dfa::from_float2(buf[in + 1][tau * P.Ns + k]));
+            }
+            yv = dfa::to_double(dfa::norm(y));
+          }
+          const double fe = fx[e];
+          const double r = fe - yv;
+          if (F64)
+            buf64[4][e] = r;
+          else
+            buf[4][e] = make_float2(dfa::from_double(r).h, dfa::from_double(r).l);
+          rr = fma(r, r, rr);
+          ff = fma(fe, fe, ff);
+        }
+      }
+      rr = block_sum<THREADS>(rr, red);
+      ff = block_sum<THREADS>(ff, red);
+      rel = ff > 0.0 ? sqrt(rr / ff) : 0.0;
+      if (threadIdx.x == 0) stop_s = (rel <= tol || !(rel == rel)) ? 1 : 0;
+      __syncthreads();
+      const bool stop = stop_s != 0;
+      __syncthreads();
+      if (stop) {
+        ++iter;
+        break;
       }
     }
-    rr = block_sum<THREADS>(rr, red);
-    ff = block_sum<THREADS>(ff, red);
     if (threadIdx.x == 0) {
-      if (relres) relres[P.item_base + item.rhs] = ff > 0.0 ? sqrt(rr / ff) : 0.0;
+      if (relres) relres[P.item_base + item.rhs] = rel;
+      if (iters) iters[P.item_base + item.rhs] = min(iter, max_it);
       times[2 * it] = t_start;
       times[2 * it + 1] = global_ns();
     }
@@ -278,14 +457,18 @@ using namespace stfd;
 
 struct stfd_batch {
   int count = 0, d = 0, n_items = 0, max_N = 0, max_n = 0, sms = 0;
+  int precision = STFD_DF32;            // STFD_FP64 or STFD_DF32
+  double tol = 0.0;                     // refinement stops once ||f - A u|| / ||f|| <= tol
+  int max_it = 1;
+  int* iters = nullptr;                 // per item (device)
   std::vector<long long> offsets;       // count + 1
   std::vector<BItem> items;             // host copy (sorted)
   BProb* probs = nullptr;
   BItem* ditems = nullptr;
-  float2* pool = nullptr;
+  void* pool = nullptr;                 // double (FP64) or float2 (double-float) entries
   int* counter = nullptr;
   unsigned long long* times = nullptr;  // 2 per item
-  float2* scratch = nullptr;
+  void* scratch = nullptr;              // 5 vectors of max_N 8-byte entries per CTA slot
   int max_ctas = 0;
   int threads = 256, ctas_per_sm = 4;
   std::vector<double> tune_ms;          // per candidate (NaN if infeasible)
@@ -301,46 +484,56 @@ namespace {
 const Candidate kCandidates[] = {{128, 2}, {128, 4}, {128, 8}, {256, 1}, {256, 2}, {256, 4}, {512, 1}, {512, 2}};
 constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 
-cudaError_t launch_batch(const stfd_batch* b, int threads, int ctas, const double* f, double* u, double* relres,
-                         cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(int), st);
-  if (e != cudaSuccess) return e;
+template <bool F64>
+cudaError_t launch_batch_t(const stfd_batch* b, int threads, int ctas, const double* f, double* u, double* relres,
+                           cudaStream_t st) {
   const int grid = b->sms * ctas;
   const size_t smem = (size_t)b->max_n * 32 * sizeof(float2);
-  count_launch();
   switch (threads) {
     case 128:
-      k_batch<128><<<grid, 128, smem, st>>>(b->probs, b->ditems, b->n_items, b->pool, f, u, relres, b->times,
-                                         b->counter, b->scratch, b->max_N);
+      k_batch<128, F64><<<grid, 128, smem, st>>>(b->probs, b->ditems, b->n_items, b->pool, f, u, relres, b->iters,
+                                                 b->times, b->counter, b->scratch, b->max_N, b->tol, b->max_it);
       break;
     case 512:
-      k_batch<512><<<grid, 512, smem, st>>>(b->probs, b->ditems, b->n_items, b->pool, f, u, relres, b->times,
-                                         b->counter, b->scratch, b->max_N);
+      k_batch<512, F64><<<grid, 512, smem, st>>>(b->probs, b->ditems, b->n_items, b->pool, f, u, relres, b->iters,
+                                                 b->times, b->counter, b->scratch, b->max_N, b->tol, b->max_it);
       break;
     default:
-      k_batch<256><<<grid, 256, smem, st>>>(b->probs, b->ditems, b->n_items, b->pool, f, u, relres, b->times,
-                                         b->counter, b->scratch, b->max_N);
+      k_batch<256, F64><<<grid, 256, smem, st>>>(b->probs, b->ditems, b->n_items, b->pool, f, u, relres, b->iters,
+                                                 b->times, b->counter, b->scratch, b->max_N, b->tol, b->max_it);
   }
   return cudaGetLastError();
 }
 
-template <int THREADS>
-cudaError_t set_smem(size_t smem) {
-  return smem > 48 * 1024
-             ? cudaFuncSetAttribute(k_batch<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-             : cudaSuccess;
+cudaError_t launch_batch(const stfd_batch* b, int threads, int ctas, const double* f, double* u, double* relres,
+                         cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  return b->precision == STFD_FP64 ? launch_batch_t<true>(b, threads, ctas, f, u, relres, st)
+                                   : launch_batch_t<false>(b, threads, ctas, f, u, relres, st);
 }
 
+template <int THREADS, bool F64>
+cudaError_t set_smem(size_t smem) {
+  return smem > 48 * 1024 ? ensure_smem_attr(k_batch<THREADS, F64>, (int)smem) : cudaSuccess;
+}
+
+template <bool F64>
 bool feasible(int threads, int ctas, size_t smem) {
   int blocks = 0;
   cudaError_t e;
   if (threads == 128)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch<128>, 128, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch<128, F64>, 128, smem);
   else if (threads == 512)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch<512>, 512, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch<512, F64>, 512, smem);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch<256>, 256, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch<256, F64>, 256, smem);
   return e == cudaSuccess && blocks >= ctas;
+}
+
+bool feasible(const stfd_batch* b, int threads, int ctas, size_t smem) {
+  return b->precision == STFD_FP64 ? feasible<true>(threads, ctas, smem) : feasible<false>(threads, ctas, smem);
 }
 
 std::vector<double> band_rows(int n, const double* A, int pb, double s) {
@@ -366,14 +559,18 @@ extern "C" void stfd_batch_destroy(stfd_batch* b) {
   cudaFree(b->counter);
   cudaFree(b->times);
   cudaFree(b->scratch);
+  cudaFree(b->iters);
   delete b;
 }
 
-extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* n_el, const int* p, const int* nrhs,
-                                 double T, double gamma, double nu, int autotune, void* stream) {
+extern "C" int stfd_batch_create_ex(stfd_batch** out, int count, int d, const int* n_el, const int* p,
+                                    const int* nrhs, double T, double gamma, double nu, int precision, double tol,
+                                    int max_it, int autotune, void* stream) {
   if (!out) return STFD_ERR_ARG;
   *out = nullptr;
   if (count < 1 || d < 1 || d > kMaxDim || !n_el || !p || !nrhs || !(T > 0.0) || !(gamma > 0.0) || !(nu > 0.0))
+    return STFD_ERR_ARG;
+  if ((precision != STFD_FP64 && precision != STFD_DF32) || !(tol >= 0.0) || max_it < 1 || max_it > 1000)
     return STFD_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   stfd_batch* b = new (std::nothrow) stfd_batch;
@@ -381,14 +578,14 @@ extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* 
   b->count = count;
   b->d = d;
   b->sms = sm_count();
+  b->precision = precision;
+  b->tol = tol;
+  b->max_it = max_it;
   std::vector<BProb> probs(count);
-  std::vector<float2> pool;
+  std::vector<double> pool;   // FP64 values; double-float pairs are split at upload
   auto put = [&](const std::vector<double>& v) {
     const long long off = (long long)pool.size();
-    for (double x : v) {
-      const float h = (float)x;
-      pool.push_back(make_float2(h, (float)(x - (double)h)));
-    }
+    pool.insert(pool.end(), v.begin(), v.end());
     return off;
   };
   b->offsets.assign(count + 1, 0);
@@ -480,19 +677,23 @@ extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* 
   // shared memory of the mode products, then the configurations that fit; the
   // scratch holds one slot per CTA of the largest grid that will be launched
   const size_t smem = (size_t)b->max_n * 32 * sizeof(float2);
-  if (set_smem<128>(smem) != cudaSuccess || set_smem<256>(smem) != cudaSuccess || set_smem<512>(smem) != cudaSuccess) {
+  const bool f64 = precision == STFD_FP64;
+  if ((f64 ? (set_smem<128, true>(smem) != cudaSuccess || set_smem<256, true>(smem) != cudaSuccess ||
+              set_smem<512, true>(smem) != cudaSuccess)
+           : (set_smem<128, false>(smem) != cudaSuccess || set_smem<256, false>(smem) != cudaSuccess ||
+              set_smem<512, false>(smem) != cudaSuccess))) {
     stfd_batch_destroy(b);
     return STFD_ERR_CUDA;
   }
   bool fits[kNumCandidates];
   b->max_ctas = 0;
   for (int c = 0; c < kNumCandidates; ++c) {
-    fits[c] = feasible(kCandidates[c].threads, kCandidates[c].ctas, smem);
+    fits[c] = feasible(b, kCandidates[c].threads, kCandidates[c].ctas, smem);
     if (fits[c] && autotune) b->max_ctas = std::max(b->max_ctas, kCandidates[c].ctas);
   }
   if (!autotune) {   // 256 threads, as many CTAs per SM (4, 2 or 1) as fit
     b->threads = 256;
-    b->ctas_per_sm = feasible(256, 4, smem) ? 4 : (feasible(256, 2, smem) ? 2 : 1);
+    b->ctas_per_sm = feasible(b, 256, 4, smem) ? 4 : (feasible(b, 256, 2, smem) ? 2 : 1);
     b->max_ctas = b->ctas_per_sm;
   }
   if (b->max_ctas == 0) {
@@ -505,13 +706,35 @@ extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* 
       return STFD_ERR_CUDA;
     return STFD_OK;
   };
+  std::vector<float2> pool2;
+  if (!f64) {
+    pool2.resize(pool.size());
+    for (size_t k = 0; k < pool.size(); ++k) {
+      const float h = (float)pool[k];
+      pool2[k] = make_float2(h, (float)(pool[k] - (double)h));
+    }
+  }
   rc = up(&b->probs, probs.data(), probs.size());
   if (rc == STFD_OK) rc = up(&b->ditems, b->items.data(), b->items.size());
-  if (rc == STFD_OK) rc = up(&b->pool, pool.data(), pool.size());
+  if (rc == STFD_OK) {
+    if (f64) {
+      double* pd = nullptr;
+      rc = up(&pd, pool.data(), pool.size());
+      b->pool = pd;
+    } else {
+      float2* pf = nullptr;
+      rc = up(&pf, pool2.data(), pool2.size());
+      b->pool = pf;
+    }
+  }
   if (rc == STFD_OK) rc = up(&b->counter, (const int*)nullptr, 1);
   if (rc == STFD_OK) rc = up(&b->times, (const unsigned long long*)nullptr, 2 * (size_t)b->n_items);
-  if (rc == STFD_OK)
-    rc = up(&b->scratch, (const float2*)nullptr, (size_t)b->sms * b->max_ctas * 4 * (size_t)b->max_N);
+  if (rc == STFD_OK) rc = up(&b->iters, (const int*)nullptr, (size_t)b->n_items);
+  if (rc == STFD_OK) {
+    double* sc = nullptr;
+    rc = up(&sc, (const double*)nullptr, (size_t)b->sms * b->max_ctas * 5 * (size_t)b->max_N);
+    b->scratch = sc;
+  }
   if (rc == STFD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = STFD_ERR_CUDA;
   if (rc == STFD_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) rc = STFD_ERR_CUDA;
   // autotune: time every feasible candidate on this batch with synthetic right-hand sides
@@ -558,6 +781,18 @@ extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* 
     return rc;
   }
   *out = b;
+  return STFD_OK;
+}
+
+extern "C" int stfd_batch_create(stfd_batch** out, int count, int d, const int* n_el, const int* p, const int* nrhs,
+                                 double T, double gamma, double nu, int autotune, void* stream) {
+  return stfd_batch_create_ex(out, count, d, n_el, p, nrhs, T, gamma, nu, STFD_DF32, 0.0, 1, autotune, stream);
+}
+
+extern "C" int stfd_batch_iterations(const stfd_batch* b, int* iters) {
+  if (!b || !iters) return STFD_ERR_ARG;
+  if (cudaMemcpy(iters, b->iters, (size_t)b->n_items * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return STFD_ERR_CUDA;
   return STFD_OK;
 }
 

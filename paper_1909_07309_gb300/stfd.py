@@ -102,6 +102,11 @@ SIGNATURES = {
     "stfd_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _c_int_p,
                                          _c_int_p, _c_int_p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_int, ctypes.c_void_p]),
+    "stfd_batch_create_ex": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _c_int_p,
+                                            _c_int_p, _c_int_p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_void_p]),
+    "stfd_batch_iterations": (ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
     "stfd_batch_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), _c_int_p,
                                          ctypes.POINTER(ctypes.c_longlong)]),
     "stfd_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -414,7 +419,8 @@ class Batch:
 
     CANDIDATES = [(128, 2), (128, 4), (128, 8), (256, 1), (256, 2), (256, 4), (512, 1), (512, 2)]
 
-    def __init__(self, n_el, p, nrhs, d=2, T=1.0, gamma=1.0, nu=1.0, autotune=True, stream=None):
+    def __init__(self, n_el, p, nrhs, d=2, T=1.0, gamma=1.0, nu=1.0, autotune=True, stream=None,
+                 precision=STFD_DF32, tol=0.0, max_it=1):
         lib = load()
         self._lib = lib
         self.handle = ctypes.c_void_p()
@@ -424,10 +430,12 @@ class Batch:
         self.count, self.d = int(n_el.size), int(d)
         self.n_el, self.p, self.nrhs = n_el, p, nrhs
         ip = ctypes.POINTER(ctypes.c_int)
-        rc = lib.stfd_batch_create(ctypes.byref(self.handle), self.count, self.d, n_el.ctypes.data_as(ip),
-                                   p.ctypes.data_as(ip), nrhs.ctypes.data_as(ip), float(T), float(gamma), float(nu),
-                                   1 if autotune else 0, _stream(stream))
-        _check(rc, "stfd_batch_create")
+        rc = lib.stfd_batch_create_ex(ctypes.byref(self.handle), self.count, self.d, n_el.ctypes.data_as(ip),
+                                      p.ctypes.data_as(ip), nrhs.ctypes.data_as(ip), float(T), float(gamma),
+                                      float(nu), int(precision), float(tol), int(max_it), 1 if autotune else 0,
+                                      _stream(stream))
+        _check(rc, "stfd_batch_create_ex")
+        self.precision, self.tol, self.max_it = int(precision), float(tol), int(max_it)
         off = (ctypes.c_longlong * (self.count + 1))()
         ni = ctypes.c_int(0)
         tot = ctypes.c_longlong(0)
@@ -435,6 +443,13 @@ class Batch:
         self.offsets = np.array(off[:], dtype=np.int64)
         self.n_items = ni.value
         self.total = tot.value
+
+    def iterations(self):
+        """Refinement iterations per item of the last completed solve (numpy int32)."""
+        it = np.zeros(self.n_items, dtype=np.int32)
+        _check(self._lib.stfd_batch_iterations(self.handle, it.ctypes.data_as(ctypes.POINTER(ctypes.c_int))),
+               "stfd_batch_iterations")
+        return it
 
     def sizes(self, k):
         """(n_s, n_t, N) of problem k."""

@@ -94,3 +94,61 @@ def test_batch_argument_checks():
     f = torch.zeros(B.total, dtype=torch.float64, device="cuda")
     with pytest.raises(stfd.StfdError):
         B.solve(f, f)                             # aliasing
+
+
+@pytest.mark.parametrize("d,T,gamma,nu", [(2, 1.0, 1.0, 1.0), (1, 0.5, 2.0, 0.3), (3, 1.0, 1.0, 1.0)])
+def test_batch_fp64_refinement_matches_oracle(d, T, gamma, nu):
+    """IEEE-FP64 batched solve with refinement to 1e-8: one iteration on the
+    unit box (P = A), the oracle's Algorithm 1 to 1e-11, and agreement with the
+    double-float batch."""
+    g = np.random.default_rng(10 + d)
+    n_el = np.array([3, 4, 7, 5, 12, 2, 9, 6] if d < 3 else [3, 4, 5, 2, 6])
+    p = np.array([1, 2, 3, 4, 2, 3, 1, 4] if d < 3 else [1, 2, 3, 4, 2])
+    nrhs = g.integers(1, 4, n_el.size)
+    B = stfd.Batch(n_el, p, nrhs, d=d, T=T, gamma=gamma, nu=nu, autotune=False,
+                   precision=stfd.STFD_FP64, tol=1e-8, max_it=5)
+    f = torch.from_numpy(g.standard_normal(B.total)).cuda()
+    u, rel = B.solve(f)
+    torch.cuda.synchronize()
+    check_against_oracle(B, f, u, rel, None, d, T, gamma, nu)
+    assert np.all(B.iterations() == 1)
+    Bd = stfd.Batch(n_el, p, nrhs, d=d, T=T, gamma=gamma, nu=nu, autotune=False)
+    ud, _ = Bd.solve(f)
+    torch.cuda.synchronize()
+    assert float(torch.linalg.norm(u - ud) / torch.linalg.norm(u)) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", [stfd.STFD_FP64, stfd.STFD_DF32])
+def test_batch_refinement_runs_to_max_it_when_tol_unreachable(precision):
+    """tol = 0 cannot be met at rounding level: every item runs max_it = 3
+    refinement steps (u += P^{-1}(f - A u)); the residual stays at rounding
+    level and the solution still matches the oracle."""
+    g = np.random.default_rng(31)
+    n_el, p, nrhs = np.array([4, 9, 6]), np.array([2, 3, 1]), np.array([2, 1, 3])
+    B = stfd.Batch(n_el, p, nrhs, autotune=False, precision=precision, tol=0.0, max_it=3)
+    f = torch.from_numpy(g.standard_normal(B.total)).cuda()
+    u, rel = B.solve(f)
+    torch.cuda.synchronize()
+    assert np.all(B.iterations() == 3)
+    check_against_oracle(B, f, u, rel, None, 2)
+
+
+def test_batch_ex_argument_checks():
+    n_el, p, nrhs = np.array([4]), np.array([2]), np.array([1])
+    for kw in (dict(precision=stfd.STFD_TF32), dict(tol=-1.0), dict(max_it=0)):
+        with pytest.raises(stfd.StfdError):
+            stfd.Batch(n_el, p, nrhs, autotune=False, **kw)
+
+
+def test_batch_workload_fp64_samples():
+    """The batched workload in IEEE FP64 with refinement to 1e-8: one iteration
+    per item, every true residual <= 1e-10, eight problems equal the oracle."""
+    cfg = inputs.BATCH
+    n_el, p, nrhs, g = inputs.batch_draws(cfg)
+    B = stfd.Batch(n_el, p, nrhs, d=cfg["d"], autotune=False, precision=stfd.STFD_FP64, tol=1e-8, max_it=5)
+    f = torch.from_numpy(g.standard_normal(B.total)).cuda()
+    u, rel = B.solve(f)
+    torch.cuda.synchronize()
+    assert float(rel.max()) <= 1e-10 and np.all(B.iterations() == 1)
+    sample = set(np.random.default_rng(2).choice(B.count, 8, replace=False).tolist())
+    check_against_oracle(B, f, u, torch.zeros(B.n_items, dtype=torch.float64), sample, cfg["d"])
