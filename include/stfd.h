@@ -201,6 +201,10 @@ void stfd_fd_destroy(stfd_fd* h);
  *                 split exactly by FMA, sums by error-free two-sum; FP64 input
  *                 and output. Agrees with STFD_OP_FP64 to about 1e-14 relative
  *                 and is several times faster on GPUs with low FP64 throughput.
+ *                 The input is scaled exactly by a power of two (its largest
+ *                 entry to [1, 2)) and the result scaled back, so FP32's exponent
+ *                 range does not limit it (two extra passes over the vector and
+ *                 one N-vector of scratch).
  *   STFD_OP_FX64  FP64 results, intermediates and inputs; each band product is
  *                 formed exactly in 64-bit integer arithmetic (every fibre of the
  *                 input and every band row written as 53-bit integers under their

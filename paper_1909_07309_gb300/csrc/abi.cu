@@ -110,6 +110,9 @@ struct stfd_fd {
   std::vector<double> diagM[kMaxDim], diagK[kMaxDim], diagWt, diagMt;
   double* dscale = nullptr;   // D^{-1/2} per dof (device), or nullptr
   double* work2 = nullptr;    // scaled right-hand side
+  // double-float paths (STFD_DF32, STFD_FP64TC): exact power-of-two range scaling
+  double* work3 = nullptr;    // the range-scaled input
+  int* bexp = nullptr;        // its exponent (device)
 };
 
 struct GmresWork {
@@ -138,6 +141,8 @@ struct stfd_op {
   double* JMt = nullptr;
   int bwW = 0, bwMt = 0;
   double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* tmp5 = nullptr;   // range-scaled input of the double-float matvec
+  int* bexp = nullptr;
   GmresWork* gw = nullptr;
   int arith = STFD_OP_FP64;
   // double-float factors (hi, lo) for STFD_OP_DF32
@@ -235,6 +240,8 @@ extern "C" void stfd_fd_destroy(stfd_fd* h) {
   }
   dev_free(h->dscale);
   dev_free(h->work2);
+  dev_free(h->work3);
+  dev_free(h->bexp);
   delete h;
 }
 
@@ -305,6 +312,10 @@ extern "C" int stfd_fd_setup(stfd_fd** out, int d, const int* n, const double* c
   if (rc == STFD_OK && f.n_pairs > 0) rc = dev_upload(&h->lamt, f.lamt.data(), f.lamt.size(), st);
   if (rc == STFD_OK) rc = dev_upload(&h->g, f.g.data(), f.g.size(), st);
   if (rc == STFD_OK) rc = dev_upload<double>(&h->work, nullptr, (size_t)h->N, st);
+  if (rc == STFD_OK && (precision == STFD_DF32 || precision == STFD_FP64TC)) {
+    rc = dev_upload<double>(&h->work3, nullptr, (size_t)h->N, st);
+    if (rc == STFD_OK) rc = dev_upload<int>(&h->bexp, nullptr, 1, st);
+  }
   std::vector<double> G(f.g.size());   // alive until the stream is synchronised below
   if (rc == STFD_OK && (precision == STFD_FP64 || precision == STFD_FP64TC7)) {
     for (size_t j = 0; j < f.g.size(); ++j) G[j] = gamma * f.g[j];
@@ -519,7 +530,15 @@ int fd_apply_one_df(const stfd_fd* h, const double* r, double* s, double* work, 
 // (U_t x U_s)^T uses the same factors; only the arrowhead core is transposed,
 // which in the real 2 x 2-block form flips the signs of lambda_j and g.
 int fd_apply_core(const stfd_fd* h, const double* r, double* s, double* work, int trans, cudaStream_t st) {
-  if (h->precision == STFD_DF32 || h->precision == STFD_FP64TC) return fd_apply_one_df(h, r, s, work, trans, st);
+  if (h->precision == STFD_DF32 || h->precision == STFD_FP64TC) {
+    // the double-float intermediates have FP32's exponent range: run on r 2^{1023 - E}
+    // (E the largest biased exponent of r) and scale the result back; both exact
+    STFD_CU(launch_range_scale(r, h->work3, h->N, h->bexp, -1, st));
+    const int rc = fd_apply_one_df(h, h->work3, s, work, trans, st);
+    if (rc != STFD_OK) return rc;
+    STFD_CU(launch_range_scale(s, s, h->N, h->bexp, 1, st));
+    return STFD_OK;
+  }
   if (h->precision != STFD_FP64 && h->precision != STFD_FP64TC7) return fd_apply_one_lowp(h, r, s, work, trans, st);
   const int d = h->d;
   const int P = 2 * (d + 1);
@@ -710,6 +729,8 @@ extern "C" void stfd_op_destroy(stfd_op* A) {
     dev_free(A->FXE[k]);
   }
   for (int k = 0; k < 4; ++k) dev_free(A->tmp[k]);
+  dev_free(A->tmp5);
+  dev_free(A->bexp);
   for (int k = 0; k < 7; ++k) dev_free(A->sbuf[k]);
   dev_free(A->MtbU);
   gmres_free(A->gw);
@@ -765,6 +786,10 @@ extern "C" int stfd_op_create_kron(stfd_op** out, int d, const int* n, const dou
     rc = dev_upload(&A->JWT, keep.back().data(), keep.back().size(), st);
   }
   for (int k = 0; k < 4 && rc == STFD_OK; ++k) rc = dev_upload<double>(&A->tmp[k], nullptr, (size_t)A->N, st);
+  if (rc == STFD_OK && arith == STFD_OP_DF32) {
+    rc = dev_upload<double>(&A->tmp5, nullptr, (size_t)A->N, st);
+    if (rc == STFD_OK) rc = dev_upload<int>(&A->bexp, nullptr, 1, st);
+  }
   if (rc == STFD_OK) {
     A->pt = A->bwMt;
     std::vector<double> MbU((size_t)n[d] * (2 * A->pt + 1), 0.0);
@@ -954,6 +979,10 @@ extern "C" int stfd_op_create_stencil(stfd_op** out, int d, const int* n, int p_
     rc = dev_upload<double>(&dst, nullptr, (size_t)A->N, st);
     A->sbuf[k] = dst;
   }
+  if (rc == STFD_OK && o.df) {
+    rc = dev_upload<double>(&A->tmp5, nullptr, (size_t)A->N, st);
+    if (rc == STFD_OK) rc = dev_upload<int>(&A->bexp, nullptr, 1, st);
+  }
   if (rc == STFD_OK) {
     o.Ms = A->sbuf[0];
     o.Ks = A->sbuf[1];
@@ -1062,14 +1091,32 @@ int matvec_one_fx(const stfd_op* A, const double* x, double* y, int trans, cudaS
   return STFD_OK;
 }
 
+int matvec_one_fp(const stfd_op* A, const double* x, double* y, int trans, cudaStream_t st);
+
 // y = A x (trans = 0) or y = A^T x (trans = 1); A^T = gamma W_t^T x M_s + nu M_t x K_s
 // since every factor but W_t is symmetric.
 int matvec_one(const stfd_op* A, const double* x, double* y, int trans, cudaStream_t st) {
-  if (A->kind == 1) {
-    STFD_CU(launch_stencil_matvec(A->sop, x, y, trans, st));
-    return STFD_OK;
+  const bool df = A->kind == 1 ? A->sop.df : A->arith == STFD_OP_DF32;
+  if (df) {
+    // double-float passes (FP32 exponent range): run on x 2^{1023 - E}, scale y back; exact
+    STFD_CU(launch_range_scale(x, A->tmp5, A->N, A->bexp, -1, st));
+    x = A->tmp5;
   }
-  if (A->arith == STFD_OP_DF32) return matvec_one_df(A, x, y, trans, st);
+  int rc = STFD_OK;
+  if (A->kind == 1) {
+    if (launch_stencil_matvec(A->sop, x, y, trans, st) != cudaSuccess) rc = STFD_ERR_CUDA;
+  } else if (df) {
+    rc = matvec_one_df(A, x, y, trans, st);
+  } else {
+    rc = matvec_one_fp(A, x, y, trans, st);
+  }
+  if (rc != STFD_OK) return rc;
+  if (df) STFD_CU(launch_range_scale(y, y, A->N, A->bexp, 1, st));
+  return STFD_OK;
+}
+
+// FP64 results: the integer-limb passes (STFD_OP_FX64) or the FP64 passes.
+int matvec_one_fp(const stfd_op* A, const double* x, double* y, int trans, cudaStream_t st) {
   if (A->fx) return matvec_one_fx(A, x, y, trans, st);
   const int d = A->d;
   double* const* T = A->tmp;

@@ -184,6 +184,35 @@ __global__ void k_arrowhead_f64(double* __restrict__ X, ArrowParamsT<double> p, 
   }
 }
 
+// ---- exact power-of-two range scaling for the double-float paths
+// (their FP32 exponent range would otherwise clip very large or very small inputs)
+__global__ void k_max_bexp(const double* __restrict__ x, long long N, int* __restrict__ out) {
+  int m = 0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (long long)gridDim.x * blockDim.x)
+    m = max(m, (int)(((unsigned long long)__double_as_longlong(x[k]) >> 52) & 0x7FF));
+  for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// y = x 2^{dir (E - 1023)} with E = *bexp (the largest biased exponent of the
+// vector the scale was taken from; E = 2047 (Inf/NaN) leaves x unscaled). Normal
+// results are formed by adding to the exponent field (integer pipe); the rare
+// others by one FP64 multiplication by the exact power of two (k >= -1023, so
+// 2^k is a double: one correctly rounded result).
+__global__ void k_scale_pow2(const double* __restrict__ x, double* __restrict__ y, long long N,
+                             const int* __restrict__ bexp, int dir) {
+  const int E = max(*bexp, 1);                                    // only subnormals: as exponent 1
+  const int k = E >= 2047 ? 0 : dir * (E - 1023);                // dir -1: 1023 - E; dir +1: E - 1023
+  const double f = k >= -1022 ? __longlong_as_double((long long)(k + 1023) << 52)
+                              : __longlong_as_double(0x0008000000000000ll);   // 2^-1023
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const long long b = __double_as_longlong(x[i]);
+    const int e = (int)(((unsigned long long)b >> 52) & 0x7FF);
+    const int ne = e + k;
+    y[i] = (e > 0 && e < 2047 && ne > 0 && ne < 2047) ? __longlong_as_double(b + ((long long)k << 52)) : x[i] * f;
+  }
+}
+
 constexpr int kDotThreads = 256;
 constexpr int kDotGroup = 4;
 
@@ -494,6 +523,21 @@ cudaError_t launch_arrowhead_fp32(float* X, const ArrowParamsT<float>& p, cudaSt
   if (p.Ns <= 0) return cudaSuccess;
   ProfScope ps("arrowhead_fp32", (double)p.Ns * (10.0 * p.n_pairs + 4.0), 8.0 * (double)p.Ns * p.nt, st);
   k_arrowhead<float><<<grid_for(p.Ns, 256), 256, 0, st>>>(X, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_range_scale(const double* x, double* y, long long N, int* bexp, int dir, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  if (dir < 0) {   // a new scale from x
+    cudaError_t e = cudaMemsetAsync(bexp, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_max_bexp<<<grid_for(N, 256), 256, 0, st>>>(x, N, bexp);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  count_launch();
+  k_scale_pow2<<<grid_for(N, 256), 256, 0, st>>>(x, y, N, bexp, dir);
   return cudaGetLastError();
 }
 

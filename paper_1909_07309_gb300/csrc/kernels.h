@@ -54,6 +54,11 @@ std::vector<unsigned char> tc_operand_image(const double* J, int n, int kind);
 // Self-test of the bounded mbarrier wait (never satisfied): sets the status flag.
 cudaError_t launch_probe_bounded_wait(int max_iters, cudaStream_t st);
 
+// Exact power-of-two range scaling: dir = -1 takes E = the largest biased
+// exponent of x into *bexp (device int) and writes y = x 2^{1023 - E}; dir = +1
+// writes y = x 2^{E - 1023} with the E stored before (y may alias x).
+cudaError_t launch_range_scale(const double* x, double* y, long long N, int* bexp, int dir, cudaStream_t st);
+
 // GMRES BLAS: partial[b*m + i] = sum over block b's range of V_i[k] * w[k].
 cudaError_t launch_dot_multi(const double* const* V, int m, const double* w, long long N,
                              double* partial, int nblocks, cudaStream_t st);

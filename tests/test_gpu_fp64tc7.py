@@ -78,3 +78,24 @@ def test_integer_limb_matvec_power_of_two_homogeneity(shift):
     x = torch.as_tensor(inputs.standard_normal(A.N, 45), device="cuda")
     two = torch.tensor(shift, device="cuda")
     assert torch.equal(torch.ldexp(A.matvec(x), two), A.matvec(torch.ldexp(x, two)))
+
+
+@pytest.mark.parametrize("shift", [100, -100, -1000, 1000])
+@pytest.mark.parametrize("which", ["fd_df32", "fd_tc48", "mv_df32"])
+def test_double_float_paths_scale_exactly(which, shift):
+    """The double-float paths (FP32 exponent range) work on the input scaled by
+    a power of two and scale back: inputs at 2^+-100 and 2^+-1000 give the
+    unscaled result times the same power of two, bit for bit."""
+    K, M, Wt, Mt = stfd.heat_problem(3, 3, 10)
+    if which == "mv_df32":
+        op = stfd.KronOp(K, M, Wt, Mt, arith=stfd.STFD_OP_DF32).matvec
+    else:
+        prec = stfd.STFD_DF32 if which == "fd_df32" else stfd.STFD_FP64TC
+        op = stfd.FD(K, M, Wt, Mt, precision=prec).apply
+    x = torch.as_tensor(inputs.standard_normal(int(np.prod([k.shape[0] for k in K]) * Wt.shape[0]), 46),
+                        device="cuda")
+    two = torch.tensor(shift, device="cuda")
+    y = op(x)
+    ys = op(torch.ldexp(x, two))
+    assert torch.equal(torch.ldexp(y, two), ys)
+    assert bool(torch.isfinite(ys).all())
