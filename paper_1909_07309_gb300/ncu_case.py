@@ -1,12 +1,14 @@
 """Small fixed workloads for Nsight Compute captures of one kernel family.
 
-  python -m paper_1909_07309_gb300.ncu_case {fd,matvec,solve} D P N_EL [REPS] [fp64|df32|fp64tc|tf32|bf16]
+  python -m paper_1909_07309_gb300.ncu_case {fd,matvec,solve} D P N_EL [REPS] [fp64|df32|fp64tc|tf32|bf16|fp64tc7|fx64]
   python -m paper_1909_07309_gb300.ncu_case {stencil,mapped_solve} D P N_EL [REPS] [fp64|df32|tf32|bf16]
   python -m paper_1909_07309_gb300.ncu_case batch COUNT [REPS]
 
 Builds the unit-cube problem (d = D, degree P, N_EL elements per direction),
 runs one warm-up and REPS applications of fd_apply, st_matvec or the
-preconditioned GMRES solve, synchronises and exits. `stencil` and
+preconditioned GMRES solve, synchronises and exits. `fp64tc7` is the
+seven-digit tensor-core preconditioner with the FP64 matvec, `fx64` the same
+preconditioner with the integer-limb matvec (the bench headline). `stencil` and
 `mapped_solve` use the quarter-annulus problem with variable coefficients
 (stencil matvec; GMRES with the geometry-aware preconditioner). `batch` runs
 the batched solver on the first COUNT problems of the batched workload
@@ -35,7 +37,9 @@ def main(argv):
     reps = int(argv[4]) if len(argv) > 4 else 2
     arith = argv[5] if len(argv) > 5 else "fp64"
     prec = {"fp64": stfd.STFD_FP64, "df32": stfd.STFD_DF32, "fp64tc": stfd.STFD_FP64TC,
-            "tf32": stfd.STFD_TF32, "bf16": stfd.STFD_BF16}[arith]
+            "tf32": stfd.STFD_TF32, "bf16": stfd.STFD_BF16, "fp64tc7": stfd.STFD_FP64TC7,
+            "fx64": stfd.STFD_FP64TC7}[arith]
+    mv = {"fp64": stfd.STFD_OP_FP64, "fp64tc7": stfd.STFD_OP_FP64, "fx64": stfd.STFD_OP_FX64}.get(arith, stfd.STFD_OP_DF32)
     if what in ("stencil", "mapped_solve"):
         prob = stfd.mapped_problem(d, p, n_el, stfd.STFD_GEOM_QUARTER_ANNULUS, c=inputs.c_bilinear,
                                    kappa=inputs.kappa_trig)
@@ -54,7 +58,7 @@ def main(argv):
         return
     K, M, Wt, Mt = stfd.heat_problem(d, p, n_el)
     P = stfd.FD(K, M, Wt, Mt, precision=prec)
-    A = stfd.KronOp(K, M, Wt, Mt, arith=stfd.STFD_OP_FP64 if arith == "fp64" else stfd.STFD_OP_DF32)
+    A = stfd.KronOp(K, M, Wt, Mt, arith=mv)
     r = torch.from_numpy(inputs.standard_normal(P.N, 1)).cuda()
     out = torch.empty_like(r)
     for _ in range(1 + reps):
