@@ -42,7 +42,8 @@ NCU_TRAFFIC = {}
 # Arithmetic of the headline solve, no narrower than FP64 anywhere: Algorithm 1
 # with the mode products on the tensor cores by seven exact digit slices per
 # entry (kept digit pairs accumulated exactly, one rounding to FP64, FP64
-# intermediates) and an IEEE-FP64 Step 3; the IEEE-FP64 banded matvec; FP64 GMRES.
+# intermediates) and an IEEE-FP64 Step 3; the banded matvec with each product formed
+# exactly in integer limbs and rounded once to FP64; FP64 GMRES.
 HEADLINE = dict(precond="STFD_FP64TC7", matvec="STFD_OP_FX64", dtype="f64",
                 precond_text="Algorithm 1, FP64: mode products on tcgen05 by seven exact BF16 digit slices per entry "
                              "(28 digit pairs, exact FP32 accumulators, one rounding to FP64; FP64 intermediates), "
@@ -194,6 +195,60 @@ def build_workload(cfg):
     for F in [Fx] * d + [Ft]:                 # vec order: direction 1 fastest, time slowest
         f = np.outer(F, f).ravel()
     return K, M, Wt, Mt, f
+
+
+def _spline_l2_misfit(p, n_el, length, bc_drop, coef, fn, nq=None):
+    """int_0^length (fn - sum_i coef_i b_i)^2 for the reduced open-uniform basis of
+    degree p (bc_drop = (first dropped, last dropped)), by Gauss-Legendre per element."""
+    from scipy.interpolate import BSpline
+    nq = nq or p + 8
+    t = np.r_[[0.0] * (p + 1), length * np.arange(1, n_el) / n_el, [length] * (p + 1)]
+    full = np.zeros(n_el + p)
+    full[int(bc_drop[0]):n_el + p - int(bc_drop[1])] = coef
+    s = BSpline(t, full, p, extrapolate=False)
+    g, w = np.polynomial.legendre.leggauss(nq)
+    h = length / n_el
+    x = (np.arange(n_el)[:, None] + 0.5 * (g[None, :] + 1.0)) * h
+    return float(np.sum(w[None, :] * (fn(x) - s(x)) ** 2) * 0.5 * h)
+
+
+def l2_error_sine(cfg, M, Mt, u_dev):
+    """Space-time L2 error of the discrete solution u_h = sum_i u_i B_i against
+    u = sin(pi x_1) ... sin(pi x_d) sin(t) (Sec. 5.1), split without cancellation:
+    ||u - u_h||^2 = ||u - Pi u||^2 + ||Pi u - u_h||^2 with Pi the L2 projection onto
+    the trial space. Pi is the tensor product of the 1D projections (u is separable),
+    so the first term is prod a_l - prod (a_l - e_l^2) with a_l = ||u_l||^2 and e_l^2
+    the 1D projection misfits (expanded over subsets); the second is d^T (M_t (x) M_s) d
+    with d = c_Pi - u_h, formed on the device by the library's Kronecker matvec."""
+    import itertools
+
+    import torch
+
+    from paper_1909_07309_gb300 import stfd
+    d, p, n_el, T = cfg["d"], cfg["p"], cfg["n_el"], cfg["T"]
+    Fx = stfd.stfd_spline_load_trig(p, n_el, 1.0, stfd.STFD_BC_DIRICHLET, np.pi, 1.0, 0.0)
+    Ft = stfd.stfd_spline_load_trig(p, n_el, T, stfd.STFD_BC_INITIAL, 1.0, 1.0, 0.0)
+    cx = np.linalg.solve(M[0], Fx)
+    ct = np.linalg.solve(Mt, Ft)
+    ex = _spline_l2_misfit(p, n_el, 1.0, (1, 1), cx, lambda x: np.sin(np.pi * x))
+    et = _spline_l2_misfit(p, n_el, T, (1, 0), ct, np.sin)
+    a = [0.5] * d + [T / 2.0 - np.sin(2.0 * T) / 4.0]
+    e = [ex] * d + [et]
+    proj = 0.0
+    for k in range(1, d + 2):
+        for S in itertools.combinations(range(d + 1), k):
+            proj += (-1) ** (k + 1) * np.prod([e[l] if l in S else a[l] for l in range(d + 1)])
+    c = np.ones(1)
+    for v in [cx] * d + [ct]:
+        c = np.outer(v, c).ravel()
+    diff = torch.from_numpy(c).to(u_dev.device) - u_dev
+    mass = stfd.KronOp(M, M, Mt, Mt, 1.0, 0.0, arith=stfd.STFD_OP_FP64)
+    Md = torch.empty_like(diff)
+    mass.matvec(diff, Md)
+    disc = float(torch.dot(diff, Md))
+    mass.close()
+    return {"l2_error": float(np.sqrt(proj + disc)), "projection_part_sq": float(proj),
+            "discrete_part_sq": disc}
 
 
 def oracle_setup(cfg):
@@ -574,6 +629,9 @@ def main():
            "overlap": "uploads and downloads on two more streams, overlapping the solves",
            "rel_diff_vs_device_run": e2e_dev,
            "h2d_bytes_per_step": int(f_np.nbytes), "d2h_bytes_per_step": int(f_np.nbytes)}
+    # the solve against the exact solution of the manufactured problem (untimed)
+    solution = l2_error_sine(cfg, M, Mt, u)
+    solution["u"] = "sin(pi x) sin(pi y) sin(pi z) sin(t)"
 
     # ---- fd_apply and st_matvec alone (CUDA events on the launching stream)
     r = torch.from_numpy(inputs.standard_normal(N, cfg["rhs_seed"])).cuda()
@@ -723,6 +781,7 @@ def main():
                    "setup_ms": setup_ms,
                    "l2": "inputs larger than L2 (working set %.2f GB > 129 MB)" % (10 * N * 8 / 1e9),
                    "parallelism": "replicas x%d" % world},
+        "solution_vs_exact": solution,
         "fd_apply": {"ms": fd_ms, "dofs_per_s": N / (fd_ms * 1e-3)},
         "st_matvec": {"ms": mv_ms, "dofs_per_s": N / (mv_ms * 1e-3), "residual_A_Pinv_r": resid},
         "gmres_time_to_1e-8_ms": ms / args.steps,

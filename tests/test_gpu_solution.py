@@ -9,11 +9,19 @@ form: ||u - u_h||^2 = ||u||^2 - 2 c^T F_u + c^T (M_t (x) M_s) c with
 F_u = int u B_i (a Kronecker product of 1D loads, eq. kron_vec_multi) and
 ||u||^2 = (1/2)^3 (1/2 - sin(2)/4). Sec. 5.1 (Fig. 2) reports the optimal
 order h^{p+1} in L2: the error ratio per halving of h approaches 2^{p+1} = 16.
+
+At the benchmarked size (n_el = 64, error ~1e-9) that expansion loses every
+digit to cancellation, so bench.py splits the error as ||u - Pi u||^2 +
+||Pi u - u_h||^2 (Pi the L2 projection, computed by 1D quadrature and a device
+mass matvec). The split is checked against the expansion where both are
+accurate, then used for the rate between n_el = 32 and 64 with the bench's
+headline arithmetic.
 """
 import numpy as np
 import pytest
 
 from oracle import kron as okron, loads as oloads, matrices as omat
+import bench
 from paper_1909_07309_gb300 import stfd
 
 pytestmark = pytest.mark.gpu
@@ -45,16 +53,22 @@ def l2_error(c, n_el):
     return np.sqrt(max(e2, 0.0))
 
 
-def solve(n_el, prec, arith):
+def solve(n_el, prec, arith, device=False):
     K, M, Wt, Mt = stfd.heat_problem(D, P_DEG, n_el)
     A = stfd.KronOp(K, M, Wt, Mt, arith=arith)
     P = stfd.FD(K, M, Wt, Mt, precision=prec)
     u, info = A.gmres(P, torch.as_tensor(_rhs(n_el), device="cuda"), tol=1e-8)
     assert info["converged"] and info["rel_res_true"] <= 1e-8
-    c = u.cpu().numpy()
     A.close()
     P.close()
-    return c
+    if device:
+        return u, M, Mt
+    return u.cpu().numpy()
+
+
+def split_error(n_el, prec, arith):
+    u, M, Mt = solve(n_el, prec, arith, device=True)
+    return bench.l2_error_sine(dict(d=D, p=P_DEG, n_el=n_el, T=1.0), M, Mt, u)["l2_error"]
 
 
 @pytest.mark.parametrize("prec,arith", [(stfd.STFD_FP64, stfd.STFD_OP_FP64),
@@ -65,3 +79,18 @@ def test_l2_error_converges_at_order_p_plus_1(prec, arith):
     # the rate approaches p + 1 = 4 from the pre-asymptotic side
     assert rates[-1] > P_DEG + 0.7 and rates[-1] < P_DEG + 1.5, (errs, rates)
     assert errs[-1] < 1e-5, errs
+
+
+@pytest.mark.parametrize("n_el", [8, 16])
+def test_split_error_matches_expansion(n_el):
+    e_split = split_error(n_el, stfd.STFD_FP64, stfd.STFD_OP_FP64)
+    e_exp = l2_error(solve(n_el, stfd.STFD_FP64, stfd.STFD_OP_FP64), n_el)
+    assert abs(e_split - e_exp) <= 1e-3 * e_exp, (e_split, e_exp)
+
+
+def test_headline_error_rate_at_full_size():
+    prec = getattr(stfd, "STFD_FP64TC7", stfd.STFD_FP64)
+    arith = getattr(stfd, "STFD_OP_FX64", stfd.STFD_OP_FP64)
+    e32, e64 = split_error(32, prec, arith), split_error(64, prec, arith)
+    rate = np.log2(e32 / e64)
+    assert P_DEG + 0.7 < rate < P_DEG + 1.5, (e32, e64, rate)
