@@ -6,9 +6,24 @@
 // consecutive tensor columns (all indices but the mode's, UMMA M = 128) and
 // i, a over the mode (UMMA N = K = n rounded up to 16). Operands sit in shared
 // memory in the no-swizzle K-major canonical layout (8-row x 16-byte core
-// matrices); the factor J stays resident for the CTA's lifetime, each X tile
-// is converted on the fly. Persistent CTAs, one accumulator of N fp32 columns
-// in TMEM per CTA.
+// matrices); the factor J stays resident for the CTA's lifetime.
+//
+// The pass is bound by HBM bandwidth (a few flops per byte against a ridge of
+// hundreds), so the kernel is built to keep loads in flight. One persistent
+// CTA per SM: 16 worker warps and one MMA warp. Each tile's entries are copied
+// asynchronously (cp.async, no registers held) into an input stage while the
+// previous tile is multiplied and stored. Per tile the workers convert the
+// staged entries into the operand buffer of the tile's parity and announce it
+// on an mbarrier, start the copies of their next tile, then read the previous
+// tile's accumulator out of tensor memory and store it; the MMA warp runs each
+// tile's MMAs as soon as its operand is complete, into one of two
+// tensor-memory accumulators. Strided modes (inner > 1): worker (row r, part
+// cg) copies and converts row r's 16-byte blocks cg, cg + 4, ... (coalesced
+// copies, one 16-byte shared store per block). Contiguous mode (inner = 1):
+// the tile is one block of 128 n entries copied as it lies, and the output
+// goes through a second stage so that the global stores are coalesced too.
+// Where the stages do not fit in shared memory (large TF32 factors) the
+// entries travel in registers instead.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -25,6 +40,8 @@ namespace stfd {
 namespace {
 
 constexpr int kTile = 128;                 // UMMA M
+constexpr int kWorkers = 512;              // 16 worker warps
+constexpr int kThreads = kWorkers + 32;    // + the MMA warp
 
 __host__ __device__ inline int esz_of(int kind) { return kind == 0 ? 2 : 4; }
 
@@ -35,17 +52,8 @@ __host__ __device__ inline size_t canon_off(int r, int k, int kcores, int esz) {
   return (size_t)(r >> 3) * (kcores * 128) + (size_t)(k / epc) * 128 + (r & 7) * 16 + (k % epc) * esz;
 }
 
-template <int KIND>
-__device__ __forceinline__ void put_operand(unsigned char* base, size_t off, float v) {
-  if (KIND == 0) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    *reinterpret_cast<__nv_bfloat16*>(base + off) = h;
-  } else {
-    uint32_t t;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
-    *reinterpret_cast<uint32_t*>(base + off) = t;
-  }
-}
+// Odd row stride (in floats) of the output stage: conflict-free column writes.
+__host__ __device__ inline int stage_stride(int n) { return n | 1; }
 
 struct TcArgs {
   const void* X;
@@ -57,39 +65,181 @@ struct TcArgs {
   long long wait;           // bounded-wait iteration limit
 };
 
-template <int KIND, typename TIn, typename TOut>
-__global__ void __launch_bounds__(kTile) k_tc_mode(TcArgs args) {
+// 16 bytes of operand from `epc` consecutive entries: 8 BF16 (round to nearest
+// even) or 4 TF32 (round to nearest, ties away, in the 32-bit container).
+template <int KIND>
+__device__ __forceinline__ uint4 pack16(const float* v) {
+  uint4 o;
+  uint32_t* w = reinterpret_cast<uint32_t*>(&o);
+  if (KIND == 0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      w[j] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[j]) : "f"(v[j]));
+  }
+  return o;
+}
+
+// Block-wide (workers only) OR of a flag; also a barrier for the workers.
+__device__ __forceinline__ bool workers_or(bool flag) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n barrier.red.or.pred p, 1, 512, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)flag)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void workers_sync() { asm volatile("barrier.sync 1, 512;" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void cp_async(T* dst, const T* src) {
+  if (sizeof(T) == 8) tc::cp_async8(dst, src);
+  else tc::cp_async4(dst, src);
+}
+
+// Kernel variants (MODE): 0 strided, staged; 1 contiguous, staged; 2 contiguous,
+// entries in registers; 3 strided, entries in registers.
+//
+// Where worker (row r, part cg) finds its entries: its row's blocks
+// blk = cg + 4 m (m < KB) of EPC columns each. Staged strided copies land at
+// stage_in[a * 128 + r] (conflict-free for a warp's consecutive rows).
+template <int KB, int EPC, typename TIn>
+__device__ __forceinline__ const TIn* strided_row(const TIn* X, long long tile, int r, int n, long long inner,
+                                                  long long Q, bool& valid) {
+  const long long q = tile * kTile + r;
+  valid = q < Q;
+  if (!valid) return X;
+  const long long o = q / inner;
+  return X + o * (long long)n * inner + (q - o * inner);
+}
+
+template <int KB, int EPC, typename TIn>
+__device__ __forceinline__ void copy_strided(const TIn* __restrict__ X, long long tile, int r, int cg, int n,
+                                             int kcores, long long inner, long long Q, TIn* stage_in) {
+  bool valid;
+  const TIn* row = strided_row<KB, EPC>(X, tile, r, n, inner, Q, valid);
+  if (!valid) return;   // rows past the end keep stale entries: their outputs are not stored
+#pragma unroll
+  for (int m = 0; m < KB; ++m) {
+    const int blk = cg + 4 * m;
+    const int a0 = blk * EPC;
+    const TIn* p = row + (long long)a0 * inner;
+#pragma unroll
+    for (int j = 0; j < EPC; ++j, p += inner)
+      if (blk < kcores && a0 + j < n) cp_async(stage_in + (a0 + j) * kTile + r, p);
+  }
+}
+
+template <int KB, int EPC, typename TIn>
+__device__ __forceinline__ void load_strided(const TIn* __restrict__ X, long long tile, int r, int cg, int n,
+                                             int kcores, long long inner, long long Q, TIn* raw) {
+  bool valid;
+  const TIn* row = strided_row<KB, EPC>(X, tile, r, n, inner, Q, valid);
+#pragma unroll
+  for (int m = 0; m < KB; ++m) {
+    const int blk = cg + 4 * m;
+    const int a0 = blk * EPC;
+    const TIn* p = row + (long long)a0 * inner;
+#pragma unroll
+    for (int j = 0; j < EPC; ++j, p += inner)
+      raw[m * EPC + j] = (valid && blk < kcores && a0 + j < n) ? __ldg(p) : (TIn)0;
+  }
+}
+
+// Contiguous mode: the tile is one block of rows x n entries; worker t takes
+// entries t, t + 512, ... (V of them; coalesced).
+template <int V, typename TIn>
+__device__ __forceinline__ void copy_flat(const TIn* __restrict__ X, long long tile, int t, int n, long long Q,
+                                          TIn* stage_in) {
+  const long long q0 = tile * kTile;
+  const int cnt = (int)min((long long)kTile, Q - q0) * n;
+  const TIn* src = X + q0 * n;
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    const int e = t + kWorkers * k;
+    if (e < cnt) cp_async(stage_in + e, src + e);
+  }
+}
+
+template <int V, typename TIn>
+__device__ __forceinline__ void load_flat(const TIn* __restrict__ X, long long tile, int t, int n, long long Q,
+                                          TIn* raw) {
+  const long long q0 = tile * kTile;
+  const int cnt = (int)min((long long)kTile, Q - q0) * n;
+  const TIn* src = X + q0 * n;
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    const int e = t + kWorkers * k;
+    raw[k] = e < cnt ? __ldg(src + e) : (TIn)0;
+  }
+}
+
+// One operand entry (row r, column a) in the K-major canonical layout.
+template <int KIND>
+__device__ __forceinline__ void put_entry(unsigned char* A, uint32_t sbo, int r, int a, float v) {
+  constexpr int epc = KIND == 0 ? 8 : 4;
+  unsigned char* p = A + (size_t)(r >> 3) * sbo + (size_t)(a / epc) * 128 + (r & 7) * 16;
+  if (KIND == 0) {
+    *reinterpret_cast<__nv_bfloat16*>(p + (a % epc) * 2) = __float2bfloat16_rn(v);
+  } else {
+    uint32_t w;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w) : "f"(v));
+    *reinterpret_cast<uint32_t*>(p + (a % epc) * 4) = w;
+  }
+}
+
+template <int KIND, typename TIn, typename TOut, int V, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_tc_mode(TcArgs args) {
   constexpr int esz = KIND == 0 ? 2 : 4;
-  constexpr int kstep_bytes = 32;          // one MMA consumes 32 bytes of K per row
+  constexpr int epc = 16 / esz;
+  constexpr int KB = (V + epc - 1) / epc;          // strided: 16-byte blocks per thread
+  constexpr bool FLAT = MODE == 1 || MODE == 2;
+  constexpr bool STAGED = MODE == 0 || MODE == 1;  // entries travel through the input stage
+  constexpr bool OSTAGE = MODE == 1;               // output through the output stage
   extern __shared__ __align__(1024) unsigned char smem[];
   const int n = args.n, npad = args.npad;
   const int kcores = npad * esz / 16;
   const uint32_t sbo = (uint32_t)kcores * 128u;
+  const size_t a_bytes = (size_t)kTile * npad * esz;
   const long long inner = args.inner, Q = args.Q;
   const TIn* X = static_cast<const TIn*>(args.X);
   TOut* Y = static_cast<TOut*>(args.Y);
+  const int ss = stage_stride(n);
+  const size_t in_bytes = STAGED ? (((size_t)kTile * n * sizeof(TIn) + 15) & ~(size_t)15) : 0;
+  const size_t out_bytes = OSTAGE ? (((size_t)kTile * ss * sizeof(float) + 15) & ~(size_t)15) : 0;
   unsigned char* sB = smem;
-  unsigned char* sA = sB + (size_t)npad * npad * esz;
-  float* stage = reinterpret_cast<float*>(sA + (size_t)kTile * npad * esz);
-  const size_t stage_bytes = (inner == 1) ? (((size_t)kTile * (n + 1) * sizeof(float) + 15) & ~(size_t)15) : 0;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(stage) + stage_bytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-  int* sflag = reinterpret_cast<int*>(tslot + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  unsigned char* sA = sB + (size_t)npad * npad * esz;   // two operand buffers
+  TIn* stage_in = reinterpret_cast<TIn*>(sA + 2 * a_bytes);
+  float* stage = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(stage_in) + in_bytes);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(stage) + out_bytes);
+  uint64_t* pl = bar;          // [2] operand buffer written (512 arrivals)
+  uint64_t* full = bar + 2;    // [2] accumulator ready (MMA commit)
+  uint64_t* empty = bar + 4;   // [2] accumulator read out (512 arrivals)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 6);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const bool mma_warp = warp == kWorkers / 32;
 
-  // factor image -> smem (16-byte vectors), zero the A tile once (K padding stays 0)
   {
     const uint4* src = reinterpret_cast<const uint4*>(args.B);
-    uint4* dstB = reinterpret_cast<uint4*>(sB);
+    uint4* dst = reinterpret_cast<uint4*>(sB);
     const int nv = npad * npad * esz / 16;
-    for (int e = tid; e < nv; e += kTile) dstB[e] = src[e];
-    uint4* dstA = reinterpret_cast<uint4*>(sA);
-    const int na = kTile * npad * esz / 16;
-    for (int e = tid; e < na; e += kTile) dstA[e] = make_uint4(0, 0, 0, 0);
+    for (int e = t; e < nv; e += kThreads) dst[e] = src[e];
+    if (FLAT) {   // the contiguous mode writes entries one by one: its K padding stays 0
+      uint4* za = reinterpret_cast<uint4*>(sA);
+      for (size_t e = t; e < 2 * a_bytes / 16; e += kThreads) za[e] = make_uint4(0u, 0u, 0u, 0u);
+    }
   }
-  if (tid == 0) {
-    tc::mbar_init(tc::smem_u32(mbar), 1);
-    *sflag = 0;
+  if (t == 0) {
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(tc::smem_u32(&pl[b]), kWorkers);
+      tc::mbar_init(tc::smem_u32(&full[b]), 1);
+      tc::mbar_init(tc::smem_u32(&empty[b]), kWorkers);
+    }
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), (uint32_t)args.ncols);
   tc::fence_async_smem();
@@ -97,120 +247,220 @@ __global__ void __launch_bounds__(kTile) k_tc_mode(TcArgs args) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = tc::instr_desc(KIND == 0 ? 1u : 2u, kTile, npad);
-  const uint32_t a_addr = tc::smem_u32(sA), b_addr = tc::smem_u32(sB);
-  uint32_t phase = 0;
-  int pend = -1;   // thread 0: phase of an MMA commit not yet seen complete
+  bool timed_out = false;
+  int pend[2] = {-1, -1};   // MMA warp: parity of the last commit on each accumulator
 
-  for (long long tile = blockIdx.x; tile < args.ntiles; tile += gridDim.x) {
-    const long long q0 = tile * kTile;
-    const int rows = (int)min((long long)kTile, Q - q0);
-    // ---- X tile -> operand A
-    long long base = 0;
-    const long long q = q0 + tid;
-    if (q < Q) {
-      const long long o = q / inner;
-      base = o * (long long)n * inner + (q - o * inner);
-    }
-    if (inner == 1) {
-      const TIn* src = X + q0 * n;
-      const int cnt = rows * n;
-      for (int e = tid; e < cnt; e += kTile) {
-        const int r = e / n, k = e - r * n;
-        put_operand<KIND>(sA, canon_off(r, k, kcores, esz), (float)src[e]);
+  if (mma_warp) {
+    // ================= MMA issue: the whole warp waits, lane 0 issues =================
+    const uint32_t idesc = tc::instr_desc(KIND == 0 ? 1u : 2u, kTile, npad);
+    const uint64_t db0 = tc::smem_desc(tc::smem_u32(sB), 128u, sbo);
+    const int ksteps = npad * esz / 32;   // one MMA consumes 32 bytes of K per row
+    int it = 0;
+    for (long long tile = blockIdx.x; tile < args.ntiles; tile += gridDim.x, ++it) {
+      const int b = it & 1;
+      const uint32_t ph = (uint32_t)(it >> 1) & 1u;
+      if (!__all_sync(0xFFFFFFFFu, tc::mbar_wait(tc::smem_u32(&pl[b]), ph, args.wait)) ||
+          (it >= 2 && !__all_sync(0xFFFFFFFFu, tc::mbar_wait(tc::smem_u32(&empty[b]), ph ^ 1u, args.wait)))) {
+        timed_out = true;
+        break;
       }
-    } else if (q < Q) {
-      for (int k = 0; k < n; ++k) put_operand<KIND>(sA, canon_off(tid, k, kcores, esz), (float)X[base + (long long)k * inner]);
-    }
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    // ---- MMA (one thread), completion tracked by the mbarrier
-    if (tid == 0) {
-      const int ksteps = npad * esz / kstep_bytes;
-      for (int s = 0; s < ksteps; ++s) {
-        const uint64_t da = tc::smem_desc(a_addr + s * 256, 128u, sbo);
-        const uint64_t db = tc::smem_desc(b_addr + s * 256, 128u, sbo);
-        tc::mma<KIND>(tmem, da, db, idesc, s > 0 ? 1u : 0u);
+      tc::fence_after_sync();
+      if (lane == 0) {
+        const uint64_t da0 = tc::smem_desc(tc::smem_u32(sA + b * a_bytes), 128u, sbo);
+        const uint32_t dcol = tmem + (uint32_t)(b * npad);
+        for (int s = 0; s < ksteps; ++s)   // start address advances 256 bytes (16 units) per K step
+          tc::mma<KIND>(dcol, da0 + (uint64_t)(16 * s), db0 + (uint64_t)(16 * s), idesc, s > 0 ? 1u : 0u);
+        tc::mma_commit(tc::smem_u32(&full[b]));
       }
-      tc::mma_commit(tc::smem_u32(mbar));
+      pend[b] = (int)ph;
     }
-    const bool ok = tc::mbar_wait(tc::smem_u32(mbar), phase, args.wait);
-    if (!ok) *sflag = 1;
-    if (tid == 0) pend = ok ? -1 : (int)phase;
-    phase ^= 1u;
-    __syncthreads();
-    if (*sflag) break;
-    tc::fence_after_sync();
-    // ---- epilogue: TMEM row tid -> Y
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < npad; c0 += 16) {
-      float v[16];
-      tc::tmem_ld16(trow + (uint32_t)c0, v);
+  } else {
+    // ================= workers =================
+    const int r = 32 * (warp & 3) + lane;      // tile row (tensor-memory lane)
+    const int cg = warp >> 2;                  // column part: blocks cg, cg + 4, ...
+    const int per = npad / 4;                  // accumulator columns read by this thread
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    constexpr int VR = STAGED ? 1 : V;         // entries held in registers
+    TIn raw[VR];
+    // contiguous mode: (row, column) of this thread's first entry and the step per 512 entries
+    const int fr0 = t / n, fa0 = t - (t / n) * n, fdr = kWorkers / n, fda = kWorkers - (kWorkers / n) * n;
+    auto fetch = [&](long long tl) {
+      if (MODE == 0) copy_strided<KB, epc>(X, tl, r, cg, n, kcores, inner, Q, stage_in);
+      if (MODE == 1) copy_flat<V>(X, tl, t, n, Q, stage_in);
+      if (MODE == 2) load_flat<V>(X, tl, t, n, Q, raw);
+      if (MODE == 3) load_strided<KB, epc>(X, tl, r, cg, n, kcores, inner, Q, raw);
+    };
+    tc::grid_dependency_wait();   // the preceding kernel's output is read from here on
+    if ((long long)blockIdx.x < args.ntiles) fetch(blockIdx.x);
+    const long long nloc = (args.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;   // this CTA's tiles
+    for (long long it = 0; it <= nloc; ++it) {
+      const long long tile = blockIdx.x + it * gridDim.x;
+      if (it + 1 >= nloc) tc::grid_launch_dependents();
+      if (it < nloc) {
+        // ---- this tile's operand
+        const int b = (int)(it & 1);
+        unsigned char* dstA = sA + b * a_bytes + (size_t)(r >> 3) * sbo + (size_t)(r & 7) * 16;
+        if (STAGED) tc::cp_async_wait_all();
+        if (MODE == 1) workers_sync();   // every thread's copies have landed
+        if (MODE == 0 || MODE == 1) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int i = c0 + j;
-        if (i < n) {
-          if (inner == 1) stage[tid * (n + 1) + i] = v[j];
-          else if (q < Q) Y[base + (long long)i * inner] = (TOut)v[j];
+          for (int m = 0; m < KB; ++m) {
+            const int blk = cg + 4 * m;
+            if (blk >= kcores) continue;
+            float e8[epc];
+#pragma unroll
+            for (int j = 0; j < epc; ++j) {
+              const int a = blk * epc + j;
+              e8[j] = a < n ? (float)(MODE == 0 ? stage_in[a * kTile + r] : stage_in[r * n + a]) : 0.0f;
+            }
+            *reinterpret_cast<uint4*>(dstA + (size_t)blk * 128) = pack16<KIND>(e8);
+          }
+        } else if (MODE == 2) {
+          int fr = fr0, fa = fa0;
+#pragma unroll
+          for (int k = 0; k < VR; ++k) {
+            if (fr < kTile) put_entry<KIND>(sA + b * a_bytes, sbo, fr, fa, (float)raw[k]);
+            fr += fdr;
+            fa += fda;
+            if (fa >= n) {
+              fa -= n;
+              ++fr;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < KB; ++m) {
+            const int blk = cg + 4 * m;
+            if (blk >= kcores) continue;
+            float e8[epc];
+#pragma unroll
+            for (int j = 0; j < epc; ++j) e8[j] = (float)raw[(m * epc + j) % VR];
+            *reinterpret_cast<uint4*>(dstA + (size_t)blk * 128) = pack16<KIND>(e8);
+          }
         }
+        tc::fence_async_smem();
+        tc::mbar_arrive(tc::smem_u32(&pl[b]));
+        if (MODE == 1) workers_sync();   // every thread has read the input stage
+        // ---- the next tile travels while this one is multiplied and the last one stored
+        if (it + 1 < nloc) fetch(tile + gridDim.x);
+      }
+      if (it == 0) continue;
+      // ---- epilogue of the previous tile
+      const long long pt = tile - gridDim.x;
+      const int b = (int)((it - 1) & 1);
+      const bool ok = __all_sync(0xFFFFFFFFu, tc::mbar_wait(tc::smem_u32(&full[b]),
+                                                             (uint32_t)((it - 1) >> 1) & 1u, args.wait));
+      const long long q0 = pt * kTile;
+      const long long q = q0 + r;
+      TOut* ydst = Y;   // this thread's row of the tile
+      if (!OSTAGE && q < Q) {
+        const long long o = q / inner;
+        ydst = Y + o * (long long)n * inner + (q - o * inner);
+      }
+      if (ok) {
+        tc::fence_after_sync();
+        // 16 accumulator columns per tensor-memory read, straight to the stage or Y
+        TOut* yp = ydst + (long long)(cg * per) * inner;
+        for (int g0 = 0; g0 < per; g0 += 16) {
+          uint32_t Tr[4][4];
+#pragma unroll
+          for (int g = 0; g < 4; ++g)
+            if (g0 + 4 * g < per) tc::tmem_ld4_async(lane_base + (uint32_t)(b * npad + cg * per + g0 + 4 * g), Tr[g]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            asm volatile("" : "+r"(Tr[g][0]), "+r"(Tr[g][1]), "+r"(Tr[g][2]), "+r"(Tr[g][3]) : : "memory");
+            if (g0 + 4 * g >= per) continue;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int i = cg * per + g0 + 4 * g + e;
+              const float val = __uint_as_float(Tr[g][e]);
+              if (OSTAGE) {
+                if (i < n) stage[r * ss + i] = val;
+              } else {
+                if (i < n && q < Q) *yp = (TOut)val;
+                yp += inner;
+              }
+            }
+          }
+        }
+        tc::fence_before_sync();
+        tc::mbar_arrive(tc::smem_u32(&empty[b]));
+      } else {
+        timed_out = true;
+      }
+      if (OSTAGE) {
+        // coalesced stores of the tile's contiguous block from the stage, one warp per row
+        if (workers_or(timed_out)) {
+          timed_out = true;
+          break;
+        }
+        const int rows = (int)min((long long)kTile, Q - q0);
+        for (int rr = warp; rr < rows; rr += kWorkers / 32) {
+          TOut* dst = Y + (q0 + rr) * n;
+          const float* src = stage + rr * ss;
+          for (int k = lane; k < n; k += 32) dst[k] = (TOut)src[k];
+        }
+        workers_sync();   // the stage is rewritten by the next epilogue
+      } else if (!ok) {
+        break;
       }
     }
-    if (inner == 1) {
-      __syncthreads();
-      TOut* dst = Y + q0 * n;
-      const int cnt = rows * n;
-      for (int e = tid; e < cnt; e += kTile) {
-        const int r = e / n;
-        dst[e] = (TOut)stage[r * (n + 1) + (e - r * n)];
-      }
-    }
-    tc::fence_before_sync();
-    __syncthreads();
+    if (STAGED) tc::cp_async_wait_all();   // no copy outlives the kernel
+  }
+  // ---- exit: a wait that ran out is reported; the MMA warp lets its own MMAs
+  // in flight finish (bounded) before tensor memory is released
+  const bool any_timeout = __syncthreads_or(timed_out ? 1 : 0) != 0;
+  if (mma_warp && lane == 0 && any_timeout) {
+    if (args.status) atomicOr(args.status, kStatusTimeout);
+    for (int b = 0; b < 2; ++b)
+      if (pend[b] >= 0) tc::mbar_wait(tc::smem_u32(&full[b]), (uint32_t)pend[b], kDrainIters);
   }
   tc::fence_after_sync();
-  if (tid == 0 && *sflag) {
-    // a wait ran out: report it and let the MMAs in flight finish (bounded)
-    // before tensor memory is released
-    if (args.status) atomicOr(args.status, kStatusTimeout);
-    if (pend >= 0) tc::mbar_wait(tc::smem_u32(mbar), (uint32_t)pend, kDrainIters);
-    tc::fence_after_sync();
-  }
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, (uint32_t)args.ncols);
+}
+
+template <int KIND, typename TIn, typename TOut, int V>
+cudaError_t launch_v(const TIn* X, TOut* Y, const unsigned char* B, int n, int npad, long long inner,
+                     long long outer, cudaStream_t st) {
+  const long long Q = inner * outer;
+  const int esz = esz_of(KIND);
+  const size_t limit = (size_t)227 * 1024;
+  const size_t base = (size_t)npad * npad * esz + 2 * (size_t)kTile * npad * esz + 6 * 8 + 16;
+  const size_t in_stage = ((size_t)kTile * n * sizeof(TIn) + 15) & ~(size_t)15;
+  const size_t out_stage = ((size_t)kTile * stage_stride(n) * sizeof(float) + 15) & ~(size_t)15;
+  if (base > limit) return cudaErrorInvalidValue;
+  const bool flat = inner == 1;
+  const int mode = flat ? (base + in_stage + out_stage <= limit ? 1 : 2) : (base + in_stage <= limit ? 0 : 3);
+  auto kern = mode == 0 ? k_tc_mode<KIND, TIn, TOut, V, 0>
+            : mode == 1 ? k_tc_mode<KIND, TIn, TOut, V, 1>
+            : mode == 2 ? k_tc_mode<KIND, TIn, TOut, V, 2> : k_tc_mode<KIND, TIn, TOut, V, 3>;
+  {
+    const cudaError_t e = ensure_smem_attr(kern, 227 * 1024);
+    if (e != cudaSuccess) return e;
+  }
+  int ncols = 32;
+  while (ncols < 2 * npad) ncols <<= 1;
+  const long long ntiles = (Q + kTile - 1) / kTile;
+  const long long grid = std::min<long long>(ntiles, sm_count_current());
+  TcArgs a{X, Y, B, n, npad, ncols, inner, Q, ntiles, status_word(), wait_limit()};
+  const double flops = 2.0 * (double)Q * n * n;
+  const double bytes = (double)Q * n * (sizeof(TIn) + sizeof(TOut));
+  ProfScope ps(KIND == 0 ? "tc_mode_bf16" : "tc_mode_tf32", flops, bytes, st);
+  // 227 KB requested so that exactly one CTA (and its tensor memory) sits on an SM
+  return tc::launch_pdl(kern, dim3((unsigned)grid), dim3(kThreads), limit, st, a);
 }
 
 template <int KIND, typename TIn, typename TOut>
 cudaError_t launch_impl(const TIn* X, TOut* Y, const unsigned char* B, int n, long long inner, long long outer,
                         cudaStream_t st) {
-  const long long Q = inner * outer;
-  if (Q <= 0) return cudaSuccess;
-  const int esz = esz_of(KIND);
+  if (inner * outer <= 0) return cudaSuccess;
+  if (n < 1 || n > 128) return cudaErrorInvalidValue;
   const int npad = (n + 15) / 16 * 16;
-  int ncols = 32;
-  while (ncols < npad) ncols <<= 1;
-  const size_t stage = (inner == 1) ? (((size_t)kTile * (n + 1) * sizeof(float) + 15) & ~(size_t)15) : 0;
-  const size_t smem = (size_t)npad * npad * esz + (size_t)kTile * npad * esz + stage + 32;
-  {
-    const cudaError_t e = ensure_smem_attr(k_tc_mode<KIND, TIn, TOut>, 227 * 1024);
-    if (e != cudaSuccess) return e;
-  }
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  const int by_smem = (int)std::max<size_t>(1, (228 * 1024) / (smem + 1024));
-  const int by_tmem = 512 / ncols;
-  const int per_sm = std::max(1, std::min(by_smem, by_tmem));
-  // Request enough shared memory that no SM can hold more CTAs than tensor
-  // memory has columns for (a surplus CTA would block in tcgen05.alloc).
-  const size_t smem_req = std::max(smem, (size_t)(228 * 1024) / per_sm - 1024 + 1);
-  const long long ntiles = (Q + kTile - 1) / kTile;
-  const long long grid = std::min<long long>(ntiles, (long long)sm_count_current() * per_sm);
-  TcArgs a{X, Y, B, n, npad, ncols, inner, Q, ntiles, status_word(), wait_limit()};
-  const double flops = 2.0 * (double)Q * n * n;
-  const double bytes = (double)Q * n * (sizeof(TIn) + sizeof(TOut));
-  ProfScope ps(KIND == 0 ? "tc_mode_bf16" : "tc_mode_tf32", flops, bytes, st);
-  k_tc_mode<KIND, TIn, TOut><<<(unsigned)grid, kTile, std::min(smem_req, (size_t)227 * 1024), st>>>(a);
-  return cudaGetLastError();
+  // 32 entries per thread cover every size up to 128: strided modes take every
+  // fourth 16-byte block of a row (npad / 4 entries), the contiguous mode 128 n / 512
+  return launch_v<KIND, TIn, TOut, 32>(X, Y, B, n, npad, inner, outer, st);
 }
 
 }  // namespace
