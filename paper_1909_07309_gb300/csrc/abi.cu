@@ -311,7 +311,8 @@ extern "C" int stfd_fd_setup(stfd_fd** out, int d, const int* n, const double* c
   }
   if (rc == STFD_OK && f.n_pairs > 0) rc = dev_upload(&h->lamt, f.lamt.data(), f.lamt.size(), st);
   if (rc == STFD_OK) rc = dev_upload(&h->g, f.g.data(), f.g.size(), st);
-  if (rc == STFD_OK) rc = dev_upload<double>(&h->work, nullptr, (size_t)h->N, st);
+  // N doubles, or two FP32 N-vectors each starting on a 16-byte boundary (+4)
+  if (rc == STFD_OK) rc = dev_upload<double>(&h->work, nullptr, (size_t)h->N + 4, st);
   if (rc == STFD_OK && (precision == STFD_DF32 || precision == STFD_FP64TC)) {
     rc = dev_upload<double>(&h->work3, nullptr, (size_t)h->N, st);
     if (rc == STFD_OK) rc = dev_upload<int>(&h->bexp, nullptr, 1, st);
@@ -442,7 +443,7 @@ namespace {
 int fd_apply_one_lowp(const stfd_fd* h, const double* r, double* s, double* work, int trans, cudaStream_t st) {
   const int d = h->d;
   const int kind = h->precision == STFD_BF16 ? 0 : 1;
-  float* buf[2] = {reinterpret_cast<float*>(work), reinterpret_cast<float*>(work) + h->N};
+  float* buf[2] = {reinterpret_cast<float*>(work), reinterpret_cast<float*>(work) + ((h->N + 3) & ~3LL)};
   int cur = -1;   // -1: the FP64 input r
   long long inner = 1;
   for (int l = 0; l <= d; ++l) {

@@ -60,6 +60,8 @@ struct TcArgs {
   void* Y;
   const unsigned char* B;   // factor image, npad x npad in the operand format
   int n, npad, ncols;
+  int vec;                  // contiguous mode: X and Y 16-byte aligned (16-byte copies and stores)
+  int nin;                  // contiguous mode: input stages (2: the copies run two tiles ahead)
   long long inner, Q, ntiles;
   int* status;              // host-mapped status word (kStatusTimeout), may be null
   long long wait;           // bounded-wait iteration limit
@@ -166,6 +168,27 @@ __device__ __forceinline__ void copy_flat(const TIn* __restrict__ X, long long t
   }
 }
 
+// The same block in 16-byte copies (X 16-byte aligned; a tile starts at a
+// multiple of 128 n entries, so every tile's block is aligned too); the bytes
+// past the last whole 16 go entry by entry.
+template <typename TIn>
+__device__ __forceinline__ void copy_flat16(const TIn* __restrict__ X, long long tile, int t, int n, long long Q,
+                                            TIn* stage_in) {
+  const long long q0 = tile * kTile;
+  const int cnt = (int)min((long long)kTile, Q - q0) * n;
+  const TIn* src = X + q0 * n;
+  const unsigned char* s8 = reinterpret_cast<const unsigned char*>(src);
+  const uint32_t d = tc::smem_u32(stage_in);
+  const int nch = (int)((cnt * sizeof(TIn)) >> 4);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {   // 128 x 128 x 8 bytes / 16 / 512 = 16 chunks at most
+    const int c = t + kWorkers * k;
+    if (c < nch) tc::cp_async16(d + 16u * c, s8 + 16 * (size_t)c);
+  }
+  const int e = nch * 16 / (int)sizeof(TIn) + t;
+  if (e < cnt) cp_async(stage_in + e, src + e);
+}
+
 template <int V, typename TIn>
 __device__ __forceinline__ void load_flat(const TIn* __restrict__ X, long long tile, int t, int n, long long Q,
                                           TIn* raw) {
@@ -210,12 +233,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mode(TcArgs args) {
   const TIn* X = static_cast<const TIn*>(args.X);
   TOut* Y = static_cast<TOut*>(args.Y);
   const int ss = stage_stride(n);
-  const size_t in_bytes = STAGED ? (((size_t)kTile * n * sizeof(TIn) + 15) & ~(size_t)15) : 0;
+  const size_t in_bytes = STAGED ? (((size_t)kTile * n * sizeof(TIn) + 15) & ~(size_t)15) : 0;   // per stage
   const size_t out_bytes = OSTAGE ? (((size_t)kTile * ss * sizeof(float) + 15) & ~(size_t)15) : 0;
   unsigned char* sB = smem;
   unsigned char* sA = sB + (size_t)npad * npad * esz;   // two operand buffers
   TIn* stage_in = reinterpret_cast<TIn*>(sA + 2 * a_bytes);
-  float* stage = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(stage_in) + in_bytes);
+  float* stage = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(stage_in) +
+                                          (MODE == 1 ? args.nin : 1) * in_bytes);
   uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(stage) + out_bytes);
   uint64_t* pl = bar;          // [2] operand buffer written (512 arrivals)
   uint64_t* full = bar + 2;    // [2] accumulator ready (MMA commit)
@@ -284,24 +308,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mode(TcArgs args) {
     TIn raw[VR];
     // contiguous mode: (row, column) of this thread's first entry and the step per 512 entries
     const int fr0 = t / n, fa0 = t - (t / n) * n, fdr = kWorkers / n, fda = kWorkers - (kWorkers / n) * n;
-    auto fetch = [&](long long tl) {
+    const int in_elems = (int)(in_bytes / sizeof(TIn));   // one input stage
+    auto fetch = [&](long long tl, int buf) {
       if (MODE == 0) copy_strided<KB, epc>(X, tl, r, cg, n, kcores, inner, Q, stage_in);
-      if (MODE == 1) copy_flat<V>(X, tl, t, n, Q, stage_in);
+      if (MODE == 1) {
+        if (args.vec) copy_flat16(X, tl, t, n, Q, stage_in + buf * in_elems);
+        else copy_flat<V>(X, tl, t, n, Q, stage_in + buf * in_elems);
+        tc::cp_async_commit();
+      }
       if (MODE == 2) load_flat<V>(X, tl, t, n, Q, raw);
       if (MODE == 3) load_strided<KB, epc>(X, tl, r, cg, n, kcores, inner, Q, raw);
     };
+    const int nin = MODE == 1 ? args.nin : 1;
     tc::grid_dependency_wait();   // the preceding kernel's output is read from here on
-    if ((long long)blockIdx.x < args.ntiles) fetch(blockIdx.x);
     const long long nloc = (args.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;   // this CTA's tiles
+    for (int k = 0; k < nin && k < nloc; ++k) fetch(blockIdx.x + k * gridDim.x, k);
     for (long long it = 0; it <= nloc; ++it) {
       const long long tile = blockIdx.x + it * gridDim.x;
       if (it + 1 >= nloc) tc::grid_launch_dependents();
       if (it < nloc) {
         // ---- this tile's operand
         const int b = (int)(it & 1);
+        const int ib = (int)(it % nin);
+        const TIn* sin = stage_in + ib * in_elems;
         unsigned char* dstA = sA + b * a_bytes + (size_t)(r >> 3) * sbo + (size_t)(r & 7) * 16;
-        if (STAGED) tc::cp_async_wait_all();
-        if (MODE == 1) workers_sync();   // every thread's copies have landed
+        if (MODE == 0) tc::cp_async_wait_all();
+        if (MODE == 1) {   // this tile's copies have landed (the next tile's may still travel)
+          if (nin == 2 && it + 1 < nloc) tc::cp_async_wait_group<1>();
+          else tc::cp_async_wait_group<0>();
+          workers_sync();
+        }
         if (MODE == 0 || MODE == 1) {
 #pragma unroll
           for (int m = 0; m < KB; ++m) {
@@ -311,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mode(TcArgs args) {
 #pragma unroll
             for (int j = 0; j < epc; ++j) {
               const int a = blk * epc + j;
-              e8[j] = a < n ? (float)(MODE == 0 ? stage_in[a * kTile + r] : stage_in[r * n + a]) : 0.0f;
+              e8[j] = a < n ? (float)(MODE == 0 ? sin[a * kTile + r] : sin[r * n + a]) : 0.0f;
             }
             *reinterpret_cast<uint4*>(dstA + (size_t)blk * 128) = pack16<KIND>(e8);
           }
@@ -340,9 +376,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mode(TcArgs args) {
         }
         tc::fence_async_smem();
         tc::mbar_arrive(tc::smem_u32(&pl[b]));
-        if (MODE == 1) workers_sync();   // every thread has read the input stage
-        // ---- the next tile travels while this one is multiplied and the last one stored
-        if (it + 1 < nloc) fetch(tile + gridDim.x);
+        // ---- the next tiles travel while this one is multiplied and the last one stored
+        if (MODE == 1) {
+          workers_sync();   // every thread has read this input stage: refill it
+          if (it + nin < nloc) fetch(tile + nin * gridDim.x, ib);
+        } else if (it + 1 < nloc) {
+          fetch(tile + gridDim.x, 0);
+        }
       }
       if (it == 0) continue;
       // ---- epilogue of the previous tile
@@ -396,10 +436,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mode(TcArgs args) {
           break;
         }
         const int rows = (int)min((long long)kTile, Q - q0);
-        for (int rr = warp; rr < rows; rr += kWorkers / 32) {
-          TOut* dst = Y + (q0 + rr) * n;
-          const float* src = stage + rr * ss;
-          for (int k = lane; k < n; k += 32) dst[k] = (TOut)src[k];
+        TOut* dst = Y + q0 * n;
+        if (args.vec) {
+          // 16-byte stores of the contiguous block: chunk c holds entries c epo .. c epo + epo - 1
+          constexpr int epo = 16 / sizeof(TOut);
+          const int cnt = rows * n;
+          const int nch = (int)((cnt * sizeof(TOut)) >> 4);
+          const int step = kWorkers * epo, sr = step / n, sa = step - sr * n;
+          int cr = t * epo / n, ca = t * epo - cr * n;
+          for (int c = t; c < nch; c += kWorkers) {
+            union {
+              uint4 u;
+              TOut v[epo];
+            } w;
+            int rr = cr, aa = ca;
+#pragma unroll
+            for (int j = 0; j < epo; ++j) {
+              w.v[j] = (TOut)stage[rr * ss + aa];
+              if (++aa == n) {
+                aa = 0;
+                ++rr;
+              }
+            }
+            *reinterpret_cast<uint4*>(dst + (size_t)c * epo) = w.u;
+            cr += sr;
+            ca += sa;
+            if (ca >= n) {
+              ca -= n;
+              ++cr;
+            }
+          }
+          const int e = nch * epo + t;
+          if (e < cnt) dst[e] = (TOut)stage[(e / n) * ss + e % n];
+        } else {
+          for (int rr = warp; rr < rows; rr += kWorkers / 32) {
+            const float* src = stage + rr * ss;
+            for (int k = lane; k < n; k += 32) dst[(size_t)rr * n + k] = (TOut)src[k];
+          }
         }
         workers_sync();   // the stage is rewritten by the next epilogue
       } else if (!ok) {
@@ -432,7 +505,9 @@ cudaError_t launch_v(const TIn* X, TOut* Y, const unsigned char* B, int n, int n
   const size_t out_stage = ((size_t)kTile * stage_stride(n) * sizeof(float) + 15) & ~(size_t)15;
   if (base > limit) return cudaErrorInvalidValue;
   const bool flat = inner == 1;
-  const int mode = flat ? (base + in_stage + out_stage <= limit ? 1 : 2) : (base + in_stage <= limit ? 0 : 3);
+  int mode = flat ? (base + in_stage + out_stage <= limit ? 1 : 2) : (base + in_stage <= limit ? 0 : 3);
+  const int nin = (mode == 1 && base + 2 * in_stage + out_stage <= limit) ? 2 : 1;
+  const int vec = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15) == 0 ? 1 : 0;
   auto kern = mode == 0 ? k_tc_mode<KIND, TIn, TOut, V, 0>
             : mode == 1 ? k_tc_mode<KIND, TIn, TOut, V, 1>
             : mode == 2 ? k_tc_mode<KIND, TIn, TOut, V, 2> : k_tc_mode<KIND, TIn, TOut, V, 3>;
@@ -444,7 +519,7 @@ cudaError_t launch_v(const TIn* X, TOut* Y, const unsigned char* B, int n, int n
   while (ncols < 2 * npad) ncols <<= 1;
   const long long ntiles = (Q + kTile - 1) / kTile;
   const long long grid = std::min<long long>(ntiles, sm_count_current());
-  TcArgs a{X, Y, B, n, npad, ncols, inner, Q, ntiles, status_word(), wait_limit()};
+  TcArgs a{X, Y, B, n, npad, ncols, vec, nin, inner, Q, ntiles, status_word(), wait_limit()};
   const double flops = 2.0 * (double)Q * n * n;
   const double bytes = (double)Q * n * (sizeof(TIn) + sizeof(TOut));
   ProfScope ps(KIND == 0 ? "tc_mode_bf16" : "tc_mode_tf32", flops, bytes, st);
