@@ -81,6 +81,8 @@ __global__ void k_arrowhead(T* __restrict__ X, ArrowParamsT<T> p) {
     const T a = p.nu * mu;
     const T gam = p.gamma * p.sgn;   // transposed system: b_j -> -b_j, B_j -> -B_j
     T y = X[(long long)(p.nt - 1) * Ns + k];
+    // unrolled: the loads of eight pairs are in flight together
+#pragma unroll 8
     for (int j = 0; j < p.n_pairs; ++j) {
       const T x1 = X[(long long)(2 * j) * Ns + k], x2 = X[(long long)(2 * j + 1) * Ns + k];
       const T b = gam * p.lamt[j];
@@ -96,6 +98,8 @@ __global__ void k_arrowhead(T* __restrict__ X, ArrowParamsT<T> p) {
     }
     const T qn = y * p.Sinv[k];
     X[(long long)(p.nt - 1) * Ns + k] = qn;
+    // unrolled: the loads of eight pairs are in flight together
+#pragma unroll 8
     for (int j = 0; j < p.n_pairs; ++j) {
       const long long o1 = (long long)(2 * j) * Ns + k, o2 = (long long)(2 * j + 1) * Ns + k;
       const T b = gam * p.lamt[j];
@@ -146,6 +150,8 @@ __global__ void k_arrowhead_f64(double* __restrict__ X, ArrowParamsT<double> p, 
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < Ns;
        k += (long long)gridDim.x * blockDim.x) {
     double y = X[(long long)(p.nt - 1) * Ns + k];
+    // unrolled: the loads of eight pairs are in flight together
+#pragma unroll 8
     for (int j = 0; j < p.n_pairs; ++j) {
       const double x1 = X[(long long)(2 * j) * Ns + k], x2 = X[(long long)(2 * j + 1) * Ns + k];
       const double2 w = W[(long long)j * Ns + k];
@@ -172,6 +178,8 @@ __global__ void k_arrowhead_f64(double* __restrict__ X, ArrowParamsT<double> p, 
     }
     const double qn = y * p.Sinv[k];
     X[(long long)(p.nt - 1) * Ns + k] = qn;
+    // unrolled: the loads of eight pairs are in flight together
+#pragma unroll 8
     for (int j = 0; j < p.n_pairs; ++j) {
       const long long o1 = (long long)(2 * j) * Ns + k, o2 = (long long)(2 * j + 1) * Ns + k;
       const double2 w = W[(long long)j * Ns + k];
