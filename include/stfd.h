@@ -208,8 +208,8 @@ void stfd_fd_destroy(stfd_fd* h);
  *   STFD_OP_FX64  FP64 results, intermediates and inputs; each band product is
  *                 formed exactly in 64-bit integer arithmetic (every fibre of the
  *                 input and every band row written as 53-bit integers under their
- *                 own powers of two, 27-bit limbs, 4 integer multiply-adds per
- *                 tap) and rounded once to FP64; an output summing two products
+ *                 own powers of two, 27-bit limbs, 3 integer multiply-adds per
+ *                 tap, Karatsuba) and rounded once to FP64; an output summing two products
  *                 of different inputs adds the two rounded FP64 values. Entries
  *                 far below their fibre's largest entry are rounded at 2^-53 of
  *                 that entry (normwise FP64 accuracy). Needs every half-bandwidth

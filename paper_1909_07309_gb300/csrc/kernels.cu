@@ -13,6 +13,7 @@
 #include "device_state.h"
 #include "kernels.h"
 #include "profile.h"
+#include "tc_common.cuh"
 
 namespace stfd {
 namespace {
@@ -110,6 +111,63 @@ __global__ void k_arrowhead(T* __restrict__ X, ArrowParamsT<T> p) {
     }
     if (p.has_zero) X[(long long)z * Ns + k] = (x0 - gam * p.g[z] * qn) / a;
   }
+}
+
+// FP32 Step 3 of the mixed-precision preconditioner, staged: a CTA owns 128
+// consecutive spatial indices; each thread copies its own index's n_t entries
+// into shared memory (asynchronous copies, all in flight together, column t of
+// an [n_t][128] tile), computes the block LU above on them and writes the
+// results back (coalesced per time index). One thread per index, as
+// k_arrowhead, without its chain of dependent global loads.
+constexpr int kArrowTile = 128;
+__global__ void __launch_bounds__(kArrowTile) k_arrowhead_staged(float* __restrict__ X, ArrowParamsT<float> p) {
+  extern __shared__ __align__(16) float sx[];   // [nt][kArrowTile]
+  const long long Ns = p.Ns;
+  const int t = threadIdx.x;
+  const long long k = (long long)blockIdx.x * kArrowTile + t;
+  tc::grid_dependency_wait();
+  if (k >= Ns) return;   // no barrier below: each thread reads only its own column
+  for (int j = 0; j < p.nt; ++j) tc::cp_async4(&sx[j * kArrowTile + t], X + (long long)j * Ns + k);
+  long long rest = k;
+  const int i1 = (int)(rest % p.n1);
+  rest /= p.n1;
+  float mu = p.lam[0][i1];
+  if (p.d >= 2) {
+    const int i2 = (int)(rest % p.n2);
+    rest /= p.n2;
+    mu += p.lam[1][i2];
+  }
+  if (p.d >= 3) mu += p.lam[2][rest];
+  const float a = p.nu * mu;
+  const float gam = p.gamma * p.sgn;   // transposed system: b_j -> -b_j, B_j -> -B_j
+  const float sinv = p.Sinv[k];
+  tc::cp_async_wait_all();
+  const float* col = sx + t;
+  float y = col[(p.nt - 1) * kArrowTile];
+  for (int j = 0; j < p.n_pairs; ++j) {
+    const float x1 = col[(2 * j) * kArrowTile], x2 = col[(2 * j + 1) * kArrowTile];
+    const float b = gam * p.lamt[j];
+    const float inv = 1.0f / fmaf(a, a, b * b);
+    const float h1 = (a * x1 - b * x2) * inv, h2 = (b * x1 + a * x2) * inv;
+    y = fmaf(gam, fmaf(p.g[2 * j], h1, p.g[2 * j + 1] * h2), y);
+  }
+  const int z = 2 * p.n_pairs;
+  float x0 = 0.0f;
+  if (p.has_zero) {
+    x0 = col[z * kArrowTile];
+    y = fmaf(gam * p.g[z], x0 / a, y);
+  }
+  const float qn = y * sinv;
+  X[(long long)(p.nt - 1) * Ns + k] = qn;
+  for (int j = 0; j < p.n_pairs; ++j) {
+    const float b = gam * p.lamt[j];
+    const float inv = 1.0f / fmaf(a, a, b * b);
+    const float r1 = col[(2 * j) * kArrowTile] - gam * p.g[2 * j] * qn;
+    const float r2 = col[(2 * j + 1) * kArrowTile] - gam * p.g[2 * j + 1] * qn;
+    X[(long long)(2 * j) * Ns + k] = (a * r1 - b * r2) * inv;
+    X[(long long)(2 * j + 1) * Ns + k] = (b * r1 + a * r2) * inv;
+  }
+  if (p.has_zero) X[(long long)z * Ns + k] = (x0 - gam * p.g[z] * qn) / a;
 }
 
 // Table of Step 3 (FP64, once per handle): for every pair j and spatial index
@@ -530,6 +588,13 @@ cudaError_t launch_arrowhead_fp64_tab(double* X, const ArrowParams& p, const dou
 cudaError_t launch_arrowhead_fp32(float* X, const ArrowParamsT<float>& p, cudaStream_t st) {
   if (p.Ns <= 0) return cudaSuccess;
   ProfScope ps("arrowhead_fp32", (double)p.Ns * (10.0 * p.n_pairs + 4.0), 8.0 * (double)p.Ns * p.nt, st);
+  const size_t smem = (size_t)p.nt * kArrowTile * sizeof(float);
+  if (smem <= 96 * 1024) {
+    const cudaError_t e = ensure_smem_attr(k_arrowhead_staged, 96 * 1024);
+    if (e != cudaSuccess) return e;
+    return tc::launch_pdl(k_arrowhead_staged, dim3((unsigned)((p.Ns + kArrowTile - 1) / kArrowTile)),
+                          dim3(kArrowTile), smem, st, X, p);
+  }
   k_arrowhead<float><<<grid_for(p.Ns, 256), 256, 0, st>>>(X, p);
   return cudaGetLastError();
 }
