@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "device_state.h"
+#include "fp64_round.cuh"
 #include "kernels.h"
 #include "profile.h"
 #include "tc_common.cuh"
@@ -95,20 +96,21 @@ __device__ __forceinline__ double round_acc(const Acc& a, int SE) {
   } else {
     return 0.0;
   }
+  const int be0 = P + SE - 2150 + 1023;      // biased exponent before rounding
+  if (be0 < 1) return round_sub(hi, lo, be0, neg);   // below the normal range: rare
   unsigned long long mant = hi >> 11;
   const unsigned rb = (unsigned)hi & 0x7FFu;
   const unsigned up = (rb > 0x400u) | ((rb == 0x400u) & ((lo != 0ull) | (unsigned)(mant & 1ull)));
   mant += up;
   const int c = (int)(mant >> 53);
   mant >>= c;
-  const int be = P + c + SE - 2150 + 1023;
-  if (be >= 1 && be <= 2046) {
+  const int be = be0 + c;
+  if (be <= 2046) {
     const unsigned long long bits =
         ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (mant & 0xFFFFFFFFFFFFFull);
     return __longlong_as_double((long long)bits);
   }
-  const double v = scalbn((double)mant, P + c - 52 + SE - 2150);   // outside the normal range: rare
-  return neg ? -v : v;
+  return neg ? -CUDART_INF : CUDART_INF;
 }
 
 // Coefficient tables (host-built, see fx_tables): per row i, two sets of W =

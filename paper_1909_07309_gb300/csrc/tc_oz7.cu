@@ -39,6 +39,7 @@
 #include <vector>
 
 #include "device_state.h"
+#include "fp64_round.cuh"
 #include "kernels.h"
 #include "profile.h"
 #include "tc_common.cuh"
@@ -77,9 +78,9 @@ __device__ __forceinline__ int bexp(long long w) {
   return max(1, (int)(((unsigned long long)w >> 52) & 0x7FF));
 }
 
-// Rare cases of combine7: |Z| below 2^24, or a result outside the normal range.
+// Rare case of combine7: |Z| below 2^24 (then zh 2^24 + zl is exact in FP64
+// and scalbn rounds once).
 __device__ __noinline__ double combine7_slow(long long zh, long long zl, int SE) {
-  // Z = zh 2^24 + zl exactly, |Z| < 2^75: two exact FP64 terms, one rounding
   const double hi = (double)zh * 16777216.0, lo = (double)zl;
   return scalbn(hi + lo, SE);
 }
@@ -105,14 +106,16 @@ __device__ __forceinline__ double combine7(const float* T, int SE) {
   const unsigned long long lo64 = (unsigned long long)mr << 40;
   const unsigned long long hi = (Mt << lz) | (lo64 >> (64 - lz));
   const unsigned long long lo = lo64 << lz;
+  const int be0 = 87 - lz + SE + 1023;                    // biased exponent before rounding
+  if (be0 < 1) return round_sub(hi, lo, be0, neg);         // below the normal range: rare
   unsigned long long mant = hi >> 11;
   const unsigned rb = (unsigned)hi & 0x7FFu;
   const unsigned up = (rb > 0x400u) | ((rb == 0x400u) & ((lo != 0ull) | (unsigned)(mant & 1ull)));
   mant += up;
   const int c = (int)(mant >> 53);
   mant >>= c;
-  const int be = 87 - lz + c + SE + 1023;
-  if (be < 1 || be > 2046) return combine7_slow(zh, zl, SE);
+  const int be = be0 + c;
+  if (be > 2046) return neg ? -CUDART_INF : CUDART_INF;
   const unsigned long long bits =
       ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (mant & 0xFFFFFFFFFFFFFull);
   return __longlong_as_double((long long)bits);
