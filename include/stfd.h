@@ -210,7 +210,8 @@ void stfd_fd_destroy(stfd_fd* h);
  *                 input and every band row written as 53-bit integers under their
  *                 own powers of two, 27-bit limbs, 3 integer multiply-adds per
  *                 tap, Karatsuba) and rounded once to FP64; an output summing two products
- *                 of different inputs adds the two rounded FP64 values. Entries
+ *                 of different inputs sums them exactly and rounds once when their
+ *                 scales are within 2^16 (else adds the two rounded FP64 values). Entries
  *                 far below their fibre's largest entry are rounded at 2^-53 of
  *                 that entry (normwise FP64 accuracy). Needs every half-bandwidth
  *                 in 1..4; otherwise the op uses the STFD_OP_FP64 passes.

@@ -12,9 +12,11 @@
 // U = U_h 2^27 + U_l and C = C_h 2^27 + C_l with 0 <= U_l, C_l < 2^27, in three
 // 64-bit sums (3 IMAD.WIDE per tap, Karatsuba) and rounded once, to nearest
 // even, to FP64: S 2^{E + E_c - 2150}. An output that sums two products of
-// different inputs (K u + M v; gamma W u + nu M_t v) adds the two rounded
-// products with one FP64 addition (on the FP64 pipe, otherwise idle here), so
-// it is within one unit in the last place of the exact sum.
+// different inputs (K u + M v; gamma W u + nu M_t v) adds the two exact sums
+// in 128-bit integers and rounds once when their scales are within 2^16 of
+// each other in every lane of the warp (the usual case); otherwise it adds the
+// two rounded products with one FP64 addition, within one unit in the last
+// place of the exact sum.
 //
 // The pass structure is that of the double-float passes (band_df.cu): a CTA
 // owns 32 fibres; with rot = 1 the fibres are contiguous (the direction is the
@@ -70,33 +72,52 @@ __device__ __forceinline__ void tap(Acc& a, int2 c, int2 u) {
   a.mm += (long long)(c.x + c.y) * (u.x + u.y);
 }
 
-// S = hh 2^54 + (mm - hh - ll) 2^27 + ll (exact) rounded to nearest even, times 2^{SE - 2150}.
-__device__ __forceinline__ double round_acc(const Acc& a, int SE) {
+// The exact sum S = hh 2^54 + (mm - hh - ll) 2^27 + ll of an accumulator as a
+// signed 128-bit integer (hi: high word, two's complement; |S| < 2^110).
+struct S128 {
+  long long hi;
+  unsigned long long lo;
+};
+__device__ __forceinline__ S128 to_s128(const Acc& a) {
   const long long hl = a.mm - a.hh - a.ll;
   const long long t1 = hl + (a.ll >> 27);
   const unsigned long long r0 = (unsigned long long)a.ll & ((1ull << 27) - 1);
   const long long t2 = a.hh + (t1 >> 27);
   const unsigned long long R = ((unsigned long long)(t1 & ((1ll << 27) - 1)) << 27) | r0;   // S = t2 2^54 + R
-  const bool neg = t2 < 0;
-  const unsigned long long Mh = neg ? (unsigned long long)(~t2) + (R == 0ull) : (unsigned long long)t2;
-  const unsigned long long Ml = neg ? (((1ull << 54) - R) & ((1ull << 54) - 1)) : R;
-  unsigned long long hi, lo;
-  int P;
-  if (Mh) {
-    const int lz = __clzll((long long)Mh);   // >= 6
-    const unsigned long long l10 = Ml << 10;
-    hi = (Mh << lz) | (l10 >> (64 - lz));
-    lo = l10 << lz;
-    P = 117 - lz;                             // (63 - lz) + 54
-  } else if (Ml) {
-    const int lz = __clzll((long long)Ml);
-    hi = Ml << lz;
-    lo = 0ull;
-    P = 63 - lz;
-  } else {
-    return 0.0;
+  return S128{t2 >> 10, ((unsigned long long)t2 << 54) | R};
+}
+
+// x 2^g + y for 0 <= g <= 16 (no overflow: |x 2^g| < 2^126).
+__device__ __forceinline__ S128 shl_add(S128 x, int g, S128 y) {
+  const unsigned long long xh = g ? ((unsigned long long)x.hi << g) | (x.lo >> (64 - g)) : (unsigned long long)x.hi;
+  const unsigned long long xl = x.lo << g;
+  const unsigned long long lo = xl + y.lo;
+  const unsigned long long hi = xh + (unsigned long long)y.hi + (lo < xl ? 1ull : 0ull);
+  return S128{(long long)hi, lo};
+}
+
+// S 2^{SE - 2150} rounded once, to nearest even, to FP64: the magnitude is
+// normalised by one 128-bit shift, its leading 53 bits rounded (round bit,
+// then the rest as sticky) and the bit pattern assembled with integer
+// instructions. Below the normal range: round_sub; above it: infinity.
+__device__ __forceinline__ double round_s128(S128 s, int SE) {
+  const bool neg = s.hi < 0;
+  unsigned long long mh = (unsigned long long)s.hi, ml = s.lo;
+  if (neg) {
+    ml = ~ml + 1ull;
+    mh = ~mh + (ml == 0ull ? 1ull : 0ull);
   }
-  const int be0 = P + SE - 2150 + 1023;      // biased exponent before rounding
+  if ((mh | ml) == 0ull) return 0.0;
+  const int lz = mh ? __clzll((long long)mh) : 64 + __clzll((long long)ml);   // >= 1: |S| < 2^127
+  unsigned long long hi, lo;
+  if (lz < 64) {
+    hi = (mh << lz) | (ml >> (64 - lz));
+    lo = ml << lz;
+  } else {
+    hi = ml << (lz - 64);
+    lo = 0ull;
+  }
+  const int be0 = 127 - lz + SE - 2150 + 1023;   // biased exponent before rounding
   if (be0 < 1) return round_sub(hi, lo, be0, neg);   // below the normal range: rare
   unsigned long long mant = hi >> 11;
   const unsigned rb = (unsigned)hi & 0x7FFu;
@@ -111,6 +132,23 @@ __device__ __forceinline__ double round_acc(const Acc& a, int SE) {
     return __longlong_as_double((long long)bits);
   }
   return neg ? -CUDART_INF : CUDART_INF;
+}
+
+// One product: S 2^{SE - 2150} rounded once.
+__device__ __forceinline__ double round_acc(const Acc& a, int SE) { return round_s128(to_s128(a), SE); }
+
+// Two products of different inputs, x 2^{SX - 2150} + y 2^{SY - 2150}: summed
+// exactly and rounded once when their scales are within 2^16 of each other
+// in every lane of the warp (the usual case: the inputs' and the rows'
+// exponents offset each other); otherwise each is rounded and the two are
+// added in FP64. The choice is made per warp so that no warp runs both paths.
+__device__ __forceinline__ double round_sum(const Acc& x, int SX, const Acc& y, int SY) {
+  const int g = SX - SY;
+  if (__all_sync(0xFFFFFFFFu, g >= -16 && g <= 16)) {
+    const bool xs = g >= 0;   // shift the operand of the larger scale
+    return round_s128(shl_add(to_s128(xs ? x : y), xs ? g : -g, to_s128(xs ? y : x)), xs ? SY : SX);
+  }
+  return round_acc(x, SX) + round_acc(y, SY);
 }
 
 // Coefficient tables (host-built, see fx_tables): per row i, two sets of W =
@@ -217,17 +255,24 @@ k_band_fx(const double* __restrict__ U, const double* __restrict__ V, const int2
         tap(a3, c1, v);   // nu M_t v
       }
     }
-    if (!valid) continue;
+    // every lane rounds (fibres past the end hold zeros; the warp votes in round_sum)
     const long long off = rot ? q + (long long)i * Q : base + (long long)i * inner;
     const int e0 = __ldg(Ce + 2 * i), e1 = __ldg(Ce + 2 * i + 1);
     if (KIND == 0) {
-      Uo[off] = round_acc(a1, Eu + e0);
-      Vo[off] = round_acc(a2, Eu + e1);
+      const double uo = round_acc(a1, Eu + e0), vo = round_acc(a2, Eu + e1);
+      if (valid) {
+        Uo[off] = uo;
+        Vo[off] = vo;
+      }
     } else if (KIND == 1) {
-      Uo[off] = round_acc(a1, Eu + e0);
-      Vo[off] = round_acc(a2, Eu + e1) + round_acc(a3, Ev + e0);
+      const double uo = round_acc(a1, Eu + e0), vo = round_sum(a2, Eu + e1, a3, Ev + e0);
+      if (valid) {
+        Uo[off] = uo;
+        Vo[off] = vo;
+      }
     } else {
-      Vo[off] = round_acc(a2, Eu + e0) + round_acc(a3, Ev + e1);
+      const double vo = round_sum(a2, Eu + e0, a3, Ev + e1);
+      if (valid) Vo[off] = vo;
     }
   }
 }
