@@ -96,42 +96,34 @@ __device__ __forceinline__ S128 shl_add(S128 x, int g, S128 y) {
   return S128{(long long)hi, lo};
 }
 
-// S 2^{SE - 2150} rounded once, to nearest even, to FP64: the magnitude is
-// normalised by one 128-bit shift, its leading 53 bits rounded (round bit,
-// then the rest as sticky) and the bit pattern assembled with integer
-// instructions. Below the normal range: round_sub; above it: infinity.
+// S 2^{SE - 2150} rounded once, to nearest even, to FP64: the top 64 bits of
+// the normalised magnitude are formed with the rest as a sticky bit, the
+// leading 53 rounded with 32-bit arithmetic on the low 11 bits, and the bit
+// pattern assembled by one addition (a rounding carry moves into the
+// exponent). Below the normal range: round_sub; above it: infinity.
 __device__ __forceinline__ double round_s128(S128 s, int SE) {
   const bool neg = s.hi < 0;
-  unsigned long long mh = (unsigned long long)s.hi, ml = s.lo;
-  if (neg) {
-    ml = ~ml + 1ull;
-    mh = ~mh + (ml == 0ull ? 1ull : 0ull);
-  }
+  const unsigned long long ml = neg ? 0ull - s.lo : s.lo;
+  const unsigned long long mh = neg ? ~(unsigned long long)s.hi + (s.lo == 0ull ? 1ull : 0ull) : (unsigned long long)s.hi;
   if ((mh | ml) == 0ull) return 0.0;
-  const int lz = mh ? __clzll((long long)mh) : 64 + __clzll((long long)ml);   // >= 1: |S| < 2^127
-  unsigned long long hi, lo;
-  if (lz < 64) {
-    hi = (mh << lz) | (ml >> (64 - lz));
-    lo = ml << lz;
+  int lz;
+  unsigned long long top, rest;
+  if (mh) {
+    lz = __clzll((long long)mh);            // >= 1: |S| < 2^127
+    top = (mh << lz) | (ml >> (64 - lz));
+    rest = ml << lz;
   } else {
-    hi = ml << (lz - 64);
-    lo = 0ull;
+    lz = 64 + __clzll((long long)ml);
+    top = ml << (lz - 64);
+    rest = 0ull;
   }
   const int be0 = 127 - lz + SE - 2150 + 1023;   // biased exponent before rounding
-  if (be0 < 1) return round_sub(hi, lo, be0, neg);   // below the normal range: rare
-  unsigned long long mant = hi >> 11;
-  const unsigned rb = (unsigned)hi & 0x7FFu;
-  const unsigned up = (rb > 0x400u) | ((rb == 0x400u) & ((lo != 0ull) | (unsigned)(mant & 1ull)));
-  mant += up;
-  const int c = (int)(mant >> 53);
-  mant >>= c;
-  const int be = be0 + c;
-  if (be <= 2046) {
-    const unsigned long long bits =
-        ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (mant & 0xFFFFFFFFFFFFFull);
-    return __longlong_as_double((long long)bits);
-  }
-  return neg ? -CUDART_INF : CUDART_INF;
+  if (be0 < 1) return round_sub(top, rest, be0, neg);          // below the normal range: rare
+  if (be0 > 2046) return neg ? -CUDART_INF : CUDART_INF;
+  const unsigned low = ((unsigned)top & 0x7FFu) | (rest != 0ull ? 1u : 0u);   // round bit at 10, sticky in 0
+  const unsigned up = (low + 0x3FFu + ((unsigned)(top >> 11) & 1u)) >> 11;     // ties to even
+  const unsigned long long bits = ((unsigned long long)(be0 - 1) << 52) + ((top >> 11) + up);
+  return __longlong_as_double((long long)(bits | ((unsigned long long)neg << 63)));
 }
 
 // One product: S 2^{SE - 2150} rounded once.
