@@ -88,8 +88,8 @@ __device__ __noinline__ double combine7_slow(long long zh, long long zl, int SE)
 // Z = sum_c T_c 256^{6-c} (exact) rounded to nearest even, times 2^SE, as FP64.
 // Z is formed exactly as zh 2^24 + zl in two 64-bit words; its magnitude
 // Mt 2^24 + mr (0 <= mr < 2^24) is normalised as a 128-bit value, the leading
-// 53 bits rounded once (round, guard and sticky bits), and the FP64 bit pattern
-// assembled with integer instructions (the FP64 pipe is not used).
+// 53 bits rounded once (round bit, then the rest as sticky), and the FP64 bit
+// pattern assembled with integer instructions (the FP64 pipe is not used).
 __device__ __forceinline__ double combine7(const float* T, int SE) {
   int I[kDig];
 #pragma unroll
@@ -108,17 +108,12 @@ __device__ __forceinline__ double combine7(const float* T, int SE) {
   const unsigned long long lo = lo64 << lz;
   const int be0 = 87 - lz + SE + 1023;                    // biased exponent before rounding
   if (be0 < 1) return round_sub(hi, lo, be0, neg);         // below the normal range: rare
-  unsigned long long mant = hi >> 11;
-  const unsigned rb = (unsigned)hi & 0x7FFu;
-  const unsigned up = (rb > 0x400u) | ((rb == 0x400u) & ((lo != 0ull) | (unsigned)(mant & 1ull)));
-  mant += up;
-  const int c = (int)(mant >> 53);
-  mant >>= c;
-  const int be = be0 + c;
-  if (be > 2046) return neg ? -CUDART_INF : CUDART_INF;
-  const unsigned long long bits =
-      ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (mant & 0xFFFFFFFFFFFFFull);
-  return __longlong_as_double((long long)bits);
+  if (be0 > 2046) return neg ? -CUDART_INF : CUDART_INF;
+  // round bit at 10, the rest as sticky in bit 0; a rounding carry moves into the exponent
+  const unsigned low = ((unsigned)hi & 0x7FFu) | (lo != 0ull ? 1u : 0u);
+  const unsigned up = (low + 0x3FFu + ((unsigned)(hi >> 11) & 1u)) >> 11;   // ties to even
+  const unsigned long long bits = ((unsigned long long)(be0 - 1) << 52) + ((hi >> 11) + up);
+  return __longlong_as_double((long long)(bits | ((unsigned long long)neg << 63)));
 }
 
 // Raw 8-byte words of tile `tile`, row r, the KC columns of part p (0 outside).
