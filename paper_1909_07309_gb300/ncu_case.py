@@ -2,7 +2,7 @@
 
   python -m paper_1909_07309_gb300.ncu_case {fd,matvec,solve} D P N_EL [REPS] [fp64|df32|fp64tc|tf32|bf16|fp64tc7|fx64]
   python -m paper_1909_07309_gb300.ncu_case {stencil,mapped_solve} D P N_EL [REPS] [fp64|df32|tf32|bf16]
-  python -m paper_1909_07309_gb300.ncu_case batch COUNT [REPS]
+  python -m paper_1909_07309_gb300.ncu_case batch COUNT [REPS] [df32|fp64]
 
 Builds the unit-cube problem (d = D, degree P, N_EL elements per direction),
 runs one warm-up and REPS applications of fd_apply, st_matvec or the
@@ -12,7 +12,8 @@ preconditioner with the integer-limb matvec (the bench headline). `stencil` and
 `mapped_solve` use the quarter-annulus problem with variable coefficients
 (stencil matvec; GMRES with the geometry-aware preconditioner). `batch` runs
 the batched solver on the first COUNT problems of the batched workload
-(256 threads x 2 CTAs per SM, no autotuning).
+(256 threads x 2 CTAs per SM, no autotuning): double-float, one step, or
+IEEE FP64 refined to 1e-8 (at most 5 steps).
 """
 import sys
 
@@ -24,14 +25,16 @@ def main(argv):
     if argv[0] == "batch":
         count = int(argv[1])
         reps = int(argv[2]) if len(argv) > 2 else 2
+        fp64 = len(argv) > 3 and argv[3] == "fp64"
         cfg = dict(inputs.BATCH)
         n_el, p, nrhs, g = inputs.batch_draws(cfg)
-        B = stfd.Batch(n_el[:count], p[:count], nrhs[:count], d=cfg["d"], autotune=False)
+        kw = dict(precision=stfd.STFD_FP64, tol=1e-8, max_it=5) if fp64 else {}
+        B = stfd.Batch(n_el[:count], p[:count], nrhs[:count], d=cfg["d"], autotune=False, **kw)
         f = torch.from_numpy(g.standard_normal(B.total)).cuda()
         for _ in range(1 + reps):
             B.solve(f)
         torch.cuda.synchronize()
-        print("ncu_case batch count=%d dofs=%d reps=%d ok" % (count, B.total, reps))
+        print("ncu_case batch count=%d dofs=%d reps=%d %s ok" % (count, B.total, reps, "fp64" if fp64 else "df32"))
         return
     what, d, p, n_el = argv[0], int(argv[1]), int(argv[2]), int(argv[3])
     reps = int(argv[4]) if len(argv) > 4 else 2
