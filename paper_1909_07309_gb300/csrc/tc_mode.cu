@@ -52,8 +52,14 @@ __host__ __device__ inline size_t canon_off(int r, int k, int kcores, int esz) {
   return (size_t)(r >> 3) * (kcores * 128) + (size_t)(k / epc) * 128 + (r & 7) * 16 + (k % epc) * esz;
 }
 
-// Odd row stride (in floats) of the output stage: conflict-free column writes.
+// Row stride (in floats) reserved for the output stage; the contiguous mode
+// stores its rows at stride n (the block as it lies in memory).
 __host__ __device__ inline int stage_stride(int n) { return n | 1; }
+
+template <typename TOut>
+__device__ __forceinline__ TOut out_of(float v) {
+  return (TOut)v;
+}
 
 struct TcArgs {
   const void* X;
@@ -232,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mode(TcArgs args) {
   const long long inner = args.inner, Q = args.Q;
   const TIn* X = static_cast<const TIn*>(args.X);
   TOut* Y = static_cast<TOut*>(args.Y);
-  const int ss = stage_stride(n);
+  const int ss = n;   // output stage rows: the tile's block as it lies in memory
   const size_t in_bytes = STAGED ? (((size_t)kTile * n * sizeof(TIn) + 15) & ~(size_t)15) : 0;   // per stage
   const size_t out_bytes = OSTAGE ? (((size_t)kTile * ss * sizeof(float) + 15) & ~(size_t)15) : 0;
   unsigned char* sB = smem;
@@ -438,41 +444,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mode(TcArgs args) {
         const int rows = (int)min((long long)kTile, Q - q0);
         TOut* dst = Y + q0 * n;
         if (args.vec) {
-          // 16-byte stores of the contiguous block: chunk c holds entries c epo .. c epo + epo - 1
+          // 16-byte stores of the contiguous block, read from the stage as it
+          // will lie in memory (16-byte shared loads: no bank conflicts)
           constexpr int epo = 16 / sizeof(TOut);
           const int cnt = rows * n;
           const int nch = (int)((cnt * sizeof(TOut)) >> 4);
-          const int step = kWorkers * epo, sr = step / n, sa = step - sr * n;
-          int cr = t * epo / n, ca = t * epo - cr * n;
           for (int c = t; c < nch; c += kWorkers) {
-            union {
-              uint4 u;
-              TOut v[epo];
-            } w;
-            int rr = cr, aa = ca;
-#pragma unroll
-            for (int j = 0; j < epo; ++j) {
-              w.v[j] = (TOut)stage[rr * ss + aa];
-              if (++aa == n) {
-                aa = 0;
-                ++rr;
-              }
-            }
-            *reinterpret_cast<uint4*>(dst + (size_t)c * epo) = w.u;
-            cr += sr;
-            ca += sa;
-            if (ca >= n) {
-              ca -= n;
-              ++cr;
+            if constexpr (sizeof(TOut) == 4) {
+              *reinterpret_cast<uint4*>(dst + (size_t)c * epo) = *reinterpret_cast<const uint4*>(stage + 4 * c);
+            } else {
+              const float2 v = *reinterpret_cast<const float2*>(stage + 2 * c);
+              union {
+                uint4 u;
+                TOut w[2];
+              } o;
+              o.w[0] = out_of<TOut>(v.x);
+              o.w[1] = out_of<TOut>(v.y);
+              *reinterpret_cast<uint4*>(dst + (size_t)c * epo) = o.u;
             }
           }
           const int e = nch * epo + t;
-          if (e < cnt) dst[e] = (TOut)stage[(e / n) * ss + e % n];
+          if (e < cnt) dst[e] = out_of<TOut>(stage[e]);
         } else {
-          for (int rr = warp; rr < rows; rr += kWorkers / 32) {
-            const float* src = stage + rr * ss;
-            for (int k = lane; k < n; k += 32) dst[(size_t)rr * n + k] = (TOut)src[k];
-          }
+          for (int e = t; e < rows * n; e += kWorkers) dst[e] = out_of<TOut>(stage[e]);
         }
         workers_sync();   // the stage is rewritten by the next epilogue
       } else if (!ok) {
