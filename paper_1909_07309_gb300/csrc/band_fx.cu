@@ -62,72 +62,14 @@ __device__ __forceinline__ int2 to_limbs(unsigned long long u, int E) {
 // acc += C U for 27-bit limbs (one tap), three 64-bit products (Karatsuba):
 // hh += C_h U_h, ll += C_l U_l, mm += (C_h + C_l)(U_h + U_l); the cross term
 // C_h U_l + C_l U_h = mm - hh - ll is recovered once per output. All sums are
-// exact: |C_h + C_l|, |U_h + U_l| < 2^28, at most 2p + 1 <= 9 taps.
-struct Acc {
-  long long hh, mm, ll;
-};
+// exact: |C_h + C_l|, |U_h + U_l| < 2^28, at most 2p + 1 <= 9 taps. The
+// accumulator and its rounding to FP64 (to_s128, round_s128) are in
+// fp64_round.cuh.
 __device__ __forceinline__ void tap(Acc& a, int2 c, int2 u) {
   a.hh += (long long)c.x * u.x;
   a.ll += (long long)c.y * u.y;
   a.mm += (long long)(c.x + c.y) * (u.x + u.y);
 }
-
-// The exact sum S = hh 2^54 + (mm - hh - ll) 2^27 + ll of an accumulator as a
-// signed 128-bit integer (hi: high word, two's complement; |S| < 2^110).
-struct S128 {
-  long long hi;
-  unsigned long long lo;
-};
-__device__ __forceinline__ S128 to_s128(const Acc& a) {
-  const long long hl = a.mm - a.hh - a.ll;
-  const long long t1 = hl + (a.ll >> 27);
-  const unsigned long long r0 = (unsigned long long)a.ll & ((1ull << 27) - 1);
-  const long long t2 = a.hh + (t1 >> 27);
-  const unsigned long long R = ((unsigned long long)(t1 & ((1ll << 27) - 1)) << 27) | r0;   // S = t2 2^54 + R
-  return S128{t2 >> 10, ((unsigned long long)t2 << 54) | R};
-}
-
-// x 2^g + y for 0 <= g <= 16 (no overflow: |x 2^g| < 2^126).
-__device__ __forceinline__ S128 shl_add(S128 x, int g, S128 y) {
-  const unsigned long long xh = g ? ((unsigned long long)x.hi << g) | (x.lo >> (64 - g)) : (unsigned long long)x.hi;
-  const unsigned long long xl = x.lo << g;
-  const unsigned long long lo = xl + y.lo;
-  const unsigned long long hi = xh + (unsigned long long)y.hi + (lo < xl ? 1ull : 0ull);
-  return S128{(long long)hi, lo};
-}
-
-// S 2^{SE - 2150} rounded once, to nearest even, to FP64: the top 64 bits of
-// the normalised magnitude are formed with the rest as a sticky bit, the
-// leading 53 rounded with 32-bit arithmetic on the low 11 bits, and the bit
-// pattern assembled by one addition (a rounding carry moves into the
-// exponent). Below the normal range: round_sub; above it: infinity.
-__device__ __forceinline__ double round_s128(S128 s, int SE) {
-  const bool neg = s.hi < 0;
-  const unsigned long long ml = neg ? 0ull - s.lo : s.lo;
-  const unsigned long long mh = neg ? ~(unsigned long long)s.hi + (s.lo == 0ull ? 1ull : 0ull) : (unsigned long long)s.hi;
-  if ((mh | ml) == 0ull) return 0.0;
-  int lz;
-  unsigned long long top, rest;
-  if (mh) {
-    lz = __clzll((long long)mh);            // >= 1: |S| < 2^127
-    top = (mh << lz) | (ml >> (64 - lz));
-    rest = ml << lz;
-  } else {
-    lz = 64 + __clzll((long long)ml);
-    top = ml << (lz - 64);
-    rest = 0ull;
-  }
-  const int be0 = 127 - lz + SE - 2150 + 1023;   // biased exponent before rounding
-  if (be0 < 1) return round_sub(top, rest, be0, neg);          // below the normal range: rare
-  if (be0 > 2046) return neg ? -CUDART_INF : CUDART_INF;
-  const unsigned low = ((unsigned)top & 0x7FFu) | (rest != 0ull ? 1u : 0u);   // round bit at 10, sticky in 0
-  const unsigned up = (low + 0x3FFu + ((unsigned)(top >> 11) & 1u)) >> 11;     // ties to even
-  const unsigned long long bits = ((unsigned long long)(be0 - 1) << 52) + ((top >> 11) + up);
-  return __longlong_as_double((long long)(bits | ((unsigned long long)neg << 63)));
-}
-
-// One product: S 2^{SE - 2150} rounded once.
-__device__ __forceinline__ double round_acc(const Acc& a, int SE) { return round_s128(to_s128(a), SE); }
 
 // Two products of different inputs, x 2^{SX - 2150} + y 2^{SY - 2150}: summed
 // exactly and rounded once when their scales are within 2^16 of each other
@@ -136,10 +78,7 @@ __device__ __forceinline__ double round_acc(const Acc& a, int SE) { return round
 // added in FP64. The choice is made per warp so that no warp runs both paths.
 __device__ __forceinline__ double round_sum(const Acc& x, int SX, const Acc& y, int SY) {
   const int g = SX - SY;
-  if (__all_sync(0xFFFFFFFFu, g >= -16 && g <= 16)) {
-    const bool xs = g >= 0;   // shift the operand of the larger scale
-    return round_s128(shl_add(to_s128(xs ? x : y), xs ? g : -g, to_s128(xs ? y : x)), xs ? SY : SX);
-  }
+  if (__all_sync(0xFFFFFFFFu, g >= -16 && g <= 16)) return round_pair_exact(x, SX, y, SY);
   return round_acc(x, SX) + round_acc(y, SY);
 }
 

@@ -78,42 +78,14 @@ __device__ __forceinline__ int bexp(long long w) {
   return max(1, (int)(((unsigned long long)w >> 52) & 0x7FF));
 }
 
-// Rare case of combine7: |Z| below 2^24 (then zh 2^24 + zl is exact in FP64
-// and scalbn rounds once).
-__device__ __noinline__ double combine7_slow(long long zh, long long zl, int SE) {
-  const double hi = (double)zh * 16777216.0, lo = (double)zl;
-  return scalbn(hi + lo, SE);
-}
-
-// Z = sum_c T_c 256^{6-c} (exact) rounded to nearest even, times 2^SE, as FP64.
-// Z is formed exactly as zh 2^24 + zl in two 64-bit words; its magnitude
-// Mt 2^24 + mr (0 <= mr < 2^24) is normalised as a 128-bit value, the leading
-// 53 bits rounded once (round bit, then the rest as sticky), and the FP64 bit
-// pattern assembled with integer instructions (the FP64 pipe is not used).
+// Z = sum_c T_c 256^{6-c} (exact) rounded to nearest even, times 2^SE, as FP64:
+// the seven FP32 sums are integers below 2^24, converted exactly, then
+// combined and rounded once by combine7_int (fp64_round.cuh).
 __device__ __forceinline__ double combine7(const float* T, int SE) {
   int I[kDig];
 #pragma unroll
   for (int c = 0; c < kDig; ++c) I[c] = __float2int_rn(T[c]);   // exact: integers below 2^24
-  const long long zh = (long long)I[0] * 16777216ll + (long long)I[1] * 65536ll + (long long)I[2] * 256ll + I[3];
-  const long long zl = (long long)I[4] * 65536ll + (long long)I[5] * 256ll + I[6];
-  const long long Zt = zh + (zl >> 24);                     // Z = Zt 2^24 + zr, 0 <= zr < 2^24
-  const unsigned zr = (unsigned)zl & 0xFFFFFFu;
-  const bool neg = Zt < 0;
-  const unsigned long long Mt = neg ? (unsigned long long)(~Zt) + (zr == 0u) : (unsigned long long)Zt;
-  const unsigned mr = neg ? ((0x1000000u - zr) & 0xFFFFFFu) : zr;
-  if (Mt == 0ull) return combine7_slow(zh, zl, SE);
-  const int lz = __clzll((long long)Mt);                   // 13 .. 63
-  const unsigned long long lo64 = (unsigned long long)mr << 40;
-  const unsigned long long hi = (Mt << lz) | (lo64 >> (64 - lz));
-  const unsigned long long lo = lo64 << lz;
-  const int be0 = 87 - lz + SE + 1023;                    // biased exponent before rounding
-  if (be0 < 1) return round_sub(hi, lo, be0, neg);         // below the normal range: rare
-  if (be0 > 2046) return neg ? -CUDART_INF : CUDART_INF;
-  // round bit at 10, the rest as sticky in bit 0; a rounding carry moves into the exponent
-  const unsigned low = ((unsigned)hi & 0x7FFu) | (lo != 0ull ? 1u : 0u);
-  const unsigned up = (low + 0x3FFu + ((unsigned)(hi >> 11) & 1u)) >> 11;   // ties to even
-  const unsigned long long bits = ((unsigned long long)(be0 - 1) << 52) + ((hi >> 11) + up);
-  return __longlong_as_double((long long)(bits | ((unsigned long long)neg << 63)));
+  return combine7_int(I, SE);
 }
 
 // Raw 8-byte words of tile `tile`, row r, the KC columns of part p (0 outside).
