@@ -304,8 +304,10 @@ def cuda_time(fn, reps, stream):
 def mapped_section(args, stream):
     """Mixed-precision workload on the mapped domain: the FP64 vs TF32 / BF16
     geometry-aware preconditioner inside FP64 flexible GMRES whose system matvec
-    is IEEE FP64 (and the plain parametric preconditioner for the iteration
-    count); the same preconditioners with the double-float stencil matvec beside."""
+    is FP64 -- the integer-limb stencil (exact row sums rounded once) first, the
+    IEEE-FP64 stencil beside it with the FP64 and BF16 preconditioners -- and the
+    same preconditioners with the double-float (~48-bit) stencil matvec (and the
+    plain parametric preconditioner for the iteration count)."""
     import torch
     from paper_1909_07309_gb300 import stfd
     cfg = dict(inputs.MAPPED)
@@ -329,14 +331,23 @@ def mapped_section(args, stream):
     out = {"workload": cfg["name"], "N": N, "host_setup_s": host_setup_s, "steps": steps}
     K, M, Wt, Mt = stfd.heat_problem(d, p, n_el, T=cfg["T"])
     y = torch.empty_like(f)
-    for mv_name, arith in (("fp64", stfd.STFD_OP_FP64), ("df32", stfd.STFD_OP_DF32)):
+    mv_desc = {"fx64": "stencil, FP64 (time pass IEEE FP64; spatial row sums exact in integer limbs, "
+                       "rounded once)",
+               "fp64": "stencil, IEEE FP64", "df32": "stencil, double-float (~48-bit)"}
+    for mv_name, arith in (("fx64", stfd.STFD_OP_FX64), ("fp64", stfd.STFD_OP_FP64), ("df32", stfd.STFD_OP_DF32)):
         A = stfd.StencilOp(n, p, prob["Ms"], prob["Ks"], prob["Wt"], prob["Mt"], cfg["gamma"], cfg["nu"], arith=arith)
         mv_ms, _ = cuda_time(lambda: A.matvec(f, y), 3, stream)
-        sec = {"matvec": "stencil, " + ("IEEE FP64" if arith == stfd.STFD_OP_FP64 else "double-float (~48-bit)"),
-               "st_matvec_ms": mv_ms, "variants": {}}
+        sec = {"matvec": mv_desc[mv_name], "st_matvec_ms": mv_ms, "variants": {}}
+        if mv_name == "fx64":
+            y_fx = y.clone()
+        elif mv_name == "fp64":   # the two FP64 matvecs on the same input
+            sec["fx64_matvec_rel_diff"] = float(torch.linalg.norm(y_fx - y) / torch.linalg.norm(y))
+            del y_fx
         s_ref = None
         plist = [("fp64_ieee", stfd.STFD_FP64, True), ("fp64_accurate_df32", stfd.STFD_DF32, True),
                  ("tf32", stfd.STFD_TF32, True), ("bf16", stfd.STFD_BF16, True)]
+        if mv_name == "fp64":   # the slowest matvec: the two ends of the comparison only
+            plist = [plist[0], plist[3]]
         if mv_name == "df32":
             plist.append(("plain_fp64_accurate_df32", stfd.STFD_DF32, False))
         for name, prec, geo in plist:
@@ -362,7 +373,7 @@ def mapped_section(args, stream):
             v["speedup_vs_fp64_ieee_precond"] = ieee / v["gmres_ms"]
         A.close()
         torch.cuda.empty_cache()
-        out["fp64_matvec" if mv_name == "fp64" else "df32_matvec"] = sec
+        out[mv_name + "_matvec"] = sec
     return out
 
 

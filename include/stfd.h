@@ -355,10 +355,21 @@ int stfd_spline_matrices_weighted(int p, int n_el, double length, int bc, const 
  * stencil layout with half-bandwidth p_s ((2p_s+1)^d * N_s doubles each),
  * n[0..d-1] = n_s per direction, n[d] = n_t, Wt and Mt the column-major time
  * factors. arith as stfd_op_create_kron (STFD_OP_DF32 keeps the coefficients
- * and intermediates as double-float pairs). The op works with
+ * and intermediates as double-float pairs). STFD_OP_FX64: the time pass in
+ * IEEE FP64, then every output of the spatial pass formed exactly in 64-bit
+ * integers and rounded once to FP64 (each coefficient row written as 53-bit
+ * integers under its largest entry's power of two, once, at creation; the
+ * entries of each time slice that a block of 256 rows reads written under
+ * their largest entry's power of two, so entries far below it are rounded at
+ * 2^-53 of it; balanced 27-bit limbs, 3 integer multiply-adds per tap; the
+ * mass and stiffness parts summed exactly and rounded once when their scales
+ * are within 2^10, else added in FP64); needs (2p_s+1)^d <= 729, otherwise
+ * the op uses IEEE FP64. A non-finite coefficient or input value gives NaN
+ * where it is read. The op works with
  * stfd_st_matvec, stfd_st_matvec_transpose (A^T: M_s and K_s are symmetric)
- * and stfd_gmres_solve. Device memory: the two coefficient arrays and two
- * N-vectors of scratch. */
+ * and stfd_gmres_solve. Device memory: the two coefficient arrays (8 bytes
+ * per entry in every arithmetic), two N-vectors of scratch and, for
+ * STFD_OP_FX64, 2 N_s row exponents. */
 int stfd_op_create_stencil(stfd_op** out, int d, const int* n, int p_s, const double* Ms, const double* Ks,
                            const double* Wt, const double* Mt, double gamma, double nu, int arith, void* stream);
 

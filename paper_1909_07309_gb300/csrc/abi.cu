@@ -927,7 +927,7 @@ extern "C" int stfd_op_create_stencil(stfd_op** out, int d, const int* n, int p_
   *out = nullptr;
   if (!sizes_ok(d, n) || !Ms || !Ks || !Wt || !Mt || p_s < 0 || p_s > 10) return STFD_ERR_ARG;
   if (!std::isfinite(gamma) || !std::isfinite(nu)) return STFD_ERR_ARG;
-  if (arith != STFD_OP_FP64 && arith != STFD_OP_DF32) return STFD_ERR_ARG;
+  if (arith != STFD_OP_FP64 && arith != STFD_OP_DF32 && arith != STFD_OP_FX64) return STFD_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   stfd_op* A = new (std::nothrow) stfd_op;
   if (!A) return STFD_ERR_ALLOC;
@@ -953,6 +953,8 @@ extern "C" int stfd_op_create_stencil(stfd_op** out, int d, const int* n, int p_
   for (int l = 0; l < d; ++l) o.n[l] = n[l];
   o.Ns = Ns;
   o.df = arith == STFD_OP_DF32;
+  // integer limbs when the row sums stay exact (at most stencil_fx_max_taps() offsets), else FP64
+  o.fx = arith == STFD_OP_FX64 && S <= stencil_fx_max_taps();
   std::vector<double> Wb = band_rows(nt, Wt, pt, gamma, false), WbT = band_rows(nt, Wt, pt, gamma, true),
                       Mb = band_rows(nt, Mt, pt, nu, false), MbU = band_rows(nt, Mt, pt, 1.0, false);
   int rc = dev_upload(&A->MtbU, MbU.data(), MbU.size(), st);
@@ -983,6 +985,16 @@ extern "C" int stfd_op_create_stencil(stfd_op** out, int d, const int* n, int p_
   if (rc == STFD_OK && o.df) {
     rc = dev_upload<double>(&A->tmp5, nullptr, (size_t)A->N, st);
     if (rc == STFD_OK) rc = dev_upload<int>(&A->bexp, nullptr, 1, st);
+  }
+  if (rc == STFD_OK && o.fx) {   // row frames, and the coefficients as limbs in place
+    for (int k = 0; k < 2 && rc == STFD_OK; ++k) {
+      rc = dev_upload<int>(&A->FXE[k], nullptr, (size_t)Ns, st);
+      if (rc == STFD_OK && launch_stencil_fx_table(static_cast<double*>(A->sbuf[k]), A->FXE[k], S, Ns, st) !=
+                               cudaSuccess)
+        rc = STFD_ERR_CUDA;
+    }
+    o.Em = A->FXE[0];
+    o.Ek = A->FXE[1];
   }
   if (rc == STFD_OK) {
     o.Ms = A->sbuf[0];

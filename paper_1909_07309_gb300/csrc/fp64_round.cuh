@@ -77,13 +77,16 @@ struct Acc {
   long long hh, mm, ll;
 };
 
-// S as a signed 128-bit integer (hi: high word, two's complement; |S| < 2^110).
+// S as a signed 128-bit integer (hi: high word, two's complement; |S| < 2^126).
 struct S128 {
   long long hi;
   unsigned long long lo;
 };
+// The cross term mm - hh - ll is formed modulo 2^64: exact whenever it fits in
+// 64 bits, even if mm itself was accumulated with wrap-around.
 __host__ __device__ __forceinline__ S128 to_s128(const Acc& a) {
-  const long long hl = a.mm - a.hh - a.ll;
+  const long long hl =
+      (long long)((unsigned long long)a.mm - (unsigned long long)a.hh - (unsigned long long)a.ll);
   const long long t1 = hl + (a.ll >> 27);
   const unsigned long long r0 = (unsigned long long)a.ll & ((1ull << 27) - 1);
   const long long t2 = a.hh + (t1 >> 27);
@@ -91,7 +94,7 @@ __host__ __device__ __forceinline__ S128 to_s128(const Acc& a) {
   return S128{t2 >> 10, ((unsigned long long)t2 << 54) | R};
 }
 
-// x 2^g + y for 0 <= g <= 16 (no overflow: |x 2^g| < 2^126).
+// x 2^g + y for 0 <= g <= 16 (no overflow when |x 2^g| + |y| < 2^127).
 __host__ __device__ __forceinline__ S128 shl_add(S128 x, int g, S128 y) {
   const unsigned long long xh = g ? ((unsigned long long)x.hi << g) | (x.lo >> (64 - g)) : (unsigned long long)x.hi;
   const unsigned long long xl = x.lo << g;
@@ -124,13 +127,52 @@ __host__ __device__ __forceinline__ double round_s128(S128 s, int SE) {
 // One product: S 2^{SE - 2150} rounded once.
 __host__ __device__ __forceinline__ double round_acc(const Acc& a, int SE) { return round_s128(to_s128(a), SE); }
 
-// Two products x 2^{SX - 2150} + y 2^{SY - 2150} summed exactly (their
-// scales within 2^16 of each other) and rounded once.
+// Two products x 2^{SX - 2150} + y 2^{SY - 2150} summed exactly and rounded
+// once; the caller keeps |SX - SY| small enough for shl_add (2^16 for sums
+// below 2^110, 2^10 for sums below 2^116).
 __host__ __device__ __forceinline__ double round_pair_exact(const Acc& x, int SX, const Acc& y, int SY) {
   const int g = SX - SY;
   const bool xs = g >= 0;   // shift the operand of the larger scale
-  return round_s128(shl_add(to_s128(xs ? x : y), xs ? g : -g, to_s128(xs ? y : x)), xs ? SY : SX);
+  const S128 sx = to_s128(x), sy = to_s128(y);
+  const S128 big{xs ? sx.hi : sy.hi, xs ? sx.lo : sy.lo}, small{xs ? sy.hi : sx.hi, xs ? sy.lo : sx.lo};
+  return round_s128(shl_add(big, xs ? g : -g, small), xs ? SY : SX);
 }
+
+// ---- integer-limb stencil row sums (up to 729 taps)
+// Balanced 27-bit limbs of a signed integer |U| < 2^53: U = h 2^27 + l with
+// l in [-2^26, 2^26), |h| <= 2^26.
+__host__ __device__ __forceinline__ int2 split_balanced(long long U) {
+  const long long lo = ((U + (1ll << 26)) & ((1ll << 27) - 1)) - (1ll << 26);
+  return make_int2((int)((U - lo) >> 27), (int)lo);
+}
+
+// The balanced limbs of U = round(m 2^{max(e,1) - E}) (halves away from zero)
+// for an FP64 bit pattern u, m its 53-bit significand, under a frame
+// E >= max(1, e): |U| < 2^53.
+__host__ __device__ __forceinline__ int2 balanced_limbs(unsigned long long u, int E) {
+  const int e = (int)((u >> 52) & 0x7FF);
+  const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(e != 0) << 52);
+  int s = E - (e > 1 ? e : 1);
+  s = s < 63 ? s : 63;
+  const unsigned long long mag = (m + ((1ull << s) >> 1)) >> s;
+  return split_balanced((u >> 63) ? -(long long)mag : (long long)mag);
+}
+
+// sum_o C_o U_o of balanced limbs in three words: hh = sum C_h U_h and
+// ll = sum C_l U_l (each term at most 2^52 in magnitude), mm = sum (C_h + C_l)
+// (U_h + U_l) modulo 2^64. For up to 729 taps the cross term mm - hh - ll =
+// sum (C_h U_l + C_l U_h) is below 729 2^53 < 2^63 in magnitude, so to_s128
+// recovers S exactly from the wrapped mm.
+struct AccW {
+  long long hh, ll;
+  unsigned long long mm;
+};
+__host__ __device__ __forceinline__ void tapw(AccW& a, int2 c, int cs, int2 u) {
+  a.hh += (long long)c.x * u.x;
+  a.ll += (long long)c.y * u.y;
+  a.mm += (unsigned long long)((long long)cs * (u.x + u.y));
+}
+__host__ __device__ __forceinline__ Acc as_acc(const AccW& a) { return Acc{a.hh, (long long)a.mm, a.ll}; }
 
 // ---- seven-digit mode products
 // Rare case of combine7: |Z| below 2^24 (then zh 2^24 + zl is exact in FP64

@@ -166,8 +166,26 @@ struct StencilOpDev {
   const void* Mtb = nullptr;          // nu M_t
   void* Z1 = nullptr;                 // scratch nt * Ns
   void* Z2 = nullptr;
+  // STFD_OP_FX64: Ms, Ks hold balanced 27-bit limbs (int2) of each row's
+  // 53-bit integers under the row frames Em, Ek (largest biased exponent)
+  bool fx = false;
+  const int* Em = nullptr;
+  const int* Ek = nullptr;
+};
+struct StencilDims {
+  int d, p;
+  int n1, n2;          // n_s per direction (n2 = 1 when d = 1; n3 implied)
+  long long Ns;
+  int nt;
 };
 cudaError_t launch_stencil_matvec(const StencilOpDev& op, const double* x, double* y, int trans, cudaStream_t st);
+// STFD_OP_FX64 stencil (stencil_fx.cu): the coefficient rows of one matrix
+// ([S][Ns] FP64, S <= stencil_fx_max_taps()) converted in place to limbs, with
+// their frames E[Ns]; the spatial pass y_t = M_s Z1_t + K_s Z2_t.
+int stencil_fx_max_taps();
+cudaError_t launch_stencil_fx_table(double* C, int* E, int S, long long Ns, cudaStream_t st);
+cudaError_t launch_stencil_space_fx(const StencilOpDev& op, const double* Z1, const double* Z2, double* y,
+                                    const StencilDims& g, cudaStream_t st);
 size_t grad_elements_smem(int d, int p);
 cudaError_t launch_grad_elements(const double* Ke, const double* lam, const double* ubar, double* g, int d, int p,
                                  int n_el, int n_s, long long Ns, int nt, double nu, cudaStream_t st);

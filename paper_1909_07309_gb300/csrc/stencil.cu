@@ -50,13 +50,6 @@ struct Num<float2> {
   __device__ static double out(acc a) { return dfa::to_double(dfa::norm(a)); }
 };
 
-struct StencilDims {
-  int d, p;
-  int n1, n2;          // n_s per direction (n2 = 1 when d = 1; n3 implied)
-  long long Ns;
-  int nt;
-};
-
 // Pass 2. Block b handles time chunk b % n_chunks of row block b / n_chunks.
 // PP > 0 fixes the half-bandwidth p at compile time (unrolled offsets,
 // immediate shared-memory offsets); PP = 0 reads it from g.
@@ -297,6 +290,9 @@ cudaError_t stencil_matvec(const StencilOpDev& op, const double* x, double* y, i
   g.n2 = op.d >= 2 ? op.n[1] : 1;
   g.Ns = Ns;
   g.nt = nt;
+  if constexpr (std::is_same<T, double>::value) {
+    if (op.fx) return launch_stencil_space_fx(op, Z1, Z2, y, g, st);
+  }
   int S = 1;
   for (int l = 0; l < op.d; ++l) S *= 2 * op.p + 1;
   ProfScope ps("stencil_space", 4.0 * S * (double)Ns * nt,

@@ -1,7 +1,7 @@
 """Small fixed workloads for Nsight Compute captures of one kernel family.
 
   python -m paper_1909_07309_gb300.ncu_case {fd,matvec,solve} D P N_EL [REPS] [fp64|df32|fp64tc|tf32|bf16|fp64tc7|fx64]
-  python -m paper_1909_07309_gb300.ncu_case {stencil,mapped_solve} D P N_EL [REPS] [fp64|df32|tf32|bf16]
+  python -m paper_1909_07309_gb300.ncu_case {stencil,mapped_solve} D P N_EL [REPS] [fp64|df32|tf32|bf16|fx64]
   python -m paper_1909_07309_gb300.ncu_case batch COUNT [REPS] [df32|fp64]
 
 Builds the unit-cube problem (d = D, degree P, N_EL elements per direction),
@@ -10,7 +10,8 @@ preconditioned GMRES solve, synchronises and exits. `fp64tc7` is the
 seven-digit tensor-core preconditioner with the FP64 matvec, `fx64` the same
 preconditioner with the integer-limb matvec (the bench headline). `stencil` and
 `mapped_solve` use the quarter-annulus problem with variable coefficients
-(stencil matvec; GMRES with the geometry-aware preconditioner). `batch` runs
+(stencil matvec; GMRES with the geometry-aware preconditioner; `fx64` there is
+the integer-limb stencil matvec with the IEEE-FP64 preconditioner). `batch` runs
 the batched solver on the first COUNT problems of the batched workload
 (256 threads x 2 CTAs per SM, no autotuning): double-float, one step, or
 IEEE FP64 refined to 1e-8 (at most 5 steps).
@@ -47,8 +48,9 @@ def main(argv):
         prob = stfd.mapped_problem(d, p, n_el, stfd.STFD_GEOM_QUARTER_ANNULUS, c=inputs.c_bilinear,
                                    kappa=inputs.kappa_trig)
         A = stfd.StencilOp(prob["n"], p, prob["Ms"], prob["Ks"], prob["Wt"], prob["Mt"],
-                           arith=stfd.STFD_OP_FP64 if arith == "fp64" else stfd.STFD_OP_DF32)
-        P = stfd.geometry_preconditioner(prob, precision=stfd.STFD_DF32 if prec == stfd.STFD_FP64TC else prec)
+                           arith={"fp64": stfd.STFD_OP_FP64, "fx64": stfd.STFD_OP_FX64}.get(arith, stfd.STFD_OP_DF32))
+        gp = {stfd.STFD_FP64TC: stfd.STFD_DF32, stfd.STFD_FP64TC7: stfd.STFD_FP64}.get(prec, prec)
+        P = stfd.geometry_preconditioner(prob, precision=gp)
         r = torch.from_numpy(inputs.standard_normal(A.N, 1)).cuda()
         out = torch.empty_like(r)
         for _ in range(1 + reps):

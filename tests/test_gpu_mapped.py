@@ -50,7 +50,7 @@ MV_CASES = [(2, 3, 12, 1.0, 1.0, 2), (2, 2, 9, 0.7, 1.6, 1), (3, 2, 5, 1.0, 1.0,
             (2, 1, 10, 1.0, 1.0, 1)]
 
 
-@pytest.mark.parametrize("arith", [stfd.STFD_OP_FP64, stfd.STFD_OP_DF32])
+@pytest.mark.parametrize("arith", [stfd.STFD_OP_FP64, stfd.STFD_OP_DF32, stfd.STFD_OP_FX64])
 @pytest.mark.parametrize("d,p,n_el,gamma,nu,nrhs", MV_CASES)
 def test_stencil_matvec_and_transpose_match_oracle(d, p, n_el, gamma, nu, nrhs, arith):
     prob = stfd.mapped_problem(d, p, n_el, QA, c=c_lib, kappa=kappa_lib)
@@ -65,8 +65,10 @@ def test_stencil_matvec_and_transpose_match_oracle(d, p, n_el, gamma, nu, nrhs, 
     # not |y| (the two terms cancel in part)
     absA = mapped.space_time(abs(Ms), abs(Ks), np.abs(Wt), np.abs(Mt), gamma, nu)
     # FP64: 1e-13; double-float (2^-48 per operation) summed over up to 2 (2p+1)^d
-    # = 1458 terms per entry: 1e-12 (a random-walk estimate is sqrt(1458) 2^-48 = 1.4e-13)
-    tol = 1e-13 if arith == stfd.STFD_OP_FP64 else 1e-12
+    # = 1458 terms per entry: 1e-12 (a random-walk estimate is sqrt(1458) 2^-48 = 1.4e-13);
+    # integer limbs (FP64 time pass, then exact row sums of entries rounded at 2^-53
+    # of their row's and neighbourhood's largest entry, one rounding): 1e-13
+    tol = 1e-12 if arith == stfd.STFD_OP_DF32 else 1e-13
     for k in range(nrhs):
         ref, reft = Ao @ x[k], Ao.T @ x[k]
         bound, boundt = absA @ np.abs(x[k]), absA.T @ np.abs(x[k])
@@ -228,8 +230,9 @@ def test_iterations_revolved_quarter_annulus_vs_table(n_el, p):
 def test_mapped_workload_full_size_sampled_rows():
     """The mixed-precision workload at full size (quarter annulus extruded, d = 3,
     p = 4, 96 elements, N = 93,178,008), in the arithmetic bench.py times:
-    (1) sampled rows of the double-float stencil matvec against rows the oracle
-    assembles one by one (rounding bound 1e-12 of the absolute-value sum);
+    (1) sampled rows of the double-float and integer-limb stencil matvecs
+    against rows the oracle assembles one by one (1e-12 and 1e-13 of the
+    absolute-value sum);
     (2) sampled rows of A~ (A~^{-1} r) = r for the FP64-accurate preconditioner
     on the weighted factors, with the oracle's own separation and univariate
     matrices (1e-10 of max |r|, as the unit-cube full-size check)."""
@@ -240,11 +243,14 @@ def test_mapped_workload_full_size_sampled_rows():
     ns, nt = n[0], n[-1]
     Ns = ns ** d
     N = Ns * nt
-    A = stfd.StencilOp(n, p, prob["Ms"], prob["Ks"], prob["Wt"], prob["Mt"], arith=stfd.STFD_OP_DF32)
     x = inputs.standard_normal(N, 61)
-    y = host(A.matvec(dev(x)))
-    A.close()
-    torch.cuda.empty_cache()
+    tols = {stfd.STFD_OP_DF32: 1e-12, stfd.STFD_OP_FX64: 1e-13}
+    ys = {}
+    for arith in tols:
+        A = stfd.StencilOp(n, p, prob["Ms"], prob["Ks"], prob["Wt"], prob["Mt"], arith=arith)
+        ys[arith] = host(A.matvec(dev(x)))
+        A.close()
+        torch.cuda.empty_cache()
     g = np.random.default_rng(62)
     samples = [(int(g.integers(Ns)), int(g.integers(nt))) for _ in range(24)]
     rows = mapped.spatial_rows(d, p, n_el, sorted({i for i, _ in samples}), "quarter_annulus", c=c_or, kappa=kappa_or)
@@ -257,8 +263,9 @@ def test_mapped_workload_full_size_sampled_rows():
             xs = X[tau, cols]
             val += Wt[t, tau] * (mv @ xs) + Mt[t, tau] * (kv @ xs)
             bound += abs(Wt[t, tau]) * (np.abs(mv) @ np.abs(xs)) + abs(Mt[t, tau]) * (np.abs(kv) @ np.abs(xs))
-        assert abs(y[i + Ns * t] - val) <= 1e-12 * bound, (i, t)
-    del y
+        for arith, tol in tols.items():
+            assert abs(ys[arith][i + Ns * t] - val) <= tol * bound, (arith, i, t)
+    del ys
     P = stfd.geometry_preconditioner(prob, precision=stfd.STFD_DF32, scaled=False)
     r = inputs.standard_normal(N, 63)
     s = host(P.apply(dev(r))).reshape(nt, ns, ns, ns)          # [t][i3][i2][i1]

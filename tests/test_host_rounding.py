@@ -1,5 +1,7 @@
 """The exact-to-FP64 rounding of the FP64 tensor-core and integer-limb kernels,
-compiled for the host, against exact rational rounding.
+compiled for the host, against exact rational rounding; and the integer-limb
+stencil's limb split and 729-tap row sums (wrapped middle word) against exact
+integers.
 
 The seven-digit mode product (STFD_FP64TC7) and the integer-limb band products
 (STFD_OP_FX64) form each result as an exact integer and round it once, to
@@ -41,9 +43,13 @@ def driver(tmp_path_factory):
     return exe
 
 
+def _raw(exe, lines):
+    return subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True,
+                          check=True).stdout.splitlines()
+
+
 def _run(exe, lines):
-    out = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True).stdout
-    return [struct.unpack("<d", struct.pack("<Q", int(v)))[0] for v in out.split()]
+    return [struct.unpack("<d", struct.pack("<Q", int(v)))[0] for v in _raw(exe, lines)]
 
 
 def _ref(fr):
@@ -117,3 +123,86 @@ def test_seven_digit_recombination_rounds_exactly(driver):
     for (I, se), g in zip(cases, got):
         Z = sum(I[c] * 256 ** (6 - c) for c in range(7))
         assert _same(g, _ref(Fraction(Z) * Fraction(2) ** se)), (I, se, g)
+
+
+def _bits(x):
+    return struct.unpack("<Q", struct.pack("<d", x))[0]
+
+
+def _round_half_away(fr):
+    n = abs(fr.numerator) * 2 + fr.denominator
+    q = n // (2 * fr.denominator)
+    return q if fr >= 0 else -q
+
+
+def test_stencil_balanced_limbs_of_fp64_entries(driver):
+    """U = round(m 2^{max(e,1) - E}), halves away from zero, split as
+    h 2^27 + l with l in [-2^26, 2^26): the entry's value in units of
+    2^{E - 1075}."""
+    rng = random.Random(14)
+    cases = []
+    for _ in range(20000):
+        x = rng.choice([rng.uniform(-1, 1), rng.gauss(0, 1) * 2.0 ** rng.randint(-40, 40), 5e-324 * rng.randint(1, 9),
+                        2.0 ** rng.randint(-1074, 1023) * rng.choice([1, -1, 1.5])])
+        e = max(1, (_bits(x) >> 52) & 0x7FF)
+        cases.append((x, min(2046, e + rng.choice([0, 0, 1, 2, 20, 52, 53, 54, 60, 70]))))
+    out = _raw(driver, ["bl %d %d" % (_bits(x), E) for x, E in cases])
+    for (x, E), line in zip(cases, out):
+        h, l = map(int, line.split())
+        assert -(2 ** 26) <= l < 2 ** 26 and abs(h) <= 2 ** 26, (x, E, h, l)
+        assert h * 2 ** 27 + l == _round_half_away(Fraction(x) / Fraction(2) ** (E - 1075)), (x, E, h, l)
+
+
+# Largest |h + l| of a balanced split, 2^27 - 2: the middle word's terms reach
+# 2^54 and 729 of them pass 2^63 (the accumulation wraps).
+WRAP = (2 ** 26 - 1) * 2 ** 27 + 2 ** 26 - 1
+
+
+def _row(rng, n, worst=False):
+    lim = 2 ** 53 - 1
+    if worst:   # every product at its largest, one sign: the sums' bounds are reached
+        s = rng.choice([1, -1])
+        return [(s * rng.choice([WRAP, lim]), WRAP) for _ in range(n)]
+    return [(rng.randint(-lim, lim) >> rng.choice([0, 0, 0, 20, 45]), rng.randint(-lim, lim) >> rng.choice([0, 0, 30]))
+            for _ in range(n)]
+
+
+def _exact(row):
+    return sum(c * u for c, u in row)
+
+
+def _split(v):
+    lo = ((v + 2 ** 26) % 2 ** 27) - 2 ** 26
+    return (v - lo) >> 27, lo
+
+
+def test_stencil_worst_rows_wrap_the_middle_word():
+    """The worst-case rows used below do overflow a signed 64-bit middle sum."""
+    (h, l) = _split(WRAP)
+    assert 729 * (h + l) ** 2 >= 2 ** 63 and abs(h) <= 2 ** 26 and -(2 ** 26) <= l < 2 ** 26
+
+
+def test_stencil_row_sums_of_729_taps_round_exactly(driver):
+    rng = random.Random(15)
+    cases = []
+    for k in range(600):
+        n = rng.choice([729, 729, 125, 27, 1])
+        cases.append((_row(rng, n, worst=k % 50 == 0), rng.choice([2150, 2100, 2200, 1040, 3000])))
+    lines = ["stw %d %d " % (se, len(r)) + " ".join("%d %d" % cu for cu in r) for r, se in cases]
+    for (r, se), g in zip(cases, _run(driver, lines)):
+        assert _same(g, _ref(Fraction(_exact(r)) * Fraction(2) ** (se - 2150))), (se, g)
+
+
+def test_stencil_row_pairs_within_2_pow_10_sum_exactly(driver):
+    rng = random.Random(16)
+    cases = []
+    for k in range(400):
+        x = _row(rng, 729, worst=k % 40 == 0)
+        y = [(-c, u) for c, u in x] if k % 17 == 0 else _row(rng, rng.choice([729, 343]), worst=k % 40 == 1)
+        sx = rng.choice([2150, 2120, 1050])
+        cases.append((x, sx, y, sx + rng.randint(-10, 10)))
+    lines = ["stp %d %d %s %d %d %s" % (sx, len(x), " ".join("%d %d" % cu for cu in x), sy, len(y),
+                                        " ".join("%d %d" % cu for cu in y)) for x, sx, y, sy in cases]
+    for (x, sx, y, sy), g in zip(cases, _run(driver, lines)):
+        exact = Fraction(_exact(x)) * Fraction(2) ** (sx - 2150) + Fraction(_exact(y)) * Fraction(2) ** (sy - 2150)
+        assert _same(g, _ref(exact)), (sx, sy, g)
