@@ -8,7 +8,9 @@
 // two as 53-bit integers C (exponent frame E_m(i), E_k(i): the largest biased
 // exponent of the row's (2p+1)^d coefficients), once, when the operator is
 // created. A CTA owns R rows and TC time slices; for each slice it writes the
-// entries of Z1_t and Z2_t that its rows read (its stencil neighbourhood)
+// entries of Z1_t and Z2_t that its rows read (its stencil neighbourhood, one
+// segment of R + 2p columns per pair of outer offsets, copied asynchronously
+// while the previous segment is multiplied)
 // under one power of two per slice (the neighbourhood's largest biased
 // exponent), exact in the top binade and rounded at 2^-53 of the
 // neighbourhood's largest entry below it. Both are split into balanced 27-bit
@@ -34,6 +36,7 @@
 #include "fp64_round.cuh"
 #include "kernels.h"
 #include "profile.h"
+#include "tc_common.cuh"
 
 namespace stfd {
 namespace {
@@ -75,8 +78,11 @@ k_stencil_fx(const int2* __restrict__ Ms, const int2* __restrict__ Ks, const int
   extern __shared__ unsigned char smem_raw[];
   const int p = PP > 0 ? PP : g.p;
   const int W = 2 * p + 1, span = kRows + 2 * p;
-  int2* z1s = reinterpret_cast<int2*>(smem_raw);      // [kTC][span]
-  int2* z2s = z1s + kTC * span;
+  // raw FP64 words of the next segment (asynchronous copies), then the limbs of
+  // two segments (double-buffered: one is converted while the other is read)
+  unsigned long long* r1s = reinterpret_cast<unsigned long long*>(smem_raw);   // [kTC][span]
+  unsigned long long* r2s = r1s + kTC * span;
+  int2* lbuf = reinterpret_cast<int2*>(r2s + kTC * span);                      // [2][2][kTC][span]
   __shared__ int sE[2 * kTC];                         // neighbourhood frames of Z1_t, Z2_t
   const int n_chunks = (g.nt + kTC - 1) / kTC;
   const long long i0 = (long long)(blockIdx.x / n_chunks) * kRows;
@@ -134,26 +140,47 @@ k_stencil_fx(const int2* __restrict__ Ms, const int2* __restrict__ Ks, const int
   AccW am[kTC], ak[kTC];
 #pragma unroll
   for (int tt = 0; tt < kTC; ++tt) am[tt] = ak[tt] = AccW{0, 0, 0ull};
-  for (int o23 = 0; o23 < S23; ++o23) {
+  // segment o23: columns base .. base + span - 1 of the slices (clamped: the
+  // coefficient is 0 for columns outside the box)
+  auto seg_base = [&](int o23) -> long long {
     const int o2 = g.d >= 2 ? o23 % W : p, o3 = g.d >= 3 ? o23 / W : p;
-    const long long base = i0 - p + (long long)(o2 - p) * g.n1 + (long long)(o3 - p) * g.n1 * g.n2;
-    __syncthreads();
-    // stage Z1, Z2 at columns base .. base + span - 1 as limbs under the frames
+    return i0 - p + (long long)(o2 - p) * g.n1 + (long long)(o3 - p) * g.n1 * g.n2;
+  };
+  auto issue = [&](int o23) {
+    const long long base = seg_base(o23);
     for (int c = threadIdx.x; c < span; c += kRows) {
       long long j = base + c;
-      j = j < 0 ? 0 : (j >= g.Ns ? g.Ns - 1 : j);   // the coefficient is 0 for columns outside the box
+      j = j < 0 ? 0 : (j >= g.Ns ? g.Ns - 1 : j);
+#pragma unroll
+      for (int tt = 0; tt < kTC; ++tt)
+        if (tt < ntc) {
+          tc::cp_async8(r1s + tt * span + c, w1 + (long long)(t0 + tt) * g.Ns + j);
+          tc::cp_async8(r2s + tt * span + c, w2 + (long long)(t0 + tt) * g.Ns + j);
+        }
+    }
+    tc::cp_async_commit();
+  };
+  auto convert = [&](int buf) {
+    int2* l1 = lbuf + (size_t)buf * 2 * kTC * span;
+    int2* l2 = l1 + kTC * span;
+    for (int c = threadIdx.x; c < span; c += kRows) {
 #pragma unroll
       for (int tt = 0; tt < kTC; ++tt) {
-        int2 v1 = make_int2(0, 0), v2 = make_int2(0, 0);
-        if (tt < ntc) {
-          v1 = balanced_limbs(__ldg(w1 + (long long)(t0 + tt) * g.Ns + j), E1[tt]);
-          v2 = balanced_limbs(__ldg(w2 + (long long)(t0 + tt) * g.Ns + j), E2[tt]);
-        }
-        z1s[tt * span + c] = v1;
-        z2s[tt * span + c] = v2;
+        const bool on = tt < ntc;
+        l1[tt * span + c] = on ? balanced_limbs(r1s[tt * span + c], E1[tt]) : make_int2(0, 0);
+        l2[tt * span + c] = on ? balanced_limbs(r2s[tt * span + c], E2[tt]) : make_int2(0, 0);
       }
     }
-    __syncthreads();
+  };
+  issue(0);
+  tc::cp_async_wait_all();
+  __syncthreads();
+  convert(0);
+  for (int o23 = 0; o23 < S23; ++o23) {
+    __syncthreads();   // limbs of segment o23 complete; the raw buffer is free
+    if (o23 + 1 < S23) issue(o23 + 1);
+    const int2* z1s = lbuf + (size_t)(o23 & 1) * 2 * kTC * span;
+    const int2* z2s = z1s + kTC * span;
     const long long ob = (long long)W * o23 * g.Ns;
 #pragma unroll
     for (int o1 = 0; o1 < (PP > 0 ? 2 * PP + 1 : W); ++o1) {
@@ -165,6 +192,11 @@ k_stencil_fx(const int2* __restrict__ Ms, const int2* __restrict__ Ks, const int
         tapw(am[tt], m, ms, z1s[tt * span + threadIdx.x + o1]);
         tapw(ak[tt], kk, ks, z2s[tt * span + threadIdx.x + o1]);
       }
+    }
+    if (o23 + 1 < S23) {   // the next segment's words have arrived: its limbs
+      tc::cp_async_wait_all();
+      __syncthreads();
+      convert((o23 + 1) & 1);
     }
   }
   // ---- one rounding per output (every lane rounds: the warp votes on the exact pair sum)
@@ -185,7 +217,7 @@ k_stencil_fx(const int2* __restrict__ Ms, const int2* __restrict__ Ks, const int
 template <int kTC, int PP>
 cudaError_t run_fx(const int2* Ms, const int2* Ks, const int* Em, const int* Ek, const double* Z1, const double* Z2,
                    double* y, const StencilDims& g, cudaStream_t st) {
-  const size_t smem = (size_t)2 * kTC * (kRows + 2 * g.p) * sizeof(int2);
+  const size_t smem = (size_t)6 * kTC * (kRows + 2 * g.p) * sizeof(int2);   // raw words + two limb tiles
   {
     const cudaError_t e = ensure_smem_attr(k_stencil_fx<kTC, PP>, 96 * 1024);
     if (e != cudaSuccess) return e;
