@@ -343,6 +343,10 @@ def mapped_section(args, stream):
         elif mv_name == "fp64":   # the two FP64 matvecs on the same input
             sec["fx64_matvec_rel_diff"] = float(torch.linalg.norm(y_fx - y) / torch.linalg.norm(y))
             del y_fx
+        # one untimed solve first, so that no timed solve allocates the Krylov workspace
+        Pw = stfd.geometry_preconditioner(prob, cfg["gamma"], cfg["nu"], precision=stfd.STFD_BF16)
+        A.gmres(Pw, f, y, tol=1e-8)
+        Pw.close()
         s_ref = None
         plist = [("fp64_ieee", stfd.STFD_FP64, True), ("fp64_accurate_df32", stfd.STFD_DF32, True),
                  ("tf32", stfd.STFD_TF32, True), ("bf16", stfd.STFD_BF16, True)]
@@ -361,7 +365,7 @@ def mapped_section(args, stream):
             err = float(torch.linalg.norm(s - s_ref) / torch.linalg.norm(s_ref)) if geo else None
             reps = steps if (geo and prec in (stfd.STFD_TF32, stfd.STFD_BF16)) else 1
             if geo and reps > 1:
-                A.gmres(P, f, y, tol=1e-8)      # warm-up (allocates the Krylov vectors)
+                A.gmres(P, f, y, tol=1e-8)      # warm-up
             gm_ms, (_, info) = cuda_time(lambda: A.gmres(P, f, y, tol=1e-8), reps, stream)
             sec["variants"][name] = {"precond": ("A^G " if geo else "A^ ") + name.replace("plain_", ""),
                                      "fd_apply_ms": fd_ms, "fd_apply_rel_err_vs_fp64_on_N01_input": err,
