@@ -26,7 +26,7 @@ class MappedHeatModel:
     """
 
     def __init__(self, d, p, n_el, geom=stfd.STFD_GEOM_QUARTER_ANNULUS, c=None, kappa_ref=None, T=1.0,
-                 gamma=1.0, nu=1.0, arith=stfd.STFD_OP_FP64, precision=stfd.STFD_FP64, tol=1e-10, nq=None,
+                 gamma=1.0, nu=1.0, arith=stfd.STFD_OP_FX64, precision=stfd.STFD_FP64, tol=1e-10, nq=None,
                  restart=100, max_it=1000):
         self.d, self.p, self.n_el, self.geom = d, p, n_el, geom
         self.gamma, self.nu, self.arith, self.tol = gamma, nu, arith, tol

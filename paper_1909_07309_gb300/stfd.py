@@ -392,9 +392,12 @@ class KronOp(_Op):
 
 class StencilOp(KronOp):
     """System operator with general spatial matrices in the stencil layout
-    (``stfd_op_create_stencil``); matvec / transpose / GMRES as KronOp."""
+    (``stfd_op_create_stencil``); matvec / transpose / GMRES as KronOp. The
+    default arithmetic is FP64 with exact integer-limb row sums
+    (STFD_OP_FX64); STFD_OP_FP64 (IEEE) and STFD_OP_DF32 (~48-bit) are the
+    others."""
 
-    def __init__(self, n, p_s, Ms, Ks, Wt, Mt, gamma=1.0, nu=1.0, arith=STFD_OP_DF32, stream=None):
+    def __init__(self, n, p_s, Ms, Ks, Wt, Mt, gamma=1.0, nu=1.0, arith=STFD_OP_FX64, stream=None):
         lib = load()
         self._lib = lib
         self.handle = ctypes.c_void_p()
