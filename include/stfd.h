@@ -213,7 +213,10 @@ void stfd_fd_destroy(stfd_fd* h);
  *                 of different inputs sums them exactly and rounds once when their
  *                 scales are within 2^16 (else adds the two rounded FP64 values). Entries
  *                 far below their fibre's largest entry are rounded at 2^-53 of
- *                 that entry (normwise FP64 accuracy). Needs every half-bandwidth
+ *                 that entry (normwise FP64 accuracy). A non-finite input entry
+ *                 makes every output of the fibres it feeds NaN (the passes
+ *                 carry it along whole fibres, so the result is NaN far beyond
+ *                 the entry's band). Needs every half-bandwidth
  *                 in 1..4; otherwise the op uses the STFD_OP_FP64 passes.
  * ------------------------------------------------------------------------ */
 typedef struct stfd_op stfd_op;

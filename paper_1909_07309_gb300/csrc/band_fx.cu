@@ -48,6 +48,12 @@ constexpr int kLd = kTC + 1;     // tile row stride in int2 (conflict-free trans
 
 __device__ __forceinline__ int bexp_d(unsigned long long u) { return max(1, (int)((u >> 52) & 0x7FF)); }
 
+// A fibre whose largest biased exponent is 2047 holds an infinity or NaN: the
+// outputs it feeds are NaN (the flag is read from shared memory at the store,
+// so that no register stays live across the row loop).
+__device__ __forceinline__ bool nonfinite(int E) { return E >= 2047; }
+#define kQNaN __longlong_as_double(0x7FF8000000000000ll)
+
 // Entry (bit pattern u) of a fibre with largest biased exponent E as the limbs
 // (U_h, U_l) of U = round(m 2^{e - E}), U = U_h 2^27 + U_l, 0 <= U_l < 2^27.
 __device__ __forceinline__ int2 to_limbs(unsigned long long u, int E) {
@@ -192,18 +198,18 @@ k_band_fx(const double* __restrict__ U, const double* __restrict__ V, const int2
     if (KIND == 0) {
       const double uo = round_acc(a1, Eu + e0), vo = round_acc(a2, Eu + e1);
       if (valid) {
-        Uo[off] = uo;
-        Vo[off] = vo;
+        Uo[off] = nonfinite(sEu[lane]) ? kQNaN : uo;
+        Vo[off] = nonfinite(sEu[lane]) ? kQNaN : vo;
       }
     } else if (KIND == 1) {
       const double uo = round_acc(a1, Eu + e0), vo = round_sum(a2, Eu + e1, a3, Ev + e0);
       if (valid) {
-        Uo[off] = uo;
-        Vo[off] = vo;
+        Uo[off] = nonfinite(sEu[lane]) ? kQNaN : uo;
+        Vo[off] = nonfinite(max(sEu[lane], sEv[lane])) ? kQNaN : vo;
       }
     } else {
       const double vo = round_sum(a2, Eu + e0, a3, Ev + e1);
-      if (valid) Vo[off] = vo;
+      if (valid) Vo[off] = nonfinite(max(sEu[lane], sEv[lane])) ? kQNaN : vo;
     }
   }
 }

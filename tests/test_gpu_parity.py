@@ -279,3 +279,24 @@ def test_fd_apply_unaligned_buffers_match(d, p, n_el, prec):
     r1.copy_(r)
     P.apply(r1, s1)
     assert torch.equal(s1, s_ref)
+
+
+@pytest.mark.parametrize("kind", ["kron", "stencil"])
+def test_fx64_matvec_nonfinite_input_gives_nan(kind):
+    """The integer-limb matvecs turn a non-finite input entry into NaN outputs
+    (as IEEE arithmetic would) instead of finite values; finite inputs stay finite."""
+    if kind == "kron":
+        K, M, Wt, Mt = stfd.heat_problem(3, 3, 6)
+        A = stfd.KronOp(K, M, Wt, Mt, arith=stfd.STFD_OP_FX64)
+    else:
+        prob = stfd.mapped_problem(2, 3, 8, stfd.STFD_GEOM_QUARTER_ANNULUS)
+        A = stfd.StencilOp(prob["n"], 3, prob["Ms"], prob["Ks"], prob["Wt"], prob["Mt"], arith=stfd.STFD_OP_FX64)
+    x = inputs.standard_normal(A.N, seed=71)
+    y = A.matvec(dev(x))
+    assert bool(torch.isfinite(y).all())
+    for bad in (np.inf, -np.inf, np.nan):
+        xb = x.copy()
+        xb[A.N // 2] = bad
+        yb = A.matvec(dev(xb))
+        assert bool(torch.isnan(yb).any())
+        assert bool(torch.isnan(yb[A.N // 2]))
